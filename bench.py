@@ -1,0 +1,290 @@
+"""Benchmark: l0 tuple-fits per second on the d = 3 workload.
+
+Workload (default): one task, n_samples = 1000, n_sis = 1000, d = 3,
+k = 100 (C(1000, 3) = 166,167,000 intercept + 3-feature least-squares fits),
+synthetic SISSO-shaped columns (see workloads/synth.py).  One step = one full
+sisso_l0_fit: centring, Gram, tuple search, merge, FP64 re-fit of the
+candidate pool, final ranking.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU FP64
+oracle instead (bounded samples of the same workload).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "l0 tuple-fits/sec at d=3 (top-100 agreement with the FP64 oracle)"
+UNIT = "tuple-fits/s"
+FP64_PEAK_TFLOPS = 1.25          # GB300 FP64 (nominal, FMA pipe)
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def fp32_peak_tflops(sm_mhz):
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def flops_per_tuple(d):
+    # hoisted per-tuple work of the tuple kernel's fast path:
+    # (d-2) FMA for h, MUL g2, FMA pp, FMA w, MUL w^2, FMA t  ->  d+1 FMA + 2 MUL
+    return 2 * (d + 1) + 2
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv") \
+            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_bench.csv"
+        self.idx = gpu_index
+
+    def start(self):
+        try:
+            f = open(self.path, "w")
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(prob, d, budget_s=12.0):
+    """The CPU FP64 oracle on a bounded sample: all d-tuples of the first m'
+    columns (same samples), m' grown until the run takes a few seconds."""
+    import oracle
+    m_prime = 40
+    while True:
+        X = prob.X[:m_prime]
+        t0 = time.perf_counter()
+        oracle.fit(X, prob.y, d, 100)
+        dt = time.perf_counter() - t0
+        n = math.comb(m_prime, d)
+        if dt > budget_s / 4 or m_prime >= prob.n_sis:
+            break
+        grow = (budget_s / 2 / max(dt, 1e-3)) ** (1.0 / d)
+        m_prime = min(prob.n_sis, max(m_prime + 10, int(m_prime * min(grow, 3.0))))
+    return {"value": n / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "all C(%d,%d)=%d tuples of the first %d columns, n_samples=%d, %.1f s"
+                      % (m_prime, d, n, m_prime, prob.n_total, dt)}
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return
+    from workloads import make_config
+    import oracle
+    prob, d, k = make_config(args.workload)
+    oracle.build()
+    # one step = the oracle on the first m' columns, sized to ~5 s of CPU work
+    base = cpu_baseline(prob, d, budget_s=8.0)
+    m_prime = int(base["sample"].split("first ")[1].split(" ")[0])
+    n = math.comb(m_prime, d)
+    for _ in range(args.warmup):
+        oracle.fit(prob.X[:m_prime], prob.y, d, k)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.fit(prob.X[:m_prime], prob.y, d, k)
+        times.append(time.perf_counter() - t0)
+    ms = 1000 * statistics.mean(times)
+    value = n / (ms / 1000)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": _workload_desc(args.workload, prob, d, k)},
+            "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "value": value,
+                             "unit": UNIT, "sample": "all C(%d,%d) tuples of the first %d columns"
+                                                     % (m_prime, d, m_prime)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def _workload_desc(name, prob, d, k):
+    return "%s: n_tasks=%d n_samples=%d n_sis=%d d=%d k=%d" % (
+        name, prob.n_tasks, prob.n_total, prob.n_sis, d, k)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import paper_2502_20072_gb300 as l0
+    from workloads import make_config
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prob, d, k = make_config(args.workload)
+    precision = {"fp64": l0.FP64, "mixed": l0.MIXED_BF16X3}[args.precision]
+    n_fits = math.comb(prob.n_sis, d) * prob.n_tasks
+    stream = torch.cuda.current_stream()
+    X = torch.from_numpy(prob.X).cuda()
+    y = torch.from_numpy(prob.y).cuda()
+    out_t = torch.empty((prob.n_tasks, k, d), dtype=torch.int32, device="cuda")
+    out_r = torch.empty((prob.n_tasks, k), dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    h = l0.Handle(precision=precision, device=local, stream=stream.cuda_stream)
+
+    def step():
+        h.fit(X, y, d, k, offsets=prob.offsets, out_tuples=out_t, out_rmse=out_r)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    tuple_ms, launches = [], 0
+    for i in range(args.steps):
+        flush.zero_()            # L2 flush (256 MB > 129 MB L2), outside the timed events
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        st = h.stats()
+        tuple_ms.append(st["ms_tuple"])
+        launches += int(st["kernel_launches"])
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    ms_step = statistics.mean(ms)
+    if ws > 1:
+        t = torch.tensor([ms_step], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = ws * n_fits / (ms_step / 1000.0)
+    st = h.stats()
+    # e2e: host buffers through the C ABI (copies inside the timed region)
+    Xh = torch.from_numpy(prob.X).pin_memory()
+    yh = torch.from_numpy(prob.y).pin_memory()
+    ot_h = np.empty((prob.n_tasks, k, d), dtype=np.int32)
+    or_h = np.empty((prob.n_tasks, k), dtype=np.float64)
+    e2e = []
+    for i in range(max(2, min(args.steps, 5))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.fit(Xh, yh, d, k, offsets=prob.offsets, out_tuples=ot_h, out_rmse=or_h)
+        e2e.append(time.perf_counter() - t0)
+    e2e_val = n_fits / statistics.median(e2e)
+    # roofline of the dominant kernel (the tuple kernel)
+    t_tuple = statistics.mean(tuple_ms) / 1000.0
+    fl = flops_per_tuple(d) * n_fits
+    achieved = fl / t_tuple / 1e12
+    if precision == l0.FP64:
+        peak, peak_note = FP64_PEAK_TFLOPS, "GB300 FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"
+    else:
+        peak = fp32_peak_tflops(2070.0)
+        peak_note = "152 SM x 128 FP32 lanes x 2 flop x 2070 MHz"
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if precision == l0.FP64 else "f32",
+        "data": "synthetic",
+        "config": {"workload": _workload_desc(args.workload, prob, d, k),
+                   "precision": args.precision,
+                   "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "flushed between steps (256 MB write, outside the timed events)",
+                   "candidate_pool": st["candidate_pool"], "certified": st["certified"],
+                   "stage_ms": {s: round(st["ms_" + s], 4) for s in
+                                ("prep", "gram", "tuple", "merge", "refit")}},
+        "e2e": {"value": e2e_val, "unit": UNIT,
+                "h2d_bytes_per_step": int(prob.X.nbytes + prob.y.nbytes),
+                "d2h_bytes_per_step": int(ot_h.nbytes + or_h.nbytes)},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "tile_kernel (tuple search)", "peak_source": peak_note,
+                     "flops_per_tuple": flops_per_tuple(d)},
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(prob, d)
+    h.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--workload", default="C2")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

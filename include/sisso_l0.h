@@ -1,0 +1,157 @@
+/*
+ * sisso_l0.h -- C ABI of the GB300 (sm_103a) l0-regularization library.
+ *
+ * The operation (paper Sec. 2.4): given the m features selected by SIS and a
+ * target, score every n-tuple of features by the least-squares fit of the
+ * features to the target and return the best tuples.  The score is the mean
+ * squared deviation of the fit; here the fit has an intercept and the
+ * reported error is the RMSE, sqrt(SSE / n_t).  Multi-task data (Sec. 3.1,
+ * "same descriptor, different coefficients per task") is given as row ranges
+ * of the same columns.
+ *
+ * Conventions shared by every entry point:
+ *   - All functions return SISSO_L0_OK (0) or one of the error codes below;
+ *     no C++ exception crosses this boundary.  After an error,
+ *     sisso_l0_last_error() describes it.
+ *   - X is FP64, feature-major: X[j * n_total + i] is feature j of sample i,
+ *     so each column is contiguous; rows are grouped by task.  X and y may
+ *     live in device memory or in host memory (the pointer kind is queried);
+ *     host inputs are copied into library-owned device memory per call.
+ *   - Outputs may be device or host pointers likewise.
+ *   - The caller owns X, y, task_offsets and the outputs; the library never
+ *     frees them and keeps no pointer to them after the call returns.
+ *   - Work is ordered on the stream given at create time; fit returns after
+ *     the results are complete (bounded by options.timeout_seconds).
+ *   - One handle must not be used by two threads at the same time.
+ */
+#ifndef SISSO_L0_H
+#define SISSO_L0_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SISSO_L0_OK 0
+#define SISSO_L0_EINVAL 1       /* bad argument: sizes, offsets, null pointers */
+#define SISSO_L0_ENOMEM 2       /* device or host allocation failed */
+#define SISSO_L0_ECUDA 3        /* a CUDA call failed */
+#define SISSO_L0_ETIMEOUT 4     /* the stream did not finish within timeout_seconds */
+#define SISSO_L0_ENONFINITE 5   /* NaN or Inf in X or y */
+#define SISSO_L0_EUNSUPPORTED 6 /* valid request this build does not handle */
+
+#define SISSO_L0_MAX_DIM 8      /* the paper's descriptors have fewer than 10 features (Sec. 2.4) */
+
+typedef enum {
+  SISSO_L0_FP64 = 0,          /* FP64 Gram (FFMA64), FP64 solves, FP64 re-fit */
+  SISSO_L0_MIXED_BF16X3 = 1,  /* split-BF16 (3-term) tensor-core Gram, FP32 solves, FP64 re-fit */
+  SISSO_L0_MIXED_TF32 = 2     /* reserved */
+} sisso_l0_precision;
+
+typedef enum {
+  SISSO_L0_PER_TASK = 0,      /* rank each task on its own: n_out = n_tasks lists */
+  SISSO_L0_SHARED = 1         /* rank by pooled mean SSE sum_t SSE_t / N: n_out = 1 list */
+} sisso_l0_task_mode;
+
+typedef struct sisso_l0_handle *sisso_l0_t;
+
+typedef struct {
+  int32_t struct_size;               /* sizeof(sisso_l0_options) */
+  int32_t device;                    /* CUDA device ordinal */
+  void *stream;                      /* cudaStream_t owned by the caller; NULL = legacy stream */
+  int32_t precision;                 /* sisso_l0_precision */
+  int32_t task_mode;                 /* sisso_l0_task_mode */
+  int32_t candidate_pool;            /* K': candidates re-fitted in FP64 (0 = auto, max(4k, 256)) */
+  int32_t max_candidate_pool;        /* ceiling for K' when the certificate doubles it (0 = 2048) */
+  double fp32_fallback_pivot_ratio;  /* FP32 pivot ratio below which a tuple is redone in FP64 (1e-6) */
+  double rank_deficient_pivot_ratio; /* FP64 Gram pivot ratio below which a tuple is ineligible (1e-12) */
+  int32_t autotune;                  /* 0 off, 1 on */
+  int32_t reserved0;
+  const char *autotune_cache_path;   /* NULL = no persisted cache */
+  double timeout_seconds;            /* host-side deadline for stream completion (<= 0: none) */
+} sisso_l0_options;
+
+typedef struct {
+  int32_t struct_size;               /* sizeof(sisso_l0_stats) */
+  int32_t candidate_pool;            /* K' used by the last fit */
+  int32_t pool_enlargements;         /* times K' was doubled by the certificate */
+  int32_t certified;                 /* 1 when every output list passed the certificate */
+  uint64_t tuple_fits;               /* (task, tuple) fits evaluated */
+  uint64_t fp64_fallback_tuples;     /* tuples recomputed in FP64 (mixed precision) */
+  int64_t n_eligible_min;            /* smallest count of filled output slots over lists */
+  double max_pool_rel_error;         /* max |SSE_gram - SSE_refit| over the pools, SSE units */
+  int64_t kernel_launches;           /* library kernels launched by the last fit */
+  double ms_prep, ms_gram, ms_tuple, ms_merge, ms_refit, ms_total;
+} sisso_l0_stats;
+
+/* Fill *opt with defaults (FP64, PER_TASK, device 0, legacy stream). */
+int sisso_l0_default_options(sisso_l0_options *opt);
+
+/* Create a handle on opt->device.  *out receives the handle. */
+int sisso_l0_create(sisso_l0_t *out, const sisso_l0_options *opt);
+
+/*
+ * Exhaustive l0 search (paper Sec. 2.4: score every n-tuple, return the best).
+ *   X            FP64 [n_sis][n_total], feature-major (see above)
+ *   y            FP64 [n_total]
+ *   task_offsets host int64 [n_tasks + 1]; offsets[0] = 0, offsets[n_tasks] =
+ *                n_total, every task has at least n_dim + 2 rows
+ *   n_dim        tuple size, 1 .. SISSO_L0_MAX_DIM
+ *   k            tuples per output list, 1 .. C(n_sis, n_dim)
+ *   out_tuples   int32 [n_out][k][n_dim], ascending 0-based column indices
+ *   out_rmse     FP64 [n_out][k]: sqrt(SSE_t / n_t) (PER_TASK) or
+ *                sqrt(sum_t SSE_t / N) (SHARED), from an FP64 Householder
+ *                re-fit on the raw centred columns
+ * Lists are ordered by error, ties by the lexicographically smaller tuple.
+ * Tuples whose FP64 pivot ratio is below rank_deficient_pivot_ratio are not
+ * eligible; unfilled slots hold index -1 and rmse +inf.
+ * Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EUNSUPPORTED
+ * (C(n_sis, n_dim) >= 2^62 or a candidate pool above 2048).
+ */
+int sisso_l0_fit(sisso_l0_t h, const double *X, const double *y,
+                 const int64_t *task_offsets, int32_t n_tasks, int64_t n_sis,
+                 int32_t n_dim, int32_t k, int32_t *out_tuples,
+                 double *out_rmse);
+
+/* Statistics of the last fit on this handle. */
+int sisso_l0_get_stats(sisso_l0_t h, sisso_l0_stats *out);
+
+/* Description of the last error on this handle (valid until the next call
+ * on the handle); a static string when h is NULL. */
+const char *sisso_l0_last_error(sisso_l0_t h);
+
+/* Synchronise the handle's stream and free everything it owns.  NULL-safe. */
+void sisso_l0_destroy(sisso_l0_t h);
+
+/*
+ * Number of n-tuples of m features, C(m, n) (paper Sec. 3.1 counts its l0
+ * models this way).  Returns 0 when it does not fit in 63 bits.  Host-only.
+ */
+uint64_t sisso_l0_count_tuples(int64_t m, int32_t n);
+
+/*
+ * Diagnostic: lexicographic rank <-> tuple, as the device code computes it
+ * (tuples of n ascending indices out of m, rank 0 = (0, 1, .., n-1)).
+ * Runs on the handle's device; ranks/tuples are host arrays of count
+ * entries.  Used by the tests to check the enumeration against an
+ * independent enumerator.
+ */
+int sisso_l0_debug_unrank(sisso_l0_t h, int64_t m, int32_t n,
+                          const uint64_t *ranks, int64_t count,
+                          int32_t *tuples_out);
+
+/*
+ * Diagnostic: the per-task augmented correlation matrix the tuple kernel
+ * reads, for task `task`: out[(m+1) x (m+1)] FP64 host array, index 0 the
+ * target, index j+1 feature j; entries (a, b) with a <= b are filled.
+ */
+int sisso_l0_debug_gram(sisso_l0_t h, const double *X, const double *y,
+                        const int64_t *task_offsets, int32_t n_tasks,
+                        int64_t n_sis, int32_t task, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SISSO_L0_H */

@@ -1,0 +1,238 @@
+"""GB300 (sm_103a) l0-regularization step of SISSO: Python binding.
+
+Thin ctypes layer over the C ABI in ``include/sisso_l0.h``: it only
+marshals arguments.  Every step of the search runs in the library's CUDA
+kernels; when the library cannot be loaded this module raises instead of
+falling back to anything else.
+
+    import paper_2502_20072_gb300 as l0
+    with l0.Handle(precision=l0.MIXED_BF16X3) as h:
+        tuples, rmse = h.fit(X, y, n_dim=3, k=100)
+
+X is FP64 feature-major [n_sis, n_total] (each column contiguous), y is FP64
+[n_total]; both may be torch CUDA tensors, torch CPU tensors or numpy arrays.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+FP64 = 0
+MIXED_BF16X3 = 1
+MIXED_TF32 = 2
+PER_TASK = 0
+SHARED = 1
+MAX_DIM = 8
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EUNSUPPORTED = range(7)
+_NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENONFINITE",
+          6: "EUNSUPPORTED"}
+
+
+class L0Error(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (_NAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("stream", ctypes.c_void_p), ("precision", ctypes.c_int32),
+                ("task_mode", ctypes.c_int32), ("candidate_pool", ctypes.c_int32),
+                ("max_candidate_pool", ctypes.c_int32),
+                ("fp32_fallback_pivot_ratio", ctypes.c_double),
+                ("rank_deficient_pivot_ratio", ctypes.c_double),
+                ("autotune", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("autotune_cache_path", ctypes.c_char_p),
+                ("timeout_seconds", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_int32), ("candidate_pool", ctypes.c_int32),
+                ("pool_enlargements", ctypes.c_int32), ("certified", ctypes.c_int32),
+                ("tuple_fits", ctypes.c_uint64), ("fp64_fallback_tuples", ctypes.c_uint64),
+                ("n_eligible_min", ctypes.c_int64), ("max_pool_rel_error", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64),
+                ("ms_prep", ctypes.c_double), ("ms_gram", ctypes.c_double),
+                ("ms_tuple", ctypes.c_double), ("ms_merge", ctypes.c_double),
+                ("ms_refit", ctypes.c_double), ("ms_total", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "struct_size"}
+
+
+_lib = None
+_lock = threading.Lock()
+
+# entry points declared in include/sisso_l0.h (checked by the tests)
+EXPORTS = ("sisso_l0_default_options", "sisso_l0_create", "sisso_l0_fit",
+           "sisso_l0_get_stats", "sisso_l0_last_error", "sisso_l0_destroy",
+           "sisso_l0_count_tuples", "sisso_l0_debug_unrank", "sisso_l0_debug_gram")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load the CUDA library (building it first when it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            path = _build.build()
+        L = ctypes.CDLL(path)
+        vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+        L.sisso_l0_default_options.argtypes = [ctypes.POINTER(Options)]
+        L.sisso_l0_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Options)]
+        L.sisso_l0_fit.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_int64), i32, i64, i32,
+                                   i32, vp, vp]
+        L.sisso_l0_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+        L.sisso_l0_last_error.argtypes = [vp]
+        L.sisso_l0_last_error.restype = ctypes.c_char_p
+        L.sisso_l0_destroy.argtypes = [vp]
+        L.sisso_l0_destroy.restype = None
+        L.sisso_l0_count_tuples.argtypes = [i64, i32]
+        L.sisso_l0_count_tuples.restype = ctypes.c_uint64
+        L.sisso_l0_debug_unrank.argtypes = [vp, i64, i32, vp, i64, vp]
+        L.sisso_l0_debug_gram.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_int64), i32, i64,
+                                          i32, vp]
+        for name in EXPORTS:
+            if name not in ("sisso_l0_last_error", "sisso_l0_destroy", "sisso_l0_count_tuples"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def count_tuples(m: int, n: int) -> int:
+    return int(lib().sisso_l0_count_tuples(int(m), int(n)))
+
+
+def _ptr(a):
+    """Raw address of a torch tensor or numpy array (kept alive by the caller)."""
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _as_f64(a):
+    if hasattr(a, "data_ptr"):
+        import torch
+        return a.to(torch.float64).contiguous()
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Handle:
+    """Owns one library handle (device workspace, stream binding)."""
+
+    def __init__(self, precision=FP64, task_mode=PER_TASK, device=0, stream=None,
+                 candidate_pool=0, max_candidate_pool=2048, timeout_seconds=0.0,
+                 fp32_fallback_pivot_ratio=1e-6, rank_deficient_pivot_ratio=1e-12,
+                 autotune=0):
+        L = lib()
+        o = Options()
+        L.sisso_l0_default_options(ctypes.byref(o))
+        o.device = int(device)
+        o.stream = ctypes.c_void_p(int(stream) if stream else 0)
+        o.precision = int(precision)
+        o.task_mode = int(task_mode)
+        o.candidate_pool = int(candidate_pool)
+        o.max_candidate_pool = int(max_candidate_pool)
+        o.timeout_seconds = float(timeout_seconds)
+        o.fp32_fallback_pivot_ratio = float(fp32_fallback_pivot_ratio)
+        o.rank_deficient_pivot_ratio = float(rank_deficient_pivot_ratio)
+        o.autotune = int(autotune)
+        self._opt = o
+        h = ctypes.c_void_p()
+        rc = L.sisso_l0_create(ctypes.byref(h), ctypes.byref(o))
+        if rc != OK:
+            raise L0Error(rc, "sisso_l0_create failed")
+        self._h = h
+        self.task_mode = int(task_mode)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sisso_l0_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != OK:
+            msg = lib().sisso_l0_last_error(self._h)
+            raise L0Error(rc, msg.decode() if msg else "")
+
+    def fit(self, X, y, n_dim, k, offsets=None, out_tuples=None, out_rmse=None):
+        """Run sisso_l0_fit.  Returns (tuples [n_out, k, n_dim] int32,
+        rmse [n_out, k] float64) as numpy arrays, or fills the given output
+        buffers (torch or numpy) and returns them."""
+        X = _as_f64(X)
+        y = _as_f64(y)
+        n_sis, n_total = int(X.shape[0]), int(X.shape[1])
+        if offsets is None:
+            offsets = [0, n_total]
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        n_tasks = len(off) - 1
+        n_out = 1 if self.task_mode == SHARED else n_tasks
+        ret_np = out_tuples is None
+        if out_tuples is None:
+            out_tuples = np.empty((n_out, k, n_dim), dtype=np.int32)
+            out_rmse = np.empty((n_out, k), dtype=np.float64)
+        rc = lib().sisso_l0_fit(self._h, ctypes.c_void_p(_ptr(X)), ctypes.c_void_p(_ptr(y)),
+                                off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n_tasks,
+                                n_sis, int(n_dim), int(k), ctypes.c_void_p(_ptr(out_tuples)),
+                                ctypes.c_void_p(_ptr(out_rmse)))
+        self._check(rc)
+        return (out_tuples, out_rmse) if ret_np else (out_tuples, out_rmse)
+
+    def stats(self) -> dict:
+        s = Stats()
+        s.struct_size = ctypes.sizeof(Stats)
+        self._check(lib().sisso_l0_get_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def debug_unrank(self, m, n, ranks):
+        ranks = np.ascontiguousarray(ranks, dtype=np.uint64)
+        out = np.empty((len(ranks), n), dtype=np.int32)
+        self._check(lib().sisso_l0_debug_unrank(self._h, int(m), int(n),
+                                                ctypes.c_void_p(ranks.ctypes.data), len(ranks),
+                                                ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def debug_gram(self, X, y, offsets=None, task=0):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        if offsets is None:
+            offsets = [0, X.shape[1]]
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        m = X.shape[0]
+        out = np.zeros((m + 1, m + 1), dtype=np.float64)
+        self._check(lib().sisso_l0_debug_gram(
+            self._h, ctypes.c_void_p(X.ctypes.data), ctypes.c_void_p(y.ctypes.data),
+            off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(off) - 1, m, int(task),
+            ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+
+def fit(X, y, n_dim, k, offsets=None, **opts):
+    """One-shot fit with a temporary handle."""
+    with Handle(**opts) as h:
+        return h.fit(X, y, n_dim, k, offsets=offsets)

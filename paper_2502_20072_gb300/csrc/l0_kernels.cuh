@@ -1,0 +1,135 @@
+// l0_kernels.cuh -- launch interfaces between the host orchestrator
+// (l0_api.cu) and the kernels (l0_prep.cu, l0_tuple.cu, l0_select.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "l0_common.cuh"
+
+namespace l0 {
+
+// tile shape of the tuple kernel: 8 warps, each warp UJ rows j, each lane UK
+// columns k (k = k0 + lane + 32 v)
+constexpr int TILE_WARPS = 8;
+constexpr int TILE_UJ = 8;
+constexpr int TILE_UK = 4;
+constexpr int TILE_TJ = TILE_WARPS * TILE_UJ;   // 64 rows
+constexpr int TILE_TK = 32 * TILE_UK;           // 128 columns
+
+// One scoring problem: a task (PER_TASK) and a tuple size d >= 2.
+struct ProbDesc {
+  long long g_off;        // element offset of the problem's Gram in the Gram buffer
+  long long ld;           // leading dimension of that Gram
+  int m, d, dp, task;     // dp = d - 2 (size of the outer prefix)
+  int n_jt, n_kt, L, prefix_off;   // j/k tile counts, prefix steps per item, row-prefix offset
+  long long item_begin, item_end;  // global work-item range
+  u64 total;              // C(m, d)
+};
+
+template <typename R>
+struct TileArgs {
+  const R *G;
+  const ProbDesc *probs;
+  int n_probs;
+  const long long *row_prefix;     // per problem: n_jt + 1 cumulative item counts
+  Binom B;
+  double ratio;                    // pivot ratio: ineligible (FP64) / redo in FP64 (FP32)
+  int K, S;                        // list capacity, staging capacity
+  u64 *item_counter;
+  u64 *gthr;                       // [n_probs] ordered score bits
+  R *out_s; u64 *out_k; int *out_cnt;   // [n_probs][n_slots][K], [n_probs][n_slots]
+  int n_slots;
+  // FP32 only: (lexrank of first tuple, count) runs of tuples redone in FP64
+  u64 *dfr_key; unsigned *dfr_len; u64 *dfr_n; long long dfr_cap;
+  int *err;
+};
+
+// work items of one j-tile row: (#k tiles reaching past j0) x (#prefix chunks)
+__host__ __device__ inline long long tile_row_items(int bj, int m, int dp, int L,
+                                                    int n_kt, u64 nprefix) {
+  int j0 = bj * TILE_TJ;
+  int bk_min = (j0 + 1) / TILE_TK;
+  long long nk = (long long)n_kt - bk_min;
+  if (nk <= 0) return 0;
+  long long nch = (long long)((nprefix + (u64)L - 1) / (u64)L);
+  return nk * nch;
+}
+
+// kernels (host launch wrappers)
+cudaError_t launch_centre(const double *X, const double *y, long long n_total,
+                          int m, const long long *offsets_dev, int T,
+                          double *mu, double *inv_s, double *W64, int *err,
+                          cudaStream_t st);
+cudaError_t launch_gram64(const double *W64, long long n_total, int m,
+                          const long long *offsets_host, int T, double *G,
+                          long long ld, long long g_stride, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_tile(const TileArgs<R> &a, int dp_lo, int dp_hi, int grid,
+                        size_t smem, cudaStream_t st);
+template <typename R>
+size_t tile_smem_bytes(int K, int S, int dp_hi);
+template <typename R>
+cudaError_t tile_occupancy(int dp_lo, int dp_hi, size_t smem, int *blocks_per_sm);
+
+template <typename R>
+cudaError_t launch_singles(const R *G, const ProbDesc *probs_host_view,
+                           const ProbDesc *probs_dev, int n_probs, int K, int S,
+                           int grid_x, u64 *gthr, R *out_s, u64 *out_k,
+                           int *out_cnt, int n_slots, cudaStream_t st);
+
+// merge all slot lists of every problem into one top-K' pool per problem
+template <typename R>
+cudaError_t launch_merge(const R *in_s, const u64 *in_k, const int *in_cnt,
+                         int n_slots, int n_probs, int K, int S, int groups,
+                         R *part_s, u64 *part_k, int *part_cnt,
+                         unsigned *done, R *pool_s, u64 *pool_k, int *pool_cnt,
+                         cudaStream_t st);
+
+struct RefitArgs {
+  const double *X, *y;
+  long long n_total;
+  int m;
+  const long long *offsets;   // device [T+1]
+  const double *mu;           // [T][m+1], index 0 = target
+  int T, shared;              // SHARED: all tasks, else the problem's task
+  const ProbDesc *probs;
+  int n_probs, K;
+  const u64 *pool_k; const int *pool_cnt;
+  Binom B;
+  double rho_min;
+  double *scratch; long long nmax;   // [n_probs*K][(d+1)][nmax]
+  double *refit;              // [n_probs][K] score (SSE or pooled mean SSE), +inf if ineligible
+};
+cudaError_t launch_refit(const RefitArgs &a, cudaStream_t st);
+
+struct CertOut {
+  double delta;        // max |gram SSE - refit SSE| over the pool
+  double pool_worst;   // gram score (SSE units) of the last pool entry
+  double kth_refit;    // k-th best refit score (SSE units)
+  int pool_cnt, pool_full, n_valid, certified;
+};
+
+template <typename R>
+struct SelectArgs {
+  const ProbDesc *probs;
+  int n_probs, K, k;
+  const R *pool_s; const u64 *pool_k; const int *pool_cnt;
+  const double *refit;
+  const double *inv_s;         // [T][m+1]: 1 / ||centred column||, index 0 the target
+  int mp1, shared;             // PER_TASK: a pool score times S_yy,t is an SSE
+  const double *rmse_div;      // [n_probs] n_t (PER_TASK) or N (SHARED)
+  Binom B;
+  int *out_tuples; double *out_rmse;   // [n_probs][k][d], [n_probs][k]
+  CertOut *cert;
+  double cert_safety;
+};
+template <typename R>
+cudaError_t launch_select(const SelectArgs<R> &a, cudaStream_t st);
+
+cudaError_t launch_unrank(const Binom &B, int m, int d, u64 total,
+                          const u64 *ranks, long long count, int *tuples,
+                          cudaStream_t st);
+
+}  // namespace l0

@@ -1,0 +1,152 @@
+// l0_prep.cu -- per-task centring/scaling (FP64) and the FP64 Gram.
+//
+// Centring every column and the target by its task mean removes the
+// intercept of the least-squares fit exactly; dividing by the centred norm
+// turns the Gram of the columns into a correlation matrix (unit diagonal),
+// which is what the tuple kernel factorises.  With the scaled target placed
+// first, the augmented Gram is
+//     G[0][0] = 1,  G[0][j+1] = r_j (Pearson r of feature j, Eq. 1),
+//     G[i+1][j+1] = corr(f_i, f_j),
+// so the l0 score of a tuple (paper Sec. 2.4) is a Schur complement of G.
+#include "l0_kernels.cuh"
+
+namespace l0 {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One warp per (column c in [0, m], task t); c == 0 is the target.
+__global__ void __launch_bounds__(256)
+centre_kernel(const double *__restrict__ X, const double *__restrict__ y,
+              long long n_total, int m, const long long *__restrict__ offsets,
+              double *__restrict__ mu, double *__restrict__ inv_s,
+              double *__restrict__ W, int *err) {
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int t = blockIdx.y;
+  if (c > m) return;
+  const long long lo = offsets[t], hi = offsets[t + 1];
+  const long long n = hi - lo;
+  const double *src = (c == 0) ? (y + lo) : (X + (long long)(c - 1) * n_total + lo);
+  double s = 0.0;
+  bool finite = true;
+  for (long long i = lane; i < n; i += 32) {
+    double v = src[i];
+    finite &= isfinite(v);
+    s += v;
+  }
+  if (__any_sync(0xffffffffu, !finite)) {
+    if (lane == 0) set_err(err, 5);
+  }
+  s = warp_sum(s);
+  const double mean = s / (double)n;
+  double ss = 0.0;
+  for (long long i = lane; i < n; i += 32) {
+    double v = src[i] - mean;
+    ss += v * v;
+  }
+  ss = warp_sum(ss);
+  const double nrm = sqrt(ss);
+  const double is = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+  if (lane == 0) {
+    mu[(long long)t * (m + 1) + c] = mean;
+    inv_s[(long long)t * (m + 1) + c] = is;
+  }
+  if (W) {
+    double *dst = W + (long long)c * n_total + lo;
+    for (long long i = lane; i < n; i += 32) dst[i] = (src[i] - mean) * is;
+  }
+}
+
+cudaError_t launch_centre(const double *X, const double *y, long long n_total,
+                          int m, const long long *offsets_dev, int T,
+                          double *mu, double *inv_s, double *W64, int *err,
+                          cudaStream_t st) {
+  dim3 grid((m + 1 + 7) / 8, T);
+  centre_kernel<<<grid, 256, 0, st>>>(X, y, n_total, m, offsets_dev, mu, inv_s,
+                                      W64, err);
+  return cudaGetLastError();
+}
+
+// FP64 Gram of the scaled columns of one task: G = W_t^T W_t over the task's
+// rows, upper-triangular 64x64 tiles only (FFMA64, 4x4 outputs per thread).
+__global__ void __launch_bounds__(256)
+gram64_kernel(const double *__restrict__ W, long long n_total, int mp1,
+              long long lo, long long hi, double *__restrict__ G, long long ld,
+              int nb) {
+  // decode the upper-triangular tile index (bi <= bj)
+  int idx = blockIdx.x;
+  int bi = 0;
+  while (idx >= nb - bi) { idx -= nb - bi; ++bi; }
+  const int bj = bi + idx;
+  __shared__ double As[16][65];
+  __shared__ double Bs[16][65];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  const int lr = tid >> 2;            // row within the tile for loads
+  const int lk = (tid & 3) * 4;       // first k of this thread's 4 loads
+  const int ra = bi * 64 + lr, rb = bj * 64 + lr;
+  for (long long k0 = lo; k0 < hi; k0 += 16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      long long kk = k0 + lk + q;
+      double a = 0.0, b = 0.0;
+      if (kk < hi) {
+        if (ra < mp1) a = W[(long long)ra * n_total + kk];
+        if (rb < mp1) b = W[(long long)rb * n_total + kk];
+      }
+      As[lk + q][lr] = a;
+      Bs[lk + q][lr] = b;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = bi * 64 + ty + 16 * i;
+    if (r >= mp1) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = bj * 64 + tx + 16 * j;
+      if (c < mp1) G[(long long)r * ld + c] = acc[i][j];
+    }
+  }
+}
+
+cudaError_t launch_gram64(const double *W64, long long n_total, int m,
+                          const long long *offsets_host, int T, double *G,
+                          long long ld, long long g_stride, cudaStream_t st) {
+  const int mp1 = m + 1;
+  const int nb = (mp1 + 63) / 64;
+  const int ntiles = nb * (nb + 1) / 2;
+  for (int t = 0; t < T; ++t) {
+    gram64_kernel<<<ntiles, 256, 0, st>>>(W64, n_total, mp1, offsets_host[t],
+                                          offsets_host[t + 1],
+                                          G + (long long)t * g_stride, ld, nb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace l0

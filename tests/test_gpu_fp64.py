@@ -1,0 +1,216 @@
+"""GPU parity of the FP64 path against the CPU oracle (through the C ABI).
+
+Tolerances (spec reading): chosen tuple indices agree exactly except
+inside tie groups (adjacent oracle SSEs within 1e-9 relative); RMSE within
+1e-10 relative of the oracle.  Integer work (rank <-> tuple) is bit-exact.
+"""
+
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2502_20072_gb300 as l0
+from workloads import make_config, make_problem
+
+pytestmark = pytest.mark.gpu
+
+RMSE_RTOL = 1e-10
+TIE_GAP = 1e-9
+
+
+def _score_fn(X, y, offsets=None, task=0):
+    def f(tuples):
+        if len(tuples) == 0:
+            return []
+        sse, _ = oracle.score(X, y, np.array(tuples, dtype=np.int32), offsets=offsets)
+        return sse[:, task]
+    return f
+
+
+def _check_against_oracle(X, y, d, k, offsets=None, **opts):
+    ref = oracle.fit(X, y, d, k, offsets=offsets)
+    with l0.Handle(**opts) as h:
+        got_t, got_r = h.fit(X, y, d, k, offsets=offsets)
+        st = h.stats()
+    n_out = ref["tuples"].shape[0]
+    for o in range(n_out):
+        ok, msg = oracle.agreement(ref["tuples"][o], ref["score"][o], got_t[o], rel_gap=TIE_GAP,
+                                   score_fn=_score_fn(X, y, offsets, o))
+        assert ok, "list %d: %s" % (o, msg)
+        fin = np.isfinite(ref["rmse"][o])
+        np.testing.assert_array_equal(np.isfinite(got_r[o]), fin)
+        np.testing.assert_allclose(got_r[o][fin], ref["rmse"][o][fin], rtol=RMSE_RTOL, atol=0)
+        assert np.all(got_t[o][~fin] == -1)
+    return got_t, got_r, st
+
+
+# ------------------------------------------------------------- ranking ----
+@pytest.mark.parametrize("m,n", [(12, 1), (12, 2), (12, 5), (40, 3), (40, 4), (23, 8)])
+def test_unrank_matches_itertools(m, n):
+    allt = list(itertools.combinations(range(m), n))
+    ranks = np.arange(len(allt), dtype=np.uint64)
+    with l0.Handle() as h:
+        got = h.debug_unrank(m, n, ranks)
+    np.testing.assert_array_equal(got, np.array(allt, dtype=np.int32))
+
+
+def test_unrank_large_m_sampled():
+    m, n = 20000, 3
+    total = math.comb(m, n)
+    rng = np.random.default_rng(5)
+    ranks = np.concatenate([[0, 1, total - 1, total - 2],
+                            rng.integers(0, total, size=2000)]).astype(np.uint64)
+    with l0.Handle() as h:
+        got = h.debug_unrank(m, n, ranks)
+    # independent lexicographic unranking (counting rule written out)
+    for r, t in zip(ranks[:200], got[:200]):
+        r = int(r)
+        exp = []
+        lo = 0
+        for pos in range(n, 0, -1):
+            v = lo
+            while True:
+                c = math.comb(m - 1 - v, pos - 1)
+                if r < c:
+                    break
+                r -= c
+                v += 1
+            exp.append(v)
+            lo = v + 1
+        assert list(t) == exp
+
+
+# ---------------------------------------------------------------- Gram ----
+def test_gram_is_task_correlation_matrix():
+    prob = make_problem([70, 130], 150, seed=8, n_planted=2, sigma=0.1)
+    with l0.Handle() as h:
+        for t in range(2):
+            G = h.debug_gram(prob.X, prob.y, prob.offsets, task=t)
+            lo, hi = prob.offsets[t], prob.offsets[t + 1]
+            A = np.vstack([prob.y[lo:hi], prob.X[:, lo:hi]])
+            C = np.corrcoef(A)
+            iu = np.triu_indices(C.shape[0])
+            np.testing.assert_allclose(G[iu], C[iu], rtol=0, atol=1e-13)
+
+
+# ----------------------------------------------------------- fit parity ---
+@pytest.mark.parametrize("n,m,d,k", [
+    (60, 150, 2, 25),     # 3 j-tiles, 2 k-tiles, ragged tails
+    (80, 150, 3, 40),
+    (50, 70, 4, 30),
+    (40, 30, 5, 20),
+    (30, 13, 8, 10),
+    (90, 300, 1, 17),
+])
+def test_fit_matches_oracle(n, m, d, k):
+    prob = make_problem(n, m, seed=100 + m + d, n_planted=min(d, 3), sigma=0.05)
+    _check_against_oracle(prob.X, prob.y, d, k)
+
+
+def test_fit_multitask_per_task():
+    prob = make_problem([40, 75, 130], 90, seed=31, n_planted=2, sigma=0.03)
+    _check_against_oracle(prob.X, prob.y, 3, 20, offsets=prob.offsets)
+
+
+def test_c1_planted_pair_first_and_parity():
+    prob, d, k = make_config("C1")
+    t, r, _ = _check_against_oracle(prob.X, prob.y, d, k)
+    assert tuple(t[0, 0]) == (16, 102)
+
+
+def test_all_tuples_returned_when_k_is_total():
+    prob = make_problem(30, 9, seed=41, n_planted=2, sigma=0.1)
+    t, r, _ = _check_against_oracle(prob.X, prob.y, 3, math.comb(9, 3))
+    assert len({tuple(x) for x in t[0]}) == math.comb(9, 3)
+
+
+def test_single_tuple_m_equals_d():
+    prob = make_problem(20, 4, seed=42, n_planted=2, sigma=0.1)
+    _check_against_oracle(prob.X, prob.y, 4, 1)
+
+
+def test_duplicate_and_constant_columns_are_ineligible():
+    prob = make_problem(50, 40, seed=43, n_planted=2, sigma=0.05)
+    X = prob.X.copy()
+    X[7] = X[3]          # exact duplicate
+    X[11] = 2.5          # constant column
+    k = math.comb(40, 2)
+    t, r, _ = _check_against_oracle(X, prob.y, 2, k)
+    got = {tuple(x) for x in t[0] if x[0] >= 0}
+    assert (3, 7) not in got
+    assert not any(11 in x for x in got)
+
+
+def test_constant_target_all_ties():
+    prob = make_problem(25, 10, seed=44, n_planted=2, sigma=0.05)
+    y = np.full(25, 3.0)
+    with l0.Handle() as h:
+        t, r = h.fit(prob.X, y, 2, 10)
+    # every SSE is 0: ties ordered lexicographically
+    assert [tuple(x) for x in t[0]] == list(itertools.combinations(range(10), 2))[:10]
+    assert np.all(r[0] == 0.0)
+
+
+def test_device_and_host_buffers_agree():
+    import torch
+    prob = make_problem(70, 120, seed=45, n_planted=3, sigma=0.02)
+    with l0.Handle() as h:
+        t1, r1 = h.fit(prob.X, prob.y, 3, 30)
+        Xd = torch.from_numpy(prob.X).cuda()
+        yd = torch.from_numpy(prob.y).cuda()
+        ot = torch.empty((1, 30, 3), dtype=torch.int32, device="cuda")
+        orr = torch.empty((1, 30), dtype=torch.float64, device="cuda")
+        h.fit(Xd, yd, 3, 30, out_tuples=ot, out_rmse=orr)
+        torch.cuda.synchronize()
+    np.testing.assert_array_equal(ot.cpu().numpy(), t1)
+    np.testing.assert_array_equal(orr.cpu().numpy(), r1)
+
+
+def test_errors_are_reported():
+    prob = make_problem(20, 10, seed=46, n_planted=2, sigma=0.05)
+    with l0.Handle() as h:
+        with pytest.raises(l0.L0Error) as e:
+            h.fit(prob.X, prob.y, 2, math.comb(10, 2) + 1)
+        assert e.value.code == l0.EINVAL
+        with pytest.raises(l0.L0Error) as e:
+            h.fit(prob.X, prob.y, 9, 1)
+        assert e.value.code == l0.EINVAL
+        with pytest.raises(l0.L0Error) as e:
+            h.fit(prob.X, prob.y, 2, 3, offsets=[0, 3, 20])   # task too small
+        assert e.value.code == l0.EINVAL
+        Xn = prob.X.copy()
+        Xn[4, 5] = np.nan
+        with pytest.raises(l0.L0Error) as e:
+            h.fit(Xn, prob.y, 2, 3)
+        assert e.value.code == l0.ENONFINITE
+        # the handle stays usable after errors
+        t, r = h.fit(prob.X, prob.y, 2, 3)
+        assert t.shape == (1, 3, 2)
+
+
+# --------------------------------------------------------- full size C2 ----
+def test_c2_full_size_fp64_sampled_against_oracle():
+    prob, d, k = make_config("C2")
+    with l0.Handle() as h:
+        t, r = h.fit(prob.X, prob.y, d, k)
+        st = h.stats()
+    assert st["certified"] == 1
+    assert tuple(t[0, 0]) == tuple(prob.planted[0])
+    # every reported tuple re-scored by the oracle
+    sse, rho = oracle.score(prob.X, prob.y, t[0])
+    n = prob.n_total
+    np.testing.assert_allclose(r[0], np.sqrt(sse[:, 0] / n), rtol=RMSE_RTOL)
+    assert np.all(np.diff(sse[:, 0]) >= -1e-9 * sse[1:, 0])
+    # no sampled tuple outside the list beats the k-th reported SSE
+    rng = np.random.default_rng(7)
+    m = prob.n_sis
+    samp = np.sort(np.array([rng.choice(m, d, replace=False) for _ in range(4000)]), axis=1)
+    ssamp, _ = oracle.score(prob.X, prob.y, samp.astype(np.int32))
+    listed = {tuple(x) for x in t[0]}
+    kth = sse[-1, 0]
+    for tup, s in zip(samp, ssamp[:, 0]):
+        if tuple(tup) not in listed:
+            assert s >= kth * (1 - TIE_GAP)
