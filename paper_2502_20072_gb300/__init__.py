@@ -134,7 +134,7 @@ class Handle:
     """Owns one library handle (device workspace, stream binding)."""
 
     def __init__(self, precision=FP64, task_mode=PER_TASK, device=0, stream=None,
-                 candidate_pool=0, max_candidate_pool=2048, timeout_seconds=0.0,
+                 candidate_pool=0, max_candidate_pool=2048, timeout_seconds=300.0,
                  fp32_fallback_pivot_ratio=1e-6, rank_deficient_pivot_ratio=1e-12,
                  autotune=0):
         L = lib()

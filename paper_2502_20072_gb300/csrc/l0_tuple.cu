@@ -429,12 +429,12 @@ tile_kernel(TileArgs<R> A) {
       }
       __syncthreads();
       cur = prob;
-      if (prob < 0) break;
-      cta_list_reset<R>(L, A.gthr + prob);
-    } else {
+      if (prob >= 0) cta_list_reset<R>(L, A.gthr + prob);
+    } else if (prob >= 0) {
       cta_list_pull_global<R>(L, A.gthr + prob);
     }
     __syncthreads();
+    if (prob < 0) break;   // past the last item (uniform)
     const ProbDesc pd = A.probs[prob];
     const long long local = item - pd.item_begin;
     const long long *rp = A.row_prefix + pd.prefix_off;
@@ -452,6 +452,10 @@ tile_kernel(TileArgs<R> A) {
     const int bk = bk_min + (int)(rem / nch);
     const u64 r0 = (u64)(rem % nch) * (u64)pd.L;
     const u64 r1 = (r0 + (u64)pd.L < np) ? r0 + (u64)pd.L : np;
+    if (bk >= pd.n_kt || r1 <= r0 || r1 - r0 > (u64)pd.L) {   // inconsistent plan
+      set_err(A.err, 9);
+      break;
+    }
     u64 *gthr = A.gthr + prob;
     switch (pd.dp) {
 #define L0_CASE(X)                                                           \
