@@ -107,7 +107,8 @@ int sisso_l0_create(sisso_l0_t *out, const sisso_l0_options *opt);
  * Tuples whose FP64 pivot ratio is below rank_deficient_pivot_ratio are not
  * eligible; unfilled slots hold index -1 and rmse +inf.
  * Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EUNSUPPORTED
- * (C(n_sis, n_dim) >= 2^62 or a candidate pool above 2048).
+ * (C(n_sis, n_dim) >= 2^62 or k above 2048; the candidate pool is capped
+ * at 2048).
  */
 int sisso_l0_fit(sisso_l0_t h, const double *X, const double *y,
                  const int64_t *task_offsets, int32_t n_tasks, int64_t n_sis,

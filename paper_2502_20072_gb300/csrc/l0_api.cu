@@ -378,10 +378,15 @@ int fit_impl(sisso_l0_t h, const double *X, const double *y, const int64_t *task
   if (total >= kSat) return fail(h, SISSO_L0_EUNSUPPORTED, "C(n_sis, n_dim) does not fit in 62 bits");
   if ((u64)k > total) return fail(h, SISSO_L0_EINVAL, "k exceeds C(n_sis, n_dim)");
   P.n_out = P.shared ? 1 : n_tasks;
-  int K = h->opt.candidate_pool > 0 ? h->opt.candidate_pool : std::max(4 * k, 256);
-  K = std::max(K, k);
-  const int Kmax = h->opt.max_candidate_pool > 0 ? h->opt.max_candidate_pool : 2048;
-  if (K > 2048 || Kmax > 2048) return fail(h, SISSO_L0_EUNSUPPORTED, "candidate pool above 2048");
+  // candidate pool K': at least k, at most 2048 (shared-memory lists), never
+  // more than the number of tuples
+  if (k > 2048) return fail(h, SISSO_L0_EUNSUPPORTED, "k above 2048");
+  int Kmax = h->opt.max_candidate_pool > 0 ? std::min(h->opt.max_candidate_pool, 2048) : 2048;
+  int K = h->opt.candidate_pool > 0 ? h->opt.candidate_pool : std::min(std::max(4 * k, 256), 2048);
+  K = std::min(std::max(K, k), 2048);
+  if ((u64)K > total) K = (int)total;
+  Kmax = std::max(Kmax, K);
+  if ((u64)Kmax > total) Kmax = (int)std::max<u64>(total, (u64)K);
   cudaStream_t st = h->st;
   const int m = P.m;
   const long long N = P.N;
