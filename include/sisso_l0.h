@@ -151,6 +151,33 @@ int sisso_l0_debug_gram(sisso_l0_t h, const double *X, const double *y,
                         const int64_t *task_offsets, int32_t n_tasks,
                         int64_t n_sis, int32_t task, double *out);
 
+/*
+ * Augmented correlation matrix of one task without allocating memory.
+ * (The paper has no counterpart: this serves callers that cannot allocate
+ * device memory while they run -- a service whose device memory is reserved
+ * up front for its own allocator, or a latency-bound loop that cannot take
+ * the device-wide synchronisation of cudaMalloc/cudaFree.)
+ *   X         device FP64 [n_sis][n_samples], feature-major, one task
+ *   y         device FP64 [n_samples]
+ *   out_gram  device FP64, row-major with leading dimension ld_out >= n_sis+1;
+ *             entries (a, b), a <= b < n_sis+1, receive what
+ *             sisso_l0_debug_gram returns for the same data (index 0 the
+ *             target, j+1 feature j); other entries are left untouched
+ *   stream    cudaStream_t (NULL = legacy stream); the call returns after
+ *             the stream has finished its work
+ * Scratch lives in a fixed 16 MiB array inside the library (held by every
+ * GPU that loads the library until the process exits), so
+ * (n_sis+1) * n_samples + 2 (n_sis+1) + 3 must not exceed 2^21 doubles;
+ * larger inputs return SISSO_L0_EUNSUPPORTED.  The first call on a device
+ * looks up the array's device address for that device (the current device).
+ * All calls share the array: calls that overlap on the GPU race and must be
+ * serialised by the caller.  Calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Errors: EINVAL, EUNSUPPORTED, ENONFINITE, ECUDA.
+ */
+int sisso_l0_gram_noalloc(const double *X, const double *y, int64_t n_samples,
+                          int64_t n_sis, double *out_gram, int64_t ld_out,
+                          void *stream);
+
 #ifdef __cplusplus
 }
 #endif
