@@ -249,6 +249,7 @@ def run_ours(args):
                    "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "flushed between steps (256 MB write, outside the timed events)",
                    "candidate_pool": st["candidate_pool"], "certified": st["certified"],
+                   "fp64_redo_tuples": int(st["fp64_fallback_tuples"]),
                    "stage_ms": {s: round(st["ms_" + s], 4) for s in
                                 ("prep", "gram", "tuple", "merge", "refit")}},
         "e2e": {"value": e2e_val, "unit": UNIT,

@@ -68,7 +68,8 @@ struct sisso_l0_handle {
   DevBuf probs, rowpre, ctr, gthr, lists_s, lists_k, lists_cnt;
   DevBuf part_s, part_k, part_cnt, done, pool_s, pool_k, pool_cnt;
   DevBuf scratch, refit, rdiv, cert, out_t, out_r, err;
-  DevBuf dfr_key, dfr_len, dfr_n;
+  DevBuf dfr_key, dfr_len, dfr_n, dfr_cnt;
+  DevBuf abf, bbf, kmeta, gram32;
   int binom_m = -1;
   cudaEvent_t ev[8] = {nullptr};
 };
@@ -156,7 +157,13 @@ struct FitPlan {
   std::vector<long long> rowpre;
   int grid = 0;
   int n_slots = 0;
+  long long gstride = 0;
+  bool have_g64 = false;       // FP64 Gram computed (always in FP64 mode)
+  unsigned long long fallback_tuples = 0;
 };
+
+constexpr int kDeferGroups = 64;
+constexpr long long kDeferCap = 1LL << 24;
 
 // choose prefix steps per work item and fill problem descriptors
 void plan_items(FitPlan &P, const std::vector<u64> &binom_row, int grid_target) {
@@ -211,7 +218,7 @@ int run_search(sisso_l0_t h, FitPlan &P, int K, int S, const R *G, int *certifie
   if (d == 1) {
     n_slots = std::max(1, std::min(64, (P.m + L0_THREADS - 1) / L0_THREADS));
   } else {
-    n_slots = P.grid;
+    n_slots = P.grid + (P.mixed ? kDeferGroups : 0);
   }
   const size_t nl = (size_t)n_probs * n_slots * K;
   L0_CK(h->lists_s.ensure(nl * sizeof(R)), "alloc lists");
@@ -219,12 +226,21 @@ int run_search(sisso_l0_t h, FitPlan &P, int K, int S, const R *G, int *certifie
   L0_CK(h->lists_cnt.ensure((size_t)n_probs * n_slots * 4), "alloc lists");
   L0_CK(cudaMemsetAsync(h->lists_cnt.p, 0, (size_t)n_probs * n_slots * 4, st), "memset");
   L0_CK(h->gthr.ensure((size_t)n_probs * 8), "alloc gthr");
-  {
-    std::vector<u64> g(n_probs, l0::ord_inf<R>());
-    L0_CK(cudaMemcpyAsync(h->gthr.p, g.data(), g.size() * 8, cudaMemcpyHostToDevice, st), "copy gthr");
-    L0_CK(cudaStreamSynchronize(st), "sync");
-  }
   L0_CK(cudaEventRecord(h->ev[2], st), "event");
+  {
+    // threshold: +inf, then the K'-th best d-tuple of the M best columns
+    int M = 0;
+    if (d >= 2) {
+      const int Mcap = std::min(std::min(P.m, 64), K);
+      M = Mcap;
+      for (int q = d; q <= Mcap; ++q)
+        if (binom_host(q, d) >= 2ull * (u64)K) { M = q; break; }
+    }
+    const double ratio = P.mixed ? h->opt.fp32_fallback_pivot_ratio : h->opt.rank_deficient_pivot_ratio;
+    L0_CK(l0::launch_seed<R>(G, h->probs.as<l0::ProbDesc>(), n_probs, K, S, M, ratio, B,
+                             h->gthr.as<u64>(), st),
+          "seed kernel");
+  }
   if (d == 1) {
     L0_CK(l0::launch_singles<R>(G, P.pd.data(), h->probs.as<l0::ProbDesc>(), n_probs, K, S,
                                 n_slots, h->gthr.as<u64>(), h->lists_s.as<R>(),
@@ -251,32 +267,77 @@ int run_search(sisso_l0_t h, FitPlan &P, int K, int S, const R *G, int *certifie
     a.dfr_key = h->dfr_key.as<u64>();
     a.dfr_len = h->dfr_len.as<unsigned>();
     a.dfr_n = h->dfr_n.as<u64>();
-    a.dfr_cap = 0;
+    a.dfr_cap = P.mixed ? kDeferCap : 0;
     a.err = h->err.as<int>();
+    if (P.mixed) L0_CK(cudaMemsetAsync(h->dfr_n.p, 0, 24, st), "memset");
     const size_t smem = l0::tile_smem_bytes<R>(K, S, d - 2);
     L0_CK(l0::launch_tile<R>(a, d - 2, d - 2, P.grid, smem, st), "tile kernel");
+    if (P.mixed) {
+      // FP64 redo of the near-singular tuples the FP32 kernel queued: the
+      // FP64 Gram and the Gram-mode redo run only when many were queued, the
+      // dot-product redo only when a few were (decided on the device)
+      const bool can_gram = P.m <= 8192;
+      if (can_gram) {
+        L0_CK(h->gram.ensure((size_t)P.T * P.gstride * 8), "alloc Gram");
+        L0_CK(l0::launch_gram64(h->w64.as<double>(), P.N, P.m, P.off.data(), P.T,
+                                h->gram.as<double>(), P.ld, P.gstride, st, h->dfr_n.as<u64>(), d),
+              "gram kernel");
+      }
+      l0::DeferArgs da;
+      da.G64 = can_gram ? h->gram.as<double>() : nullptr;
+      da.ld64 = P.ld;
+      da.g64_stride = P.gstride;
+      da.W64 = h->w64.as<double>();
+      da.n_total = P.N;
+      da.offsets = h->offs.as<long long>();
+      da.probs = h->probs.as<l0::ProbDesc>();
+      da.B = B;
+      da.ratio = h->opt.rank_deficient_pivot_ratio;
+      da.run_key = h->dfr_key.as<u64>();
+      da.run_len = h->dfr_len.as<unsigned>();
+      da.n_runs = h->dfr_n.as<u64>();
+      da.cap = kDeferCap;
+      da.K = K;
+      da.S = S;
+      da.gthr = (u64 *)h->gthr.p;
+      da.out_s = (float *)h->lists_s.p;
+      da.out_k = h->lists_k.as<u64>();
+      da.out_cnt = h->lists_cnt.as<int>();
+      da.n_slots = n_slots;
+      da.slot0 = P.grid;
+      da.n_tuples = h->dfr_n.as<u64>() + 2;
+      L0_CK(l0::launch_defer(da, kDeferGroups, n_probs, st), "defer kernel");
+    }
   }
   L0_CK(cudaEventRecord(h->ev[3], st), "event");
   // merge
-  const int groups = std::max(1, std::min(n_slots, 16));
-  const size_t np = (size_t)n_probs * groups * K;
-  L0_CK(h->part_s.ensure(np * sizeof(R)), "alloc merge");
-  L0_CK(h->part_k.ensure(np * 8), "alloc merge");
+  const int groups = std::max(1, std::min(n_slots, 32));
+  L0_CK(h->part_s.ensure((size_t)n_probs * groups * K * sizeof(R)), "alloc merge");
+  L0_CK(h->part_k.ensure((size_t)n_probs * groups * K * 8), "alloc merge");
   L0_CK(h->part_cnt.ensure((size_t)n_probs * groups * 4), "alloc merge");
-  L0_CK(h->done.ensure((size_t)n_probs * 4), "alloc merge");
-  L0_CK(cudaMemsetAsync(h->done.p, 0, (size_t)n_probs * 4, st), "memset");
+  L0_CK(h->done.ensure((size_t)n_probs * 16), "alloc merge");
+  {
+    // per problem: done counter, pad, ordered +inf bound
+    std::vector<unsigned> c0(4 * (size_t)n_probs, 0u);
+    for (int q = 0; q < n_probs; ++q) {
+      const u64 inf = l0::ord_inf<R>();
+      memcpy(&c0[4 * q + 2], &inf, 8);
+    }
+    L0_CK(cudaMemcpyAsync(h->done.p, c0.data(), c0.size() * 4, cudaMemcpyHostToDevice, st), "copy");
+  }
   L0_CK(h->pool_s.ensure((size_t)n_probs * K * sizeof(R)), "alloc pool");
   L0_CK(h->pool_k.ensure((size_t)n_probs * K * 8), "alloc pool");
   L0_CK(h->pool_cnt.ensure((size_t)n_probs * 4), "alloc pool");
   L0_CK(l0::launch_merge<R>(h->lists_s.as<R>(), h->lists_k.as<u64>(), h->lists_cnt.as<int>(),
-                            n_slots, n_probs, K, S, groups, h->part_s.as<R>(),
+                            n_slots, n_probs, K, S, groups, h->gthr.as<u64>(), h->part_s.as<R>(),
                             h->part_k.as<u64>(), h->part_cnt.as<int>(), h->done.as<unsigned>(),
                             h->pool_s.as<R>(), h->pool_k.as<u64>(), h->pool_cnt.as<int>(), st),
         "merge kernel");
   L0_CK(cudaEventRecord(h->ev[4], st), "event");
   // re-fit
   const int n_rows_max = (int)P.nmax;
-  L0_CK(h->scratch.ensure((size_t)n_probs * K * (d + 1) * (size_t)n_rows_max * 8), "alloc refit scratch");
+  if ((size_t)(d + 1) * (size_t)n_rows_max * 8 > 200 * 1024)
+    L0_CK(h->scratch.ensure((size_t)n_probs * K * (d + 1) * (size_t)n_rows_max * 8), "alloc refit scratch");
   L0_CK(h->refit.ensure((size_t)n_probs * K * 8), "alloc refit");
   l0::RefitArgs ra;
   ra.X = P.Xd;
@@ -296,6 +357,8 @@ int run_search(sisso_l0_t h, FitPlan &P, int K, int S, const R *G, int *certifie
   ra.rho_min = std::sqrt(h->opt.rank_deficient_pivot_ratio);
   ra.scratch = h->scratch.as<double>();
   ra.nmax = n_rows_max;
+  ra.dmax = d;
+  ra.smem_rows = 0;
   ra.refit = h->refit.as<double>();
   L0_CK(l0::launch_refit(ra, st), "refit kernel");
   // select
@@ -318,16 +381,24 @@ int run_search(sisso_l0_t h, FitPlan &P, int K, int S, const R *G, int *certifie
   sa.out_rmse = h->out_r.as<double>();
   sa.cert = h->cert.as<l0::CertOut>();
   sa.cert_safety = 4.0;
+  sa.gthr = h->gthr.as<u64>();
   L0_CK(l0::launch_select<R>(sa, st), "select kernel");
   L0_CK(cudaEventRecord(h->ev[5], st), "event");
   std::vector<l0::CertOut> cert(n_probs);
   L0_CK(cudaMemcpyAsync(cert.data(), h->cert.p, n_probs * sizeof(l0::CertOut), cudaMemcpyDeviceToHost, st), "copy cert");
+  u64 dfr_stats[3] = {0, 0, 0};
+  if (P.mixed && d >= 2)
+    L0_CK(cudaMemcpyAsync(dfr_stats, h->dfr_n.p, 24, cudaMemcpyDeviceToHost, st), "copy");
   int rc = wait_stream(h);
   if (rc) return rc;
   int hostErr = 0;
   L0_CK(cudaMemcpy(&hostErr, h->err.p, 4, cudaMemcpyDeviceToHost), "copy err");
   if (hostErr == 5) return fail(h, SISSO_L0_ENONFINITE, "NaN or Inf in X or y");
+  if (hostErr == 7)
+    return fail(h, SISSO_L0_EUNSUPPORTED,
+                "too many near-singular tuples for the FP32 search; use SISSO_L0_FP64");
   if (hostErr != 0) return fail(h, SISSO_L0_ECUDA, "device error flag " + std::to_string(hostErr));
+  P.fallback_tuples += dfr_stats[2];
   *certified = 1;
   *delta_max = 0;
   for (auto &c : cert) {
@@ -364,7 +435,6 @@ int fit_impl(sisso_l0_t h, const double *X, const double *y, const int64_t *task
   P.mixed = (h->opt.precision == SISSO_L0_MIXED_BF16X3) ? 1 : 0;
   if (h->opt.precision != SISSO_L0_FP64 && h->opt.precision != SISSO_L0_MIXED_BF16X3)
     return fail(h, SISSO_L0_EUNSUPPORTED, "precision not supported");
-  if (P.mixed) return fail(h, SISSO_L0_EUNSUPPORTED, "mixed precision not built yet");
   if (P.shared) return fail(h, SISSO_L0_EUNSUPPORTED, "SHARED task mode not built yet");
   P.off.assign(task_offsets, task_offsets + n_tasks + 1);
   P.nmax = 0;
@@ -411,22 +481,56 @@ int fit_impl(sisso_l0_t h, const double *X, const double *y, const int64_t *task
   int rc = ensure_binom(h, m);
   if (rc) return rc;
   L0_CK(cudaEventRecord(h->ev[0], st), "event");
-  // 1. centre and scale
+  // 1-2. centre and scale (FP64), then the augmented Gram per task
   const int mp1 = m + 1;
+  P.ld = ((long long)mp1 + 31) / 32 * 32;
+  P.gstride = (long long)mp1 * P.ld;
+  const long long gstride = P.gstride;
   L0_CK(h->mu.ensure((size_t)n_tasks * mp1 * 8), "alloc mu");
   L0_CK(h->inv_s.ensure((size_t)n_tasks * mp1 * 8), "alloc inv_s");
   L0_CK(h->w64.ensure((size_t)mp1 * N * 8), "alloc W");
-  L0_CK(l0::launch_centre(Xd, yd, N, m, h->offs.as<long long>(), n_tasks, h->mu.as<double>(),
-                          h->inv_s.as<double>(), h->w64.as<double>(), h->err.as<int>(), st),
-        "centre kernel");
-  L0_CK(cudaEventRecord(h->ev[1], st), "event");
-  // 2. Gram
-  P.ld = ((long long)mp1 + 31) / 32 * 32;
-  const long long gstride = (long long)mp1 * P.ld;
-  L0_CK(h->gram.ensure((size_t)n_tasks * gstride * 8), "alloc Gram");
-  L0_CK(l0::launch_gram64(h->w64.as<double>(), N, m, P.off.data(), n_tasks, h->gram.as<double>(),
-                          P.ld, gstride, st),
-        "gram kernel");
+  if (!P.mixed) {
+    L0_CK(l0::launch_centre(Xd, yd, N, m, h->offs.as<long long>(), n_tasks, h->mu.as<double>(),
+                            h->inv_s.as<double>(), h->w64.as<double>(), h->err.as<int>(), st),
+          "centre kernel");
+    L0_CK(cudaEventRecord(h->ev[1], st), "event");
+    L0_CK(h->gram.ensure((size_t)n_tasks * gstride * 8), "alloc Gram");
+    L0_CK(l0::launch_gram64(h->w64.as<double>(), N, m, P.off.data(), n_tasks,
+                            h->gram.as<double>(), P.ld, gstride, st),
+          "gram kernel");
+    P.have_g64 = true;
+  } else {
+    // split-BF16 rows: per task three segments of npad_t = roundup(n_t, 64)
+    std::vector<int> meta(3 * n_tasks);
+    long long ldk = 0;
+    for (int t = 0; t < n_tasks; ++t) {
+      const long long nt = P.off[t + 1] - P.off[t];
+      const long long np = (nt + 63) / 64 * 64;
+      if (ldk + 3 * np > (1LL << 30)) return fail(h, SISSO_L0_EUNSUPPORTED, "too many samples");
+      meta[t] = (int)ldk;                      // kbeg
+      meta[n_tasks + t] = (int)np;             // npad
+      meta[2 * n_tasks + t] = (int)(3 * np / 64);   // K blocks
+      ldk += 3 * np;
+    }
+    const size_t abytes = (size_t)mp1 * ldk * 2;
+    L0_CK(h->abf.ensure(abytes), "alloc split rows");
+    L0_CK(h->bbf.ensure(abytes), "alloc split rows");
+    L0_CK(h->kmeta.ensure(meta.size() * 4), "alloc");
+    L0_CK(cudaMemcpyAsync(h->kmeta.p, meta.data(), meta.size() * 4, cudaMemcpyHostToDevice, st), "copy");
+    L0_CK(cudaMemsetAsync(h->abf.p, 0, abytes, st), "memset");
+    L0_CK(cudaMemsetAsync(h->bbf.p, 0, abytes, st), "memset");
+    const int *kbeg = h->kmeta.as<int>();
+    L0_CK(l0::launch_centre_split(Xd, yd, N, m, h->offs.as<long long>(), n_tasks,
+                                  h->mu.as<double>(), h->inv_s.as<double>(), h->w64.as<double>(),
+                                  h->abf.p, h->bbf.p, ldk, kbeg, kbeg + n_tasks, h->err.as<int>(),
+                                  st),
+          "centre kernel");
+    L0_CK(cudaEventRecord(h->ev[1], st), "event");
+    L0_CK(h->gram32.ensure((size_t)n_tasks * gstride * 4), "alloc Gram");
+    L0_CK(l0::launch_gram_tc(h->abf.p, h->bbf.p, ldk, m, n_tasks, kbeg, kbeg + 2 * n_tasks,
+                             h->gram32.as<float>(), P.ld, gstride, h->err.as<int>(), st),
+          "tensor-core gram kernel");
+  }
   L0_CK(cudaEventRecord(h->ev[6], st), "event");
   // problems
   P.pd.clear();
@@ -446,9 +550,14 @@ int fit_impl(sisso_l0_t h, const double *X, const double *y, const int64_t *task
   if (n_dim >= 2) {
     int S0 = 1024;
     while (S0 < 2 * Kmax) S0 <<= 1;
-    const size_t smem = l0::tile_smem_bytes<double>(Kmax, S0, dp);
     int bps = 0;
-    L0_CK(l0::tile_occupancy<double>(dp, dp, smem, &bps), "occupancy");
+    if (P.mixed) {
+      const size_t smem = l0::tile_smem_bytes<float>(Kmax, S0, dp);
+      L0_CK(l0::tile_occupancy<float>(dp, dp, smem, &bps), "occupancy");
+    } else {
+      const size_t smem = l0::tile_smem_bytes<double>(Kmax, S0, dp);
+      L0_CK(l0::tile_occupancy<double>(dp, dp, smem, &bps), "occupancy");
+    }
     if (bps < 1) return fail(h, SISSO_L0_EUNSUPPORTED, "tuple kernel does not fit on an SM");
     P.grid = h->n_sm * bps;
   }
@@ -468,15 +577,23 @@ int fit_impl(sisso_l0_t h, const double *X, const double *y, const int64_t *task
   }
   L0_CK(h->out_t.ensure((size_t)P.n_out * k * n_dim * 4), "alloc out");
   L0_CK(h->out_r.ensure((size_t)P.n_out * k * 8), "alloc out");
-  L0_CK(h->dfr_n.ensure(8), "alloc");
+  L0_CK(h->dfr_n.ensure(24), "alloc");   // queued runs, queued tuples, redone tuples
+  if (P.mixed && n_dim >= 2) {
+    L0_CK(h->dfr_key.ensure((size_t)kDeferCap * 8), "alloc deferral buffer");
+    L0_CK(h->dfr_len.ensure((size_t)kDeferCap * 4), "alloc deferral buffer");
+  }
   int certified = 0, enl = 0;
   double delta = 0;
   float ms_tuple = 0, ms_merge = 0, ms_refit = 0;
   for (;;) {
     int S = 1024;
     while (S < 2 * K) S <<= 1;
-    rc = run_search<double>(h, P, K, S, h->gram.as<double>(), &certified, &delta, &ms_tuple,
-                            &ms_merge, &ms_refit);
+    if (P.mixed)
+      rc = run_search<float>(h, P, K, S, h->gram32.as<float>(), &certified, &delta, &ms_tuple,
+                             &ms_merge, &ms_refit);
+    else
+      rc = run_search<double>(h, P, K, S, h->gram.as<double>(), &certified, &delta, &ms_tuple,
+                              &ms_merge, &ms_refit);
     if (rc) break;
     if (certified || K >= Kmax) break;
     K = std::min(2 * K, Kmax);
@@ -499,8 +616,9 @@ int fit_impl(sisso_l0_t h, const double *X, const double *y, const int64_t *task
   S.certified = certified;
   S.tuple_fits = total * (u64)n_tasks * (u64)(enl + 1);
   S.max_pool_rel_error = delta;
-  // centre + Gram per task, then per search pass: tuple, merge, refit, select
-  S.kernel_launches = 1 + n_tasks + 4LL * (enl + 1);
+  S.fp64_fallback_tuples = P.fallback_tuples;
+  // centre + Gram, then per search pass: seed, tuple, merge, refit, select
+  S.kernel_launches = (P.mixed ? 2 : 1 + n_tasks) + 5LL * (enl + 1);
   S.ms_prep = t_prep;
   S.ms_gram = t_gram;
   S.ms_tuple = ms_tuple;
@@ -593,7 +711,8 @@ void sisso_l0_destroy(sisso_l0_t h) {
                     &h->probs, &h->rowpre, &h->ctr, &h->gthr, &h->lists_s, &h->lists_k,
                     &h->lists_cnt, &h->part_s, &h->part_k, &h->part_cnt, &h->done, &h->pool_s,
                     &h->pool_k, &h->pool_cnt, &h->scratch, &h->refit, &h->rdiv,
-                    &h->cert, &h->out_t, &h->out_r, &h->err, &h->dfr_key, &h->dfr_len, &h->dfr_n};
+                    &h->cert, &h->out_t, &h->out_r, &h->err, &h->dfr_key, &h->dfr_len, &h->dfr_n,
+                    &h->dfr_cnt, &h->abf, &h->bbf, &h->kmeta, &h->gram32};
   for (DevBuf *b : bufs) b->release();
   for (int i = 0; i < 8; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);

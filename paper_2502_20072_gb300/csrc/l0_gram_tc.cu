@@ -1,0 +1,364 @@
+// l0_gram_tc.cu -- split-BF16 Gram on the 5th-generation tensor cores.
+//
+// The tuple search needs the augmented correlation matrix of every task,
+// G = W^T W with W the centred, scaled columns (target first).  In FP32 this
+// is a dense contraction, so it runs as a BF16 GEMM with FP32 accumulation
+// in tensor memory.  Each scaled value z is split as z = hi + lo + r with
+// hi = bf16(z), lo = bf16(z - hi) (|r| <~ 2^-17 |z|), and
+//     z_a z_b ~= hi_a hi_b + hi_a lo_b + lo_a hi_b          (3 terms)
+// which is one GEMM over a K axis three times longer: row a of A is
+// [hi_a | hi_a | lo_a], row b of B is [hi_b | lo_b | hi_b] (per task, each
+// segment padded to a multiple of 64 samples with zeros).
+//
+// Kernel: one CTA per upper-triangular 128 x 128 output tile and task.
+// Thread 0 streams 64-wide K blocks of A and B into a 4-stage shared-memory
+// ring with TMA (128-byte swizzle); thread 32 issues tcgen05.mma
+// (M = N = 128, K = 16, BF16 -> FP32 in TMEM) and frees each stage through
+// tcgen05.commit; all four warps then read the accumulator with tcgen05.ld
+// and store the tile.  Every wait is bounded (2 s on the global timer);
+// on expiry the kernel records an error, waits (bounded) for its own copies
+// and MMAs, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "l0_kernels.cuh"
+
+namespace l0 {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
+constexpr int THREADS = 128;
+constexpr uint32_t TILE_A_BYTES = BM * BK * 2;     // 16 KB
+constexpr uint32_t TILE_B_BYTES = BN * BK * 2;     // 16 KB
+constexpr uint32_t STAGE_BYTES = TILE_A_BYTES + TILE_B_BYTES;
+constexpr uint32_t TMEM_COLS = 128;
+constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait on an mbarrier phase; false (and the error word set) on expiry
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > WAIT_NS) {
+      set_err(err, 10);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"((unsigned long long)map), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+// shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
+// rows of 128 B grouped by 8 (stride 1024 B between groups)
+__device__ __forceinline__ unsigned long long sw128_desc(uint32_t saddr) {
+  unsigned long long d = 0;
+  d |= (unsigned long long)((saddr & 0x3FFFFu) >> 4);
+  d |= (unsigned long long)(16u >> 4) << 16;      // leading byte offset (unused here)
+  d |= (unsigned long long)(1024u >> 4) << 32;    // stride byte offset
+  d |= 1ull << 46;                                // descriptor version
+  d |= 2ull << 61;                                // 128-byte swizzle
+  return d;
+}
+// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, unsigned long long a,
+                                          unsigned long long b, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// grid (upper-triangular tile pairs, tasks), 128 threads
+__global__ void __launch_bounds__(THREADS, 1)
+gram_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+               float *__restrict__ G, long long ld, long long g_stride, int mp1,
+               const int *__restrict__ kbeg, const int *__restrict__ nkb, int nb, int *err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem =
+      (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) unsigned long long full_bar[STAGES];
+  __shared__ __align__(8) unsigned long long empty_bar[STAGES];
+  __shared__ __align__(8) unsigned long long done_bar;
+  __shared__ uint32_t s_tmem;
+
+  int idx = blockIdx.x;
+  int bi = 0;
+  while (idx >= nb - bi) { idx -= nb - bi; ++bi; }
+  const int bj = bi + idx;
+  const int task = blockIdx.y;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    mbar_init(smem_u32(&done_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s_tmem)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+  const int nk = nkb[task];
+  const int k0 = kbeg[task];
+  const uint32_t sbase = smem_u32(smem);
+
+  if (tid == 0) {
+    // producer: TMA loads of K blocks into the ring
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (kb >= STAGES) {
+        if (!mbar_wait(smem_u32(&empty_bar[s]), ((kb / STAGES) - 1) & 1, err)) {
+          break;
+        }
+      }
+      const uint32_t fb = smem_u32(&full_bar[s]);
+      mbar_expect_tx(fb, STAGE_BYTES);
+      const uint32_t a_dst = sbase + s * STAGE_BYTES;
+      tma_load_2d(a_dst, &mapA, fb, k0 + kb * BK, bi * BM);
+      tma_load_2d(a_dst + TILE_A_BYTES, &mapB, fb, k0 + kb * BK, bj * BN);
+    }
+  } else if (tid == 32) {
+    // MMA issuer
+    const uint32_t idesc = idesc_bf16(BM, BN);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(smem_u32(&full_bar[s]), (kb / STAGES) & 1, err)) {
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a_s = sbase + s * STAGE_BYTES;
+      const uint32_t b_s = a_s + TILE_A_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        umma_bf16(tmem, sw128_desc(a_s + kk * 32), sw128_desc(b_s + kk * 32), idesc,
+                  (kb | kk) != 0 ? 1u : 0u);
+      }
+      umma_commit(smem_u32(&empty_bar[s]));
+    }
+    umma_commit(smem_u32(&done_bar));
+  }
+  __syncwarp();
+  // everyone: wait for the accumulator (the commit also fires when nothing
+  // was issued, so this wait ends after a failure too)
+  // warp-uniform: the tcgen05.ld below is .sync.aligned
+  const bool done = __all_sync(0xffffffffu, mbar_wait(smem_u32(&done_bar), 0, err));
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (done && nk > 0) {
+    const int row = bi * BM + warp * 32 + lane;
+    float *grow = G + (long long)task * g_stride + (long long)row * ld;
+    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      float v[16];
+      tmem_ld16(tbase + (uint32_t)c0, v);
+      if (row < mp1) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int col = bj * BN + c0 + i;
+          if (col < mp1) grow[col] = v[i];
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------- centring + BF16 split --
+// One warp per (column c in [0, m], task t), c == 0 the target.  Same
+// two-pass FP64 mean / norm as the FP64 path, then the split rows:
+//   A[c][kbeg_t + s*np_t + i] = (hi, hi, lo)[s],  B[c][...] = (hi, lo, hi)[s]
+__global__ void __launch_bounds__(256)
+centre_split_kernel(const double *__restrict__ X, const double *__restrict__ y,
+                    long long n_total, int m, const long long *__restrict__ offsets,
+                    double *__restrict__ mu, double *__restrict__ inv_s,
+                    double *__restrict__ W, __nv_bfloat16 *__restrict__ A,
+                    __nv_bfloat16 *__restrict__ B, long long ldk,
+                    const int *__restrict__ kbeg, const int *__restrict__ npad, int *err) {
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int t = blockIdx.y;
+  if (c > m) return;
+  const long long lo = offsets[t], hi = offsets[t + 1];
+  const long long n = hi - lo;
+  const double *src = (c == 0) ? (y + lo) : (X + (long long)(c - 1) * n_total + lo);
+  double s = 0.0;
+  bool finite = true;
+  for (long long i = lane; i < n; i += 32) {
+    const double v = src[i];
+    finite &= isfinite(v);
+    s += v;
+  }
+  if (__any_sync(0xffffffffu, !finite) && lane == 0) set_err(err, 5);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  const double mean = s / (double)n;
+  double ss = 0.0;
+  for (long long i = lane; i < n; i += 32) {
+    const double v = src[i] - mean;
+    ss += v * v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  const double nrm = sqrt(ss);
+  const double is = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+  if (lane == 0) {
+    mu[(long long)t * (m + 1) + c] = mean;
+    inv_s[(long long)t * (m + 1) + c] = is;
+  }
+  const long long kb = kbeg[t];
+  const long long np = npad[t];
+  __nv_bfloat16 *Ar = A + (long long)c * ldk + kb;
+  __nv_bfloat16 *Br = B + (long long)c * ldk + kb;
+  for (long long i = lane; i < n; i += 32) {
+    const double z = (src[i] - mean) * is;
+    if (W) W[(long long)c * n_total + lo + i] = z;
+    const __nv_bfloat16 h = __double2bfloat16(z);
+    const __nv_bfloat16 l = __double2bfloat16(z - (double)__bfloat162float(h));
+    Ar[i] = h;
+    Ar[np + i] = h;
+    Ar[2 * np + i] = l;
+    Br[i] = h;
+    Br[np + i] = l;
+    Br[2 * np + i] = h;
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap *map, const void *base, long long rows, long long ldk) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)ldk, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ldk * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims,
+                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+cudaError_t launch_centre_split(const double *X, const double *y, long long n_total, int m,
+                                const long long *offsets_dev, int T, double *mu, double *inv_s,
+                                double *W64, void *A, void *B, long long ldk,
+                                const int *kbeg_dev, const int *npad_dev, int *err,
+                                cudaStream_t st) {
+  dim3 grid((m + 1 + 7) / 8, T);
+  centre_split_kernel<<<grid, 256, 0, st>>>(X, y, n_total, m, offsets_dev, mu, inv_s, W64,
+                                            (__nv_bfloat16 *)A, (__nv_bfloat16 *)B, ldk,
+                                            kbeg_dev, npad_dev, err);
+  return cudaGetLastError();
+}
+
+size_t gram_tc_smem_bytes() { return (size_t)STAGES * STAGE_BYTES + 1024; }
+
+cudaError_t launch_gram_tc(const void *A, const void *B, long long ldk, int m, int T,
+                           const int *kbeg_dev, const int *nkb_dev, float *G, long long ld,
+                           long long g_stride, int *err, cudaStream_t st) {
+  const int mp1 = m + 1;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, mp1, ldk) || !make_map(&mb, B, mp1, ldk)) return cudaErrorInvalidValue;
+  const int nb = (mp1 + BM - 1) / BM;
+  const int ntiles = nb * (nb + 1) / 2;
+  const size_t smem = gram_tc_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  gram_tc_kernel<<<dim3(ntiles, T), THREADS, smem, st>>>(ma, mb, G, ld, g_stride, mp1, kbeg_dev,
+                                                         nkb_dev, nb, err);
+  return cudaGetLastError();
+}
+
+}  // namespace l0

@@ -40,7 +40,8 @@ struct TileArgs {
   u64 *gthr;                       // [n_probs] ordered score bits
   R *out_s; u64 *out_k; int *out_cnt;   // [n_probs][n_slots][K], [n_probs][n_slots]
   int n_slots;
-  // FP32 only: (lexrank of first tuple, count) runs of tuples redone in FP64
+  // FP32 only: runs of tuples redone in FP64: lexicographic rank of the first
+  // tuple, (problem << 8) | run length (<= 128); dfr_n[0] runs, dfr_n[1] tuples
   u64 *dfr_key; unsigned *dfr_len; u64 *dfr_n; long long dfr_cap;
   int *err;
 };
@@ -56,14 +57,27 @@ __host__ __device__ inline long long tile_row_items(int bj, int m, int dp, int L
   return nk * nch;
 }
 
+// The FP32 search queues near-singular tuples for an FP64 redo.  Building the
+// full FP64 Gram for that pays off only when many tuples were queued (and
+// n_sis is moderate); otherwise the redo computes the few FP64 entries it
+// needs as dot products.  Host and device evaluate the same rule on the
+// queued-tuple counter.
+__host__ __device__ inline bool defer_wants_gram(u64 n_tuples, int m, int d) {
+  if (m > 8192) return false;
+  return (double)n_tuples * (double)((d + 1) * (d + 2) / 2) * 8.0 >
+         (double)(m + 1) * (double)(m + 1);
+}
+
 // kernels (host launch wrappers)
 cudaError_t launch_centre(const double *X, const double *y, long long n_total,
                           int m, const long long *offsets_dev, int T,
                           double *mu, double *inv_s, double *W64, int *err,
                           cudaStream_t st);
+// gate (optional): run only when defer_wants_gram(gate[1], m, gate_d)
 cudaError_t launch_gram64(const double *W64, long long n_total, int m,
                           const long long *offsets_host, int T, double *G,
-                          long long ld, long long g_stride, cudaStream_t st);
+                          long long ld, long long g_stride, cudaStream_t st,
+                          const u64 *gate = nullptr, int gate_d = 0);
 
 template <typename R>
 cudaError_t launch_tile(const TileArgs<R> &a, int dp_lo, int dp_hi, int grid,
@@ -79,13 +93,15 @@ cudaError_t launch_singles(const R *G, const ProbDesc *probs_host_view,
                            int grid_x, u64 *gthr, R *out_s, u64 *out_k,
                            int *out_cnt, int n_slots, cudaStream_t st);
 
-// merge all slot lists of every problem into one top-K' pool per problem
+// merge all slot lists of every problem into one top-K' pool per problem.
+// part_*: [n_probs][groups][K] partial lists; counters: [n_probs][4]
+// (done counter, pad, ordered bound of the partials) -- initialise with
+// merge_counters_init and they are left initialised.
 template <typename R>
 cudaError_t launch_merge(const R *in_s, const u64 *in_k, const int *in_cnt,
-                         int n_slots, int n_probs, int K, int S, int groups,
-                         R *part_s, u64 *part_k, int *part_cnt,
-                         unsigned *done, R *pool_s, u64 *pool_k, int *pool_cnt,
-                         cudaStream_t st);
+                         int n_slots, int n_probs, int K, int S, int groups, const u64 *gthr,
+                         R *part_s, u64 *part_k, int *part_cnt, unsigned *counters,
+                         R *pool_s, u64 *pool_k, int *pool_cnt, cudaStream_t st);
 
 struct RefitArgs {
   const double *X, *y;
@@ -99,14 +115,16 @@ struct RefitArgs {
   const u64 *pool_k; const int *pool_cnt;
   Binom B;
   double rho_min;
-  double *scratch; long long nmax;   // [n_probs*K][(d+1)][nmax]
+  double *scratch; long long nmax;   // [n_probs*K][(d+1)][nmax] (when not in shared memory)
+  int dmax;                   // largest d over the problems
+  int smem_rows;              // set by launch_refit: columns in shared memory
   double *refit;              // [n_probs][K] score (SSE or pooled mean SSE), +inf if ineligible
 };
 cudaError_t launch_refit(const RefitArgs &a, cudaStream_t st);
 
 struct CertOut {
   double delta;        // max |gram SSE - refit SSE| over the pool
-  double pool_worst;   // gram score (SSE units) of the last pool entry
+  double pool_worst;   // bound (SSE units) under which the pool holds every tuple
   double kth_refit;    // k-th best refit score (SSE units)
   int pool_cnt, pool_full, n_valid, certified;
 };
@@ -124,9 +142,51 @@ struct SelectArgs {
   int *out_tuples; double *out_rmse;   // [n_probs][k][d], [n_probs][k]
   CertOut *cert;
   double cert_safety;
+  const u64 *gthr;             // [n_probs] final search threshold (ordered bits of R)
 };
 template <typename R>
 cudaError_t launch_select(const SelectArgs<R> &a, cudaStream_t st);
+
+// mixed precision: centring + split-BF16 rows, tensor-core Gram
+cudaError_t launch_centre_split(const double *X, const double *y, long long n_total, int m,
+                                const long long *offsets_dev, int T, double *mu, double *inv_s,
+                                double *W64, void *A, void *B, long long ldk,
+                                const int *kbeg_dev, const int *npad_dev, int *err,
+                                cudaStream_t st);
+size_t gram_tc_smem_bytes();
+cudaError_t launch_gram_tc(const void *A, const void *B, long long ldk, int m, int T,
+                           const int *kbeg_dev, const int *nkb_dev, float *G, long long ld,
+                           long long g_stride, int *err, cudaStream_t st);
+
+// FP64 redo of the runs the FP32 tuple kernel queued
+struct DeferArgs {
+  const double *G64;           // FP64 Gram per task (null: dot products of W64)
+  long long ld64, g64_stride;
+  const double *W64;           // scaled columns [(m+1)][n_total]
+  long long n_total;
+  const long long *offsets;    // device [T+1]
+  const ProbDesc *probs;
+  Binom B;
+  double ratio;                // FP64 rank-deficiency pivot ratio
+  const u64 *run_key; const unsigned *run_len;
+  const u64 *n_runs;           // [0] queued runs, [1] queued tuples
+  long long cap;
+  int K, S;
+  u64 *gthr;
+  float *out_s; u64 *out_k; int *out_cnt;
+  int n_slots, slot0;          // lists go to slots slot0 + blockIdx.x
+  u64 *n_tuples;               // tuples redone (statistics)
+};
+// both launched; exactly one does work (see defer_wants_gram)
+cudaError_t launch_defer(const DeferArgs &a, int groups, int n_probs, cudaStream_t st);
+
+// initial search threshold per problem: +inf, then the K'-th best score of
+// all d-tuples of the M best single columns (a valid bound: real tuples)
+template <typename R>
+cudaError_t launch_seed(const R *G, const ProbDesc *probs_dev, int n_probs, int K, int S,
+                        int M, double ratio, const Binom &B, u64 *gthr, cudaStream_t st);
+template <typename R>
+size_t seed_smem_bytes(int K, int S);
 
 cudaError_t launch_unrank(const Binom &B, int m, int d, u64 total,
                           const u64 *ranks, long long count, int *tuples,

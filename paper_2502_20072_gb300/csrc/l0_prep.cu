@@ -76,7 +76,8 @@ cudaError_t launch_centre(const double *X, const double *y, long long n_total,
 __global__ void __launch_bounds__(256)
 gram64_kernel(const double *__restrict__ W, long long n_total, int mp1,
               long long lo, long long hi, double *__restrict__ G, long long ld,
-              int nb) {
+              int nb, const u64 *gate, int gate_d) {
+  if (gate && !defer_wants_gram(gate[1], mp1 - 1, gate_d)) return;
   // decode the upper-triangular tile index (bi <= bj)
   int idx = blockIdx.x;
   int bi = 0;
@@ -135,14 +136,15 @@ gram64_kernel(const double *__restrict__ W, long long n_total, int mp1,
 
 cudaError_t launch_gram64(const double *W64, long long n_total, int m,
                           const long long *offsets_host, int T, double *G,
-                          long long ld, long long g_stride, cudaStream_t st) {
+                          long long ld, long long g_stride, cudaStream_t st,
+                          const u64 *gate, int gate_d) {
   const int mp1 = m + 1;
   const int nb = (mp1 + 63) / 64;
   const int ntiles = nb * (nb + 1) / 2;
   for (int t = 0; t < T; ++t) {
     gram64_kernel<<<ntiles, 256, 0, st>>>(W64, n_total, mp1, offsets_host[t],
                                           offsets_host[t + 1],
-                                          G + (long long)t * g_stride, ld, nb);
+                                          G + (long long)t * g_stride, ld, nb, gate, gate_d);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

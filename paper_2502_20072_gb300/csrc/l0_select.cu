@@ -27,101 +27,200 @@ __device__ void stream_entries(CtaList<R> &L, const R *s, const u64 *k, int n) {
   }
 }
 
-// grid (groups, n_probs).  Phase 1: CTA g folds slots [g*n/G, (g+1)*n/G) of
-// its problem into one list.  Phase 2: the last CTA of the problem to finish
-// (counter, no waiting) folds the G partial lists into the pool.
+// Gather the prefix (score <= cut) of n_lists sorted lists into shared
+// memory (up to cap entries), sort once, keep the first K.  Returns the
+// number kept, or -1 when more than cap entries qualified (nothing written).
 template <typename R>
-__global__ void __launch_bounds__(L0_THREADS)
-merge_kernel(const R *in_s, const u64 *in_k, const int *in_cnt, int n_slots,
-             int K, int S, R *part_s, u64 *part_k, int *part_cnt,
-             unsigned *done, R *pool_s, u64 *pool_k, int *pool_cnt) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ int gather_sort_lists(const R *ls_base, const u64 *lk_base, const int *cnt,
+                                 size_t stride, int n_lists, R cut, int K, int cap, R *ss,
+                                 u64 *sk, R *out_s, u64 *out_k, int *s_tot) {
+  if (threadIdx.x == 0) *s_tot = 0;
+  __syncthreads();
+  // one warp per list: binary search of the prefix, then copy
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int l = warp; l < n_lists; l += nw) {
+    const R *ls = ls_base + (size_t)l * stride;
+    const u64 *lk = lk_base + (size_t)l * stride;
+    int lo = 0, hi = cnt[l];
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (ls[mid] <= cut) lo = mid + 1; else hi = mid;
+    }
+    int base = 0;
+    if (lane == 0 && lo > 0) base = atomicAdd(s_tot, lo);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int i = lane; i < lo; i += 32) {
+      if (base + i < cap) {
+        ss[base + i] = ls[i];
+        sk[base + i] = lk[i];
+      }
+    }
+  }
+  __syncthreads();
+  const int total = *s_tot;
+  if (total > cap) return -1;
+  int P = 1;
+  while (P < total) P <<= 1;
+  for (int i = total + threadIdx.x; i < P; i += blockDim.x) {
+    ss[i] = r_inf<R>();
+    sk[i] = ~0ull;
+  }
+  __syncthreads();
+  cta_bitonic_sort<R>(ss, sk, P);
+  const int nout = total < K ? total : K;
+  for (int i = threadIdx.x; i < nout; i += blockDim.x) {
+    out_s[i] = ss[i];
+    out_k[i] = sk[i];
+  }
+  __syncthreads();
+  return nout;
+}
+
+// Streaming fallback: the same prefixes through a CTA list.
+template <typename R>
+__device__ int stream_lists(const R *ls_base, const u64 *lk_base, const int *cnt, size_t stride,
+                            int n_lists, R cut, unsigned char *smem, int K, int S, R *out_s,
+                            u64 *out_k) {
   unsigned char *p = smem;
   CtaList<R> L = cta_list_carve<R>(p, K, S);
-  __shared__ int s_last;
-  const int prob = blockIdx.y, g = blockIdx.x, G = gridDim.x;
   cta_list_reset<R>(L, nullptr);
   __syncthreads();
+  for (int l = 0; l < n_lists; ++l) {
+    const R *ls = ls_base + (size_t)l * stride;
+    int lo = 0, hi = cnt[l];
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (ls[mid] <= cut) lo = mid + 1; else hi = mid;
+    }
+    if (lo > 0) stream_entries<R>(L, ls, lk_base + (size_t)l * stride, lo);
+  }
+  const int n = *(volatile int *)L.n_list;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    out_s[i] = L.ls[i];
+    out_k[i] = L.lk[i];
+  }
+  __syncthreads();
+  return n;
+}
+
+// grid (groups, n_probs), 1024 threads.  The slot lists are sorted and only
+// their prefixes at or below the search threshold g can reach the pool.
+// Level 1: CTA x sorts the qualifying entries of its share of slots and keeps
+// its best K' (a partial list); a full partial's K'-th score is a tighter
+// bound g2 (atomicMin).  Level 2: the last CTA of the problem (counter, no
+// waiting) gathers the partial prefixes <= g2, sorts them once and keeps K'.
+template <typename R>
+__global__ void __launch_bounds__(1024)
+merge_kernel(const R *in_s, const u64 *in_k, const int *in_cnt, int n_slots,
+             int K, int S, const u64 *gthr, R *part_s, u64 *part_k, int *part_cnt, int cap,
+             unsigned *counters, R *pool_s, u64 *pool_k, int *pool_cnt) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_last, s_tot;
+  const int prob = blockIdx.y, g = blockIdx.x, G = gridDim.x;
+  unsigned *done = counters + 4 * prob;
+  u64 *g2 = (u64 *)(counters + 4 * prob + 2);
+  R *ss = (R *)smem;
+  u64 *sk = (u64 *)(smem + (size_t)cap * sizeof(R));
+  const R gcut = from_ord<R>(gthr[prob]);
   const int a = (int)((long long)n_slots * g / G);
   const int b = (int)((long long)n_slots * (g + 1) / G);
-  for (int sl = a; sl < b; ++sl) {
-    const size_t slot = (size_t)prob * n_slots + sl;
-    const int n = in_cnt[slot];
-    if (n > 0) stream_entries<R>(L, in_s + slot * K, in_k + slot * K, n);
+  const size_t pslot = (size_t)prob * G + g;
+  R *ps = part_s + pslot * K;
+  u64 *pk = part_k + pslot * K;
+  const size_t s0 = (size_t)prob * n_slots + a;
+  int n = gather_sort_lists<R>(in_s + s0 * K, in_k + s0 * K, in_cnt + s0, (size_t)K, b - a,
+                               gcut, K, cap, ss, sk, ps, pk, &s_tot);
+  if (n < 0)
+    n = stream_lists<R>(in_s + s0 * K, in_k + s0 * K, in_cnt + s0, (size_t)K, b - a, gcut, smem,
+                        K, S, ps, pk);
+  if (threadIdx.x == 0) {
+    part_cnt[pslot] = n;
+    if (n >= K) atomicMin(g2, ord_of(ps[K - 1]));
   }
-  const size_t ps = (size_t)prob * G + g;
-  cta_list_flush<R>(L, part_s + ps * K, part_k + ps * K, part_cnt + ps);
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(done + prob, 1u) == (unsigned)(G - 1));
+  if (threadIdx.x == 0) s_last = (atomicAdd(done, 1u) == (unsigned)(G - 1));
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  cta_list_reset<R>(L, nullptr);
-  __syncthreads();
-  for (int q = 0; q < G; ++q) {
-    const size_t qs = (size_t)prob * G + q;
-    const int n = *(volatile const int *)(part_cnt + qs);
-    if (n > 0) stream_entries<R>(L, part_s + qs * K, part_k + qs * K, n);
+  R cut2 = from_ord<R>(*(volatile u64 *)g2);
+  if (gcut < cut2) cut2 = gcut;
+  const size_t p0 = (size_t)prob * G;
+  R *os = pool_s + (size_t)prob * K;
+  u64 *ok = pool_k + (size_t)prob * K;
+  int n2 = gather_sort_lists<R>(part_s + p0 * K, part_k + p0 * K, part_cnt + p0, (size_t)K, G,
+                                cut2, K, cap, ss, sk, os, ok, &s_tot);
+  if (n2 < 0)
+    n2 = stream_lists<R>(part_s + p0 * K, part_k + p0 * K, part_cnt + p0, (size_t)K, G, cut2,
+                         smem, K, S, os, ok);
+  if (threadIdx.x == 0) {
+    pool_cnt[prob] = n2;
+    *done = 0u;
+    *g2 = ord_inf<R>();
   }
-  cta_list_flush<R>(L, pool_s + (size_t)prob * K, pool_k + (size_t)prob * K, pool_cnt + prob);
-  if (threadIdx.x == 0) done[prob] = 0u;
 }
 
 // ------------------------------------------------------------------ re-fit --
-__device__ double block_sum(double v, double *red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < nw; ++i) s += red[i];
-  return s;
-}
+constexpr int REFIT_THREADS = 128;
 
-__device__ double block_max(double v, double *red) {
+// sum (or max) of nv values per thread over the CTA; every thread gets the
+// results.  red: [REFIT_THREADS / 32][L0_DMAX + 1]
+__device__ void block_reduce(double *v, int nv, bool take_max, double (*red)[L0_DMAX + 1]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = 0; i < nv; ++i) {
+    double x = v[i];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < nw; ++i) s = fmax(s, red[i]);
-  return s;
-}
-
-// scaled two-pass 2-norm of v[lo..n) (strided ownership by thread)
-__device__ double block_norm(const double *v, long long lo, long long n, double *red) {
-  double mx = 0.0;
-  for (long long i = lo + threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, fabs(v[i]));
-  mx = block_max(mx, red);
-  if (mx == 0.0) return 0.0;
-  double ss = 0.0;
-  for (long long i = lo + threadIdx.x; i < n; i += blockDim.x) {
-    double r = v[i] / mx;
-    ss += r * r;
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_xor_sync(0xffffffffu, x, o);
+      x = take_max ? fmax(x, y) : x + y;
+    }
+    if (lane == 0) red[w][i] = x;
   }
-  ss = block_sum(ss, red);
-  return mx * sqrt(ss);
+  __syncthreads();
+  for (int i = 0; i < nv; ++i) {
+    double x = red[0][i];
+    for (int q = 1; q < REFIT_THREADS / 32; ++q) x = take_max ? fmax(x, red[q][i]) : x + red[q][i];
+    v[i] = x;
+  }
+  __syncthreads();
 }
 
 // Householder least squares of one task's rows (paper Sec. 2.4: QR by
-// Householder reflections, least-squares fit, squared deviation).
-// A holds d centred columns and the centred target as column d, each of
-// length n, in global scratch.  Returns SSE; *rho = min |R_jj| / ||a_j||.
-__device__ double householder_sse(double *A, long long n, int d, double *red,
-                                  double *rho) {
-  double cn[L0_DMAX];
-  for (int j = 0; j < d; ++j) cn[j] = block_norm(A + (long long)j * n, 0, n, red);
+// Householder reflections, least-squares fit, squared deviation) by one CTA.
+// A holds the d centred columns and the centred target as column d, each of
+// length n; row i is owned by thread i mod REFIT_THREADS.  Norms are scaled
+// two-pass sums of squares.  Returns SSE; *rho = min_j |R_jj| / ||a_j||.
+__device__ double householder_cta(double *A, long long n, int d,
+                                  double (*red)[L0_DMAX + 1], double *rho) {
+  const int tid = threadIdx.x;
+  double v[L0_DMAX + 1], cn[L0_DMAX];
+  // norms of the original centred columns
+  for (int j = 0; j < d; ++j) v[j] = 0.0;
+  for (long long i = tid; i < n; i += REFIT_THREADS)
+    for (int j = 0; j < d; ++j) v[j] = fmax(v[j], fabs(A[(long long)j * n + i]));
+  block_reduce(v, d, true, red);
+  double mx[L0_DMAX];
+  for (int j = 0; j < d; ++j) { mx[j] = v[j]; v[j] = 0.0; }
+  for (long long i = tid; i < n; i += REFIT_THREADS)
+    for (int j = 0; j < d; ++j)
+      if (mx[j] > 0.0) { const double r = A[(long long)j * n + i] / mx[j]; v[j] += r * r; }
+  block_reduce(v, d, false, red);
+  for (int j = 0; j < d; ++j) cn[j] = mx[j] > 0.0 ? mx[j] * sqrt(v[j]) : 0.0;
   double r = DBL_MAX;
-  __shared__ double s_dots[L0_DMAX + 1];
   for (int j = 0; j < d; ++j) {
     double *aj = A + (long long)j * n;
-    const double sigma = block_norm(aj, j, n, red);
-    __syncthreads();
+    // sigma = ||aj[j..n)||, scaled two-pass
+    v[0] = 0.0;
+    for (long long i = j + tid; i < n; i += REFIT_THREADS) v[0] = fmax(v[0], fabs(aj[i]));
+    block_reduce(v, 1, true, red);
+    const double m1 = v[0];
+    double sigma = 0.0;
+    if (m1 > 0.0) {
+      v[0] = 0.0;
+      for (long long i = j + tid; i < n; i += REFIT_THREADS) { const double q = aj[i] / m1; v[0] += q * q; }
+      block_reduce(v, 1, false, red);
+      sigma = m1 * sqrt(v[0]);
+    }
     if (sigma == 0.0) {
       r = 0.0;
       continue;
@@ -130,37 +229,40 @@ __device__ double householder_sse(double *A, long long n, int d, double *red,
     const double alpha = (x0 >= 0.0) ? -sigma : sigma;
     const double v0 = x0 - alpha;
     const double beta = 1.0 / (sigma * (sigma + fabs(x0)));
-    // dots v^T a_c for c = j+1 .. d (the target is column d)
-    for (int c = j + 1; c <= d; ++c) {
-      const double *ac = A + (long long)c * n;
-      double s = 0.0;
-      for (long long i = j + 1 + threadIdx.x; i < n; i += blockDim.x) s += aj[i] * ac[i];
-      s = block_sum(s, red);
-      if (threadIdx.x == 0) s_dots[c] = (s + v0 * ac[j]) * beta;
+    const int nc = d - j;   // columns j+1 .. d (the target is column d)
+    for (int c = 0; c < nc; ++c) v[c] = 0.0;
+    for (long long i = j + 1 + tid; i < n; i += REFIT_THREADS) {
+      const double ai = aj[i];
+      for (int c = 0; c < nc; ++c) v[c] += ai * A[(long long)(j + 1 + c) * n + i];
+    }
+    block_reduce(v, nc, false, red);
+    for (int c = 0; c < nc; ++c) {
+      double *ac = A + (long long)(j + 1 + c) * n;
+      const double sdot = (v[c] + v0 * ac[j]) * beta;
+      for (long long i = j + 1 + tid; i < n; i += REFIT_THREADS) ac[i] -= sdot * aj[i];
+      v[c] = sdot;
     }
     __syncthreads();
-    for (int c = j + 1; c <= d; ++c) {
-      double *ac = A + (long long)c * n;
-      const double s = s_dots[c];
-      for (long long i = j + 1 + threadIdx.x; i < n; i += blockDim.x) ac[i] -= s * aj[i];
-      if (threadIdx.x == 0) ac[j] -= s * v0;
-    }
+    if (tid == (int)(j % REFIT_THREADS))
+      for (int c = 0; c < nc; ++c) A[(long long)(j + 1 + c) * n + j] -= v[c] * v0;
     __syncthreads();
-    const double q = (cn[j] > 0.0) ? fabs(alpha) / cn[j] : 0.0;
-    r = fmin(r, q);
+    r = fmin(r, (cn[j] > 0.0) ? fabs(alpha) / cn[j] : 0.0);
   }
   const double *b = A + (long long)d * n;
-  double ss = 0.0;
-  for (long long i = d + threadIdx.x; i < n; i += blockDim.x) ss += b[i] * b[i];
-  ss = block_sum(ss, red);
+  v[0] = 0.0;
+  for (long long i = d + tid; i < n; i += REFIT_THREADS) v[0] += b[i] * b[i];
+  block_reduce(v, 1, false, red);
   *rho = r;
-  return ss;
+  return v[0];
 }
 
-// grid (K, n_probs): one CTA per candidate
-__global__ void __launch_bounds__(L0_THREADS)
+// grid (K, n_probs), REFIT_THREADS threads: one CTA per candidate.  The
+// columns live in dynamic shared memory when they fit (a.smem_rows), else in
+// the global scratch.
+__global__ void __launch_bounds__(REFIT_THREADS)
 refit_kernel(RefitArgs a) {
-  __shared__ double red[32];
+  extern __shared__ __align__(16) double sA[];
+  __shared__ double red[REFIT_THREADS / 32][L0_DMAX + 1];
   __shared__ int s_t[L0_DMAX];
   const int prob = blockIdx.y, cidx = blockIdx.x;
   const ProbDesc pd = a.probs[prob];
@@ -173,24 +275,24 @@ refit_kernel(RefitArgs a) {
     for (int q = 0; q < d; ++q) s_t[q] = t[q];
   }
   __syncthreads();
-  double *A = a.scratch + ((size_t)prob * a.K + cidx) * (size_t)(d + 1) * a.nmax;
+  double *A = a.smem_rows ? sA
+                          : a.scratch + ((size_t)prob * a.K + cidx) * (size_t)(d + 1) * a.nmax;
   const int t_lo = a.shared ? 0 : pd.task;
   const int t_hi = a.shared ? a.T : pd.task + 1;
   double total = 0.0;
   bool elig = true;
-  for (int t = t_lo; t < t_hi; ++t) {
-    const long long lo = a.offsets[t], hi = a.offsets[t + 1], n = hi - lo;
-    const double *mu = a.mu + (size_t)t * (a.m + 1);
+  for (int tk = t_lo; tk < t_hi; ++tk) {
+    const long long lo = a.offsets[tk], hi = a.offsets[tk + 1], n = hi - lo;
+    const double *mu = a.mu + (size_t)tk * (a.m + 1);
     for (int q = 0; q <= d; ++q) {
       const double *src = (q < d) ? a.X + (long long)s_t[q] * a.n_total + lo : a.y + lo;
       const double mean = (q < d) ? mu[s_t[q] + 1] : mu[0];
       double *dst = A + (long long)q * n;
-      for (long long i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i] - mean;
+      for (long long i = threadIdx.x; i < n; i += REFIT_THREADS) dst[i] = src[i] - mean;
     }
     __syncthreads();
     double rho;
-    const double sse = householder_sse(A, n, d, red, &rho);
-    total += sse;
+    total += householder_cta(A, n, d, red, &rho);
     if (!(rho >= a.rho_min)) elig = false;
     __syncthreads();
   }
@@ -201,11 +303,24 @@ refit_kernel(RefitArgs a) {
   }
 }
 
+// ---------------------------------------------------------- block helpers --
+__device__ double block_max(double v, double *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nw; ++i) s = fmax(s, red[i]);
+  return s;
+}
+
 // --------------------------------------------------------------- select --
 // One CTA per problem: sort the pool by (refit score, key), emit the best k,
 // and evaluate the certificate.
 template <typename R>
-__global__ void __launch_bounds__(L0_THREADS)
+__global__ void __launch_bounds__(1024)
 select_kernel(SelectArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int prob = blockIdx.x;
@@ -239,12 +354,12 @@ select_kernel(SelectArgs<R> a) {
   __syncthreads();
   cta_bitonic_sort<double>(ss, sk, P);
   dmax = block_max(dmax, red);
+  int nv_local = 0;
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) nv_local += isfinite(ss[i]) ? 1 : 0;
   __shared__ int s_valid;
-  if (threadIdx.x == 0) {
-    int nv = 0;
-    for (int i = 0; i < cnt; ++i) nv += isfinite(ss[i]) ? 1 : 0;
-    s_valid = nv;
-  }
+  if (threadIdx.x == 0) s_valid = 0;
+  __syncthreads();
+  if (nv_local) atomicAdd(&s_valid, nv_local);
   __syncthreads();
   const int nvalid = s_valid;
   const int d = pd.d;
@@ -267,12 +382,20 @@ select_kernel(SelectArgs<R> a) {
     c.pool_cnt = cnt;
     c.pool_full = (cnt >= a.K) ? 1 : 0;
     c.n_valid = nvalid;
-    c.pool_worst = (cnt > 0) ? (double)a.pool_s[(size_t)prob * a.K + cnt - 1] * scale : 0.0;
-    c.kth_refit = (nvalid >= a.k) ? ss[a.k - 1] : __longlong_as_double(0x7ff0000000000000ll);
-    // Every tuple outside the pool has a Gram score >= pool_worst; its exact
-    // score is at least pool_worst - safety * delta.  The pool provably holds
-    // the exact top k when that bound clears the k-th re-fitted score.
-    if (!c.pool_full) c.certified = 1;
+    // Tuples outside the pool were either cut by the search threshold (their
+    // Gram score exceeded it, and it only ever decreased to its final value
+    // g) or lost to the pool's K'-th entry when the pool is full.  So every
+    // outside tuple has a Gram score >= bound = min(g, pool K'-th).
+    const double g = (double)from_ord<R>(a.gthr[prob]);
+    double bound = g;
+    if (c.pool_full) bound = fmin(bound, (double)a.pool_s[(size_t)prob * a.K + cnt - 1]);
+    const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    c.pool_worst = isinf(bound) ? inf : bound * scale;
+    c.kth_refit = (nvalid >= a.k) ? ss[a.k - 1] : inf;
+    // Its exact score is then at least bound - safety * delta; the pool holds
+    // the exact top k when that clears the k-th re-fitted score, or trivially
+    // when nothing was excluded at all.
+    if (isinf(bound)) c.certified = 1;
     else c.certified = (c.pool_worst - a.cert_safety * dmax >= c.kth_refit) ? 1 : 0;
     a.cert[prob] = c;
   }
@@ -290,21 +413,39 @@ __global__ void unrank_kernel(Binom B, int m, int d, u64 total, const u64 *ranks
 }  // namespace
 
 template <typename R>
+size_t merge_smem_bytes(int K, int S, int cap) {
+  size_t a = (size_t)cap * (sizeof(R) + 8);
+  size_t b = cta_list_bytes<R>(K, S);
+  return (a > b ? a : b) + 16;
+}
+
+template <typename R>
+int merge_cap() { return sizeof(R) == 4 ? 16384 : 8192; }
+
+template <typename R>
 cudaError_t launch_merge(const R *in_s, const u64 *in_k, const int *in_cnt,
-                         int n_slots, int n_probs, int K, int S, int groups,
-                         R *part_s, u64 *part_k, int *part_cnt, unsigned *done,
+                         int n_slots, int n_probs, int K, int S, int groups, const u64 *gthr,
+                         R *part_s, u64 *part_k, int *part_cnt, unsigned *counters,
                          R *pool_s, u64 *pool_k, int *pool_cnt, cudaStream_t st) {
-  size_t smem = cta_list_bytes<R>(K, S) + 16;
+  const int cap = merge_cap<R>();
+  const size_t smem = merge_smem_bytes<R>(K, S, cap);
   cudaError_t e = cudaFuncSetAttribute(merge_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  merge_kernel<R><<<dim3(groups, n_probs), L0_THREADS, smem, st>>>(
-      in_s, in_k, in_cnt, n_slots, K, S, part_s, part_k, part_cnt, done, pool_s,
+  merge_kernel<R><<<dim3(groups, n_probs), 1024, smem, st>>>(
+      in_s, in_k, in_cnt, n_slots, K, S, gthr, part_s, part_k, part_cnt, cap, counters, pool_s,
       pool_k, pool_cnt);
   return cudaGetLastError();
 }
 
-cudaError_t launch_refit(const RefitArgs &a, cudaStream_t st) {
-  refit_kernel<<<dim3(a.K, a.n_probs), L0_THREADS, 0, st>>>(a);
+cudaError_t launch_refit(const RefitArgs &a_in, cudaStream_t st) {
+  RefitArgs a = a_in;
+  const size_t bytes = (size_t)(a.dmax + 1) * (size_t)a.nmax * 8;
+  a.smem_rows = bytes <= 200 * 1024 ? 1 : 0;
+  const size_t smem = a.smem_rows ? bytes : 0;
+  cudaError_t e = cudaFuncSetAttribute(refit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(smem > 0 ? smem : 16));
+  if (e != cudaSuccess) return e;
+  refit_kernel<<<dim3(a.K, a.n_probs), REFIT_THREADS, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -315,7 +456,7 @@ cudaError_t launch_select(const SelectArgs<R> &a, cudaStream_t st) {
   size_t smem = (size_t)P * 16;
   cudaError_t e = cudaFuncSetAttribute(select_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  select_kernel<R><<<a.n_probs, L0_THREADS, smem, st>>>(a);
+  select_kernel<R><<<a.n_probs, 1024, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -327,8 +468,8 @@ cudaError_t launch_unrank(const Binom &B, int m, int d, u64 total, const u64 *ra
   return cudaGetLastError();
 }
 
-template cudaError_t launch_merge<double>(const double *, const u64 *, const int *, int, int, int, int, int, double *, u64 *, int *, unsigned *, double *, u64 *, int *, cudaStream_t);
-template cudaError_t launch_merge<float>(const float *, const u64 *, const int *, int, int, int, int, int, float *, u64 *, int *, unsigned *, float *, u64 *, int *, cudaStream_t);
+template cudaError_t launch_merge<double>(const double *, const u64 *, const int *, int, int, int, int, int, const u64 *, double *, u64 *, int *, unsigned *, double *, u64 *, int *, cudaStream_t);
+template cudaError_t launch_merge<float>(const float *, const u64 *, const int *, int, int, int, int, int, const u64 *, float *, u64 *, int *, unsigned *, float *, u64 *, int *, cudaStream_t);
 template cudaError_t launch_select<double>(const SelectArgs<double> &, cudaStream_t);
 template cudaError_t launch_select<float>(const SelectArgs<float> &, cudaStream_t);
 

@@ -32,7 +32,6 @@ namespace l0 {
 
 namespace {
 
-constexpr int NW = TILE_WARPS;
 constexpr int UJ = TILE_UJ;
 constexpr int UK = TILE_UK;
 constexpr int TJ = TILE_TJ;
@@ -84,7 +83,7 @@ template <typename R>
 struct ItemCtx {
   const R *G;
   long long ld;
-  int m, d, j0, k0;
+  int m, d, j0, k0, prob;
   bool diag;
   u64 total;
   Binom B;
@@ -101,10 +100,11 @@ __device__ __forceinline__ void defer_run(const TileArgs<R> &A, const ItemCtx<R>
   t[DP] = j;
   t[DP + 1] = kfirst;
   u64 key = lex_rank(c.B, c.m, c.d, t, c.total);
+  atomicAdd(A.dfr_n + 1, (u64)count);
   u64 slot = atomicAdd(A.dfr_n, 1ull);
   if ((long long)slot < A.dfr_cap) {
     A.dfr_key[slot] = key;
-    A.dfr_len[slot] = (unsigned)count;
+    A.dfr_len[slot] = ((unsigned)c.prob << 8) | (unsigned)count;
   } else {
     set_err(A.err, 7);   // deferral buffer overflow
   }
@@ -324,22 +324,44 @@ __device__ __forceinline__ void tuple_step(const TileArgs<R> &A, const ItemCtx<R
       }
     }
   }
-  if (acc >= R(0) || exact_rows) {
-    const bool fast_hit = acc >= R(0);
+  if (exact_rows) {
 #pragma unroll
     for (int u = 0; u < UJ; ++u) {
+      if (!((exact_rows >> u) & 1u)) continue;
       const int jl = w * UJ + u;
-      const bool go = ((exact_rows >> u) & 1u) || (fast_hit && rb.jflag[jl] == 1);
-      if (!go) continue;
 #pragma unroll
       for (int v = 0; v < UK; ++v)
         slow_tuple<R, DP>(A, c, rb, L, jl, v, creg[u][v], kv[v]);
     }
   }
+  if (acc >= R(0)) {
+    // a flagged tuple in this thread's block: recompute the cheap test and
+    // re-evaluate only the flagged tuples exactly
+#pragma unroll
+    for (int u = 0; u < UJ; ++u) {
+      const int jl = w * UJ + u;
+      if (rb.jflag[jl] != 1) continue;
+      R jg[DPM];
+#pragma unroll
+      for (int p = 0; p < DPM; ++p) jg[p] = rb.jg[p * TJ + jl];
+      const R invl = rb.jinvl[jl], z2 = rb.jz2[jl], e = rb.je[jl];
+#pragma unroll
+      for (int v = 0; v < UK; ++v) {
+        R h = creg[u][v];
+#pragma unroll
+        for (int p = 0; p < DP; ++p) h = fma(-jg[p], kv[v].kg[p], h);
+        const R g2 = h * invl;
+        const R pp = fma(-g2, g2, kv[v].kp);
+        const R wv = fma(-g2, z2, kv[v].kw);
+        const R t = fma(-e, pp, wv * wv);
+        if (t >= R(0)) slow_tuple<R, DP>(A, c, rb, L, jl, v, creg[u][v], kv[v]);
+      }
+    }
+  }
 }
 
 template <typename R, int DP>
-__device__ void run_item(const TileArgs<R> &A, const ProbDesc &pd, int bj, int bk,
+__device__ void run_item(const TileArgs<R> &A, const ProbDesc &pd, int prob, int bj, int bk,
                          u64 r0, u64 r1, CtaList<R> &L, unsigned char *recbase,
                          u64 *gthr) {
   constexpr int DPM = DP > 0 ? DP : 1;
@@ -348,6 +370,7 @@ __device__ void run_item(const TileArgs<R> &A, const ProbDesc &pd, int bj, int b
   ItemCtx<R> c;
   c.G = A.G + pd.g_off;
   c.ld = pd.ld;
+  c.prob = prob;
   c.m = pd.m;
   c.d = pd.d;
   c.j0 = bj * TJ;
@@ -461,7 +484,7 @@ tile_kernel(TileArgs<R> A) {
 #define L0_CASE(X)                                                           \
   case X:                                                                    \
     if (X >= DPLO && X <= DPHI)                                              \
-      run_item<R, (X >= DPLO && X <= DPHI ? X : DPLO)>(A, pd, bj, bk,        \
+      run_item<R, (X >= DPLO && X <= DPHI ? X : DPLO)>(A, pd, prob, bj, bk,  \
                                                              r0, r1, L,      \
                                                              recbase, gthr); \
     break;

@@ -17,34 +17,7 @@ from workloads import make_config, make_problem
 
 pytestmark = pytest.mark.gpu
 
-RMSE_RTOL = 1e-10
-TIE_GAP = 1e-9
-
-
-def _score_fn(X, y, offsets=None, task=0):
-    def f(tuples):
-        if len(tuples) == 0:
-            return []
-        sse, _ = oracle.score(X, y, np.array(tuples, dtype=np.int32), offsets=offsets)
-        return sse[:, task]
-    return f
-
-
-def _check_against_oracle(X, y, d, k, offsets=None, **opts):
-    ref = oracle.fit(X, y, d, k, offsets=offsets)
-    with l0.Handle(**opts) as h:
-        got_t, got_r = h.fit(X, y, d, k, offsets=offsets)
-        st = h.stats()
-    n_out = ref["tuples"].shape[0]
-    for o in range(n_out):
-        ok, msg = oracle.agreement(ref["tuples"][o], ref["score"][o], got_t[o], rel_gap=TIE_GAP,
-                                   score_fn=_score_fn(X, y, offsets, o))
-        assert ok, "list %d: %s" % (o, msg)
-        fin = np.isfinite(ref["rmse"][o])
-        np.testing.assert_array_equal(np.isfinite(got_r[o]), fin)
-        np.testing.assert_allclose(got_r[o][fin], ref["rmse"][o][fin], rtol=RMSE_RTOL, atol=0)
-        assert np.all(got_t[o][~fin] == -1)
-    return got_t, got_r, st
+from l0_testutil import RMSE_RTOL, TIE_GAP, check_against_oracle as _check_against_oracle
 
 
 # ------------------------------------------------------------- ranking ----
