@@ -182,7 +182,7 @@ void plan_items(FitPlan &P, const std::vector<u64> &binom_row, int grid_target) 
       long long items = 0;
       for (int bj = 0; bj < n_jt; ++bj) items += l0::tile_row_items(bj, P.m, dp, L, n_kt, np_of(bj));
       Lsel = L;
-      if (items * (long long)P.pd.size() >= 8LL * grid_target) break;
+      if (items * (long long)P.pd.size() >= 2LL * grid_target) break;
     }
   }
   (void)binom_row;
@@ -254,6 +254,7 @@ int run_search(sisso_l0_t h, FitPlan &P, int K, int S, const R *G, int *certifie
     a.probs = h->probs.as<l0::ProbDesc>();
     a.n_probs = n_probs;
     a.row_prefix = h->rowpre.as<long long>();
+    a.rowpre_len = (int)P.rowpre.size();
     a.B = B;
     a.ratio = P.mixed ? h->opt.fp32_fallback_pivot_ratio : h->opt.rank_deficient_pivot_ratio;
     a.K = K;

@@ -110,6 +110,29 @@ __device__ __forceinline__ void colex_unrank(const Binom &B, int p, u64 r,
   }
 }
 
+// C(x, p) by the multiplicative formula (exact while C(x, p) * x < 2^64)
+__host__ __device__ __forceinline__ u64 binom_arith(int x, int p) {
+  if (p < 0 || x < p) return 0ull;
+  u64 r = 1ull;
+  for (int i = 0; i < p; ++i) r = r * (u64)(x - i) / (u64)(i + 1);
+  return r;
+}
+
+// colex unrank with arithmetic binomials (no table loads)
+__device__ __forceinline__ void colex_unrank_arith(int p, u64 r, int xmax, int *a) {
+  int hi = xmax - 1;
+  for (int i = p; i >= 1; --i) {
+    int lo = i - 1, h = hi;
+    while (lo < h) {
+      const int mid = (lo + h + 1) >> 1;
+      if (binom_arith(mid, i) <= r) lo = mid; else h = mid - 1;
+    }
+    r -= binom_arith(lo, i);
+    a[i - 1] = lo;
+    hi = lo - 1;
+  }
+}
+
 // next p-combination in colex order
 template <int P>
 __device__ __forceinline__ void colex_next(int *a) {
@@ -230,15 +253,17 @@ __device__ __forceinline__ bool cta_list_admits(const CtaList<R> &L, R s,
 // through the error word instead of looping
 #define L0_MAX_REDO 4096
 
+// append to the staging area; false (and the overflow flag set) when full
 template <typename R>
-__device__ __forceinline__ void cta_list_push(CtaList<R> &L, R s, u64 k) {
+__device__ __forceinline__ bool cta_list_push(CtaList<R> &L, R s, u64 k) {
   int idx = atomicAdd(L.n_stage, 1);
   if (idx < L.S) {
     L.ss[idx] = s;
     L.sk[idx] = k;
-  } else {
-    *(volatile int *)L.ovf = 1;
+    return true;
   }
+  *(volatile int *)L.ovf = 1;
+  return false;
 }
 
 // Fold the staging area into the list.  Call with all threads, after a
@@ -295,6 +320,55 @@ __device__ bool cta_list_fold(CtaList<R> &L, u64 *gthr) {
   }
   __syncthreads();
   return ovf != 0;
+}
+
+// Commit every staged entry (all are real tuples that passed the threshold
+// when staged) into the list, whatever the overflow flag says; entries that
+// did not fit were not staged and their producers know it.  All threads,
+// after a barrier that follows the last push.
+template <typename R>
+__device__ void cta_list_commit(CtaList<R> &L, u64 *gthr) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int ns = *(volatile int *)L.n_stage;
+  if (ns == 0) return;
+  if (ns > L.S) ns = L.S;
+  int P = 1;
+  while (P < ns) P <<= 1;
+  for (int i = ns + tid; i < P; i += nt) {
+    L.ss[i] = r_inf<R>();
+    L.sk[i] = ~0ull;
+  }
+  __syncthreads();
+  cta_bitonic_sort<R>(L.ss, L.sk, P);
+  const int nl = *(volatile int *)L.n_list;
+  const int nout = min(L.K, nl + ns);
+  for (int i = tid; i < nl; i += nt) {
+    int pos = i + lower_count<R>(L.ss, L.sk, ns, L.ls[i], L.lk[i]);
+    if (pos < L.K) { L.ts[pos] = L.ls[i]; L.tk[pos] = L.lk[i]; }
+  }
+  for (int i = tid; i < ns; i += nt) {
+    int pos = i + lower_count<R>(L.ls, L.lk, nl, L.ss[i], L.sk[i]);
+    if (pos < L.K) { L.ts[pos] = L.ss[i]; L.tk[pos] = L.sk[i]; }
+  }
+  __syncthreads();
+  for (int i = tid; i < nout; i += nt) { L.ls[i] = L.ts[i]; L.lk[i] = L.tk[i]; }
+  if (tid == 0) {
+    R ts = r_inf<R>();
+    u64 tk = ~0ull;
+    if (nout >= L.K) { ts = L.ts[L.K - 1]; tk = L.tk[L.K - 1]; }
+    if (gthr) {
+      if (nout >= L.K) atomicMin(gthr, ord_of(ts));
+      R g = from_ord<R>(*(volatile u64 *)gthr);
+      if (g < ts) { ts = g; tk = ~0ull; }
+    }
+    R cs = *L.thr_s;
+    u64 ck = *L.thr_k;
+    if (cand_less(ts, tk, cs, ck)) { *L.thr_s = ts; *L.thr_k = tk; }
+    *L.n_list = nout;
+    *L.n_stage = 0;
+    *L.ovf = 0;
+  }
+  __syncthreads();
 }
 
 // tighten the CTA threshold from the global one (thread 0; barrier after)

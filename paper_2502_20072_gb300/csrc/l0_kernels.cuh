@@ -33,6 +33,7 @@ struct TileArgs {
   const ProbDesc *probs;
   int n_probs;
   const long long *row_prefix;     // per problem: n_jt + 1 cumulative item counts
+  int rowpre_len;                  // total entries of row_prefix
   Binom B;
   double ratio;                    // pivot ratio: ineligible (FP64) / redo in FP64 (FP32)
   int K, S;                        // list capacity, staging capacity
