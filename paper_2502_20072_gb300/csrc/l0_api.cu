@@ -230,7 +230,7 @@ int run_search(sisso_l0_t h, FitPlan &P, int K, int S, const R *G, int *certifie
   {
     // threshold: +inf, then the K'-th best d-tuple of the M best columns
     int M = 0;
-    if (d >= 2) {
+    if (d >= 2 && !P.shared) {
       const int Mcap = std::min(std::min(P.m, 64), K);
       M = Mcap;
       for (int q = d; q <= Mcap; ++q)
@@ -244,7 +244,8 @@ int run_search(sisso_l0_t h, FitPlan &P, int K, int S, const R *G, int *certifie
   if (d == 1) {
     L0_CK(l0::launch_singles<R>(G, P.pd.data(), h->probs.as<l0::ProbDesc>(), n_probs, K, S,
                                 n_slots, h->gthr.as<u64>(), h->lists_s.as<R>(),
-                                h->lists_k.as<u64>(), h->lists_cnt.as<int>(), n_slots, st),
+                                h->lists_k.as<u64>(), h->lists_cnt.as<int>(), n_slots, st,
+                                P.shared ? P.T : 0, P.gstride, h->inv_s.as<double>(), P.m + 1, P.N),
           "singles kernel");
   } else {
     L0_CK(h->ctr.ensure(8), "alloc counter");
@@ -270,9 +271,17 @@ int run_search(sisso_l0_t h, FitPlan &P, int K, int S, const R *G, int *certifie
     a.dfr_n = h->dfr_n.as<u64>();
     a.dfr_cap = P.mixed ? kDeferCap : 0;
     a.err = h->err.as<int>();
+    a.shared_T = P.shared ? P.T : 0;
+    a.shared_gstride = P.gstride;
+    a.inv_s = h->inv_s.as<double>();
+    a.mp1 = P.m + 1;
+    a.n_total = P.N;
     if (P.mixed) L0_CK(cudaMemsetAsync(h->dfr_n.p, 0, 24, st), "memset");
     const size_t smem = l0::tile_smem_bytes<R>(K, S, d - 2);
-    L0_CK(l0::launch_tile<R>(a, d - 2, d - 2, P.grid, smem, st), "tile kernel");
+    if (P.shared)
+      L0_CK(l0::launch_tile_shared<R>(a, d - 2, P.grid, smem, st), "shared tile kernel");
+    else
+      L0_CK(l0::launch_tile<R>(a, d - 2, d - 2, P.grid, smem, st), "tile kernel");
     if (P.mixed) {
       // FP64 redo of the near-singular tuples the FP32 kernel queued: the
       // FP64 Gram and the Gram-mode redo run only when many were queued, the
@@ -307,6 +316,9 @@ int run_search(sisso_l0_t h, FitPlan &P, int K, int S, const R *G, int *certifie
       da.n_slots = n_slots;
       da.slot0 = P.grid;
       da.n_tuples = h->dfr_n.as<u64>() + 2;
+      da.shared_T = P.shared ? P.T : 0;
+      da.inv_s = h->inv_s.as<double>();
+      da.mp1 = P.m + 1;
       L0_CK(l0::launch_defer(da, kDeferGroups, n_probs, st), "defer kernel");
     }
   }
@@ -436,7 +448,6 @@ int fit_impl(sisso_l0_t h, const double *X, const double *y, const int64_t *task
   P.mixed = (h->opt.precision == SISSO_L0_MIXED_BF16X3) ? 1 : 0;
   if (h->opt.precision != SISSO_L0_FP64 && h->opt.precision != SISSO_L0_MIXED_BF16X3)
     return fail(h, SISSO_L0_EUNSUPPORTED, "precision not supported");
-  if (P.shared) return fail(h, SISSO_L0_EUNSUPPORTED, "SHARED task mode not built yet");
   P.off.assign(task_offsets, task_offsets + n_tasks + 1);
   P.nmax = 0;
   for (int t = 0; t < n_tasks; ++t) {
@@ -534,8 +545,9 @@ int fit_impl(sisso_l0_t h, const double *X, const double *y, const int64_t *task
   }
   L0_CK(cudaEventRecord(h->ev[6], st), "event");
   // problems
+  // problems: one per task (PER_TASK), or one spanning all tasks (SHARED)
   P.pd.clear();
-  for (int t = 0; t < n_tasks; ++t) {
+  for (int t = 0; t < (P.shared ? 1 : n_tasks); ++t) {
     l0::ProbDesc d{};
     d.g_off = (long long)t * gstride;
     d.ld = P.ld;
@@ -554,10 +566,12 @@ int fit_impl(sisso_l0_t h, const double *X, const double *y, const int64_t *task
     int bps = 0;
     if (P.mixed) {
       const size_t smem = l0::tile_smem_bytes<float>(Kmax, S0, dp);
-      L0_CK(l0::tile_occupancy<float>(dp, dp, smem, &bps), "occupancy");
+      if (P.shared) L0_CK(l0::shared_occupancy<float>(dp, smem, &bps), "occupancy");
+      else L0_CK(l0::tile_occupancy<float>(dp, dp, smem, &bps), "occupancy");
     } else {
       const size_t smem = l0::tile_smem_bytes<double>(Kmax, S0, dp);
-      L0_CK(l0::tile_occupancy<double>(dp, dp, smem, &bps), "occupancy");
+      if (P.shared) L0_CK(l0::shared_occupancy<double>(dp, smem, &bps), "occupancy");
+      else L0_CK(l0::tile_occupancy<double>(dp, dp, smem, &bps), "occupancy");
     }
     if (bps < 1) return fail(h, SISSO_L0_EUNSUPPORTED, "tuple kernel does not fit on an SM");
     P.grid = h->n_sm * bps;
@@ -568,11 +582,12 @@ int fit_impl(sisso_l0_t h, const double *X, const double *y, const int64_t *task
   L0_CK(h->rowpre.ensure(std::max<size_t>(1, P.rowpre.size()) * 8), "alloc rowpre");
   if (!P.rowpre.empty())
     L0_CK(cudaMemcpyAsync(h->rowpre.p, P.rowpre.data(), P.rowpre.size() * 8, cudaMemcpyHostToDevice, st), "copy rowpre");
-  // rmse divisor per problem: n_t (PER_TASK) or N (SHARED)
+  // rmse divisor per problem: n_t (PER_TASK); SHARED scores are already the
+  // pooled mean SSE
   {
     std::vector<double> div(P.pd.size());
     for (size_t q = 0; q < P.pd.size(); ++q)
-      div[q] = P.shared ? (double)N : (double)(P.off[P.pd[q].task + 1] - P.off[P.pd[q].task]);
+      div[q] = P.shared ? 1.0 : (double)(P.off[P.pd[q].task + 1] - P.off[P.pd[q].task]);
     L0_CK(h->rdiv.ensure(div.size() * 8), "alloc");
     L0_CK(cudaMemcpyAsync(h->rdiv.p, div.data(), div.size() * 8, cudaMemcpyHostToDevice, st), "copy");
   }

@@ -90,7 +90,8 @@ defer_gram_kernel(DeferArgs a) {
   unsigned char *p = smem;
   CtaList<float> L = cta_list_carve<float>(p, a.K, a.S);
   const int d = pd.d;
-  GramEnt ent{a.G64 + (long long)pd.task * a.g64_stride, a.ld64};
+  const int t_lo = a.shared_T > 0 ? 0 : pd.task;
+  const int t_hi = a.shared_T > 0 ? a.shared_T : pd.task + 1;
   cta_list_reset<float>(L, a.gthr + prob);
   __syncthreads();
   const long long nr = (long long)a.n_runs[0];
@@ -109,20 +110,32 @@ defer_gram_kernel(DeferArgs a) {
       key0 = a.run_key[r];
     }
     int t[L0_DMAX];
-    PrefixFactor f;
-    f.ok = false;
     if (mine && len > 0) {
       lex_unrank(a.B, pd.m, d, key0, pd.total, t);
-      factor_prefix(ent, t, d - 1, a.ratio, f);
       done_tuples += (unsigned long long)len;
     }
     int redo = 0;
     do {
-      if (f.ok) {
+      if (mine && len > 0) {
         for (int e = 0; e < len; ++e) {
-          double rel;
-          if (!score_last(ent, t, d - 1, t[d - 1] + e, a.ratio, f, &rel)) continue;
-          const float s = (float)rel;
+          // SHARED: pooled over the tasks (ineligible if any task is)
+          double score = 0.0;
+          bool ok = true;
+          for (int tk = t_lo; tk < t_hi && ok; ++tk) {
+            GramEnt ent{a.G64 + (long long)tk * a.g64_stride, a.ld64};
+            PrefixFactor f;
+            factor_prefix(ent, t, d - 1, a.ratio, f);
+            double rel;
+            ok = f.ok && score_last(ent, t, d - 1, t[d - 1] + e, a.ratio, f, &rel);
+            if (ok && a.shared_T > 0) {
+              const double is = a.inv_s[(long long)tk * a.mp1];
+              score += (is > 0.0 ? 1.0 / (is * is * (double)a.n_total) : 0.0) * rel;
+            } else if (ok) {
+              score = rel;
+            }
+          }
+          if (!ok) continue;
+          const float s = (float)score;
           const u64 key = key0 + (u64)e;
           if (cta_list_admits<float>(L, s, key)) cta_list_push<float>(L, s, key);
         }
@@ -179,8 +192,8 @@ defer_dot_kernel(DeferArgs a) {
   unsigned char *p = smem;
   CtaList<float> L = cta_list_carve<float>(p, a.K, a.S);
   const int d = pd.d, dp = d - 1;
-  const long long lo = a.offsets[pd.task];
-  const long long n = a.offsets[pd.task + 1] - lo;
+  const int t_lo = a.shared_T > 0 ? 0 : pd.task;
+  const int t_hi = a.shared_T > 0 ? a.shared_T : pd.task + 1;
   cta_list_reset<float>(L, a.gthr + prob);
   __syncthreads();
   const long long nrun = nr < a.cap ? nr : a.cap;
@@ -202,39 +215,54 @@ defer_dot_kernel(DeferArgs a) {
     const int nbase = dp + 1;
     const int kfirst = s_t[d - 1];
     const int ncol = nbase + len;
-    // dots: base rows x all columns, plus each k with itself
     const int npairs = nbase * ncol + len;
-    for (int q = warp; q < npairs; q += nw) {
-      int ra, cb;
-      if (q < nbase * ncol) {
-        const int rr = q / ncol, cc = q % ncol;
-        ra = s_idx[rr];
-        cb = (cc < nbase) ? s_idx[cc] : kfirst + (cc - nbase) + 1;
-      } else {
-        ra = kfirst + (q - nbase * ncol) + 1;
-        cb = ra;
-      }
-      const double *x = a.W64 + (long long)ra * a.n_total + lo;
-      const double *z = a.W64 + (long long)cb * a.n_total + lo;
-      double sacc = 0.0;
-      for (long long i = lane; i < n; i += 32) sacc = fma(x[i], z[i], sacc);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-      if (lane == 0) {
-        if (q < nbase * ncol) Gs[(q / ncol) * DOT_MAXC + (q % ncol)] = sacc;
-        else Gkk[q - nbase * ncol] = sacc;
-      }
-    }
-    __syncthreads();
-    SmemEnt ent{Gs, Gkk, nullptr, nbase, kfirst, s_idx};
-    bool scored = false;
-    double rel = 0.0;
     const int e = threadIdx.x;
-    if (e < len) {
-      PrefixFactor f;
-      factor_prefix(ent, s_t, dp, a.ratio, f);
-      if (f.ok) scored = score_last(ent, s_t, dp, kfirst + e, a.ratio, f, &rel);
+    bool scored = e < len;
+    double score = 0.0;
+    for (int tk = t_lo; tk < t_hi; ++tk) {
+      const long long lo = a.offsets[tk];
+      const long long n = a.offsets[tk + 1] - lo;
+      // dots: base rows x all columns, plus each k with itself
+      for (int q = warp; q < npairs; q += nw) {
+        int ra, cb;
+        if (q < nbase * ncol) {
+          const int rr = q / ncol, cc = q % ncol;
+          ra = s_idx[rr];
+          cb = (cc < nbase) ? s_idx[cc] : kfirst + (cc - nbase) + 1;
+        } else {
+          ra = kfirst + (q - nbase * ncol) + 1;
+          cb = ra;
+        }
+        const double *x = a.W64 + (long long)ra * a.n_total + lo;
+        const double *z = a.W64 + (long long)cb * a.n_total + lo;
+        double sacc = 0.0;
+        for (long long i = lane; i < n; i += 32) sacc = fma(x[i], z[i], sacc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+        if (lane == 0) {
+          if (q < nbase * ncol) Gs[(q / ncol) * DOT_MAXC + (q % ncol)] = sacc;
+          else Gkk[q - nbase * ncol] = sacc;
+        }
+      }
+      __syncthreads();
+      SmemEnt ent{Gs, Gkk, nullptr, nbase, kfirst, s_idx};
+      if (scored) {
+        PrefixFactor f;
+        factor_prefix(ent, s_t, dp, a.ratio, f);
+        double rel = 0.0;
+        scored = f.ok && score_last(ent, s_t, dp, kfirst + e, a.ratio, f, &rel);
+        if (scored) {
+          if (a.shared_T > 0) {
+            const double is = a.inv_s[(long long)tk * a.mp1];
+            score += (is > 0.0 ? 1.0 / (is * is * (double)a.n_total) : 0.0) * rel;
+          } else {
+            score = rel;
+          }
+        }
+      }
+      __syncthreads();
     }
+    const double rel = score;
     done_tuples += (threadIdx.x == 0) ? (unsigned long long)len : 0ull;
     int redo = 0;
     do {

@@ -45,6 +45,13 @@ struct TileArgs {
   // tuple, (problem << 8) | run length (<= 128); dfr_n[0] runs, dfr_n[1] tuples
   u64 *dfr_key; unsigned *dfr_len; u64 *dfr_n; long long dfr_cap;
   int *err;
+  // SHARED mode (shared_T > 0): Grams of tasks 0..T-1 at G + t * shared_gstride;
+  // task weights S_yy,t / N from inv_s[t * mp1] and n_total
+  int shared_T;
+  long long shared_gstride;
+  const double *inv_s;
+  int mp1;
+  long long n_total;
 };
 
 // work items of one j-tile row: (#k tiles reaching past j0) x (#prefix chunks)
@@ -88,11 +95,20 @@ size_t tile_smem_bytes(int K, int S, int dp_hi);
 template <typename R>
 cudaError_t tile_occupancy(int dp_lo, int dp_hi, size_t smem, int *blocks_per_sm);
 
+// SHARED mode tuple kernel (one problem spanning all tasks)
+template <typename R>
+cudaError_t launch_tile_shared(const TileArgs<R> &a, int dp, int grid, size_t smem,
+                               cudaStream_t st);
+template <typename R>
+cudaError_t shared_occupancy(int dp, size_t smem, int *blocks_per_sm);
+
 template <typename R>
 cudaError_t launch_singles(const R *G, const ProbDesc *probs_host_view,
                            const ProbDesc *probs_dev, int n_probs, int K, int S,
                            int grid_x, u64 *gthr, R *out_s, u64 *out_k,
-                           int *out_cnt, int n_slots, cudaStream_t st);
+                           int *out_cnt, int n_slots, cudaStream_t st,
+                           int shared_T, long long gstride, const double *inv_s,
+                           int mp1, long long n_total);
 
 // merge all slot lists of every problem into one top-K' pool per problem.
 // part_*: [n_probs][groups][K] partial lists; counters: [n_probs][4]
@@ -138,7 +154,7 @@ struct SelectArgs {
   const double *refit;
   const double *inv_s;         // [T][m+1]: 1 / ||centred column||, index 0 the target
   int mp1, shared;             // PER_TASK: a pool score times S_yy,t is an SSE
-  const double *rmse_div;      // [n_probs] n_t (PER_TASK) or N (SHARED)
+  const double *rmse_div;      // [n_probs] n_t (PER_TASK) or 1 (SHARED: pooled mean)
   Binom B;
   int *out_tuples; double *out_rmse;   // [n_probs][k][d], [n_probs][k]
   CertOut *cert;
@@ -177,6 +193,10 @@ struct DeferArgs {
   float *out_s; u64 *out_k; int *out_cnt;
   int n_slots, slot0;          // lists go to slots slot0 + blockIdx.x
   u64 *n_tuples;               // tuples redone (statistics)
+  // SHARED mode (shared_T > 0): pooled score sum_t S_yy,t rel_t / N
+  int shared_T;
+  const double *inv_s;
+  int mp1;
 };
 // both launched; exactly one does work (see defer_wants_gram)
 cudaError_t launch_defer(const DeferArgs &a, int groups, int n_probs, cudaStream_t st);
