@@ -66,9 +66,11 @@ typedef struct {
   int32_t max_candidate_pool;        /* ceiling for K' when the certificate doubles it (0 = 2048) */
   double fp32_fallback_pivot_ratio;  /* FP32 pivot ratio below which a tuple is redone in FP64 (1e-6) */
   double rank_deficient_pivot_ratio; /* FP64 Gram pivot ratio below which a tuple is ineligible (1e-12) */
-  int32_t autotune;                  /* 0 off, 1 on */
-  int32_t reserved0;
-  const char *autotune_cache_path;   /* NULL = no persisted cache */
+  int32_t autotune;                  /* 1: time preset launch configurations on the first
+                                        search of a shape and keep the fastest (0 off) */
+  int32_t use_graph;                 /* 1: capture the device work of a search pass in a
+                                        CUDA graph on the first call of a shape, replay after */
+  const char *autotune_cache_path;   /* file that persists autotuner choices (NULL: none) */
   double timeout_seconds;            /* host-side deadline for stream completion (<= 0: none) */
 } sisso_l0_options;
 
@@ -82,6 +84,10 @@ typedef struct {
   int64_t n_eligible_min;            /* smallest count of filled output slots over lists */
   double max_pool_rel_error;         /* max |SSE_gram - SSE_refit| over the pools, SSE units */
   int64_t kernel_launches;           /* library kernels launched by the last fit */
+  int32_t graph_replayed;            /* 1 when the last search pass replayed a CUDA graph */
+  int32_t tuned_items_factor;        /* autotuner choice: work items per CTA (x2) */
+  int32_t tuned_ctas_per_sm;         /* autotuner choice: resident CTAs per SM */
+  int32_t reserved1;
   double ms_prep, ms_gram, ms_tuple, ms_merge, ms_refit, ms_total;
 } sisso_l0_stats;
 
@@ -114,6 +120,29 @@ int sisso_l0_fit(sisso_l0_t h, const double *X, const double *y,
                  const int64_t *task_offsets, int32_t n_tasks, int64_t n_sis,
                  int32_t n_dim, int32_t k, int32_t *out_tuples,
                  double *out_rmse);
+
+/* One output request of sisso_l0_fit_multi. */
+typedef struct {
+  int32_t n_dim;           /* tuple size, 1 .. SISSO_L0_MAX_DIM */
+  int32_t k;               /* tuples per output list, 1 .. min(2048, C(n_sis, n_dim)) */
+  int32_t *out_tuples;     /* [n_out][k][n_dim], device or host */
+  double *out_rmse;        /* [n_out][k], device or host */
+} sisso_l0_request;
+
+/*
+ * Several searches over the same data in one pass.  SISSO grows the
+ * descriptor dimension over the same selected features (paper Sec. 2,
+ * Fig. 1b); here every request (tuple size n_dim, list length k) of every
+ * task is one problem, all problems share the centring and the Gram, and
+ * their tuple spaces run in one persistent launch (tuple sizes in one call
+ * must lie within a span of three, e.g. {2, 3, 4}; n_dim = 1 requests may be
+ * mixed in).  Arguments X, y, task_offsets, n_tasks, n_sis as for
+ * sisso_l0_fit; each request's outputs as out_tuples / out_rmse there.
+ * Errors: as sisso_l0_fit; EUNSUPPORTED for tuple sizes spread wider.
+ */
+int sisso_l0_fit_multi(sisso_l0_t h, const double *X, const double *y,
+                       const int64_t *task_offsets, int32_t n_tasks, int64_t n_sis,
+                       const sisso_l0_request *reqs, int32_t n_reqs);
 
 /* Statistics of the last fit on this handle. */
 int sisso_l0_get_stats(sisso_l0_t h, sisso_l0_stats *out);

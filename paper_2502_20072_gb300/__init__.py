@@ -48,9 +48,14 @@ class Options(ctypes.Structure):
                 ("max_candidate_pool", ctypes.c_int32),
                 ("fp32_fallback_pivot_ratio", ctypes.c_double),
                 ("rank_deficient_pivot_ratio", ctypes.c_double),
-                ("autotune", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("autotune", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("autotune_cache_path", ctypes.c_char_p),
                 ("timeout_seconds", ctypes.c_double)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("n_dim", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("out_tuples", ctypes.c_void_p), ("out_rmse", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -58,7 +63,9 @@ class Stats(ctypes.Structure):
                 ("pool_enlargements", ctypes.c_int32), ("certified", ctypes.c_int32),
                 ("tuple_fits", ctypes.c_uint64), ("fp64_fallback_tuples", ctypes.c_uint64),
                 ("n_eligible_min", ctypes.c_int64), ("max_pool_rel_error", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("graph_replayed", ctypes.c_int32),
+                ("tuned_items_factor", ctypes.c_int32), ("tuned_ctas_per_sm", ctypes.c_int32),
+                ("reserved1", ctypes.c_int32),
                 ("ms_prep", ctypes.c_double), ("ms_gram", ctypes.c_double),
                 ("ms_tuple", ctypes.c_double), ("ms_merge", ctypes.c_double),
                 ("ms_refit", ctypes.c_double), ("ms_total", ctypes.c_double)]
@@ -71,7 +78,7 @@ _lib = None
 _lock = threading.Lock()
 
 # entry points declared in include/sisso_l0.h (checked by the tests)
-EXPORTS = ("sisso_l0_default_options", "sisso_l0_create", "sisso_l0_fit",
+EXPORTS = ("sisso_l0_default_options", "sisso_l0_create", "sisso_l0_fit", "sisso_l0_fit_multi",
            "sisso_l0_get_stats", "sisso_l0_last_error", "sisso_l0_destroy",
            "sisso_l0_count_tuples", "sisso_l0_debug_unrank", "sisso_l0_debug_gram")
 
@@ -95,6 +102,8 @@ def lib():
         L.sisso_l0_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Options)]
         L.sisso_l0_fit.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_int64), i32, i64, i32,
                                    i32, vp, vp]
+        L.sisso_l0_fit_multi.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_int64), i32, i64,
+                                         ctypes.POINTER(Request), i32]
         L.sisso_l0_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
         L.sisso_l0_last_error.argtypes = [vp]
         L.sisso_l0_last_error.restype = ctypes.c_char_p
@@ -136,7 +145,7 @@ class Handle:
     def __init__(self, precision=FP64, task_mode=PER_TASK, device=0, stream=None,
                  candidate_pool=0, max_candidate_pool=2048, timeout_seconds=300.0,
                  fp32_fallback_pivot_ratio=1e-6, rank_deficient_pivot_ratio=1e-12,
-                 autotune=0):
+                 autotune=0, use_graph=0, autotune_cache_path=None):
         L = lib()
         o = Options()
         L.sisso_l0_default_options(ctypes.byref(o))
@@ -150,6 +159,10 @@ class Handle:
         o.fp32_fallback_pivot_ratio = float(fp32_fallback_pivot_ratio)
         o.rank_deficient_pivot_ratio = float(rank_deficient_pivot_ratio)
         o.autotune = int(autotune)
+        o.use_graph = int(use_graph)
+        self._cache_path = (autotune_cache_path.encode() if isinstance(autotune_cache_path, str)
+                            else autotune_cache_path)
+        o.autotune_cache_path = self._cache_path
         self._opt = o
         h = ctypes.c_void_p()
         rc = L.sisso_l0_create(ctypes.byref(h), ctypes.byref(o))
@@ -202,6 +215,32 @@ class Handle:
                                 ctypes.c_void_p(_ptr(out_rmse)))
         self._check(rc)
         return (out_tuples, out_rmse) if ret_np else (out_tuples, out_rmse)
+
+    def fit_multi(self, X, y, requests, offsets=None):
+        """Several searches in one pass.  requests: list of (n_dim, k).
+        Returns a list of (tuples [n_out, k, n_dim], rmse [n_out, k])."""
+        X = _as_f64(X)
+        y = _as_f64(y)
+        n_sis, n_total = int(X.shape[0]), int(X.shape[1])
+        if offsets is None:
+            offsets = [0, n_total]
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        n_tasks = len(off) - 1
+        n_out = 1 if self.task_mode == SHARED else n_tasks
+        outs = []
+        reqs = (Request * len(requests))()
+        for i, (d, k) in enumerate(requests):
+            t = np.empty((n_out, k, d), dtype=np.int32)
+            r = np.empty((n_out, k), dtype=np.float64)
+            outs.append((t, r))
+            reqs[i].n_dim, reqs[i].k = int(d), int(k)
+            reqs[i].out_tuples = t.ctypes.data
+            reqs[i].out_rmse = r.ctypes.data
+        rc = lib().sisso_l0_fit_multi(self._h, ctypes.c_void_p(_ptr(X)), ctypes.c_void_p(_ptr(y)),
+                                      off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n_tasks,
+                                      n_sis, reqs, len(requests))
+        self._check(rc)
+        return outs
 
     def stats(self) -> dict:
         s = Stats()

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <thread>
@@ -59,7 +60,10 @@ struct Status {
 
 struct sisso_l0_handle {
   sisso_l0_options opt;
-  cudaStream_t st = nullptr;
+  cudaStream_t st = nullptr;        // stream the library's work is ordered on
+  cudaStream_t user_st = nullptr;   // the caller's stream (options.stream)
+  bool own_st = false;              // st created by the handle (graph capture
+                                    // cannot use the legacy stream)
   int n_sm = 0;
   std::string last_error;
   sisso_l0_stats stats;
@@ -71,7 +75,12 @@ struct sisso_l0_handle {
   DevBuf dfr_key, dfr_len, dfr_n, dfr_cnt;
   DevBuf abf, bbf, kmeta, gram32;
   int binom_m = -1;
+  int done_init_for = 0;
   cudaEvent_t ev[8] = {nullptr};
+  cudaEvent_t ev_user = nullptr;    // orders the handle's stream after the caller's
+  cudaGraphExec_t graph_exec = nullptr;
+  std::string graph_key;
+  std::map<std::string, std::pair<int, int>> tune;   // autotuner choices
 };
 
 namespace {
@@ -147,153 +156,304 @@ int ensure_binom(sisso_l0_t h, int m) {
   return SISSO_L0_OK;
 }
 
+struct Req {
+  int d, k;
+  int32_t *out_t;
+  double *out_r;
+};
+
 struct FitPlan {
-  int T, m, d, k, n_out, shared, mixed;
+  int T = 0, m = 0, n_out = 0, shared = 0, mixed = 0;
+  int dmax = 0, dp_lo = -1, dp_hi = -1;    // tuple sizes; dp range of the d >= 2 requests
+  bool has_singles = false, has_tuples = false;
   const double *Xd = nullptr, *yd = nullptr;   // device copies of the inputs
-  long long N, nmax;
-  long long ld;
+  long long N = 0, nmax = 0, ld = 0, gstride = 0, ldk = 0;
   std::vector<long long> off;
+  std::vector<Req> req;
   std::vector<l0::ProbDesc> pd;
   std::vector<long long> rowpre;
-  int grid = 0;
-  int n_slots = 0;
-  long long gstride = 0;
-  bool have_g64 = false;       // FP64 Gram computed (always in FP64 mode)
+  int grid = 0;             // tuple-kernel CTAs
+  int max_bps = 1;          // largest resident CTAs per SM the kernel allows
+  int items_factor = 2;     // work items per tuple-kernel CTA (at least)
+  long long n_items = 0;
+  long long out_t_total = 0, out_r_total = 0;
+  bool have_g64 = false;    // FP64 Gram computed (always in FP64 mode)
   unsigned long long fallback_tuples = 0;
+  u64 fits_per_pass = 0;    // (task, tuple) fits of one search pass
 };
 
 constexpr int kDeferGroups = 64;
 constexpr long long kDeferCap = 1LL << 24;
 
-// choose prefix steps per work item and fill problem descriptors
-void plan_items(FitPlan &P, const std::vector<u64> &binom_row, int grid_target) {
+int staging_for(int K) {
+  int S = 1024;
+  while (S < 2 * K) S <<= 1;
+  return S;
+}
+
+// problem descriptors: one per (request, task) -- or per request in SHARED
+// mode -- and their work items (prefix steps per item chosen so that there
+// are at least items_factor items per CTA)
+void plan_problems(FitPlan &P) {
   const int TJ = l0::TILE_TJ, TK = l0::TILE_TK;
   const int n_jt = (P.m + TJ - 1) / TJ;
   const int n_kt = (P.m + TK - 1) / TK;
-  const int dp = P.d - 2;
-  auto np_of = [&](int bj) -> u64 {
+  P.pd.clear();
+  long long ot = 0, orr = 0;
+  for (const Req &r : P.req) {
+    for (int t = 0; t < (P.shared ? 1 : P.T); ++t) {
+      l0::ProbDesc d{};
+      d.g_off = (long long)t * P.gstride;
+      d.ld = P.ld;
+      d.m = P.m;
+      d.d = r.d;
+      d.dp = r.d - 2;
+      d.task = t;
+      d.total = binom_host(P.m, r.d);
+      d.k = r.k;
+      d.out_t_off = ot;
+      d.out_r_off = orr;
+      ot += (long long)r.k * r.d;
+      orr += r.k;
+      P.pd.push_back(d);
+    }
+  }
+  P.out_t_total = ot;
+  P.out_r_total = orr;
+  auto np_of = [&](int bj, int dp) -> u64 {
     int jend = std::min((bj + 1) * TJ, P.m);
     return binom_host(jend - 1, dp);
   };
+  // one prefix-chunk length for all problems
   int Lsel = 1;
-  if (dp > 0) {
+  if (P.dp_hi > 0) {
     const int cands[] = {256, 128, 64, 32, 16, 8, 4, 2, 1};
     for (int L : cands) {
       long long items = 0;
-      for (int bj = 0; bj < n_jt; ++bj) items += l0::tile_row_items(bj, P.m, dp, L, n_kt, np_of(bj));
+      for (const l0::ProbDesc &d : P.pd) {
+        if (d.d < 2) continue;
+        for (int bj = 0; bj < n_jt; ++bj)
+          items += l0::tile_row_items(bj, P.m, d.dp, L, n_kt, np_of(bj, d.dp));
+      }
       Lsel = L;
-      if (items * (long long)P.pd.size() >= 2LL * grid_target) break;
+      if (items >= (long long)P.items_factor * std::max(1, P.grid)) break;
     }
   }
-  (void)binom_row;
   long long item = 0;
   P.rowpre.clear();
-  for (size_t q = 0; q < P.pd.size(); ++q) {
-    l0::ProbDesc &d = P.pd[q];
+  for (l0::ProbDesc &d : P.pd) {
     d.n_jt = n_jt;
     d.n_kt = n_kt;
     d.L = Lsel;
     d.prefix_off = (int)P.rowpre.size();
     d.item_begin = item;
     long long acc = 0;
-    for (int bj = 0; bj < n_jt; ++bj) {
+    if (d.d >= 2) {
+      for (int bj = 0; bj < n_jt; ++bj) {
+        P.rowpre.push_back(acc);
+        acc += l0::tile_row_items(bj, P.m, d.dp, Lsel, n_kt, np_of(bj, d.dp));
+      }
       P.rowpre.push_back(acc);
-      acc += l0::tile_row_items(bj, P.m, dp, Lsel, n_kt, np_of(bj));
+    } else {
+      for (int bj = 0; bj <= n_jt; ++bj) P.rowpre.push_back(0);
     }
-    P.rowpre.push_back(acc);
     item += acc;
     d.item_end = item;
   }
+  P.n_items = item;
 }
 
 template <typename R>
-int run_search(sisso_l0_t h, FitPlan &P, int K, int S, const R *G, int *certified,
-               double *delta_max, float *ms_tuple, float *ms_merge, float *ms_refit) {
+int tile_bps(sisso_l0_t h, const FitPlan &P, int Kmax, int *bps) {
+  const int S0 = staging_for(Kmax);
+  const size_t smem = l0::tile_smem_bytes<R>(Kmax, S0, std::max(P.dp_hi, 0));
+  if (P.shared) L0_CK(l0::shared_occupancy<R>(std::max(P.dp_hi, 0), smem, bps), "occupancy");
+  else L0_CK(l0::tile_occupancy<R>(std::max(P.dp_lo, 0), std::max(P.dp_hi, 0), smem, bps), "occupancy");
+  return SISSO_L0_OK;
+}
+
+// upload the problem table, row prefixes, divisors; size the search buffers
+template <typename R>
+int setup_search(sisso_l0_t h, FitPlan &P, int K) {
   cudaStream_t st = h->st;
   const int n_probs = (int)P.pd.size();
-  const int d = P.d;
-  l0::Binom B{h->binom.as<u64>(), P.m + 1};
-  // slots
-  int n_slots;
-  if (d == 1) {
-    n_slots = std::max(1, std::min(64, (P.m + L0_THREADS - 1) / L0_THREADS));
-  } else {
-    n_slots = P.grid + (P.mixed ? kDeferGroups : 0);
+  L0_CK(h->probs.ensure(P.pd.size() * sizeof(l0::ProbDesc)), "alloc probs");
+  L0_CK(cudaMemcpyAsync(h->probs.p, P.pd.data(), P.pd.size() * sizeof(l0::ProbDesc),
+                        cudaMemcpyHostToDevice, st), "copy probs");
+  L0_CK(h->rowpre.ensure(std::max<size_t>(1, P.rowpre.size()) * 8), "alloc rowpre");
+  if (!P.rowpre.empty())
+    L0_CK(cudaMemcpyAsync(h->rowpre.p, P.rowpre.data(), P.rowpre.size() * 8,
+                          cudaMemcpyHostToDevice, st), "copy rowpre");
+  // rmse divisor per problem: n_t (PER_TASK); SHARED scores are already the
+  // pooled mean SSE
+  std::vector<double> div(P.pd.size());
+  for (size_t q = 0; q < P.pd.size(); ++q)
+    div[q] = P.shared ? 1.0 : (double)(P.off[P.pd[q].task + 1] - P.off[P.pd[q].task]);
+  L0_CK(h->rdiv.ensure(div.size() * 8), "alloc");
+  L0_CK(cudaMemcpyAsync(h->rdiv.p, div.data(), div.size() * 8, cudaMemcpyHostToDevice, st), "copy");
+  L0_CK(h->out_t.ensure((size_t)P.out_t_total * 4), "alloc out");
+  L0_CK(h->out_r.ensure((size_t)P.out_r_total * 8), "alloc out");
+  L0_CK(h->dfr_n.ensure(24), "alloc");   // queued runs, queued tuples, redone tuples
+  if (P.mixed && P.has_tuples) {
+    L0_CK(h->dfr_key.ensure((size_t)kDeferCap * 8), "alloc deferral buffer");
+    L0_CK(h->dfr_len.ensure((size_t)kDeferCap * 4), "alloc deferral buffer");
+    if (P.m <= 8192) L0_CK(h->gram.ensure((size_t)P.T * P.gstride * 8), "alloc Gram");
   }
+  const int S = staging_for(K);
+  const int n_slots = std::max(P.has_singles ? 64 : 0, P.grid) + (P.mixed ? kDeferGroups : 0);
   const size_t nl = (size_t)n_probs * n_slots * K;
   L0_CK(h->lists_s.ensure(nl * sizeof(R)), "alloc lists");
   L0_CK(h->lists_k.ensure(nl * 8), "alloc lists");
   L0_CK(h->lists_cnt.ensure((size_t)n_probs * n_slots * 4), "alloc lists");
-  L0_CK(cudaMemsetAsync(h->lists_cnt.p, 0, (size_t)n_probs * n_slots * 4, st), "memset");
   L0_CK(h->gthr.ensure((size_t)n_probs * 8), "alloc gthr");
+  L0_CK(h->ctr.ensure(8), "alloc counter");
+  const int groups = std::max(1, std::min(n_slots, 32));
+  L0_CK(h->part_s.ensure((size_t)n_probs * groups * K * sizeof(R)), "alloc merge");
+  L0_CK(h->part_k.ensure((size_t)n_probs * groups * K * 8), "alloc merge");
+  L0_CK(h->part_cnt.ensure((size_t)n_probs * groups * 4), "alloc merge");
+  if (h->done.n < (size_t)n_probs * 16 || h->done_init_for != (int)sizeof(R)) {
+    // per problem: done counter, pad, ordered +inf bound; the merge leaves
+    // them in this state
+    L0_CK(h->done.ensure((size_t)n_probs * 16), "alloc merge");
+    std::vector<unsigned> c0(4 * (size_t)(h->done.n / 16), 0u);
+    for (size_t q = 0; q < h->done.n / 16; ++q) {
+      const u64 inf = l0::ord_inf<R>();
+      memcpy(&c0[4 * q + 2], &inf, 8);
+    }
+    L0_CK(cudaMemcpy(h->done.p, c0.data(), c0.size() * 4, cudaMemcpyHostToDevice), "copy");
+    h->done_init_for = (int)sizeof(R);
+  }
+  L0_CK(h->pool_s.ensure((size_t)n_probs * K * sizeof(R)), "alloc pool");
+  L0_CK(h->pool_k.ensure((size_t)n_probs * K * 8), "alloc pool");
+  L0_CK(h->pool_cnt.ensure((size_t)n_probs * 4), "alloc pool");
+  if ((size_t)(P.dmax + 1) * (size_t)P.nmax * 8 > 200 * 1024)
+    L0_CK(h->scratch.ensure((size_t)n_probs * K * (P.dmax + 1) * (size_t)P.nmax * 8),
+          "alloc refit scratch");
+  L0_CK(h->refit.ensure((size_t)n_probs * K * 8), "alloc refit");
+  L0_CK(h->cert.ensure((size_t)n_probs * sizeof(l0::CertOut)), "alloc cert");
+  return SISSO_L0_OK;
+}
+
+// centring (+ split rows) and the Gram: device work only
+int prep_pass(sisso_l0_t h, FitPlan &P) {
+  cudaStream_t st = h->st;
+  const int m = P.m, n_tasks = P.T;
+  const long long N = P.N;
+  L0_CK(cudaMemsetAsync(h->err.p, 0, 16, st), "memset");
+  L0_CK(cudaEventRecord(h->ev[0], st), "event");
+  if (!P.mixed) {
+    L0_CK(l0::launch_centre(P.Xd, P.yd, N, m, h->offs.as<long long>(), n_tasks, h->mu.as<double>(),
+                            h->inv_s.as<double>(), h->w64.as<double>(), h->err.as<int>(), st),
+          "centre kernel");
+    L0_CK(cudaEventRecord(h->ev[1], st), "event");
+    L0_CK(l0::launch_gram64(h->w64.as<double>(), N, m, P.off.data(), n_tasks,
+                            h->gram.as<double>(), P.ld, P.gstride, st),
+          "gram kernel");
+  } else {
+    const size_t abytes = (size_t)(m + 1) * P.ldk * 2;
+    L0_CK(cudaMemsetAsync(h->abf.p, 0, abytes, st), "memset");
+    L0_CK(cudaMemsetAsync(h->bbf.p, 0, abytes, st), "memset");
+    const int *kbeg = h->kmeta.as<int>();
+    L0_CK(l0::launch_centre_split(P.Xd, P.yd, N, m, h->offs.as<long long>(), n_tasks,
+                                  h->mu.as<double>(), h->inv_s.as<double>(), h->w64.as<double>(),
+                                  h->abf.p, h->bbf.p, P.ldk, kbeg, kbeg + n_tasks,
+                                  h->err.as<int>(), st),
+          "centre kernel");
+    L0_CK(cudaEventRecord(h->ev[1], st), "event");
+    L0_CK(l0::launch_gram_tc(h->abf.p, h->bbf.p, P.ldk, m, n_tasks, kbeg, kbeg + 2 * n_tasks,
+                             h->gram32.as<float>(), P.ld, P.gstride, h->err.as<int>(), st),
+          "tensor-core gram kernel");
+  }
+  L0_CK(cudaEventRecord(h->ev[6], st), "event");
+  return SISSO_L0_OK;
+}
+
+template <typename R>
+l0::TileArgs<R> tile_args(sisso_l0_t h, const FitPlan &P, int K, int S, const R *G, int n_slots,
+                          long long item_limit) {
+  l0::TileArgs<R> a{};
+  a.G = G;
+  a.probs = h->probs.as<l0::ProbDesc>();
+  a.n_probs = (int)P.pd.size();
+  a.row_prefix = h->rowpre.as<long long>();
+  a.rowpre_len = (int)P.rowpre.size();
+  a.B = l0::Binom{h->binom.as<u64>(), P.m + 1};
+  a.ratio = P.mixed ? h->opt.fp32_fallback_pivot_ratio : h->opt.rank_deficient_pivot_ratio;
+  a.K = K;
+  a.S = S;
+  a.item_counter = h->ctr.as<u64>();
+  a.item_limit = item_limit;
+  a.gthr = h->gthr.as<u64>();
+  a.out_s = h->lists_s.as<R>();
+  a.out_k = h->lists_k.as<u64>();
+  a.out_cnt = h->lists_cnt.as<int>();
+  a.n_slots = n_slots;
+  a.dfr_key = h->dfr_key.as<u64>();
+  a.dfr_len = h->dfr_len.as<unsigned>();
+  a.dfr_n = h->dfr_n.as<u64>();
+  a.dfr_cap = P.mixed ? kDeferCap : 0;
+  a.err = h->err.as<int>();
+  a.shared_T = P.shared ? P.T : 0;
+  a.shared_gstride = P.gstride;
+  a.inv_s = h->inv_s.as<double>();
+  a.mp1 = P.m + 1;
+  a.n_total = P.N;
+  return a;
+}
+
+template <typename R>
+int launch_tuple_kernel(sisso_l0_t h, const FitPlan &P, const l0::TileArgs<R> &a) {
+  const size_t smem = l0::tile_smem_bytes<R>(a.K, a.S, std::max(P.dp_hi, 0));
+  if (P.shared)
+    L0_CK(l0::launch_tile_shared<R>(a, std::max(P.dp_hi, 0), P.grid, smem, h->st), "shared tile kernel");
+  else
+    L0_CK(l0::launch_tile<R>(a, std::max(P.dp_lo, 0), std::max(P.dp_hi, 0), P.grid, smem, h->st),
+          "tile kernel");
+  return SISSO_L0_OK;
+}
+
+// One search pass (device work only, so that it can be captured in a graph):
+// seed, tuple kernel(s), FP64 redo, merge, re-fit, select.
+template <typename R>
+int search_pass(sisso_l0_t h, FitPlan &P, int K, const R *G) {
+  cudaStream_t st = h->st;
+  const int n_probs = (int)P.pd.size();
+  const int S = staging_for(K);
+  l0::Binom B{h->binom.as<u64>(), P.m + 1};
+  const int n_slots = std::max(P.has_singles ? 64 : 0, P.grid) + (P.mixed ? kDeferGroups : 0);
+  L0_CK(cudaMemsetAsync(h->lists_cnt.p, 0, (size_t)n_probs * n_slots * 4, st), "memset");
   L0_CK(cudaEventRecord(h->ev[2], st), "event");
   {
-    // threshold: +inf, then the K'-th best d-tuple of the M best columns
-    int M = 0;
-    if (d >= 2 && !P.shared) {
-      const int Mcap = std::min(std::min(P.m, 64), K);
-      M = Mcap;
-      for (int q = d; q <= Mcap; ++q)
-        if (binom_host(q, d) >= 2ull * (u64)K) { M = q; break; }
-    }
     const double ratio = P.mixed ? h->opt.fp32_fallback_pivot_ratio : h->opt.rank_deficient_pivot_ratio;
-    L0_CK(l0::launch_seed<R>(G, h->probs.as<l0::ProbDesc>(), n_probs, K, S, M, ratio, B,
-                             h->gthr.as<u64>(), st),
+    L0_CK(l0::launch_seed<R>(G, h->probs.as<l0::ProbDesc>(), n_probs, K, S, P.shared ? 0 : 1,
+                             ratio, B, h->gthr.as<u64>(), st),
           "seed kernel");
   }
-  if (d == 1) {
-    L0_CK(l0::launch_singles<R>(G, P.pd.data(), h->probs.as<l0::ProbDesc>(), n_probs, K, S,
-                                n_slots, h->gthr.as<u64>(), h->lists_s.as<R>(),
-                                h->lists_k.as<u64>(), h->lists_cnt.as<int>(), n_slots, st,
-                                P.shared ? P.T : 0, P.gstride, h->inv_s.as<double>(), P.m + 1, P.N),
+  if (P.has_singles) {
+    const int gx = std::max(1, std::min(64, (P.m + L0_THREADS - 1) / L0_THREADS));
+    L0_CK(l0::launch_singles<R>(G, P.pd.data(), h->probs.as<l0::ProbDesc>(), n_probs, K, S, gx,
+                                h->gthr.as<u64>(), h->lists_s.as<R>(), h->lists_k.as<u64>(),
+                                h->lists_cnt.as<int>(), n_slots, st, P.shared ? P.T : 0,
+                                P.gstride, h->inv_s.as<double>(), P.m + 1, P.N),
           "singles kernel");
-  } else {
-    L0_CK(h->ctr.ensure(8), "alloc counter");
+  }
+  if (P.has_tuples) {
     L0_CK(cudaMemsetAsync(h->ctr.p, 0, 8, st), "memset");
-    l0::TileArgs<R> a;
-    a.G = G;
-    a.probs = h->probs.as<l0::ProbDesc>();
-    a.n_probs = n_probs;
-    a.row_prefix = h->rowpre.as<long long>();
-    a.rowpre_len = (int)P.rowpre.size();
-    a.B = B;
-    a.ratio = P.mixed ? h->opt.fp32_fallback_pivot_ratio : h->opt.rank_deficient_pivot_ratio;
-    a.K = K;
-    a.S = S;
-    a.item_counter = h->ctr.as<u64>();
-    a.gthr = h->gthr.as<u64>();
-    a.out_s = h->lists_s.as<R>();
-    a.out_k = h->lists_k.as<u64>();
-    a.out_cnt = h->lists_cnt.as<int>();
-    a.n_slots = n_slots;
-    a.dfr_key = h->dfr_key.as<u64>();
-    a.dfr_len = h->dfr_len.as<unsigned>();
-    a.dfr_n = h->dfr_n.as<u64>();
-    a.dfr_cap = P.mixed ? kDeferCap : 0;
-    a.err = h->err.as<int>();
-    a.shared_T = P.shared ? P.T : 0;
-    a.shared_gstride = P.gstride;
-    a.inv_s = h->inv_s.as<double>();
-    a.mp1 = P.m + 1;
-    a.n_total = P.N;
     if (P.mixed) L0_CK(cudaMemsetAsync(h->dfr_n.p, 0, 24, st), "memset");
-    const size_t smem = l0::tile_smem_bytes<R>(K, S, d - 2);
-    if (P.shared)
-      L0_CK(l0::launch_tile_shared<R>(a, d - 2, P.grid, smem, st), "shared tile kernel");
-    else
-      L0_CK(l0::launch_tile<R>(a, d - 2, d - 2, P.grid, smem, st), "tile kernel");
+    l0::TileArgs<R> a = tile_args<R>(h, P, K, S, G, n_slots, P.n_items);
+    int rc = launch_tuple_kernel<R>(h, P, a);
+    if (rc) return rc;
     if (P.mixed) {
       // FP64 redo of the near-singular tuples the FP32 kernel queued: the
       // FP64 Gram and the Gram-mode redo run only when many were queued, the
       // dot-product redo only when a few were (decided on the device)
       const bool can_gram = P.m <= 8192;
-      if (can_gram) {
-        L0_CK(h->gram.ensure((size_t)P.T * P.gstride * 8), "alloc Gram");
+      if (can_gram)
         L0_CK(l0::launch_gram64(h->w64.as<double>(), P.N, P.m, P.off.data(), P.T,
-                                h->gram.as<double>(), P.ld, P.gstride, st, h->dfr_n.as<u64>(), d),
+                                h->gram.as<double>(), P.ld, P.gstride, st, h->dfr_n.as<u64>(),
+                                P.dmax),
               "gram kernel");
-      }
-      l0::DeferArgs da;
+      l0::DeferArgs da{};
       da.G64 = can_gram ? h->gram.as<double>() : nullptr;
       da.ld64 = P.ld;
       da.g64_stride = P.gstride;
@@ -314,7 +474,7 @@ int run_search(sisso_l0_t h, FitPlan &P, int K, int S, const R *G, int *certifie
       da.out_k = h->lists_k.as<u64>();
       da.out_cnt = h->lists_cnt.as<int>();
       da.n_slots = n_slots;
-      da.slot0 = P.grid;
+      da.slot0 = n_slots - kDeferGroups;
       da.n_tuples = h->dfr_n.as<u64>() + 2;
       da.shared_T = P.shared ? P.T : 0;
       da.inv_s = h->inv_s.as<double>();
@@ -323,36 +483,14 @@ int run_search(sisso_l0_t h, FitPlan &P, int K, int S, const R *G, int *certifie
     }
   }
   L0_CK(cudaEventRecord(h->ev[3], st), "event");
-  // merge
   const int groups = std::max(1, std::min(n_slots, 32));
-  L0_CK(h->part_s.ensure((size_t)n_probs * groups * K * sizeof(R)), "alloc merge");
-  L0_CK(h->part_k.ensure((size_t)n_probs * groups * K * 8), "alloc merge");
-  L0_CK(h->part_cnt.ensure((size_t)n_probs * groups * 4), "alloc merge");
-  L0_CK(h->done.ensure((size_t)n_probs * 16), "alloc merge");
-  {
-    // per problem: done counter, pad, ordered +inf bound
-    std::vector<unsigned> c0(4 * (size_t)n_probs, 0u);
-    for (int q = 0; q < n_probs; ++q) {
-      const u64 inf = l0::ord_inf<R>();
-      memcpy(&c0[4 * q + 2], &inf, 8);
-    }
-    L0_CK(cudaMemcpyAsync(h->done.p, c0.data(), c0.size() * 4, cudaMemcpyHostToDevice, st), "copy");
-  }
-  L0_CK(h->pool_s.ensure((size_t)n_probs * K * sizeof(R)), "alloc pool");
-  L0_CK(h->pool_k.ensure((size_t)n_probs * K * 8), "alloc pool");
-  L0_CK(h->pool_cnt.ensure((size_t)n_probs * 4), "alloc pool");
   L0_CK(l0::launch_merge<R>(h->lists_s.as<R>(), h->lists_k.as<u64>(), h->lists_cnt.as<int>(),
                             n_slots, n_probs, K, S, groups, h->gthr.as<u64>(), h->part_s.as<R>(),
                             h->part_k.as<u64>(), h->part_cnt.as<int>(), h->done.as<unsigned>(),
                             h->pool_s.as<R>(), h->pool_k.as<u64>(), h->pool_cnt.as<int>(), st),
         "merge kernel");
   L0_CK(cudaEventRecord(h->ev[4], st), "event");
-  // re-fit
-  const int n_rows_max = (int)P.nmax;
-  if ((size_t)(d + 1) * (size_t)n_rows_max * 8 > 200 * 1024)
-    L0_CK(h->scratch.ensure((size_t)n_probs * K * (d + 1) * (size_t)n_rows_max * 8), "alloc refit scratch");
-  L0_CK(h->refit.ensure((size_t)n_probs * K * 8), "alloc refit");
-  l0::RefitArgs ra;
+  l0::RefitArgs ra{};
   ra.X = P.Xd;
   ra.y = P.yd;
   ra.n_total = P.N;
@@ -369,18 +507,15 @@ int run_search(sisso_l0_t h, FitPlan &P, int K, int S, const R *G, int *certifie
   ra.B = B;
   ra.rho_min = std::sqrt(h->opt.rank_deficient_pivot_ratio);
   ra.scratch = h->scratch.as<double>();
-  ra.nmax = n_rows_max;
-  ra.dmax = d;
+  ra.nmax = P.nmax;
+  ra.dmax = P.dmax;
   ra.smem_rows = 0;
   ra.refit = h->refit.as<double>();
   L0_CK(l0::launch_refit(ra, st), "refit kernel");
-  // select
-  L0_CK(h->cert.ensure((size_t)n_probs * sizeof(l0::CertOut)), "alloc cert");
-  l0::SelectArgs<R> sa;
+  l0::SelectArgs<R> sa{};
   sa.probs = h->probs.as<l0::ProbDesc>();
   sa.n_probs = n_probs;
   sa.K = K;
-  sa.k = P.k;
   sa.pool_s = h->pool_s.as<R>();
   sa.pool_k = h->pool_k.as<u64>();
   sa.pool_cnt = h->pool_cnt.as<int>();
@@ -397,20 +532,29 @@ int run_search(sisso_l0_t h, FitPlan &P, int K, int S, const R *G, int *certifie
   sa.gthr = h->gthr.as<u64>();
   L0_CK(l0::launch_select<R>(sa, st), "select kernel");
   L0_CK(cudaEventRecord(h->ev[5], st), "event");
+  return SISSO_L0_OK;
+}
+
+// after a pass: error word, certificate, statistics (host sync)
+int finish_pass(sisso_l0_t h, FitPlan &P, int *certified, double *delta_max, float *ms_tuple,
+                float *ms_merge, float *ms_refit) {
+  cudaStream_t st = h->st;
+  const int n_probs = (int)P.pd.size();
   std::vector<l0::CertOut> cert(n_probs);
-  L0_CK(cudaMemcpyAsync(cert.data(), h->cert.p, n_probs * sizeof(l0::CertOut), cudaMemcpyDeviceToHost, st), "copy cert");
+  L0_CK(cudaMemcpyAsync(cert.data(), h->cert.p, n_probs * sizeof(l0::CertOut),
+                        cudaMemcpyDeviceToHost, st), "copy cert");
   u64 dfr_stats[3] = {0, 0, 0};
-  if (P.mixed && d >= 2)
+  if (P.mixed && P.has_tuples)
     L0_CK(cudaMemcpyAsync(dfr_stats, h->dfr_n.p, 24, cudaMemcpyDeviceToHost, st), "copy");
+  int host_err = 0;
+  L0_CK(cudaMemcpyAsync(&host_err, h->err.p, 4, cudaMemcpyDeviceToHost, st), "copy err");
   int rc = wait_stream(h);
   if (rc) return rc;
-  int hostErr = 0;
-  L0_CK(cudaMemcpy(&hostErr, h->err.p, 4, cudaMemcpyDeviceToHost), "copy err");
-  if (hostErr == 5) return fail(h, SISSO_L0_ENONFINITE, "NaN or Inf in X or y");
-  if (hostErr == 7)
+  if (host_err == 5) return fail(h, SISSO_L0_ENONFINITE, "NaN or Inf in X or y");
+  if (host_err == 7)
     return fail(h, SISSO_L0_EUNSUPPORTED,
                 "too many near-singular tuples for the FP32 search; use SISSO_L0_FP64");
-  if (hostErr != 0) return fail(h, SISSO_L0_ECUDA, "device error flag " + std::to_string(hostErr));
+  if (host_err != 0) return fail(h, SISSO_L0_ECUDA, "device error flag " + std::to_string(host_err));
   P.fallback_tuples += dfr_stats[2];
   *certified = 1;
   *delta_max = 0;
@@ -428,50 +572,227 @@ int run_search(sisso_l0_t h, FitPlan &P, int K, int S, const R *G, int *certifie
   return SISSO_L0_OK;
 }
 
-int fit_impl(sisso_l0_t h, const double *X, const double *y, const int64_t *task_offsets,
-             int32_t n_tasks, int64_t n_sis, int32_t n_dim, int32_t k, int32_t *out_tuples,
-             double *out_rmse) {
-  if (!X || !y || !task_offsets || !out_tuples || !out_rmse)
-    return fail(h, SISSO_L0_EINVAL, "null pointer argument");
+// ---------------------------------------------------------------- tuning --
+// Like the paper's launch tuning (Sec. 2.4: the first batch is timed under a
+// preset list of launch configurations and the best is kept), the first
+// search of a shape times the tuple kernel on the first quarter of its work
+// items under each (work items per CTA, resident CTAs per SM) pair and keeps
+// the fastest; choices persist in autotune_cache_path.
+std::string tune_key(sisso_l0_t h, const FitPlan &P) {
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, h->opt.device);
+  int mb = 1;
+  while (mb < P.m) mb <<= 1;
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s|prec=%d|shared=%d|dp=%d-%d|m<=%d|T=%d", prop.name, P.mixed,
+           P.shared, P.dp_lo, P.dp_hi, mb, P.T);
+  std::string s(buf);
+  for (char &c : s)
+    if (c == ' ') c = '_';
+  return s;
+}
+
+void load_tune_cache(sisso_l0_t h) {
+  if (!h->opt.autotune_cache_path) return;
+  FILE *f = fopen(h->opt.autotune_cache_path, "r");
+  if (!f) return;
+  char key[512];
+  int fa = 0, ba = 0;
+  while (fscanf(f, "%511s %d %d", key, &fa, &ba) == 3) h->tune[key] = {fa, ba};
+  fclose(f);
+}
+
+void store_tune(sisso_l0_t h, const std::string &key, int f, int b) {
+  h->tune[key] = {f, b};
+  if (!h->opt.autotune_cache_path) return;
+  FILE *fp = fopen(h->opt.autotune_cache_path, "a");
+  if (!fp) return;
+  fprintf(fp, "%s %d %d\n", key.c_str(), f, b);
+  fclose(fp);
+}
+
+template <typename R>
+int autotune(sisso_l0_t h, FitPlan &P, int K, const R *G) {
+  const std::string key = tune_key(h, P);
+  auto it = h->tune.find(key);
+  if (it != h->tune.end()) {
+    P.items_factor = it->second.first;
+    P.grid = h->n_sm * std::min(it->second.second, P.max_bps);
+    return SISSO_L0_OK;
+  }
+  cudaStream_t st = h->st;
+  const int S = staging_for(K);
+  const int n_probs = (int)P.pd.size();
+  l0::Binom B{h->binom.as<u64>(), P.m + 1};
+  float best = 1e30f;
+  int best_f = P.items_factor, best_b = 1;
+  const int factors[] = {1, 2, 4, 8};
+  for (int b = 1; b <= std::min(P.max_bps, 2); ++b) {
+    for (int f : factors) {
+      P.grid = h->n_sm * b;
+      P.items_factor = f;
+      plan_problems(P);
+      int rc = setup_search<R>(h, P, K);
+      if (rc) return rc;
+      const int n_slots = std::max(P.has_singles ? 64 : 0, P.grid) + (P.mixed ? kDeferGroups : 0);
+      L0_CK(cudaMemsetAsync(h->lists_cnt.p, 0, (size_t)n_probs * n_slots * 4, st), "memset");
+      L0_CK(l0::launch_seed<R>(G, h->probs.as<l0::ProbDesc>(), n_probs, K, S, P.shared ? 0 : 1,
+                               P.mixed ? h->opt.fp32_fallback_pivot_ratio
+                                       : h->opt.rank_deficient_pivot_ratio,
+                               B, h->gthr.as<u64>(), st),
+            "seed kernel");
+      L0_CK(cudaMemsetAsync(h->ctr.p, 0, 8, st), "memset");
+      if (P.mixed) L0_CK(cudaMemsetAsync(h->dfr_n.p, 0, 24, st), "memset");
+      l0::TileArgs<R> a = tile_args<R>(h, P, K, S, G, n_slots, std::max(1LL, P.n_items / 4));
+      L0_CK(cudaEventRecord(h->ev[2], st), "event");
+      rc = launch_tuple_kernel<R>(h, P, a);
+      if (rc) return rc;
+      L0_CK(cudaEventRecord(h->ev[3], st), "event");
+      rc = wait_stream(h);
+      if (rc) return rc;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]);
+      // the slice is a quarter of the items, whatever their size
+      if (ms < best) { best = ms; best_f = f; best_b = b; }
+    }
+  }
+  P.items_factor = best_f;
+  P.grid = h->n_sm * best_b;
+  store_tune(h, key, best_f, best_b);
+  return SISSO_L0_OK;
+}
+
+// ----------------------------------------------------------------- graphs --
+// With use_graph, the device work of prep + one search pass is captured once
+// per (shape, input pointers, buffer addresses) and replayed afterwards.
+std::string graph_key(sisso_l0_t h, const FitPlan &P, int K) {
+  std::string k;
+  char buf[128];
+  snprintf(buf, sizeof(buf), "%p|%p|m=%d|N=%lld|T=%d|K=%d|g=%d|f=%d|p=%d|s=%d|", (const void *)P.Xd,
+           (const void *)P.yd, P.m, P.N, P.T, K, P.grid, P.items_factor, P.mixed, P.shared);
+  k += buf;
+  for (long long o : P.off) k += std::to_string(o) + ",";
+  for (const Req &r : P.req) k += "r" + std::to_string(r.d) + "x" + std::to_string(r.k);
+  const DevBuf *bufs[] = {&h->xin, &h->yin, &h->offs, &h->mu, &h->inv_s, &h->w64, &h->gram,
+                          &h->binom, &h->probs, &h->rowpre, &h->ctr, &h->gthr, &h->lists_s,
+                          &h->lists_k, &h->lists_cnt, &h->part_s, &h->part_k, &h->part_cnt,
+                          &h->done, &h->pool_s, &h->pool_k, &h->pool_cnt, &h->scratch, &h->refit,
+                          &h->rdiv, &h->cert, &h->out_t, &h->out_r, &h->err, &h->dfr_key,
+                          &h->dfr_len, &h->dfr_n, &h->abf, &h->bbf, &h->kmeta, &h->gram32};
+  for (const DevBuf *b : bufs) {
+    snprintf(buf, sizeof(buf), "|%p", b->p);
+    k += buf;
+  }
+  return k;
+}
+
+template <typename R>
+int run_pass(sisso_l0_t h, FitPlan &P, int K, const R *G, bool with_prep, bool *replayed) {
+  *replayed = false;
+  if (!h->opt.use_graph) {
+    int rc = with_prep ? prep_pass(h, P) : SISSO_L0_OK;
+    if (rc) return rc;
+    return search_pass<R>(h, P, K, G);
+  }
+  const std::string key = graph_key(h, P, K) + (with_prep ? "|prep" : "");
+  if (h->graph_exec && h->graph_key == key) {
+    L0_CK(cudaGraphLaunch(h->graph_exec, h->st), "graph launch");
+    *replayed = true;
+    return SISSO_L0_OK;
+  }
+  if (h->graph_exec) {
+    cudaGraphExecDestroy(h->graph_exec);
+    h->graph_exec = nullptr;
+  }
+  L0_CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal), "begin capture");
+  int rc = with_prep ? prep_pass(h, P) : SISSO_L0_OK;
+  if (!rc) rc = search_pass<R>(h, P, K, G);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->st, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
+  e = cudaGraphInstantiate(&h->graph_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
+  h->graph_key = key;
+  L0_CK(cudaGraphLaunch(h->graph_exec, h->st), "graph launch");
+  return SISSO_L0_OK;
+}
+
+int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *task_offsets,
+                 int32_t n_tasks, int64_t n_sis, const sisso_l0_request *reqs, int32_t n_reqs) {
+  if (!X || !y || !task_offsets || !reqs) return fail(h, SISSO_L0_EINVAL, "null pointer argument");
   if (n_tasks < 1) return fail(h, SISSO_L0_EINVAL, "n_tasks must be >= 1");
-  if (n_dim < 1 || n_dim > SISSO_L0_MAX_DIM) return fail(h, SISSO_L0_EINVAL, "n_dim must be in [1, 8]");
-  if (n_sis < n_dim) return fail(h, SISSO_L0_EINVAL, "n_sis must be >= n_dim");
+  if (n_reqs < 1) return fail(h, SISSO_L0_EINVAL, "at least one request");
+  if (n_sis < 1) return fail(h, SISSO_L0_EINVAL, "n_sis must be >= 1");
   if (n_sis > (1LL << 30)) return fail(h, SISSO_L0_EUNSUPPORTED, "n_sis too large");
-  if (k < 1) return fail(h, SISSO_L0_EINVAL, "k must be >= 1");
   if (task_offsets[0] != 0) return fail(h, SISSO_L0_EINVAL, "task_offsets[0] must be 0");
+  if (h->opt.precision != SISSO_L0_FP64 && h->opt.precision != SISSO_L0_MIXED_BF16X3)
+    return fail(h, SISSO_L0_EUNSUPPORTED, "precision not supported");
   FitPlan P;
   P.T = n_tasks;
   P.m = (int)n_sis;
-  P.d = n_dim;
-  P.k = k;
   P.shared = (h->opt.task_mode == SISSO_L0_SHARED) ? 1 : 0;
   P.mixed = (h->opt.precision == SISSO_L0_MIXED_BF16X3) ? 1 : 0;
-  if (h->opt.precision != SISSO_L0_FP64 && h->opt.precision != SISSO_L0_MIXED_BF16X3)
-    return fail(h, SISSO_L0_EUNSUPPORTED, "precision not supported");
+  P.n_out = P.shared ? 1 : n_tasks;
+  int kmax = 0;
+  for (int q = 0; q < n_reqs; ++q) {
+    const sisso_l0_request &r = reqs[q];
+    if (!r.out_tuples || !r.out_rmse) return fail(h, SISSO_L0_EINVAL, "null output pointer");
+    if (r.n_dim < 1 || r.n_dim > SISSO_L0_MAX_DIM)
+      return fail(h, SISSO_L0_EINVAL, "n_dim must be in [1, 8]");
+    if (n_sis < r.n_dim) return fail(h, SISSO_L0_EINVAL, "n_sis must be >= n_dim");
+    if (r.k < 1) return fail(h, SISSO_L0_EINVAL, "k must be >= 1");
+    const u64 total = binom_host(n_sis, r.n_dim);
+    if (total >= kSat)
+      return fail(h, SISSO_L0_EUNSUPPORTED, "C(n_sis, n_dim) does not fit in 62 bits");
+    if ((u64)r.k > total) return fail(h, SISSO_L0_EINVAL, "k exceeds C(n_sis, n_dim)");
+    if (r.k > 2048) return fail(h, SISSO_L0_EUNSUPPORTED, "k above 2048");
+    P.req.push_back(Req{r.n_dim, r.k, r.out_tuples, r.out_rmse});
+    P.dmax = std::max(P.dmax, r.n_dim);
+    kmax = std::max(kmax, r.k);
+    if (r.n_dim == 1) {
+      P.has_singles = true;
+    } else {
+      P.has_tuples = true;
+      const int dp = r.n_dim - 2;
+      P.dp_lo = P.dp_lo < 0 ? dp : std::min(P.dp_lo, dp);
+      P.dp_hi = std::max(P.dp_hi, dp);
+    }
+    P.fits_per_pass += total * (u64)n_tasks;
+  }
+  if (P.has_tuples && P.dp_hi - P.dp_lo > 0 &&
+      !((P.dp_lo == 0 && P.dp_hi <= 2) || (P.dp_lo == 1 && P.dp_hi == 2)) )
+    return fail(h, SISSO_L0_EUNSUPPORTED, "tuple sizes of one call must lie within {2, 3, 4}");
+  if (P.shared && P.dp_hi > P.dp_lo)
+    return fail(h, SISSO_L0_EUNSUPPORTED, "SHARED mode takes one tuple size >= 2 per call");
   P.off.assign(task_offsets, task_offsets + n_tasks + 1);
-  P.nmax = 0;
   for (int t = 0; t < n_tasks; ++t) {
-    long long nt = P.off[t + 1] - P.off[t];
-    if (nt < n_dim + 2) return fail(h, SISSO_L0_EINVAL, "every task needs at least n_dim + 2 rows");
+    const long long nt = P.off[t + 1] - P.off[t];
+    if (nt < P.dmax + 2) return fail(h, SISSO_L0_EINVAL, "every task needs at least n_dim + 2 rows");
     P.nmax = std::max(P.nmax, nt);
   }
   P.N = P.off[n_tasks];
-  const u64 total = binom_host(n_sis, n_dim);
-  if (total >= kSat) return fail(h, SISSO_L0_EUNSUPPORTED, "C(n_sis, n_dim) does not fit in 62 bits");
-  if ((u64)k > total) return fail(h, SISSO_L0_EINVAL, "k exceeds C(n_sis, n_dim)");
-  P.n_out = P.shared ? 1 : n_tasks;
-  // candidate pool K': at least k, at most 2048 (shared-memory lists), never
-  // more than the number of tuples
-  if (k > 2048) return fail(h, SISSO_L0_EUNSUPPORTED, "k above 2048");
-  int Kmax = h->opt.max_candidate_pool > 0 ? std::min(h->opt.max_candidate_pool, 2048) : 2048;
-  int K = h->opt.candidate_pool > 0 ? h->opt.candidate_pool : std::min(std::max(4 * k, 256), 2048);
-  K = std::min(std::max(K, k), 2048);
-  if ((u64)K > total) K = (int)total;
-  Kmax = std::max(Kmax, K);
-  if ((u64)Kmax > total) Kmax = (int)std::max<u64>(total, (u64)K);
-  cudaStream_t st = h->st;
   const int m = P.m;
   const long long N = P.N;
+  // candidate pool K': at least every k, at most 2048 (shared-memory lists),
+  // never more than the number of tuples of the smallest request
+  u64 total_min = ~0ull;
+  for (const Req &r : P.req) total_min = std::min(total_min, binom_host(m, r.d));
+  int Kmax = h->opt.max_candidate_pool > 0 ? std::min(h->opt.max_candidate_pool, 2048) : 2048;
+  int K = h->opt.candidate_pool > 0 ? h->opt.candidate_pool : std::min(std::max(4 * kmax, 256), 2048);
+  K = std::min(std::max(K, kmax), 2048);
+  if ((u64)K > total_min) K = (int)std::max<u64>(total_min, (u64)kmax);
+  Kmax = std::max(Kmax, K);
+  cudaStream_t st = h->st;
+  if (h->own_st) {
+    // the caller's earlier work (e.g. producing X) precedes ours
+    L0_CK(cudaEventRecord(h->ev_user, h->user_st), "event");
+    L0_CK(cudaStreamWaitEvent(st, h->ev_user, 0), "stream wait");
+  }
   // inputs on the device
   const double *Xd = X, *yd = y;
   if (!is_device_ptr(X)) {
@@ -487,29 +808,20 @@ int fit_impl(sisso_l0_t h, const double *X, const double *y, const int64_t *task
   P.Xd = Xd;
   P.yd = yd;
   L0_CK(h->offs.ensure((n_tasks + 1) * 8), "alloc offsets");
-  L0_CK(cudaMemcpyAsync(h->offs.p, P.off.data(), (n_tasks + 1) * 8, cudaMemcpyHostToDevice, st), "copy offsets");
+  L0_CK(cudaMemcpyAsync(h->offs.p, P.off.data(), (n_tasks + 1) * 8, cudaMemcpyHostToDevice, st),
+        "copy offsets");
   L0_CK(h->err.ensure(16), "alloc err");
-  L0_CK(cudaMemsetAsync(h->err.p, 0, 16, st), "memset");
   int rc = ensure_binom(h, m);
   if (rc) return rc;
-  L0_CK(cudaEventRecord(h->ev[0], st), "event");
-  // 1-2. centre and scale (FP64), then the augmented Gram per task
+  // buffers of the centring and the Gram
   const int mp1 = m + 1;
   P.ld = ((long long)mp1 + 31) / 32 * 32;
   P.gstride = (long long)mp1 * P.ld;
-  const long long gstride = P.gstride;
   L0_CK(h->mu.ensure((size_t)n_tasks * mp1 * 8), "alloc mu");
   L0_CK(h->inv_s.ensure((size_t)n_tasks * mp1 * 8), "alloc inv_s");
   L0_CK(h->w64.ensure((size_t)mp1 * N * 8), "alloc W");
   if (!P.mixed) {
-    L0_CK(l0::launch_centre(Xd, yd, N, m, h->offs.as<long long>(), n_tasks, h->mu.as<double>(),
-                            h->inv_s.as<double>(), h->w64.as<double>(), h->err.as<int>(), st),
-          "centre kernel");
-    L0_CK(cudaEventRecord(h->ev[1], st), "event");
-    L0_CK(h->gram.ensure((size_t)n_tasks * gstride * 8), "alloc Gram");
-    L0_CK(l0::launch_gram64(h->w64.as<double>(), N, m, P.off.data(), n_tasks,
-                            h->gram.as<double>(), P.ld, gstride, st),
-          "gram kernel");
+    L0_CK(h->gram.ensure((size_t)n_tasks * P.gstride * 8), "alloc Gram");
     P.have_g64 = true;
   } else {
     // split-BF16 rows: per task three segments of npad_t = roundup(n_t, 64)
@@ -519,97 +831,63 @@ int fit_impl(sisso_l0_t h, const double *X, const double *y, const int64_t *task
       const long long nt = P.off[t + 1] - P.off[t];
       const long long np = (nt + 63) / 64 * 64;
       if (ldk + 3 * np > (1LL << 30)) return fail(h, SISSO_L0_EUNSUPPORTED, "too many samples");
-      meta[t] = (int)ldk;                      // kbeg
-      meta[n_tasks + t] = (int)np;             // npad
+      meta[t] = (int)ldk;                           // first K column of the task
+      meta[n_tasks + t] = (int)np;                  // padded samples
       meta[2 * n_tasks + t] = (int)(3 * np / 64);   // K blocks
       ldk += 3 * np;
     }
+    P.ldk = ldk;
     const size_t abytes = (size_t)mp1 * ldk * 2;
     L0_CK(h->abf.ensure(abytes), "alloc split rows");
     L0_CK(h->bbf.ensure(abytes), "alloc split rows");
     L0_CK(h->kmeta.ensure(meta.size() * 4), "alloc");
-    L0_CK(cudaMemcpyAsync(h->kmeta.p, meta.data(), meta.size() * 4, cudaMemcpyHostToDevice, st), "copy");
-    L0_CK(cudaMemsetAsync(h->abf.p, 0, abytes, st), "memset");
-    L0_CK(cudaMemsetAsync(h->bbf.p, 0, abytes, st), "memset");
-    const int *kbeg = h->kmeta.as<int>();
-    L0_CK(l0::launch_centre_split(Xd, yd, N, m, h->offs.as<long long>(), n_tasks,
-                                  h->mu.as<double>(), h->inv_s.as<double>(), h->w64.as<double>(),
-                                  h->abf.p, h->bbf.p, ldk, kbeg, kbeg + n_tasks, h->err.as<int>(),
-                                  st),
-          "centre kernel");
-    L0_CK(cudaEventRecord(h->ev[1], st), "event");
-    L0_CK(h->gram32.ensure((size_t)n_tasks * gstride * 4), "alloc Gram");
-    L0_CK(l0::launch_gram_tc(h->abf.p, h->bbf.p, ldk, m, n_tasks, kbeg, kbeg + 2 * n_tasks,
-                             h->gram32.as<float>(), P.ld, gstride, h->err.as<int>(), st),
-          "tensor-core gram kernel");
+    L0_CK(cudaMemcpyAsync(h->kmeta.p, meta.data(), meta.size() * 4, cudaMemcpyHostToDevice, st),
+          "copy");
+    L0_CK(h->gram32.ensure((size_t)n_tasks * P.gstride * 4), "alloc Gram");
   }
-  L0_CK(cudaEventRecord(h->ev[6], st), "event");
-  // problems
-  // problems: one per task (PER_TASK), or one spanning all tasks (SHARED)
-  P.pd.clear();
-  for (int t = 0; t < (P.shared ? 1 : n_tasks); ++t) {
-    l0::ProbDesc d{};
-    d.g_off = (long long)t * gstride;
-    d.ld = P.ld;
-    d.m = m;
-    d.d = n_dim;
-    d.dp = n_dim - 2;
-    d.task = t;
-    d.total = total;
-    P.pd.push_back(d);
-  }
-  // grid size: persistent CTAs
-  const int dp = std::max(0, n_dim - 2);
-  if (n_dim >= 2) {
-    int S0 = 1024;
-    while (S0 < 2 * Kmax) S0 <<= 1;
+  // persistent grid of the tuple kernel
+  if (P.has_tuples) {
     int bps = 0;
-    if (P.mixed) {
-      const size_t smem = l0::tile_smem_bytes<float>(Kmax, S0, dp);
-      if (P.shared) L0_CK(l0::shared_occupancy<float>(dp, smem, &bps), "occupancy");
-      else L0_CK(l0::tile_occupancy<float>(dp, dp, smem, &bps), "occupancy");
-    } else {
-      const size_t smem = l0::tile_smem_bytes<double>(Kmax, S0, dp);
-      if (P.shared) L0_CK(l0::shared_occupancy<double>(dp, smem, &bps), "occupancy");
-      else L0_CK(l0::tile_occupancy<double>(dp, dp, smem, &bps), "occupancy");
-    }
+    rc = P.mixed ? tile_bps<float>(h, P, Kmax, &bps) : tile_bps<double>(h, P, Kmax, &bps);
+    if (rc) return rc;
     if (bps < 1) return fail(h, SISSO_L0_EUNSUPPORTED, "tuple kernel does not fit on an SM");
+    P.max_bps = bps;
     P.grid = h->n_sm * bps;
   }
-  plan_items(P, {}, std::max(1, P.grid));
-  L0_CK(h->probs.ensure(P.pd.size() * sizeof(l0::ProbDesc)), "alloc probs");
-  L0_CK(cudaMemcpyAsync(h->probs.p, P.pd.data(), P.pd.size() * sizeof(l0::ProbDesc), cudaMemcpyHostToDevice, st), "copy probs");
-  L0_CK(h->rowpre.ensure(std::max<size_t>(1, P.rowpre.size()) * 8), "alloc rowpre");
-  if (!P.rowpre.empty())
-    L0_CK(cudaMemcpyAsync(h->rowpre.p, P.rowpre.data(), P.rowpre.size() * 8, cudaMemcpyHostToDevice, st), "copy rowpre");
-  // rmse divisor per problem: n_t (PER_TASK); SHARED scores are already the
-  // pooled mean SSE
-  {
-    std::vector<double> div(P.pd.size());
-    for (size_t q = 0; q < P.pd.size(); ++q)
-      div[q] = P.shared ? 1.0 : (double)(P.off[P.pd[q].task + 1] - P.off[P.pd[q].task]);
-    L0_CK(h->rdiv.ensure(div.size() * 8), "alloc");
-    L0_CK(cudaMemcpyAsync(h->rdiv.p, div.data(), div.size() * 8, cudaMemcpyHostToDevice, st), "copy");
-  }
-  L0_CK(h->out_t.ensure((size_t)P.n_out * k * n_dim * 4), "alloc out");
-  L0_CK(h->out_r.ensure((size_t)P.n_out * k * 8), "alloc out");
-  L0_CK(h->dfr_n.ensure(24), "alloc");   // queued runs, queued tuples, redone tuples
-  if (P.mixed && n_dim >= 2) {
-    L0_CK(h->dfr_key.ensure((size_t)kDeferCap * 8), "alloc deferral buffer");
-    L0_CK(h->dfr_len.ensure((size_t)kDeferCap * 4), "alloc deferral buffer");
+  P.items_factor = 2;
+  plan_problems(P);
+  rc = P.mixed ? setup_search<float>(h, P, K) : setup_search<double>(h, P, K);
+  if (rc) return rc;
+  // autotuning needs the Gram: run the prep once outside any graph
+  bool prep_done = false;
+  h->stats.tuned_items_factor = 0;
+  h->stats.tuned_ctas_per_sm = 0;
+  if (h->opt.autotune && P.has_tuples) {
+    rc = prep_pass(h, P);
+    if (rc) return rc;
+    prep_done = true;
+    rc = P.mixed ? autotune<float>(h, P, K, h->gram32.as<float>())
+                 : autotune<double>(h, P, K, h->gram.as<double>());
+    if (rc) return rc;
+    plan_problems(P);
+    rc = P.mixed ? setup_search<float>(h, P, K) : setup_search<double>(h, P, K);
+    if (rc) return rc;
   }
   int certified = 0, enl = 0;
   double delta = 0;
   float ms_tuple = 0, ms_merge = 0, ms_refit = 0;
+  bool replayed = false;
   for (;;) {
-    int S = 1024;
-    while (S < 2 * K) S <<= 1;
-    if (P.mixed)
-      rc = run_search<float>(h, P, K, S, h->gram32.as<float>(), &certified, &delta, &ms_tuple,
-                             &ms_merge, &ms_refit);
-    else
-      rc = run_search<double>(h, P, K, S, h->gram.as<double>(), &certified, &delta, &ms_tuple,
-                              &ms_merge, &ms_refit);
+    if (enl > 0) {
+      rc = P.mixed ? setup_search<float>(h, P, K) : setup_search<double>(h, P, K);
+      if (rc) break;
+    }
+    const bool with_prep = !prep_done;
+    rc = P.mixed ? run_pass<float>(h, P, K, h->gram32.as<float>(), with_prep, &replayed)
+                 : run_pass<double>(h, P, K, h->gram.as<double>(), with_prep, &replayed);
+    if (rc) break;
+    prep_done = true;
+    rc = finish_pass(h, P, &certified, &delta, &ms_tuple, &ms_merge, &ms_refit);
     if (rc) break;
     if (certified || K >= Kmax) break;
     K = std::min(2 * K, Kmax);
@@ -617,24 +895,38 @@ int fit_impl(sisso_l0_t h, const double *X, const double *y, const int64_t *task
   }
   if (rc) return rc;
   // outputs to the caller
-  L0_CK(cudaMemcpyAsync(out_tuples, h->out_t.p, (size_t)P.n_out * k * n_dim * 4, cudaMemcpyDefault, st), "copy out");
-  L0_CK(cudaMemcpyAsync(out_rmse, h->out_r.p, (size_t)P.n_out * k * 8, cudaMemcpyDefault, st), "copy out");
+  for (size_t q = 0; q < P.req.size(); ++q) {
+    const Req &r = P.req[q];
+    const l0::ProbDesc &first = P.pd[q * (P.shared ? 1 : P.T)];
+    const size_t nt = (size_t)P.n_out * r.k * r.d, nr = (size_t)P.n_out * r.k;
+    L0_CK(cudaMemcpyAsync(r.out_t, h->out_t.as<int>() + first.out_t_off, nt * 4, cudaMemcpyDefault,
+                          st), "copy out");
+    L0_CK(cudaMemcpyAsync(r.out_r, h->out_r.as<double>() + first.out_r_off, nr * 8,
+                          cudaMemcpyDefault, st), "copy out");
+  }
   rc = wait_stream(h);
   if (rc) return rc;
   float t_prep = 0, t_gram = 0;
   cudaEventElapsedTime(&t_prep, h->ev[0], h->ev[1]);
   cudaEventElapsedTime(&t_gram, h->ev[1], h->ev[6]);
   sisso_l0_stats &S = h->stats;
+  const int tf = S.tuned_items_factor, tb = S.tuned_ctas_per_sm;
   memset(&S, 0, sizeof(S));
   S.struct_size = sizeof(S);
   S.candidate_pool = K;
   S.pool_enlargements = enl;
   S.certified = certified;
-  S.tuple_fits = total * (u64)n_tasks * (u64)(enl + 1);
+  S.tuple_fits = P.fits_per_pass * (u64)(enl + 1);
   S.max_pool_rel_error = delta;
   S.fp64_fallback_tuples = P.fallback_tuples;
-  // centre + Gram, then per search pass: seed, tuple, merge, refit, select
-  S.kernel_launches = (P.mixed ? 2 : 1 + n_tasks) + 5LL * (enl + 1);
+  // centring + Gram, then per pass: seed, singles?, tuple, redo (mixed: gated
+  // FP64 Gram + two redo kernels), merge, re-fit, select
+  const long long per_pass = 5 + (P.has_singles ? 1 : 0) + (P.mixed && P.has_tuples ? 3 : 0) -
+                             (P.has_tuples ? 0 : 1);
+  S.kernel_launches = (P.mixed ? 2 : 1 + n_tasks) + per_pass * (enl + 1);
+  S.graph_replayed = replayed ? 1 : 0;
+  S.tuned_items_factor = h->opt.autotune ? P.items_factor : tf;
+  S.tuned_ctas_per_sm = h->opt.autotune ? P.grid / std::max(1, h->n_sm) : tb;
   S.ms_prep = t_prep;
   S.ms_gram = t_gram;
   S.ms_tuple = ms_tuple;
@@ -661,6 +953,7 @@ int sisso_l0_default_options(sisso_l0_options *opt) {
   opt->fp32_fallback_pivot_ratio = 1e-6;
   opt->rank_deficient_pivot_ratio = 1e-12;
   opt->autotune = 0;
+  opt->use_graph = 0;
   opt->autotune_cache_path = nullptr;
   opt->timeout_seconds = 0.0;
   return SISSO_L0_OK;
@@ -681,13 +974,20 @@ int sisso_l0_create(sisso_l0_t *out, const sisso_l0_options *opt) {
   if (!h) return SISSO_L0_ENOMEM;
   h->opt = o;
   h->st = (cudaStream_t)o.stream;
+  h->user_st = h->st;
   cudaError_t e = cudaSetDevice(o.device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, o.device);
   for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaEventCreate(&h->ev[i]);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_user, cudaEventDisableTiming);
+  if (e == cudaSuccess && o.use_graph && h->st == nullptr) {
+    e = cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking);
+    h->own_st = (e == cudaSuccess);
+  }
   if (e != cudaSuccess) {
     delete h;
     return (e == cudaErrorMemoryAllocation) ? SISSO_L0_ENOMEM : SISSO_L0_ECUDA;
   }
+  load_tune_cache(h);
   *out = h;
   return SISSO_L0_OK;
 }
@@ -699,7 +999,23 @@ int sisso_l0_fit(sisso_l0_t h, const double *X, const double *y, const int64_t *
   try {
     cudaError_t e = cudaSetDevice(h->opt.device);
     if (e != cudaSuccess) return cuda_fail(h, e, "set device");
-    return fit_impl(h, X, y, task_offsets, n_tasks, n_sis, n_dim, k, out_tuples, out_rmse);
+    sisso_l0_request r{n_dim, k, out_tuples, out_rmse};
+    return fit_requests(h, X, y, task_offsets, n_tasks, n_sis, &r, 1);
+  } catch (const std::bad_alloc &) {
+    return fail(h, SISSO_L0_ENOMEM, "host allocation failed");
+  } catch (...) {
+    return fail(h, SISSO_L0_ECUDA, "unexpected host exception");
+  }
+}
+
+int sisso_l0_fit_multi(sisso_l0_t h, const double *X, const double *y,
+                       const int64_t *task_offsets, int32_t n_tasks, int64_t n_sis,
+                       const sisso_l0_request *reqs, int32_t n_reqs) {
+  if (!h) return SISSO_L0_EINVAL;
+  try {
+    cudaError_t e = cudaSetDevice(h->opt.device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set device");
+    return fit_requests(h, X, y, task_offsets, n_tasks, n_sis, reqs, n_reqs);
   } catch (const std::bad_alloc &) {
     return fail(h, SISSO_L0_ENOMEM, "host allocation failed");
   } catch (...) {
@@ -723,6 +1039,7 @@ void sisso_l0_destroy(sisso_l0_t h) {
   cudaSetDevice(h->opt.device);
   if (h->st) cudaStreamSynchronize(h->st);
   else cudaDeviceSynchronize();
+  if (h->own_st && h->user_st) cudaStreamSynchronize(h->user_st);
   DevBuf *bufs[] = {&h->xin, &h->yin, &h->offs, &h->mu, &h->inv_s, &h->w64, &h->gram, &h->binom,
                     &h->probs, &h->rowpre, &h->ctr, &h->gthr, &h->lists_s, &h->lists_k,
                     &h->lists_cnt, &h->part_s, &h->part_k, &h->part_cnt, &h->done, &h->pool_s,
@@ -732,6 +1049,9 @@ void sisso_l0_destroy(sisso_l0_t h) {
   for (DevBuf *b : bufs) b->release();
   for (int i = 0; i < 8; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->ev_user) cudaEventDestroy(h->ev_user);
+  if (h->own_st) cudaStreamDestroy(h->st);
   delete h;
 }
 

@@ -25,6 +25,9 @@ struct ProbDesc {
   int n_jt, n_kt, L, prefix_off;   // j/k tile counts, prefix steps per item, row-prefix offset
   long long item_begin, item_end;  // global work-item range
   u64 total;              // C(m, d)
+  int k, pad;             // requested list length
+  long long out_t_off;    // offset of this problem's tuples in the output staging
+  long long out_r_off;    // offset of this problem's errors in the output staging
 };
 
 template <typename R>
@@ -38,6 +41,7 @@ struct TileArgs {
   double ratio;                    // pivot ratio: ineligible (FP64) / redo in FP64 (FP32)
   int K, S;                        // list capacity, staging capacity
   u64 *item_counter;
+  long long item_limit;            // items at or past this index are not processed
   u64 *gthr;                       // [n_probs] ordered score bits
   R *out_s; u64 *out_k; int *out_cnt;   // [n_probs][n_slots][K], [n_probs][n_slots]
   int n_slots;
@@ -148,15 +152,15 @@ struct CertOut {
 
 template <typename R>
 struct SelectArgs {
-  const ProbDesc *probs;
-  int n_probs, K, k;
+  const ProbDesc *probs;       // per problem: k, d, output offsets
+  int n_probs, K;
   const R *pool_s; const u64 *pool_k; const int *pool_cnt;
   const double *refit;
   const double *inv_s;         // [T][m+1]: 1 / ||centred column||, index 0 the target
   int mp1, shared;             // PER_TASK: a pool score times S_yy,t is an SSE
   const double *rmse_div;      // [n_probs] n_t (PER_TASK) or 1 (SHARED: pooled mean)
   Binom B;
-  int *out_tuples; double *out_rmse;   // [n_probs][k][d], [n_probs][k]
+  int *out_tuples; double *out_rmse;   // staging; problem q at its out_*_off
   CertOut *cert;
   double cert_safety;
   const u64 *gthr;             // [n_probs] final search threshold (ordered bits of R)
@@ -203,9 +207,10 @@ cudaError_t launch_defer(const DeferArgs &a, int groups, int n_probs, cudaStream
 
 // initial search threshold per problem: +inf, then the K'-th best score of
 // all d-tuples of the M best single columns (a valid bound: real tuples)
+// seed == 0: only the +inf initialisation
 template <typename R>
 cudaError_t launch_seed(const R *G, const ProbDesc *probs_dev, int n_probs, int K, int S,
-                        int M, double ratio, const Binom &B, u64 *gthr, cudaStream_t st);
+                        int seed, double ratio, const Binom &B, u64 *gthr, cudaStream_t st);
 template <typename R>
 size_t seed_smem_bytes(int K, int S);
 

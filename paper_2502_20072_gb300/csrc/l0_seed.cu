@@ -31,7 +31,7 @@ constexpr int SEED_THREADS = 1024;
 
 template <typename R>
 __global__ void __launch_bounds__(SEED_THREADS)
-seed_kernel(const R *Gbase, const ProbDesc *probs, int K, int S, int M, double ratio,
+seed_kernel(const R *Gbase, const ProbDesc *probs, int K, int S, int seed, double ratio,
             Binom B, u64 *gthr) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int cols[64];
@@ -41,7 +41,12 @@ seed_kernel(const R *Gbase, const ProbDesc *probs, int K, int S, int M, double r
   const int prob = blockIdx.x;
   const ProbDesc pd = probs[prob];
   if (threadIdx.x == 0) gthr[prob] = ord_inf<R>();
-  if (M <= 0 || pd.d < 2) return;
+  if (!seed || pd.d < 2) return;
+  // smallest M with C(M, d) >= 2 K', at most min(m, 64, K')
+  const int Mcap = min(min(pd.m, 64), K);
+  int M = Mcap;
+  for (int q = pd.d; q <= Mcap; ++q)
+    if (small_binom(q, pd.d) >= 2ull * (u64)K) { M = q; break; }
   const R *G = Gbase + pd.g_off;
   const long long ld = pd.ld;
   const int m = pd.m, d = pd.d;
@@ -149,13 +154,13 @@ size_t seed_smem_bytes(int K, int S) {
 }
 
 template <typename R>
-cudaError_t launch_seed(const R *G, const ProbDesc *probs_dev, int n_probs, int K, int S, int M,
-                        double ratio, const Binom &B, u64 *gthr, cudaStream_t st) {
+cudaError_t launch_seed(const R *G, const ProbDesc *probs_dev, int n_probs, int K, int S,
+                        int seed, double ratio, const Binom &B, u64 *gthr, cudaStream_t st) {
   const size_t smem = seed_smem_bytes<R>(K, S);
   cudaError_t e =
       cudaFuncSetAttribute(seed_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  seed_kernel<R><<<n_probs, SEED_THREADS, smem, st>>>(G, probs_dev, K, S, M, ratio, B, gthr);
+  seed_kernel<R><<<n_probs, SEED_THREADS, smem, st>>>(G, probs_dev, K, S, seed, ratio, B, gthr);
   return cudaGetLastError();
 }
 

@@ -362,18 +362,19 @@ select_kernel(SelectArgs<R> a) {
   if (nv_local) atomicAdd(&s_valid, nv_local);
   __syncthreads();
   const int nvalid = s_valid;
-  const int d = pd.d;
+  const int d = pd.d, kq = pd.k;
   const double div = a.rmse_div[prob];
-  for (int i = threadIdx.x; i < a.k; i += blockDim.x) {
-    int *ot = a.out_tuples + ((size_t)prob * a.k + i) * d;
+  for (int i = threadIdx.x; i < kq; i += blockDim.x) {
+    int *ot = a.out_tuples + pd.out_t_off + (size_t)i * d;
+    double *orr = a.out_rmse + pd.out_r_off + i;
     if (i < nvalid) {
       int t[L0_DMAX];
       lex_unrank(a.B, pd.m, d, sk[i], pd.total, t);
       for (int q = 0; q < d; ++q) ot[q] = t[q];
-      a.out_rmse[(size_t)prob * a.k + i] = sqrt(fmax(ss[i], 0.0) / div);
+      *orr = sqrt(fmax(ss[i], 0.0) / div);
     } else {
       for (int q = 0; q < d; ++q) ot[q] = -1;
-      a.out_rmse[(size_t)prob * a.k + i] = __longlong_as_double(0x7ff0000000000000ll);
+      *orr = __longlong_as_double(0x7ff0000000000000ll);
     }
   }
   if (threadIdx.x == 0) {
@@ -391,7 +392,7 @@ select_kernel(SelectArgs<R> a) {
     if (c.pool_full) bound = fmin(bound, (double)a.pool_s[(size_t)prob * a.K + cnt - 1]);
     const double inf = __longlong_as_double(0x7ff0000000000000ll);
     c.pool_worst = isinf(bound) ? inf : bound * scale;
-    c.kth_refit = (nvalid >= a.k) ? ss[a.k - 1] : inf;
+    c.kth_refit = (nvalid >= kq) ? ss[kq - 1] : inf;
     // Its exact score is then at least bound - safety * delta; the pool holds
     // the exact top k when that clears the k-th re-fitted score, or trivially
     // when nothing was excluded at all.

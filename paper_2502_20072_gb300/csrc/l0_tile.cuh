@@ -558,8 +558,9 @@ __device__ __forceinline__ void persistent_items(const TileArgs<R> &A, RunItem r
     __syncthreads();
     const long long item = s_item;
     int prob = -1;
-    for (int q = 0; q < A.n_probs; ++q)
-      if (item >= A.probs[q].item_begin && item < A.probs[q].item_end) { prob = q; break; }
+    if (item < A.item_limit)
+      for (int q = 0; q < A.n_probs; ++q)
+        if (item >= A.probs[q].item_begin && item < A.probs[q].item_end) { prob = q; break; }
     if (prob != cur) {
       if (cur >= 0) {
         const size_t slot = (size_t)cur * A.n_slots + blockIdx.x;

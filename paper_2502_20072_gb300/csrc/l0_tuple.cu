@@ -130,6 +130,7 @@ singles_kernel(const R *Gbase, const ProbDesc *probs, int K, int S, u64 *gthr,
   CtaList<R> L = cta_list_carve<R>(p, K, S);
   const int prob = blockIdx.y;
   const ProbDesc pd = probs[prob];
+  if (pd.d != 1) return;          // other problems run in the tuple kernel
   const R *G = Gbase + pd.g_off;
   const long long ld = pd.ld;
   cta_list_reset<R>(L, gthr + prob);
@@ -189,6 +190,7 @@ static const void *tile_fn(int dp_lo, int dp_hi) {
 #define L0_K(LO, HI) \
   if (dp_lo == LO && dp_hi == HI) return (const void *)tile_kernel<R, LO, HI>;
   L0_K(0, 0) L0_K(1, 1) L0_K(2, 2) L0_K(3, 3) L0_K(4, 4) L0_K(5, 5) L0_K(6, 6)
+  L0_K(0, 1) L0_K(1, 2) L0_K(0, 2)
 #undef L0_K
   return nullptr;
 }
