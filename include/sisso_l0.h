@@ -88,7 +88,9 @@ typedef struct {
   int32_t tuned_items_factor;        /* autotuner choice: work items per CTA (x2) */
   int32_t tuned_ctas_per_sm;         /* autotuner choice: resident CTAs per SM */
   int32_t reserved1;
+  /* phase times (ms, CUDA events on the handle's stream); 0 when unavailable */
   double ms_prep, ms_gram, ms_tuple, ms_merge, ms_refit, ms_total;
+  double ms_tuple_kernel;            /* the tuple kernel alone (last search pass) */
 } sisso_l0_stats;
 
 /* Fill *opt with defaults (FP64, PER_TASK, device 0, legacy stream). */

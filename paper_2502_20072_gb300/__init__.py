@@ -68,7 +68,8 @@ class Stats(ctypes.Structure):
                 ("reserved1", ctypes.c_int32),
                 ("ms_prep", ctypes.c_double), ("ms_gram", ctypes.c_double),
                 ("ms_tuple", ctypes.c_double), ("ms_merge", ctypes.c_double),
-                ("ms_refit", ctypes.c_double), ("ms_total", ctypes.c_double)]
+                ("ms_refit", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("ms_tuple_kernel", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "struct_size"}

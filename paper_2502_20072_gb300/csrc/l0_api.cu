@@ -78,6 +78,8 @@ struct sisso_l0_handle {
   int done_init_for = 0;
   cudaEvent_t ev[8] = {nullptr};
   cudaEvent_t ev_user = nullptr;    // orders the handle's stream after the caller's
+  cudaEvent_t ev_k[2] = {nullptr, nullptr};   // around the tuple kernel
+  float ms_tuple_kernel = 0.f;
   cudaGraphExec_t graph_exec = nullptr;
   std::string graph_key;
   std::map<std::string, std::pair<int, int>> tune;   // autotuner choices
@@ -441,8 +443,10 @@ int search_pass(sisso_l0_t h, FitPlan &P, int K, const R *G) {
     L0_CK(cudaMemsetAsync(h->ctr.p, 0, 8, st), "memset");
     if (P.mixed) L0_CK(cudaMemsetAsync(h->dfr_n.p, 0, 24, st), "memset");
     l0::TileArgs<R> a = tile_args<R>(h, P, K, S, G, n_slots, P.n_items);
+    L0_CK(cudaEventRecord(h->ev_k[0], st), "event");
     int rc = launch_tuple_kernel<R>(h, P, a);
     if (rc) return rc;
+    L0_CK(cudaEventRecord(h->ev_k[1], st), "event");
     if (P.mixed) {
       // FP64 redo of the near-singular tuples the FP32 kernel queued: the
       // FP64 Gram and the Gram-mode redo run only when many were queued, the
@@ -562,10 +566,15 @@ int finish_pass(sisso_l0_t h, FitPlan &P, int *certified, double *delta_max, flo
     if (!c.certified) *certified = 0;
     *delta_max = std::max(*delta_max, c.delta);
   }
+  // phase timings are statistics only: a failed read (e.g. events recorded
+  // inside a replayed graph) leaves them 0 and must not leave a pending error
   float t1 = 0, t2 = 0, t3 = 0;
-  cudaEventElapsedTime(&t1, h->ev[2], h->ev[3]);
-  cudaEventElapsedTime(&t2, h->ev[3], h->ev[4]);
-  cudaEventElapsedTime(&t3, h->ev[4], h->ev[5]);
+  if (cudaEventElapsedTime(&t1, h->ev[2], h->ev[3]) != cudaSuccess) t1 = 0;
+  if (cudaEventElapsedTime(&t2, h->ev[3], h->ev[4]) != cudaSuccess) t2 = 0;
+  if (cudaEventElapsedTime(&t3, h->ev[4], h->ev[5]) != cudaSuccess) t3 = 0;
+  if (!P.has_tuples || cudaEventElapsedTime(&h->ms_tuple_kernel, h->ev_k[0], h->ev_k[1]) != cudaSuccess)
+    h->ms_tuple_kernel = 0.f;
+  (void)cudaGetLastError();
   *ms_tuple += t1;
   *ms_merge += t2;
   *ms_refit += t3;
@@ -907,8 +916,9 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
   rc = wait_stream(h);
   if (rc) return rc;
   float t_prep = 0, t_gram = 0;
-  cudaEventElapsedTime(&t_prep, h->ev[0], h->ev[1]);
-  cudaEventElapsedTime(&t_gram, h->ev[1], h->ev[6]);
+  if (cudaEventElapsedTime(&t_prep, h->ev[0], h->ev[1]) != cudaSuccess) t_prep = 0;
+  if (cudaEventElapsedTime(&t_gram, h->ev[1], h->ev[6]) != cudaSuccess) t_gram = 0;
+  (void)cudaGetLastError();
   sisso_l0_stats &S = h->stats;
   const int tf = S.tuned_items_factor, tb = S.tuned_ctas_per_sm;
   memset(&S, 0, sizeof(S));
@@ -933,6 +943,7 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
   S.ms_merge = ms_merge;
   S.ms_refit = ms_refit;
   S.ms_total = t_prep + t_gram + ms_tuple + ms_merge + ms_refit;
+  S.ms_tuple_kernel = h->ms_tuple_kernel;
   return SISSO_L0_OK;
 }
 
@@ -979,6 +990,7 @@ int sisso_l0_create(sisso_l0_t *out, const sisso_l0_options *opt) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, o.device);
   for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaEventCreate(&h->ev[i]);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_user, cudaEventDisableTiming);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreate(&h->ev_k[i]);
   if (e == cudaSuccess && o.use_graph && h->st == nullptr) {
     e = cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking);
     h->own_st = (e == cudaSuccess);
@@ -1051,6 +1063,8 @@ void sisso_l0_destroy(sisso_l0_t h) {
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   if (h->ev_user) cudaEventDestroy(h->ev_user);
+  for (int i = 0; i < 2; ++i)
+    if (h->ev_k[i]) cudaEventDestroy(h->ev_k[i]);
   if (h->own_st) cudaStreamDestroy(h->st);
   delete h;
 }
