@@ -39,6 +39,27 @@ def fp32_peak_tflops(sm_mhz):
     return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
+# DRAM bytes (read + write) of one tuple-kernel launch on the d=3 workload,
+# from the ncu captures summarised in profiles/tile_kernel_l0_d3_n1000_m1000.md.
+# They describe the kernel built from sources with this hash; once the sources
+# change the figure no longer applies and the bench reports null.
+TRAFFIC_SOURCES = ("l0_common.cuh", "l0_tile.cuh", "l0_tuple.cu", "l0_kernels.cuh")
+TRAFFIC_CAPTURED = {("C2", "mixed"): (2534656 + 4608, "f444b96a3d3c3245"),
+                    ("C2", "fp64"): (5858048 + 15104, "f444b96a3d3c3245")}
+
+
+def tile_traffic(workload, precision):
+    import hashlib
+    rec = TRAFFIC_CAPTURED.get((workload, precision))
+    if rec is None:
+        return None
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2502_20072_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return rec[0] if h.hexdigest()[:16] == rec[1] else None
+
+
 def flops_per_tuple(d):
     # hoisted per-tuple work of the tuple kernel's fast path:
     # (d-2) FMA for h, MUL g2, FMA pp, FMA w, MUL w^2, FMA t  ->  d+1 FMA + 2 MUL
@@ -261,16 +282,22 @@ def run_ours(args):
     # roofline of the dominant kernel (the tuple kernel), timed by CUDA events
     # around its launch on the library's stream; events inside a replayed
     # graph may not be timeable, so measure extra un-graphed fits then
+    stage = {s: st["ms_" + s] for s in ("prep", "gram", "tuple", "merge", "refit")}
     if min(tuple_ms) <= 0.0:
         hk = l0.Handle(precision=precision, device=local, stream=stream.cuda_stream,
-                       autotune=int(not args.no_autotune))
+                       autotune=int(not args.no_autotune), use_graph=0)
         tuple_ms = []
+        acc = {s: [] for s in stage}
         for i in range(max(3, args.warmup) + max(2, min(args.steps, 5))):
             flush.zero_()
             hk.fit(X, y, d, k, offsets=prob.offsets, out_tuples=out_t, out_rmse=out_r)
             if i >= max(3, args.warmup):
-                tuple_ms.append(hk.stats()["ms_tuple_kernel"])
+                sk = hk.stats()
+                tuple_ms.append(sk["ms_tuple_kernel"])
+                for s in acc:
+                    acc[s].append(sk["ms_" + s])
         hk.close()
+        stage = {s: statistics.mean(v) for s, v in acc.items()}
     t_tuple = statistics.mean(tuple_ms) / 1000.0
     fl = flops_per_tuple(d) * n_fits
     achieved = fl / t_tuple / 1e12
@@ -293,14 +320,16 @@ def run_ours(args):
                    "fp64_redo_tuples": int(st["fp64_fallback_tuples"]),
                    "graph_replayed": int(st["graph_replayed"]),
                    "tuned": [int(st["tuned_items_factor"]), int(st["tuned_ctas_per_sm"])],
-                   "stage_ms": {s: round(st["ms_" + s], 4) for s in
-                                ("prep", "gram", "tuple", "merge", "refit")}},
+                   "stage_ms": {s: round(v, 4) for s, v in stage.items()},
+                   "stage_ms_source": ("un-graphed fits on the same inputs"
+                                       if st["graph_replayed"] else "the timed fits")},
         "e2e": {"value": e2e_val, "unit": UNIT,
                 "h2d_bytes_per_step": int(prob.X.nbytes + prob.y.nbytes),
                 "d2h_bytes_per_step": int(ot_h.nbytes + or_h.nbytes)},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": tile_traffic(args.workload, args.precision),
                      "kernel": "tile_kernel (tuple search)", "peak_source": peak_note,
                      "flops_per_tuple": flops_per_tuple(d)},
         "clocks": clk,

@@ -69,7 +69,7 @@ struct sisso_l0_handle {
   sisso_l0_stats stats;
   // workspace
   DevBuf xin, yin, offs, mu, inv_s, w64, gram, binom;
-  DevBuf probs, rowpre, ctr, gthr, lists_s, lists_k, lists_cnt;
+  DevBuf probs, rowpre, ctr, gthr, hist, lists_s, lists_k, lists_cnt;
   DevBuf part_s, part_k, part_cnt, done, pool_s, pool_k, pool_cnt;
   DevBuf scratch, refit, rdiv, cert, out_t, out_r, err;
   DevBuf dfr_key, dfr_len, dfr_n, dfr_cnt;
@@ -308,6 +308,7 @@ int setup_search(sisso_l0_t h, FitPlan &P, int K) {
   L0_CK(h->lists_k.ensure(nl * 8), "alloc lists");
   L0_CK(h->lists_cnt.ensure((size_t)n_probs * n_slots * 4), "alloc lists");
   L0_CK(h->gthr.ensure((size_t)n_probs * 8), "alloc gthr");
+  L0_CK(h->hist.ensure((size_t)n_probs * L0_HIST_WORDS * 4), "alloc histogram");
   L0_CK(h->ctr.ensure(8), "alloc counter");
   const int groups = std::max(1, std::min(n_slots, 32));
   L0_CK(h->part_s.ensure((size_t)n_probs * groups * K * sizeof(R)), "alloc merge");
@@ -386,6 +387,7 @@ l0::TileArgs<R> tile_args(sisso_l0_t h, const FitPlan &P, int K, int S, const R 
   a.item_counter = h->ctr.as<u64>();
   a.item_limit = item_limit;
   a.gthr = h->gthr.as<u64>();
+  a.hist = h->hist.as<unsigned>();
   a.out_s = h->lists_s.as<R>();
   a.out_k = h->lists_k.as<u64>();
   a.out_cnt = h->lists_cnt.as<int>();
@@ -428,7 +430,7 @@ int search_pass(sisso_l0_t h, FitPlan &P, int K, const R *G) {
   {
     const double ratio = P.mixed ? h->opt.fp32_fallback_pivot_ratio : h->opt.rank_deficient_pivot_ratio;
     L0_CK(l0::launch_seed<R>(G, h->probs.as<l0::ProbDesc>(), n_probs, K, S, P.shared ? 0 : 1,
-                             ratio, B, h->gthr.as<u64>(), st),
+                             ratio, B, h->gthr.as<u64>(), h->hist.as<unsigned>(), st),
           "seed kernel");
   }
   if (P.has_singles) {
@@ -648,7 +650,7 @@ int autotune(sisso_l0_t h, FitPlan &P, int K, const R *G) {
       L0_CK(l0::launch_seed<R>(G, h->probs.as<l0::ProbDesc>(), n_probs, K, S, P.shared ? 0 : 1,
                                P.mixed ? h->opt.fp32_fallback_pivot_ratio
                                        : h->opt.rank_deficient_pivot_ratio,
-                               B, h->gthr.as<u64>(), st),
+                               B, h->gthr.as<u64>(), h->hist.as<unsigned>(), st),
             "seed kernel");
       L0_CK(cudaMemsetAsync(h->ctr.p, 0, 8, st), "memset");
       if (P.mixed) L0_CK(cudaMemsetAsync(h->dfr_n.p, 0, 24, st), "memset");
@@ -683,7 +685,7 @@ std::string graph_key(sisso_l0_t h, const FitPlan &P, int K) {
   for (long long o : P.off) k += std::to_string(o) + ",";
   for (const Req &r : P.req) k += "r" + std::to_string(r.d) + "x" + std::to_string(r.k);
   const DevBuf *bufs[] = {&h->xin, &h->yin, &h->offs, &h->mu, &h->inv_s, &h->w64, &h->gram,
-                          &h->binom, &h->probs, &h->rowpre, &h->ctr, &h->gthr, &h->lists_s,
+                          &h->binom, &h->probs, &h->rowpre, &h->ctr, &h->gthr, &h->hist, &h->lists_s,
                           &h->lists_k, &h->lists_cnt, &h->part_s, &h->part_k, &h->part_cnt,
                           &h->done, &h->pool_s, &h->pool_k, &h->pool_cnt, &h->scratch, &h->refit,
                           &h->rdiv, &h->cert, &h->out_t, &h->out_r, &h->err, &h->dfr_key,
@@ -1053,7 +1055,7 @@ void sisso_l0_destroy(sisso_l0_t h) {
   else cudaDeviceSynchronize();
   if (h->own_st && h->user_st) cudaStreamSynchronize(h->user_st);
   DevBuf *bufs[] = {&h->xin, &h->yin, &h->offs, &h->mu, &h->inv_s, &h->w64, &h->gram, &h->binom,
-                    &h->probs, &h->rowpre, &h->ctr, &h->gthr, &h->lists_s, &h->lists_k,
+                    &h->probs, &h->rowpre, &h->ctr, &h->gthr, &h->hist, &h->lists_s, &h->lists_k,
                     &h->lists_cnt, &h->part_s, &h->part_k, &h->part_cnt, &h->done, &h->pool_s,
                     &h->pool_k, &h->pool_cnt, &h->scratch, &h->refit, &h->rdiv,
                     &h->cert, &h->out_t, &h->out_r, &h->err, &h->dfr_key, &h->dfr_len, &h->dfr_n,

@@ -189,6 +189,87 @@ __device__ void cta_bitonic_sort(R *s, u64 *k, int n) {
   }
 }
 
+// --------------------------------------------- global score histogram --
+// Per problem, counts of the scores every tuple kernel CTA has staged:
+// L0_HIST_FINE bins of 1/16 octave over the FP32 image of a score (rounded
+// down), then L0_HIST_COARSE per-octave totals.  Every staged entry is a
+// distinct real tuple (each tuple is evaluated once per search), so the
+// upper edge of the first bin at which the running count reaches K' bounds
+// the K'-th best score from above: it is a valid global cut long before any
+// single CTA has K' candidates of its own.
+#define L0_HIST_FINE 4096
+#define L0_HIST_COARSE 256
+#define L0_HIST_WORDS (L0_HIST_FINE + L0_HIST_COARSE)
+
+__device__ __forceinline__ float f32_down(float s) { return s; }
+__device__ __forceinline__ float f32_down(double s) { return __double2float_rd(s); }
+
+// fine bin of a score, -1 for NaN
+template <typename R>
+__device__ __forceinline__ int score_bin(R s) {
+  const float f = f32_down(s);
+  if (f != f) return -1;
+  if (!(f > 0.f)) return 0;
+  const unsigned b = __float_as_uint(f) >> 19;
+  return b < (unsigned)L0_HIST_FINE ? (int)b : L0_HIST_FINE - 1;
+}
+
+template <typename R>
+__device__ __forceinline__ void hist_count(unsigned *hist, R s) {
+  const int b = score_bin<R>(s);
+  if (b < 0) return;
+  atomicAdd(hist + b, 1u);
+  atomicAdd(hist + L0_HIST_FINE + (b >> 4), 1u);
+}
+
+// Called by a whole warp: the ordered image of the smallest bin edge that at
+// least K counted scores lie below, or ~0 when fewer than K were counted.
+// The counts are read while other CTAs add to them; any snapshot undercounts,
+// so the bound it gives is still valid.
+template <typename R>
+__device__ u64 hist_bound(const unsigned *hist, int K) {
+  const int lane = threadIdx.x & 31;
+  const unsigned FULL = 0xffffffffu;
+  unsigned c[8], s = 0u;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    c[i] = __ldcg(hist + L0_HIST_FINE + lane * 8 + i);
+    s += c[i];
+  }
+  unsigned inc = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned t = __shfl_up_sync(FULL, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (__shfl_sync(FULL, inc, 31) < (unsigned)K) return ~0ull;
+  const int lk = __ffs(__ballot_sync(FULL, inc >= (unsigned)K)) - 1;
+  int oct = 0;
+  unsigned before = 0u;
+  if (lane == lk) {
+    unsigned acc = inc - s;
+    bool found = false;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (!found && acc + c[i] >= (unsigned)K) { oct = lane * 8 + i; before = acc; found = true; }
+      if (!found) acc += c[i];
+    }
+  }
+  oct = __shfl_sync(FULL, oct, lk);
+  before = __shfl_sync(FULL, before, lk);
+  unsigned f = (lane < 16) ? __ldcg(hist + oct * 16 + lane) : 0u;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned t = __shfl_up_sync(FULL, f, o);
+    if (lane >= o) f += t;
+  }
+  const unsigned bl = __ballot_sync(FULL, lane < 16 && before + f >= (unsigned)K);
+  // the fine counts may lag the coarse ones: then the octave's top edge
+  const int b = bl ? oct * 16 + __ffs(bl) - 1 : oct * 16 + 15;
+  if (b + 1 >= (int)(0x7f800000u >> 19)) return ~0ull;
+  return ord_of((R)__uint_as_float((unsigned)(b + 1) << 19));
+}
+
 template <typename R>
 struct CtaList {
   R *ls; u64 *lk;   // list [K], sorted ascending
@@ -196,7 +277,10 @@ struct CtaList {
   R *ts; u64 *tk;   // merge temp [K]
   int K, S;
   int *n_list, *n_stage, *ovf;
-  R *thr_s; u64 *thr_k;   // current composite threshold
+  R *thr_s; u64 *thr_k;   // current composite threshold (list K'-th, global cut)
+  R *gcut;                // global score cut, tightened between barriers
+  int *dirty;             // staged since the histogram bound was last taken
+  unsigned *hist;         // the problem's score histogram (tuple kernels only)
 };
 
 // bytes of shared memory a CtaList needs (plus 64 B of scalars)
@@ -222,7 +306,9 @@ __device__ inline CtaList<R> cta_list_carve(unsigned char *&p, int K, int S) {
   L.n_list = (int *)p; p += 4;
   L.n_stage = (int *)p; p += 4;
   L.ovf = (int *)p; p += 4;
-  p += 4;
+  L.dirty = (int *)p; p += 4;
+  L.gcut = (R *)p; p += 8;
+  L.hist = nullptr;
   return L;
 }
 
@@ -234,7 +320,16 @@ __device__ inline void cta_list_reset(CtaList<R> &L, const u64 *gthr) {
     *L.ovf = 0;
     *L.thr_s = gthr ? from_ord<R>(*(volatile const u64 *)gthr) : r_inf<R>();
     *L.thr_k = ~0ull;
+    *L.gcut = *L.thr_s;
+    *L.dirty = 0;
   }
+}
+
+// the score cut in force: a tuple scoring above it cannot be among the best K'
+template <typename R>
+__device__ __forceinline__ R cta_cut(const CtaList<R> &L) {
+  const R a = *(volatile R *)L.thr_s, b = *(volatile R *)L.gcut;
+  return b < a ? b : a;
 }
 
 // composite test against the current threshold, inclusive: the threshold
@@ -260,6 +355,10 @@ __device__ __forceinline__ bool cta_list_push(CtaList<R> &L, R s, u64 k) {
   if (idx < L.S) {
     L.ss[idx] = s;
     L.sk[idx] = k;
+    if (L.hist) {
+      hist_count<R>(L.hist, s);
+      *(volatile int *)L.dirty = 1;
+    }
     return true;
   }
   *(volatile int *)L.ovf = 1;
@@ -364,11 +463,36 @@ __device__ void cta_list_commit(CtaList<R> &L, u64 *gthr) {
     R cs = *L.thr_s;
     u64 ck = *L.thr_k;
     if (cand_less(ts, tk, cs, ck)) { *L.thr_s = ts; *L.thr_k = tk; }
+    if (ts < *L.gcut) *L.gcut = ts;
     *L.n_list = nout;
     *L.n_stage = 0;
     *L.ovf = 0;
   }
   __syncthreads();
+}
+
+// After a step, by warp 0 with no barrier: turn new stagings into a global
+// bound through the histogram and pull the global bound (read at the start
+// of the step, gprev) into the CTA's cut.  Other warps may read the cut
+// meanwhile; both the old and the new value are valid cuts.
+template <typename R>
+__device__ __forceinline__ void cta_step_sync(CtaList<R> &L, u64 *gthr, u64 gprev) {
+  if (threadIdx.x >= 32) return;
+  u64 g = gprev;
+  int dirty = 0;
+  if (threadIdx.x == 0 && L.hist) dirty = atomicExch(L.dirty, 0);
+  dirty = __shfl_sync(0xffffffffu, dirty, 0);
+  if (dirty) {
+    const u64 b = hist_bound<R>(L.hist, L.K);
+    if (threadIdx.x == 0 && b < g) {
+      atomicMin(gthr, b);
+      g = b;
+    }
+  }
+  if (threadIdx.x == 0 && g != ~0ull) {
+    const R gs = from_ord<R>(g);
+    if (gs < *(volatile R *)L.gcut) *(volatile R *)L.gcut = gs;
+  }
 }
 
 // tighten the CTA threshold from the global one (thread 0; barrier after)
@@ -390,6 +514,14 @@ __device__ inline void cta_list_flush(CtaList<R> &L, R *out_s, u64 *out_k,
     out_k[i] = L.lk[i];
   }
   if (threadIdx.x == 0) *out_cnt = n;
+}
+
+// Relaxed GPU-scope load of a word other CTAs update.  The load is issued
+// where it stands and waited for only where its value is first used.
+__device__ __forceinline__ u64 ld_relaxed(const u64 *p) {
+  u64 v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
 }
 
 // --------------------------------------------------------- misc helpers --

@@ -43,6 +43,7 @@ struct TileArgs {
   u64 *item_counter;
   long long item_limit;            // items at or past this index are not processed
   u64 *gthr;                       // [n_probs] ordered score bits
+  unsigned *hist;                  // [n_probs][L0_HIST_WORDS] staged-score counts
   R *out_s; u64 *out_k; int *out_cnt;   // [n_probs][n_slots][K], [n_probs][n_slots]
   int n_slots;
   // FP32 only: runs of tuples redone in FP64: lexicographic rank of the first
@@ -210,7 +211,8 @@ cudaError_t launch_defer(const DeferArgs &a, int groups, int n_probs, cudaStream
 // seed == 0: only the +inf initialisation
 template <typename R>
 cudaError_t launch_seed(const R *G, const ProbDesc *probs_dev, int n_probs, int K, int S,
-                        int seed, double ratio, const Binom &B, u64 *gthr, cudaStream_t st);
+                        int seed, double ratio, const Binom &B, u64 *gthr, unsigned *hist,
+                        cudaStream_t st);
 template <typename R>
 size_t seed_smem_bytes(int K, int S);
 

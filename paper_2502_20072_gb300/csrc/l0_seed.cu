@@ -32,7 +32,7 @@ constexpr int SEED_THREADS = 1024;
 template <typename R>
 __global__ void __launch_bounds__(SEED_THREADS)
 seed_kernel(const R *Gbase, const ProbDesc *probs, int K, int S, int seed, double ratio,
-            Binom B, u64 *gthr) {
+            Binom B, u64 *gthr, unsigned *hist) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int cols[64];
   __shared__ u64 s_total;
@@ -41,6 +41,9 @@ seed_kernel(const R *Gbase, const ProbDesc *probs, int K, int S, int seed, doubl
   const int prob = blockIdx.x;
   const ProbDesc pd = probs[prob];
   if (threadIdx.x == 0) gthr[prob] = ord_inf<R>();
+  if (hist)   // the search's score histogram starts empty
+    for (int i = threadIdx.x; i < L0_HIST_WORDS; i += blockDim.x)
+      hist[(size_t)prob * L0_HIST_WORDS + i] = 0u;
   if (!seed || pd.d < 2) return;
   // smallest M with C(M, d) >= 2 K', at most min(m, 64, K')
   const int Mcap = min(min(pd.m, 64), K);
@@ -155,20 +158,22 @@ size_t seed_smem_bytes(int K, int S) {
 
 template <typename R>
 cudaError_t launch_seed(const R *G, const ProbDesc *probs_dev, int n_probs, int K, int S,
-                        int seed, double ratio, const Binom &B, u64 *gthr, cudaStream_t st) {
+                        int seed, double ratio, const Binom &B, u64 *gthr, unsigned *hist,
+                        cudaStream_t st) {
   const size_t smem = seed_smem_bytes<R>(K, S);
   cudaError_t e =
       cudaFuncSetAttribute(seed_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  seed_kernel<R><<<n_probs, SEED_THREADS, smem, st>>>(G, probs_dev, K, S, seed, ratio, B, gthr);
+  seed_kernel<R><<<n_probs, SEED_THREADS, smem, st>>>(G, probs_dev, K, S, seed, ratio, B, gthr,
+                                                                hist);
   return cudaGetLastError();
 }
 
 template size_t seed_smem_bytes<double>(int, int);
 template size_t seed_smem_bytes<float>(int, int);
 template cudaError_t launch_seed<double>(const double *, const ProbDesc *, int, int, int, int,
-                                         double, const Binom &, u64 *, cudaStream_t);
+                                         double, const Binom &, u64 *, unsigned *, cudaStream_t);
 template cudaError_t launch_seed<float>(const float *, const ProbDesc *, int, int, int, int,
-                                        double, const Binom &, u64 *, cudaStream_t);
+                                        double, const Binom &, u64 *, unsigned *, cudaStream_t);
 
 }  // namespace l0

@@ -50,7 +50,10 @@ __device__ void run_item_shared(const TileArgs<R> &A, const ProbDesc &pd, int pr
   int idx;
   const int col = record_col(c.j0, c.k0, isj, isk, idx);
   const int T = A.shared_T;
+  u64 gnext = ~0ull;   // warp 0: the global bound, read a step before it is used
   for (u64 r = r0; r < r1; ++r) {
+    const u64 gprev = gnext;
+    if (threadIdx.x < 32) gnext = ld_relaxed(gthr);
     R score[UJ][UK];
 #pragma unroll
     for (int u = 0; u < UJ; ++u)
@@ -117,7 +120,7 @@ __device__ void run_item_shared(const TileArgs<R> &A, const ProbDesc &pd, int pr
     // stage the pooled scores that beat the threshold
     unsigned done = 0u;
     for (int pass = 0;; ++pass) {
-      const R ts = *(volatile R *)L.thr_s;
+      const R ts = cta_cut<R>(L);
 #pragma unroll
       for (int u = 0; u < UJ; ++u) {
         const int j = c.j0 + w * UJ + u;
@@ -152,6 +155,7 @@ __device__ void run_item_shared(const TileArgs<R> &A, const ProbDesc &pd, int pr
         break;
       }
     }
+    cta_step_sync<R>(L, gthr, gprev);
     if (DP > 0) colex_next<DP>(pidx);
   }
   cta_list_commit<R>(L, gthr);

@@ -291,8 +291,7 @@ __device__ __noinline__ int slow_tuple(const TileArgs<R> &A, const ItemCtx<R> &c
   }
   const R p = pp + rb.kpt[kk];
   const R rel = rb.jpP[jl] - wn * wn / p;
-  const R ts = *(volatile R *)L.thr_s;
-  if (rel > ts) return 1;
+  if (rel > cta_cut<R>(L)) return 1;
   int t[L0_DMAX];
 #pragma unroll
   for (int q = 0; q < DP; ++q) t[q] = rb.pidx[q];
@@ -499,19 +498,21 @@ __device__ __forceinline__ void run_steps(const TileArgs<R> &A, const ItemCtx<R>
   const bool rec = isj || isk;
   RecRaw<R, DP> raw;
   if (rec) load_raw<R, DP>(c, pidx, col, raw);
-  make_record<R, DP>(c, pidx, raw, isj, isk, idx, col, cdiag, cy, G00, *(volatile R *)L.thr_s,
-                     rbs[0]);
+  make_record<R, DP>(c, pidx, raw, isj, isk, idx, col, cdiag, cy, G00, cta_cut<R>(L), rbs[0]);
   int pn[DPM];   // prefix of step r + 1
 #pragma unroll
   for (int p = 0; p < DPM; ++p) pn[p] = pidx[p];
   if (DP > 0) colex_next<DP>(pn);
   if (rec && r0 + 1 < r1) load_raw<R, DP>(c, pn, col, raw);
   __syncthreads();
+  u64 gnext = ~0ull;   // warp 0: the global bound, read a step before it is used
   for (u64 r = r0; r < r1; ++r) {
     const int buf = (int)((r - r0) & 1ull);
+    const u64 gprev = gnext;
+    if (threadIdx.x < 32) gnext = ld_relaxed(gthr);
     if (r + 1 < r1) {
-      make_record<R, DP>(c, pn, raw, isj, isk, idx, col, cdiag, cy, G00,
-                         *(volatile R *)L.thr_s, rbs[buf ^ 1]);
+      make_record<R, DP>(c, pn, raw, isj, isk, idx, col, cdiag, cy, G00, cta_cut<R>(L),
+                         rbs[buf ^ 1]);
       if (DP > 0) colex_next<DP>(pn);
       if (rec && r + 2 < r1) load_raw<R, DP>(c, pn, col, raw);
     }
@@ -530,6 +531,7 @@ __device__ __forceinline__ void run_steps(const TileArgs<R> &A, const ItemCtx<R>
         break;
       }
     }
+    cta_step_sync<R>(L, gthr, gprev);
   }
   // staged entries are committed by the caller at the end of the item
 }
@@ -569,6 +571,7 @@ __device__ __forceinline__ void persistent_items(const TileArgs<R> &A, RunItem r
       __syncthreads();
       cur = prob;
       if (prob >= 0) cta_list_reset<R>(L, A.gthr + prob);
+      L.hist = (prob >= 0 && A.hist) ? A.hist + (size_t)prob * L0_HIST_WORDS : nullptr;
     } else if (prob >= 0) {
       cta_list_pull_global<R>(L, A.gthr + prob);
     }

@@ -93,7 +93,7 @@ __device__ void run_item(const TileArgs<R> &A, const ProbDesc &pd, int prob, int
 }
 
 template <typename R, int DPLO, int DPHI>
-__global__ void __launch_bounds__(L0_THREADS, sizeof(R) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(L0_THREADS, 1)
 tile_kernel(TileArgs<R> A) {
   persistent_items<R>(A, [&](const ProbDesc &pd, int prob, int bj, int bk, u64 r0, u64 r1,
                              CtaList<R> &L, unsigned char *recbase, u64 *gthr) {
