@@ -91,6 +91,7 @@ typedef struct {
   /* phase times (ms, CUDA events on the handle's stream); 0 when unavailable */
   double ms_prep, ms_gram, ms_tuple, ms_merge, ms_refit, ms_total;
   double ms_tuple_kernel;            /* the tuple kernel alone (last search pass) */
+  int64_t proposal_pairs;            /* pairs the pair-restricted search started from */
 } sisso_l0_stats;
 
 /* Fill *opt with defaults (FP64, PER_TASK, device 0, legacy stream). */
@@ -208,6 +209,86 @@ int sisso_l0_debug_gram(sisso_l0_t h, const double *X, const double *y,
 int sisso_l0_gram_noalloc(const double *X, const double *y, int64_t n_samples,
                           int64_t n_sis, double *out_gram, int64_t ld_out,
                           void *stream);
+
+/* ------------------------------------------------ learned proposals ----
+ * The paper's l0 step scores every n-tuple exhaustively (Sec. 2.4).  The
+ * learned form of the d = 3 search ranks the (d-1)-subsets -- pairs of
+ * features -- with a small network trained on the exhaustive search's own
+ * results, and fits exactly only the triples reachable from the best pairs;
+ * the exhaustive search stays the reference and judges the network's
+ * recall.  Pairs are ranked in colex order: rank(i, j) = j (j - 1) / 2 + i,
+ * i < j.
+ *
+ * Network: 6 -> 256 -> 256 -> 1, ReLU, inputs per pair (i, j) (from the
+ * task's correlation matrix): r_i, r_j (Pearson r, Eq. 1), C_ij = corr(f_i,
+ * f_j), rho_j.i = corr(f_j, residual of y after the fit on f_i), rho_i.j, and
+ * R2_ij of the two-feature fit.  Target: log(min over k of SSE(i, j, k) /
+ * S_yy), clamped to [log 1e-12, 0] (0 when no completion is eligible).
+ * BF16 operands (features, W1, W2, w3, h1, h2 and the back-propagated dh2),
+ * FP32 sums and FP32 master weights; squared-error loss, Adam (beta1 0.9,
+ * beta2 0.999, eps 1e-8).  Parameters, flat FP32, SISSO_L0_SCORER_PARAMS
+ * floats: W1 [256][6] | b1 [256] | W2 [256][256] (row = output unit) |
+ * b2 [256] | w3 [256] | b3.
+ */
+#define SISSO_L0_SCORER_PARAMS 67841
+#define SISSO_L0_PAIR_FEATURES_LD 8   /* floats per feature row (6 used) */
+
+typedef struct sisso_l0_scorer *sisso_l0_scorer_t;
+
+/* New scorer on `device`: He-uniform weights drawn from splitmix64(seed),
+ * zero biases.  The scorer owns its device memory and stream.  Errors:
+ * EINVAL, ENOMEM, ECUDA. */
+int sisso_l0_scorer_create(sisso_l0_scorer_t *out, int32_t device, uint64_t seed);
+void sisso_l0_scorer_destroy(sisso_l0_scorer_t s);   /* NULL-safe, syncs first */
+const char *sisso_l0_scorer_last_error(sisso_l0_scorer_t s);
+
+/* Copy the flat parameter vector in (host or device; resets Adam) or out.
+ * n must be SISSO_L0_SCORER_PARAMS. */
+int sisso_l0_scorer_set_params(sisso_l0_scorer_t s, const float *params, int64_t n);
+int sisso_l0_scorer_get_params(sisso_l0_scorer_t s, float *params, int64_t n);
+
+/* Mean squared error of the network over n_rows rows and its gradient, no
+ * update.  feats: device [n_rows][8], labels: device [n_rows]; loss (1 float)
+ * and grad (SISSO_L0_SCORER_PARAMS floats) may be host or device, or NULL. */
+int sisso_l0_scorer_loss_grad(sisso_l0_scorer_t s, const float *feats, const float *labels,
+                              int64_t n_rows, float *loss, float *grad);
+
+/* `steps` Adam steps with learning rate lr on consecutive windows of
+ * batch_rows rows (wrapping around the data); losses (steps floats, host or
+ * device, or NULL) receive each step's loss before its update. */
+int sisso_l0_scorer_train(sisso_l0_scorer_t s, const float *feats, const float *labels,
+                          int64_t n_rows, int32_t batch_rows, int32_t steps, float lr,
+                          float *losses);
+
+/* Network outputs (predicted log best completion) of n_rows feature rows;
+ * feats and out are device pointers. */
+int sisso_l0_scorer_predict(sisso_l0_scorer_t s, const float *feats, int64_t n_rows, float *out);
+
+/* Training data of one task (single task, mixed precision handle): the
+ * features of every pair in colex order into feats (device,
+ * [C(n_sis, 2)][8]) and, when labels is not NULL, every pair's target
+ * (device, [C(n_sis, 2)]), both from the FP32 tensor-core Gram.  X, y as in
+ * sisso_l0_fit with one task of n_total rows. */
+int sisso_l0_pair_data(sisso_l0_t h, const double *X, const double *y, int64_t n_total,
+                       int64_t n_sis, float *feats, float *labels);
+
+/* Exact d = 3 search over the triples {i, j, k} reachable from a pair list
+ * (host or device, int32 [n_pairs][2], any order within a pair, repeats
+ * allowed), each triple fitted once, then the FP64 re-fit and ranking of
+ * sisso_l0_fit; outputs as sisso_l0_fit with n_dim = 3, one task.  An index
+ * outside [0, n_sis) or i == j gives EINVAL. */
+int sisso_l0_fit_pairs(sisso_l0_t h, const double *X, const double *y, int64_t n_total,
+                       int64_t n_sis, const int32_t *pairs, int64_t n_pairs, int32_t k,
+                       int32_t *out_tuples, double *out_rmse);
+
+/* Learned d = 3 search: the scorer ranks every pair (inference fused with
+ * the features, on the tensor cores), the pairs in the lowest score bins
+ * holding at least ceil(fraction * C(n_sis, 2)) pairs are kept, and the
+ * search of sisso_l0_fit_pairs runs over them.  Mixed-precision, single-task
+ * handle; get_stats reports proposal_pairs and the triples fitted. */
+int sisso_l0_fit_learned(sisso_l0_t h, sisso_l0_scorer_t s, const double *X, const double *y,
+                         int64_t n_total, int64_t n_sis, int32_t k, double fraction,
+                         int32_t *out_tuples, double *out_rmse);
 
 #ifdef __cplusplus
 }

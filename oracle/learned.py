@@ -16,7 +16,8 @@ definition:
   and R2_ij = 1 - SSE(i, j) / S_yy of the two-feature least-squares fit
   (Householder QR through ``oracle.score``);
 * the label of a pair: the best completion, min over k not in {i, j} of
-  SSE(i, j, k) / S_yy over eligible triples, as log(max(., LABEL_FLOOR));
+  SSE(i, j, k) / S_yy over eligible triples, as log(clip(., LABEL_FLOOR, 1))
+  (0 when no completion is eligible: the worst possible fit);
 * a 6-256-256-1 ReLU network whose matrix products take BF16 operands with
   exact (here FP64) accumulation, FP32 master weights, squared-error loss,
   its gradient and an Adam step;
@@ -131,9 +132,9 @@ def best_completion(X, y, pairs=None):
 
 
 def labels(X, y, pairs=None):
-    """log(max(best completion, LABEL_FLOOR)) of each pair."""
+    """log(clip(best completion, LABEL_FLOOR, 1)) of each pair."""
     b = best_completion(X, y, pairs)
-    return np.log(np.maximum(b, LABEL_FLOOR))
+    return np.log(np.clip(b, LABEL_FLOOR, 1.0))
 
 
 # ------------------------------------------------------------ the network --

@@ -69,7 +69,7 @@ class Stats(ctypes.Structure):
                 ("ms_prep", ctypes.c_double), ("ms_gram", ctypes.c_double),
                 ("ms_tuple", ctypes.c_double), ("ms_merge", ctypes.c_double),
                 ("ms_refit", ctypes.c_double), ("ms_total", ctypes.c_double),
-                ("ms_tuple_kernel", ctypes.c_double)]
+                ("ms_tuple_kernel", ctypes.c_double), ("proposal_pairs", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "struct_size"}
@@ -81,7 +81,14 @@ _lock = threading.Lock()
 # entry points declared in include/sisso_l0.h (checked by the tests)
 EXPORTS = ("sisso_l0_default_options", "sisso_l0_create", "sisso_l0_fit", "sisso_l0_fit_multi",
            "sisso_l0_get_stats", "sisso_l0_last_error", "sisso_l0_destroy",
-           "sisso_l0_count_tuples", "sisso_l0_debug_unrank", "sisso_l0_debug_gram")
+           "sisso_l0_count_tuples", "sisso_l0_debug_unrank", "sisso_l0_debug_gram",
+           "sisso_l0_scorer_create", "sisso_l0_scorer_destroy", "sisso_l0_scorer_last_error",
+           "sisso_l0_scorer_set_params", "sisso_l0_scorer_get_params",
+           "sisso_l0_scorer_loss_grad", "sisso_l0_scorer_train", "sisso_l0_scorer_predict",
+           "sisso_l0_pair_data", "sisso_l0_fit_pairs", "sisso_l0_fit_learned")
+
+SCORER_PARAMS = 67841
+PAIR_FEATURES_LD = 8
 
 
 def library_path() -> str:
@@ -115,8 +122,24 @@ def lib():
         L.sisso_l0_debug_unrank.argtypes = [vp, i64, i32, vp, i64, vp]
         L.sisso_l0_debug_gram.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_int64), i32, i64,
                                           i32, vp]
+        fp = ctypes.c_float
+        L.sisso_l0_scorer_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.c_uint64]
+        L.sisso_l0_scorer_destroy.argtypes = [vp]
+        L.sisso_l0_scorer_destroy.restype = None
+        L.sisso_l0_scorer_last_error.argtypes = [vp]
+        L.sisso_l0_scorer_last_error.restype = ctypes.c_char_p
+        L.sisso_l0_scorer_set_params.argtypes = [vp, vp, i64]
+        L.sisso_l0_scorer_get_params.argtypes = [vp, vp, i64]
+        L.sisso_l0_scorer_loss_grad.argtypes = [vp, vp, vp, i64, vp, vp]
+        L.sisso_l0_scorer_train.argtypes = [vp, vp, vp, i64, i32, i32, fp, vp]
+        L.sisso_l0_scorer_predict.argtypes = [vp, vp, i64, vp]
+        L.sisso_l0_pair_data.argtypes = [vp, dp, dp, i64, i64, vp, vp]
+        L.sisso_l0_fit_pairs.argtypes = [vp, dp, dp, i64, i64, vp, i64, i32, vp, vp]
+        L.sisso_l0_fit_learned.argtypes = [vp, vp, dp, dp, i64, i64, i32, ctypes.c_double, vp, vp]
+        no_int = ("sisso_l0_last_error", "sisso_l0_destroy", "sisso_l0_count_tuples",
+                  "sisso_l0_scorer_destroy", "sisso_l0_scorer_last_error")
         for name in EXPORTS:
-            if name not in ("sisso_l0_last_error", "sisso_l0_destroy", "sisso_l0_count_tuples"):
+            if name not in no_int:
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -249,6 +272,59 @@ class Handle:
         self._check(lib().sisso_l0_get_stats(self._h, ctypes.byref(s)))
         return s.as_dict()
 
+    # ----------------------------------------------- learned proposals --
+    def pair_data(self, X, y, labels=True):
+        """Features [C(m,2), 8] and (optionally) labels [C(m,2)] of every pair
+        of one task, as CUDA tensors (mixed-precision handle)."""
+        import torch
+        X = _as_f64(X)
+        y = _as_f64(y)
+        m, n = int(X.shape[0]), int(X.shape[1])
+        npairs = m * (m - 1) // 2
+        dev = torch.device("cuda", self._opt.device)
+        feats = torch.empty((npairs, PAIR_FEATURES_LD), dtype=torch.float32, device=dev)
+        lab = torch.empty(npairs, dtype=torch.float32, device=dev) if labels else None
+        rc = lib().sisso_l0_pair_data(self._h, ctypes.c_void_p(_ptr(X)), ctypes.c_void_p(_ptr(y)),
+                                      n, m, ctypes.c_void_p(feats.data_ptr()),
+                                      ctypes.c_void_p(lab.data_ptr() if lab is not None else 0))
+        self._check(rc)
+        return feats, lab
+
+    def fit_pairs(self, X, y, pairs, k):
+        """Exact d = 3 search over the triples reachable from pairs [P, 2]
+        (one task).  Returns (tuples [k, 3], rmse [k])."""
+        X = _as_f64(X)
+        y = _as_f64(y)
+        m, n = int(X.shape[0]), int(X.shape[1])
+        if hasattr(pairs, "data_ptr"):
+            import torch
+            pairs = pairs.to(torch.int32).contiguous()
+        else:
+            pairs = np.ascontiguousarray(pairs, dtype=np.int32)
+        out_t = np.empty((k, 3), dtype=np.int32)
+        out_r = np.empty(k, dtype=np.float64)
+        rc = lib().sisso_l0_fit_pairs(self._h, ctypes.c_void_p(_ptr(X)), ctypes.c_void_p(_ptr(y)),
+                                      n, m, ctypes.c_void_p(_ptr(pairs)), int(pairs.shape[0]),
+                                      int(k), ctypes.c_void_p(out_t.ctypes.data),
+                                      ctypes.c_void_p(out_r.ctypes.data))
+        self._check(rc)
+        return out_t, out_r
+
+    def fit_learned(self, X, y, scorer, k, fraction=0.01, out_tuples=None, out_rmse=None):
+        """Learned d = 3 search (one task): returns (tuples [k, 3], rmse [k])."""
+        X = _as_f64(X)
+        y = _as_f64(y)
+        m, n = int(X.shape[0]), int(X.shape[1])
+        if out_tuples is None:
+            out_tuples = np.empty((k, 3), dtype=np.int32)
+            out_rmse = np.empty(k, dtype=np.float64)
+        rc = lib().sisso_l0_fit_learned(self._h, scorer._s, ctypes.c_void_p(_ptr(X)),
+                                        ctypes.c_void_p(_ptr(y)), n, m, int(k), float(fraction),
+                                        ctypes.c_void_p(_ptr(out_tuples)),
+                                        ctypes.c_void_p(_ptr(out_rmse)))
+        self._check(rc)
+        return out_tuples, out_rmse
+
     def debug_unrank(self, m, n, ranks):
         ranks = np.ascontiguousarray(ranks, dtype=np.uint64)
         out = np.empty((len(ranks), n), dtype=np.int32)
@@ -276,3 +352,76 @@ def fit(X, y, n_dim, k, offsets=None, **opts):
     """One-shot fit with a temporary handle."""
     with Handle(**opts) as h:
         return h.fit(X, y, n_dim, k, offsets=offsets)
+
+
+class Scorer:
+    """The learned pair scorer (6-256-256-1, BF16 tensor-core kernels)."""
+
+    def __init__(self, device=0, seed=0):
+        L = lib()
+        s = ctypes.c_void_p()
+        rc = L.sisso_l0_scorer_create(ctypes.byref(s), int(device), int(seed) & (2**64 - 1))
+        if rc != OK:
+            raise L0Error(rc, "sisso_l0_scorer_create failed")
+        self._s = s
+        self.device = int(device)
+
+    def close(self):
+        if getattr(self, "_s", None):
+            lib().sisso_l0_scorer_destroy(self._s)
+            self._s = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != OK:
+            msg = lib().sisso_l0_scorer_last_error(self._s)
+            raise L0Error(rc, msg.decode() if msg else "")
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        self._check(lib().sisso_l0_scorer_set_params(self._s, ctypes.c_void_p(flat.ctypes.data),
+                                                     flat.size))
+
+    def get_params(self):
+        out = np.empty(SCORER_PARAMS, dtype=np.float32)
+        self._check(lib().sisso_l0_scorer_get_params(self._s, ctypes.c_void_p(out.ctypes.data),
+                                                     out.size))
+        return out
+
+    def loss_grad(self, feats, labels):
+        """(loss, gradient [SCORER_PARAMS]) over CUDA tensors feats [B, 8], labels [B]."""
+        loss = np.zeros(1, dtype=np.float32)
+        grad = np.empty(SCORER_PARAMS, dtype=np.float32)
+        self._check(lib().sisso_l0_scorer_loss_grad(
+            self._s, ctypes.c_void_p(feats.data_ptr()), ctypes.c_void_p(labels.data_ptr()),
+            int(labels.shape[0]), ctypes.c_void_p(loss.ctypes.data),
+            ctypes.c_void_p(grad.ctypes.data)))
+        return float(loss[0]), grad
+
+    def train(self, feats, labels, batch_rows, steps, lr):
+        """Adam steps on CUDA tensors; returns the per-step losses."""
+        losses = np.zeros(max(1, int(steps)), dtype=np.float32)
+        self._check(lib().sisso_l0_scorer_train(
+            self._s, ctypes.c_void_p(feats.data_ptr()), ctypes.c_void_p(labels.data_ptr()),
+            int(labels.shape[0]), int(batch_rows), int(steps), float(lr),
+            ctypes.c_void_p(losses.ctypes.data)))
+        return losses[:int(steps)]
+
+    def predict(self, feats):
+        import torch
+        out = torch.empty(int(feats.shape[0]), dtype=torch.float32, device=feats.device)
+        self._check(lib().sisso_l0_scorer_predict(self._s, ctypes.c_void_p(feats.data_ptr()),
+                                                  int(feats.shape[0]),
+                                                  ctypes.c_void_p(out.data_ptr())))
+        return out

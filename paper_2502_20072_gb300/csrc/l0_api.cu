@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <new>
 #include <string>
@@ -74,6 +75,7 @@ struct sisso_l0_handle {
   DevBuf scratch, refit, rdiv, cert, out_t, out_r, err;
   DevBuf dfr_key, dfr_len, dfr_n, dfr_cnt;
   DevBuf abf, bbf, kmeta, gram32;
+  DevBuf prop_in, prop_pairs, prop_bits, prop_ctr, sel_hist, sel_bin, scores, diag;
   int binom_m = -1;
   int done_init_for = 0;
   cudaEvent_t ev[8] = {nullptr};
@@ -182,6 +184,13 @@ struct FitPlan {
   bool have_g64 = false;    // FP64 Gram computed (always in FP64 mode)
   unsigned long long fallback_tuples = 0;
   u64 fits_per_pass = 0;    // (task, tuple) fits of one search pass
+  // learned forms (d = 3, one task): the search runs over the triples of a
+  // pair list (proposal); or the call stops after the Gram (prep_only).
+  // after_prep runs once the symmetric Gram and its diagonal exist.
+  int proposal = 0, prep_only = 0;
+  long long n_pairs = 0;
+  u64 prop_fits = 0;
+  std::function<int(sisso_l0_t, FitPlan &)> after_prep;
 };
 
 constexpr int kDeferGroups = 64;
@@ -429,8 +438,11 @@ int search_pass(sisso_l0_t h, FitPlan &P, int K, const R *G) {
   L0_CK(cudaEventRecord(h->ev[2], st), "event");
   {
     const double ratio = P.mixed ? h->opt.fp32_fallback_pivot_ratio : h->opt.rank_deficient_pivot_ratio;
-    L0_CK(l0::launch_seed<R>(G, h->probs.as<l0::ProbDesc>(), n_probs, K, S, P.shared ? 0 : 1,
-                             ratio, B, h->gthr.as<u64>(), h->hist.as<unsigned>(), st),
+    // a proposal search ranks only its reachable triples: no seed bound from
+    // tuples outside them
+    L0_CK(l0::launch_seed<R>(G, h->probs.as<l0::ProbDesc>(), n_probs, K, S,
+                             (P.shared || P.proposal) ? 0 : 1, ratio, B, h->gthr.as<u64>(),
+                             h->hist.as<unsigned>(), st),
           "seed kernel");
   }
   if (P.has_singles) {
@@ -444,10 +456,41 @@ int search_pass(sisso_l0_t h, FitPlan &P, int K, const R *G) {
   if (P.has_tuples) {
     L0_CK(cudaMemsetAsync(h->ctr.p, 0, 8, st), "memset");
     if (P.mixed) L0_CK(cudaMemsetAsync(h->dfr_n.p, 0, 24, st), "memset");
-    l0::TileArgs<R> a = tile_args<R>(h, P, K, S, G, n_slots, P.n_items);
     L0_CK(cudaEventRecord(h->ev_k[0], st), "event");
-    int rc = launch_tuple_kernel<R>(h, P, a);
-    if (rc) return rc;
+    if (P.proposal) {
+      L0_CK(cudaMemsetAsync(h->prop_ctr.p, 0, 16, st), "memset");
+      l0::PropArgs<R> pa{};
+      pa.G = G;
+      pa.ld = P.ld;
+      pa.diag = h->diag.as<R>();
+      pa.m = P.m;
+      pa.pairs = h->prop_pairs.as<int>();
+      pa.n_pairs = P.n_pairs;
+      pa.bits = h->prop_bits.as<unsigned>();
+      pa.pair_ctr = h->prop_ctr.as<u64>();
+      pa.fits = h->prop_ctr.as<u64>() + 1;
+      pa.B = B;
+      pa.total = binom_host(P.m, 3);
+      pa.ratio = P.mixed ? h->opt.fp32_fallback_pivot_ratio : h->opt.rank_deficient_pivot_ratio;
+      pa.mixed = P.mixed;
+      pa.K = K;
+      pa.S = S;
+      pa.gthr = h->gthr.as<u64>();
+      pa.hist = h->hist.as<unsigned>();
+      pa.out_s = h->lists_s.as<R>();
+      pa.out_k = h->lists_k.as<u64>();
+      pa.out_cnt = h->lists_cnt.as<int>();
+      pa.dfr_key = h->dfr_key.as<u64>();
+      pa.dfr_len = h->dfr_len.as<unsigned>();
+      pa.dfr_n = h->dfr_n.as<u64>();
+      pa.dfr_cap = P.mixed ? kDeferCap : 0;
+      pa.err = h->err.as<int>();
+      L0_CK(l0::launch_proposal<R>(pa, P.grid, st), "proposal kernel");
+    } else {
+      l0::TileArgs<R> a = tile_args<R>(h, P, K, S, G, n_slots, P.n_items);
+      int rc = launch_tuple_kernel<R>(h, P, a);
+      if (rc) return rc;
+    }
     L0_CK(cudaEventRecord(h->ev_k[1], st), "event");
     if (P.mixed) {
       // FP64 redo of the near-singular tuples the FP32 kernel queued: the
@@ -552,6 +595,9 @@ int finish_pass(sisso_l0_t h, FitPlan &P, int *certified, double *delta_max, flo
   u64 dfr_stats[3] = {0, 0, 0};
   if (P.mixed && P.has_tuples)
     L0_CK(cudaMemcpyAsync(dfr_stats, h->dfr_n.p, 24, cudaMemcpyDeviceToHost, st), "copy");
+  u64 pfits[2] = {0, 0};
+  if (P.proposal)
+    L0_CK(cudaMemcpyAsync(pfits, h->prop_ctr.p, 16, cudaMemcpyDeviceToHost, st), "copy");
   int host_err = 0;
   L0_CK(cudaMemcpyAsync(&host_err, h->err.p, 4, cudaMemcpyDeviceToHost, st), "copy err");
   int rc = wait_stream(h);
@@ -560,8 +606,10 @@ int finish_pass(sisso_l0_t h, FitPlan &P, int *certified, double *delta_max, flo
   if (host_err == 7)
     return fail(h, SISSO_L0_EUNSUPPORTED,
                 "too many near-singular tuples for the FP32 search; use SISSO_L0_FP64");
+  if (host_err == 11) return fail(h, SISSO_L0_EINVAL, "pair list holds an index outside [0, n_sis) or i == j");
   if (host_err != 0) return fail(h, SISSO_L0_ECUDA, "device error flag " + std::to_string(host_err));
   P.fallback_tuples += dfr_stats[2];
+  P.prop_fits += pfits[1];
   *certified = 1;
   *delta_max = 0;
   for (auto &c : cert) {
@@ -700,7 +748,7 @@ std::string graph_key(sisso_l0_t h, const FitPlan &P, int K) {
 template <typename R>
 int run_pass(sisso_l0_t h, FitPlan &P, int K, const R *G, bool with_prep, bool *replayed) {
   *replayed = false;
-  if (!h->opt.use_graph) {
+  if (!h->opt.use_graph || P.proposal) {
     int rc = with_prep ? prep_pass(h, P) : SISSO_L0_OK;
     if (rc) return rc;
     return search_pass<R>(h, P, K, G);
@@ -733,8 +781,15 @@ int run_pass(sisso_l0_t h, FitPlan &P, int K, const R *G, bool with_prep, bool *
   return SISSO_L0_OK;
 }
 
+// the learned forms' additions to a fit (see FitPlan)
+struct Special {
+  int proposal = 0, prep_only = 0;
+  std::function<int(sisso_l0_t, FitPlan &)> after_prep;
+};
+
 int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *task_offsets,
-                 int32_t n_tasks, int64_t n_sis, const sisso_l0_request *reqs, int32_t n_reqs) {
+                 int32_t n_tasks, int64_t n_sis, const sisso_l0_request *reqs, int32_t n_reqs,
+                 const Special *sp = nullptr) {
   if (!X || !y || !task_offsets || !reqs) return fail(h, SISSO_L0_EINVAL, "null pointer argument");
   if (n_tasks < 1) return fail(h, SISSO_L0_EINVAL, "n_tasks must be >= 1");
   if (n_reqs < 1) return fail(h, SISSO_L0_EINVAL, "at least one request");
@@ -749,6 +804,11 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
   P.shared = (h->opt.task_mode == SISSO_L0_SHARED) ? 1 : 0;
   P.mixed = (h->opt.precision == SISSO_L0_MIXED_BF16X3) ? 1 : 0;
   P.n_out = P.shared ? 1 : n_tasks;
+  if (sp) {
+    P.proposal = sp->proposal;
+    P.prep_only = sp->prep_only;
+    P.after_prep = sp->after_prep;
+  }
   int kmax = 0;
   for (int q = 0; q < n_reqs; ++q) {
     const sisso_l0_request &r = reqs[q];
@@ -856,8 +916,17 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
           "copy");
     L0_CK(h->gram32.ensure((size_t)n_tasks * P.gstride * 4), "alloc Gram");
   }
-  // persistent grid of the tuple kernel
-  if (P.has_tuples) {
+  // persistent grid of the tuple kernel (or of the proposal search)
+  if (P.has_tuples && P.proposal) {
+    int bps = 0;
+    const int S0 = staging_for(Kmax);
+    cudaError_t e = P.mixed ? l0::proposal_occupancy<float>(Kmax, S0, &bps)
+                            : l0::proposal_occupancy<double>(Kmax, S0, &bps);
+    if (e != cudaSuccess) return cuda_fail(h, e, "proposal occupancy");
+    if (bps < 1) return fail(h, SISSO_L0_EUNSUPPORTED, "proposal kernel does not fit on an SM");
+    P.max_bps = bps;
+    P.grid = h->n_sm * bps;
+  } else if (P.has_tuples) {
     int bps = 0;
     rc = P.mixed ? tile_bps<float>(h, P, Kmax, &bps) : tile_bps<double>(h, P, Kmax, &bps);
     if (rc) return rc;
@@ -873,7 +942,35 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
   bool prep_done = false;
   h->stats.tuned_items_factor = 0;
   h->stats.tuned_ctas_per_sm = 0;
-  if (h->opt.autotune && P.has_tuples) {
+  if (P.proposal || P.prep_only) {
+    // the learned forms: Gram, its symmetric copy, then the pair list (or
+    // the pair data) before any search
+    rc = prep_pass(h, P);
+    if (rc) return rc;
+    prep_done = true;
+    if (P.mixed) {
+      L0_CK(h->diag.ensure((size_t)m * 4), "alloc diagonal");
+      L0_CK(l0::launch_gram_mirror<float>(h->gram32.as<float>(), P.ld, m + 1, h->diag.as<float>(), st),
+            "mirror kernel");
+    } else {
+      L0_CK(h->diag.ensure((size_t)m * 8), "alloc diagonal");
+      L0_CK(l0::launch_gram_mirror<double>(h->gram.as<double>(), P.ld, m + 1, h->diag.as<double>(), st),
+            "mirror kernel");
+    }
+    if (P.after_prep) {
+      rc = P.after_prep(h, P);
+      if (rc) return rc;
+    }
+    if (P.prep_only) {
+      int host_err = 0;
+      L0_CK(cudaMemcpyAsync(&host_err, h->err.p, 4, cudaMemcpyDeviceToHost, st), "copy err");
+      rc = wait_stream(h);
+      if (rc) return rc;
+      if (host_err == 5) return fail(h, SISSO_L0_ENONFINITE, "NaN or Inf in X or y");
+      if (host_err != 0) return fail(h, SISSO_L0_ECUDA, "device error flag " + std::to_string(host_err));
+      return SISSO_L0_OK;
+    }
+  } else if (h->opt.autotune && P.has_tuples) {
     rc = prep_pass(h, P);
     if (rc) return rc;
     prep_done = true;
@@ -928,7 +1025,8 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
   S.candidate_pool = K;
   S.pool_enlargements = enl;
   S.certified = certified;
-  S.tuple_fits = P.fits_per_pass * (u64)(enl + 1);
+  S.tuple_fits = P.proposal ? P.prop_fits : P.fits_per_pass * (u64)(enl + 1);
+  S.proposal_pairs = P.proposal ? P.n_pairs : 0;
   S.max_pool_rel_error = delta;
   S.fp64_fallback_tuples = P.fallback_tuples;
   // centring + Gram, then per pass: seed, singles?, tuple, redo (mixed: gated
@@ -1059,7 +1157,9 @@ void sisso_l0_destroy(sisso_l0_t h) {
                     &h->lists_cnt, &h->part_s, &h->part_k, &h->part_cnt, &h->done, &h->pool_s,
                     &h->pool_k, &h->pool_cnt, &h->scratch, &h->refit, &h->rdiv,
                     &h->cert, &h->out_t, &h->out_r, &h->err, &h->dfr_key, &h->dfr_len, &h->dfr_n,
-                    &h->dfr_cnt, &h->abf, &h->bbf, &h->kmeta, &h->gram32};
+                    &h->dfr_cnt, &h->abf, &h->bbf, &h->kmeta, &h->gram32, &h->prop_in,
+                    &h->prop_pairs, &h->prop_bits, &h->prop_ctr, &h->sel_hist, &h->sel_bin,
+                    &h->scores, &h->diag};
   for (DevBuf *b : bufs) b->release();
   for (int i = 0; i < 8; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
@@ -1146,6 +1246,369 @@ int sisso_l0_debug_gram(sisso_l0_t h, const double *X, const double *y, const in
   DevBuf *bufs[] = {&xd, &yd, &od, &mu, &is, &w, &g, &err};
   for (DevBuf *b : bufs) b->release();
   return rc;
+}
+
+}  // extern "C"
+
+// ====================================================== learned proposals ==
+// The pair scorer (a 6-256-256-1 network, kernels in l0_mlp.cu) and the
+// pair-restricted d = 3 search (l0_pairs.cu).
+
+struct sisso_l0_scorer {
+  int device = 0;
+  int n_sm = 0;
+  cudaStream_t st = nullptr;
+  DevBuf params, m1, m2, w2b, w2tb, partial, grad, loss, err;
+  int t = 0;   // Adam steps taken
+  std::string last_error;
+};
+
+namespace {
+
+int sfail(sisso_l0_scorer_t s, int code, const std::string &m) {
+  if (s) s->last_error = m;
+  return code;
+}
+int scuda(sisso_l0_scorer_t s, cudaError_t e, const char *where) {
+  return sfail(s, (e == cudaErrorMemoryAllocation) ? SISSO_L0_ENOMEM : SISSO_L0_ECUDA,
+               std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define SC_CK(call, where)                                \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return scuda(s, e_, where);    \
+  } while (0)
+
+// BF16 copies of W2 / W2^T from the master weights (no step)
+int scorer_refresh(sisso_l0_scorer_t s) {
+  SC_CK(l0::launch_mlp_adam(s->params.as<float>(), s->m1.as<float>(), s->m2.as<float>(),
+                            s->partial.as<float>(), 0, 0.f, 1, 0, nullptr, nullptr, s->w2b.p,
+                            s->w2tb.p, s->st),
+        "adam kernel");
+  return SISSO_L0_OK;
+}
+
+int scorer_sync(sisso_l0_scorer_t s) {
+  int herr = 0;
+  SC_CK(cudaMemcpyAsync(&herr, s->err.p, 4, cudaMemcpyDeviceToHost, s->st), "copy");
+  SC_CK(cudaStreamSynchronize(s->st), "scorer stream");
+  if (herr != 0) return sfail(s, SISSO_L0_ECUDA, "device error flag " + std::to_string(herr));
+  return SISSO_L0_OK;
+}
+
+// splitmix64 (Steele, Lea and Flood, 2014): the weights' initial draw
+u64 splitmix64(u64 &x) {
+  u64 z = (x += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+int train_rows(sisso_l0_scorer_t s, const float *feats, const float *labels, long long row0,
+               long long n, float lr, int do_step, float *loss_dev) {
+  const int grid = (int)((n + 127) / 128);
+  SC_CK(s->partial.ensure((size_t)grid * l0::MLP_PSTRIDE * 4), "alloc partial gradients");
+  l0::MlpArgs a{};
+  a.params = s->params.as<float>();
+  a.feats = feats;
+  a.label = labels;
+  a.row0 = row0;
+  a.n_rows = n;
+  a.partial = s->partial.as<float>();
+  a.inv_B = 1.0 / (double)n;
+  a.err = s->err.as<int>();
+  SC_CK(l0::launch_mlp(l0::MLP_TRAIN, a, s->w2b.p, s->w2tb.p, grid, s->st), "mlp kernel");
+  if (do_step) ++s->t;
+  SC_CK(l0::launch_mlp_adam(s->params.as<float>(), s->m1.as<float>(), s->m2.as<float>(),
+                            s->partial.as<float>(), grid, lr, std::max(1, s->t), do_step,
+                            s->grad.as<float>(), loss_dev, s->w2b.p, s->w2tb.p, s->st),
+        "adam kernel");
+  return SISSO_L0_OK;
+}
+
+// single-task inputs for the learned forms
+int check_single(sisso_l0_t h, const double *X, const double *y, int64_t n_total, int64_t n_sis,
+                 int need_m) {
+  if (!X || !y) return fail(h, SISSO_L0_EINVAL, "null pointer argument");
+  if (n_sis < need_m) return fail(h, SISSO_L0_EINVAL, "n_sis too small");
+  if (n_total < 5) return fail(h, SISSO_L0_EINVAL, "n_total must be >= 5 (d + 2)");
+  if (n_sis > 65535) return fail(h, SISSO_L0_EUNSUPPORTED, "n_sis above 65535 for pair ranks");
+  return SISSO_L0_OK;
+}
+
+template <typename F>
+int guarded(sisso_l0_t h, F f) {
+  if (!h) return SISSO_L0_EINVAL;
+  try {
+    cudaError_t e = cudaSetDevice(h->opt.device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set device");
+    return f();
+  } catch (const std::bad_alloc &) {
+    return fail(h, SISSO_L0_ENOMEM, "host allocation failed");
+  } catch (...) {
+    return fail(h, SISSO_L0_ECUDA, "unexpected host exception");
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int sisso_l0_scorer_create(sisso_l0_scorer_t *out, int32_t device, uint64_t seed) {
+  if (!out) return SISSO_L0_EINVAL;
+  *out = nullptr;
+  sisso_l0_scorer *s = new (std::nothrow) sisso_l0_scorer();
+  if (!s) return SISSO_L0_ENOMEM;
+  s->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+  const size_t pb = (size_t)l0::MLP_N_PARAMS * 4;
+  if (e == cudaSuccess) e = s->params.ensure(pb);
+  if (e == cudaSuccess) e = s->m1.ensure(pb);
+  if (e == cudaSuccess) e = s->m2.ensure(pb);
+  if (e == cudaSuccess) e = s->grad.ensure(pb);
+  if (e == cudaSuccess) e = s->w2b.ensure((size_t)l0::MLP_NH * l0::MLP_NH * 2);
+  if (e == cudaSuccess) e = s->w2tb.ensure((size_t)l0::MLP_NH * l0::MLP_NH * 2);
+  if (e == cudaSuccess) e = s->partial.ensure((size_t)l0::MLP_PSTRIDE * 4);
+  if (e == cudaSuccess) e = s->loss.ensure(4096 * 4);
+  if (e == cudaSuccess) e = s->err.ensure(16);
+  if (e != cudaSuccess) {
+    sisso_l0_scorer_destroy(s);
+    return (e == cudaErrorMemoryAllocation) ? SISSO_L0_ENOMEM : SISSO_L0_ECUDA;
+  }
+  // He-uniform weights (bound sqrt(6 / fan_in)), zero biases
+  std::vector<float> w(l0::MLP_N_PARAMS, 0.f);
+  u64 st = seed;
+  auto uni = [&](double bound) {
+    const double u = (double)(splitmix64(st) >> 11) * (1.0 / 9007199254740992.0);
+    return (float)((2.0 * u - 1.0) * bound);
+  };
+  for (int q = 0; q < l0::MLP_NH * l0::MLP_NIN; ++q) w[l0::MLP_OFF_W1 + q] = uni(std::sqrt(6.0 / l0::MLP_NIN));
+  for (int q = 0; q < l0::MLP_NH * l0::MLP_NH; ++q) w[l0::MLP_OFF_W2 + q] = uni(std::sqrt(6.0 / l0::MLP_NH));
+  for (int q = 0; q < l0::MLP_NH; ++q) w[l0::MLP_OFF_W3 + q] = uni(std::sqrt(6.0 / l0::MLP_NH));
+  int rc = sisso_l0_scorer_set_params(s, w.data(), l0::MLP_N_PARAMS);
+  if (rc) {
+    sisso_l0_scorer_destroy(s);
+    return rc;
+  }
+  *out = s;
+  return SISSO_L0_OK;
+}
+
+void sisso_l0_scorer_destroy(sisso_l0_scorer_t s) {
+  if (!s) return;
+  cudaSetDevice(s->device);
+  if (s->st) cudaStreamSynchronize(s->st);
+  DevBuf *bufs[] = {&s->params, &s->m1, &s->m2, &s->w2b, &s->w2tb, &s->partial, &s->grad,
+                    &s->loss, &s->err};
+  for (DevBuf *b : bufs) b->release();
+  if (s->st) cudaStreamDestroy(s->st);
+  delete s;
+}
+
+const char *sisso_l0_scorer_last_error(sisso_l0_scorer_t s) {
+  return s ? s->last_error.c_str() : kNullHandleMsg;
+}
+
+int sisso_l0_scorer_set_params(sisso_l0_scorer_t s, const float *params, int64_t n) {
+  if (!s || !params) return SISSO_L0_EINVAL;
+  if (n != l0::MLP_N_PARAMS) return sfail(s, SISSO_L0_EINVAL, "parameter count");
+  SC_CK(cudaSetDevice(s->device), "set device");
+  SC_CK(cudaMemcpyAsync(s->params.p, params, (size_t)n * 4, cudaMemcpyDefault, s->st), "copy");
+  SC_CK(cudaMemsetAsync(s->m1.p, 0, (size_t)n * 4, s->st), "memset");
+  SC_CK(cudaMemsetAsync(s->m2.p, 0, (size_t)n * 4, s->st), "memset");
+  SC_CK(cudaMemsetAsync(s->err.p, 0, 16, s->st), "memset");
+  s->t = 0;
+  int rc = scorer_refresh(s);
+  if (rc) return rc;
+  return scorer_sync(s);
+}
+
+int sisso_l0_scorer_get_params(sisso_l0_scorer_t s, float *params, int64_t n) {
+  if (!s || !params) return SISSO_L0_EINVAL;
+  if (n != l0::MLP_N_PARAMS) return sfail(s, SISSO_L0_EINVAL, "parameter count");
+  SC_CK(cudaSetDevice(s->device), "set device");
+  SC_CK(cudaMemcpyAsync(params, s->params.p, (size_t)n * 4, cudaMemcpyDefault, s->st), "copy");
+  return scorer_sync(s);
+}
+
+int sisso_l0_scorer_loss_grad(sisso_l0_scorer_t s, const float *feats, const float *labels,
+                              int64_t n_rows, float *loss, float *grad) {
+  if (!s || !feats || !labels || n_rows < 1) return SISSO_L0_EINVAL;
+  if (!is_device_ptr(feats) || !is_device_ptr(labels))
+    return sfail(s, SISSO_L0_EINVAL, "features and labels must be device pointers");
+  SC_CK(cudaSetDevice(s->device), "set device");
+  SC_CK(cudaMemsetAsync(s->err.p, 0, 16, s->st), "memset");
+  int rc = train_rows(s, feats, labels, 0, n_rows, 0.f, 0, s->loss.as<float>());
+  if (rc) return rc;
+  if (loss) SC_CK(cudaMemcpyAsync(loss, s->loss.p, 4, cudaMemcpyDefault, s->st), "copy");
+  if (grad)
+    SC_CK(cudaMemcpyAsync(grad, s->grad.p, (size_t)l0::MLP_N_PARAMS * 4, cudaMemcpyDefault, s->st),
+          "copy");
+  return scorer_sync(s);
+}
+
+int sisso_l0_scorer_train(sisso_l0_scorer_t s, const float *feats, const float *labels,
+                          int64_t n_rows, int32_t batch_rows, int32_t steps, float lr,
+                          float *losses) {
+  if (!s || !feats || !labels || n_rows < 1 || batch_rows < 1 || steps < 0 || !(lr >= 0.f))
+    return SISSO_L0_EINVAL;
+  if (!is_device_ptr(feats) || !is_device_ptr(labels))
+    return sfail(s, SISSO_L0_EINVAL, "features and labels must be device pointers");
+  SC_CK(cudaSetDevice(s->device), "set device");
+  SC_CK(cudaMemsetAsync(s->err.p, 0, 16, s->st), "memset");
+  SC_CK(s->loss.ensure((size_t)std::max(1, steps) * 4), "alloc");
+  long long row0 = 0;
+  for (int q = 0; q < steps; ++q) {
+    if (row0 >= n_rows) row0 = 0;
+    const long long n = std::min<long long>(batch_rows, n_rows - row0);
+    int rc = train_rows(s, feats, labels, row0, n, lr, 1, s->loss.as<float>() + q);
+    if (rc) return rc;
+    row0 += n;
+  }
+  if (losses && steps > 0)
+    SC_CK(cudaMemcpyAsync(losses, s->loss.p, (size_t)steps * 4, cudaMemcpyDefault, s->st), "copy");
+  return scorer_sync(s);
+}
+
+int sisso_l0_scorer_predict(sisso_l0_scorer_t s, const float *feats, int64_t n_rows, float *out) {
+  if (!s || !feats || !out || n_rows < 1) return SISSO_L0_EINVAL;
+  if (!is_device_ptr(feats) || !is_device_ptr(out))
+    return sfail(s, SISSO_L0_EINVAL, "features and output must be device pointers");
+  SC_CK(cudaSetDevice(s->device), "set device");
+  SC_CK(cudaMemsetAsync(s->err.p, 0, 16, s->st), "memset");
+  l0::MlpArgs a{};
+  a.params = s->params.as<float>();
+  a.feats = feats;
+  a.n_rows = n_rows;
+  a.out = out;
+  a.err = s->err.as<int>();
+  const int grid = (int)std::min<long long>((n_rows + 127) / 128, s->n_sm);
+  SC_CK(l0::launch_mlp(l0::MLP_INFER_FEATS, a, s->w2b.p, s->w2tb.p, grid, s->st), "mlp kernel");
+  return scorer_sync(s);
+}
+
+int sisso_l0_pair_data(sisso_l0_t h, const double *X, const double *y, int64_t n_total,
+                       int64_t n_sis, float *feats, float *labels) {
+  return guarded(h, [&]() -> int {
+    int rc = check_single(h, X, y, n_total, n_sis, 3);
+    if (rc) return rc;
+    if (!feats) return fail(h, SISSO_L0_EINVAL, "null output pointer");
+    if (h->opt.precision != SISSO_L0_MIXED_BF16X3)
+      return fail(h, SISSO_L0_EUNSUPPORTED, "pair data come from the FP32 (mixed-precision) Gram");
+    if (!is_device_ptr(feats) || (labels && !is_device_ptr(labels)))
+      return fail(h, SISSO_L0_EINVAL, "outputs must be device pointers");
+    const int64_t off[2] = {0, n_total};
+    int32_t dt[2];
+    double dr;
+    sisso_l0_request r{2, 1, dt, &dr};
+    Special sp;
+    sp.prep_only = 1;
+    sp.after_prep = [&](sisso_l0_t hh, FitPlan &P) -> int {
+      sisso_l0_t h = hh;
+      const long long np = (long long)P.m * (P.m - 1) / 2;
+      L0_CK(l0::launch_pair_features(h->gram32.as<float>(), P.ld, 0, np, feats, h->st),
+            "pair features kernel");
+      if (labels)
+        L0_CK(l0::launch_pair_best(h->gram32.as<float>(), P.ld, h->diag.as<float>(), P.m, np,
+                                   h->opt.fp32_fallback_pivot_ratio, 1e-12f, labels, h->st),
+              "pair label kernel");
+      return SISSO_L0_OK;
+    };
+    return fit_requests(h, X, y, off, 1, n_sis, &r, 1, &sp);
+  });
+}
+
+int sisso_l0_fit_pairs(sisso_l0_t h, const double *X, const double *y, int64_t n_total,
+                       int64_t n_sis, const int32_t *pairs, int64_t n_pairs, int32_t k,
+                       int32_t *out_tuples, double *out_rmse) {
+  return guarded(h, [&]() -> int {
+    int rc = check_single(h, X, y, n_total, n_sis, 3);
+    if (rc) return rc;
+    if (!pairs || n_pairs < 1) return fail(h, SISSO_L0_EINVAL, "empty pair list");
+    if (h->opt.task_mode != SISSO_L0_PER_TASK)
+      return fail(h, SISSO_L0_EUNSUPPORTED, "pair-restricted search is single-task");
+    const int64_t off[2] = {0, n_total};
+    sisso_l0_request r{3, k, out_tuples, out_rmse};
+    Special sp;
+    sp.proposal = 1;
+    sp.after_prep = [&](sisso_l0_t hh, FitPlan &P) -> int {
+      sisso_l0_t h = hh;
+      const long long np = (long long)P.m * (P.m - 1) / 2;
+      L0_CK(h->prop_pairs.ensure((size_t)n_pairs * 8), "alloc pairs");
+      L0_CK(h->prop_bits.ensure((size_t)((np + 31) / 32) * 4), "alloc pair bitmap");
+      L0_CK(h->prop_ctr.ensure(32), "alloc");
+      const int *src = pairs;
+      if (!is_device_ptr(pairs)) {
+        L0_CK(h->prop_in.ensure((size_t)n_pairs * 8), "alloc pairs");
+        L0_CK(cudaMemcpyAsync(h->prop_in.p, pairs, (size_t)n_pairs * 8, cudaMemcpyHostToDevice,
+                              h->st), "copy pairs");
+        src = h->prop_in.as<int>();
+      }
+      L0_CK(l0::launch_pairs_from_list(src, n_pairs, P.m, h->prop_pairs.as<int>(),
+                                       h->prop_bits.as<unsigned>(), h->err.as<int>(), h->st),
+            "pair list kernel");
+      P.n_pairs = n_pairs;
+      return SISSO_L0_OK;
+    };
+    return fit_requests(h, X, y, off, 1, n_sis, &r, 1, &sp);
+  });
+}
+
+int sisso_l0_fit_learned(sisso_l0_t h, sisso_l0_scorer_t s, const double *X, const double *y,
+                         int64_t n_total, int64_t n_sis, int32_t k, double fraction,
+                         int32_t *out_tuples, double *out_rmse) {
+  return guarded(h, [&]() -> int {
+    int rc = check_single(h, X, y, n_total, n_sis, 3);
+    if (rc) return rc;
+    if (!s) return fail(h, SISSO_L0_EINVAL, "null scorer");
+    if (s->device != h->opt.device) return fail(h, SISSO_L0_EINVAL, "scorer on another device");
+    if (!(fraction > 0.0) || fraction > 1.0) return fail(h, SISSO_L0_EINVAL, "fraction in (0, 1]");
+    if (h->opt.precision != SISSO_L0_MIXED_BF16X3)
+      return fail(h, SISSO_L0_EUNSUPPORTED, "the scorer reads the FP32 (mixed-precision) Gram");
+    if (h->opt.task_mode != SISSO_L0_PER_TASK)
+      return fail(h, SISSO_L0_EUNSUPPORTED, "learned search is single-task");
+    L0_CK(cudaStreamSynchronize(s->st), "scorer stream");
+    const int64_t off[2] = {0, n_total};
+    sisso_l0_request r{3, k, out_tuples, out_rmse};
+    Special sp;
+    sp.proposal = 1;
+    sp.after_prep = [&](sisso_l0_t hh, FitPlan &P) -> int {
+      sisso_l0_t h = hh;
+      cudaStream_t st = h->st;
+      const long long np = (long long)P.m * (P.m - 1) / 2;
+      L0_CK(h->scores.ensure((size_t)np * 4), "alloc scores");
+      L0_CK(h->prop_pairs.ensure((size_t)np * 8), "alloc pairs");
+      L0_CK(h->prop_bits.ensure((size_t)((np + 31) / 32) * 4), "alloc pair bitmap");
+      L0_CK(h->prop_ctr.ensure(32), "alloc");
+      L0_CK(h->sel_hist.ensure((size_t)4 << 20), "alloc");
+      L0_CK(h->sel_bin.ensure(16), "alloc");
+      l0::MlpArgs a{};
+      a.params = s->params.as<float>();
+      a.row0 = 0;
+      a.n_rows = np;
+      a.G = h->gram32.as<float>();
+      a.ld = P.ld;
+      a.out = h->scores.as<float>();
+      a.err = h->err.as<int>();
+      const int grid = (int)std::min<long long>((np + 127) / 128, h->n_sm);
+      L0_CK(l0::launch_mlp(l0::MLP_INFER_GRAM, a, s->w2b.p, s->w2tb.p, grid, st), "mlp kernel");
+      const long long want = std::max<long long>(1, (long long)std::ceil(fraction * (double)np));
+      L0_CK(l0::launch_select_pairs(h->scores.as<float>(), np, want, h->sel_hist.as<unsigned>(),
+                                    h->sel_bin.as<unsigned>(), h->prop_pairs.as<int>(),
+                                    h->prop_ctr.as<unsigned long long>() + 2,
+                                    h->prop_bits.as<unsigned>(), st),
+            "pair selection");
+      u64 cnt = 0;
+      L0_CK(cudaMemcpyAsync(&cnt, h->prop_ctr.as<u64>() + 2, 8, cudaMemcpyDeviceToHost, st), "copy");
+      int rc2 = wait_stream(h);
+      if (rc2) return rc2;
+      P.n_pairs = (long long)cnt;
+      return SISSO_L0_OK;
+    };
+    return fit_requests(h, X, y, off, 1, n_sis, &r, 1, &sp);
+  });
 }
 
 }  // extern "C"

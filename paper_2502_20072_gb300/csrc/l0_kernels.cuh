@@ -216,6 +216,105 @@ cudaError_t launch_seed(const R *G, const ProbDesc *probs_dev, int n_probs, int 
 template <typename R>
 size_t seed_smem_bytes(int K, int S);
 
+// ------------------------------------------------ learned pair scorer --
+// 6-256-256-1 ReLU network; flat FP32 parameter vector
+// [W1 (256 x 6) | b1 | W2 (256 x 256, row = output unit) | b2 | w3 | b3]
+constexpr int MLP_NIN = 6, MLP_NH = 256;
+constexpr int MLP_OFF_W1 = 0;
+constexpr int MLP_OFF_B1 = MLP_OFF_W1 + MLP_NH * MLP_NIN;
+constexpr int MLP_OFF_W2 = MLP_OFF_B1 + MLP_NH;
+constexpr int MLP_OFF_B2 = MLP_OFF_W2 + MLP_NH * MLP_NH;
+constexpr int MLP_OFF_W3 = MLP_OFF_B2 + MLP_NH;
+constexpr int MLP_OFF_B3 = MLP_OFF_W3 + MLP_NH;
+constexpr int MLP_N_PARAMS = MLP_OFF_B3 + 1;
+constexpr int MLP_PSTRIDE = (MLP_N_PARAMS + 1 + 3) / 4 * 4;   // partial gradients + loss
+constexpr int MLP_FEAT_LD = 8;                                 // floats per feature row
+enum { MLP_INFER_FEATS = 0, MLP_INFER_GRAM = 1, MLP_TRAIN = 2 };
+
+struct MlpArgs {
+  const float *params;          // FP32 master parameters
+  const float *feats;           // [rows][MLP_FEAT_LD] (INFER_FEATS, TRAIN)
+  const float *label;           // [rows] (TRAIN)
+  long long row0, n_rows;       // rows [row0, row0 + n_rows); pair ranks in INFER_GRAM
+  const float *G;               // FP32 augmented Gram (INFER_GRAM)
+  long long ld;
+  float *out;                   // [n_rows] network outputs (INFER_*)
+  float *partial;               // [grid][MLP_PSTRIDE] partial gradients (TRAIN)
+  double inv_B;                 // 1 / rows of the training step
+  int *err;
+};
+size_t mlp_smem_bytes(int mode);
+cudaError_t launch_mlp(int mode, const MlpArgs &a, const void *W2b, const void *W2Tb, int grid,
+                       cudaStream_t st);
+cudaError_t launch_mlp_adam(float *params, float *m1, float *m2, const float *partial,
+                            int n_parts, float lr, int t, int do_step, float *grad_out,
+                            float *loss_out, void *W2b, void *W2Tb, cudaStream_t st);
+
+// Features of the pair i < j from the augmented correlation Gram (target at
+// index 0, upper triangle): r_i, r_j (Pearson r, Eq. 1), C_ij, the
+// correlations rho_j.i, rho_i.j of each column with the residual of the
+// one-feature fit on the other, and the two-feature R^2.
+__device__ __forceinline__ void pair_feature_vec(const float *G, long long ld, int i, int j,
+                                                 float *x) {
+  const float g00 = G[0];
+  const float gii = G[(long long)(i + 1) * ld + i + 1], gjj = G[(long long)(j + 1) * ld + j + 1];
+  const float gij = G[(long long)(i + 1) * ld + j + 1];
+  const float ri = G[i + 1] * rsqrtf(fmaxf(g00 * gii, 1e-30f));
+  const float rj = G[j + 1] * rsqrtf(fmaxf(g00 * gjj, 1e-30f));
+  const float c = gij * rsqrtf(fmaxf(gii * gjj, 1e-30f));
+  const float ei = fmaxf(1.f - ri * ri, 1e-12f), ej = fmaxf(1.f - rj * rj, 1e-12f);
+  const float dc = 1.f - c * c;
+  x[0] = ri;
+  x[1] = rj;
+  x[2] = c;
+  x[3] = (rj - c * ri) * rsqrtf(ei);
+  x[4] = (ri - c * rj) * rsqrtf(ej);
+  x[5] = dc > 1e-6f ? fminf(fmaxf((ri * ri + rj * rj - 2.f * ri * rj * c) / dc, 0.f), 1.f)
+                    : fmaxf(ri * ri, rj * rj);
+}
+
+// symmetric copy of an upper-triangular Gram (lower triangle filled) and
+// its diagonal in a contiguous array
+template <typename T>
+cudaError_t launch_gram_mirror(T *G, long long ld, int mp1, T *diag, cudaStream_t st);
+// features [n][MLP_FEAT_LD] of the pairs with colex ranks [p0, p0 + n)
+cudaError_t launch_pair_features(const float *G, long long ld, long long p0, long long n,
+                                 float *feats, cudaStream_t st);
+// per pair: log(clamp(min over k of SSE(i, j, k) / S_yy, floor, 1)) over the
+// eligible completions, from the mirrored FP32 Gram
+cudaError_t launch_pair_best(const float *G, long long ld, const float *diag, int m,
+                             long long n_pairs, double ratio, float floor_, float *label,
+                             cudaStream_t st);
+// top pairs by network score: all pairs whose score falls in the lowest
+// histogram bins holding at least `want` pairs; writes their (i, j) and a
+// bitmap over colex pair ranks; counter[0] = pairs written
+cudaError_t launch_select_pairs(const float *score, long long n_pairs, long long want,
+                                unsigned *hist, unsigned *bin_out, int *pairs,
+                                unsigned long long *counter, unsigned *bits, cudaStream_t st);
+// bitmap and canonical copy of an explicit pair list
+cudaError_t launch_pairs_from_list(const int *in, long long n, int m, int *pairs, unsigned *bits,
+                                   int *err, cudaStream_t st);
+
+template <typename R>
+struct PropArgs {
+  const R *G; long long ld; const R *diag; int m;
+  const int *pairs; long long n_pairs; const unsigned *bits;
+  u64 *pair_ctr; u64 *fits;
+  Binom B; u64 total;
+  double ratio; int mixed;
+  int K, S;
+  u64 *gthr; unsigned *hist;
+  R *out_s; u64 *out_k; int *out_cnt;
+  u64 *dfr_key; unsigned *dfr_len; u64 *dfr_n; long long dfr_cap;
+  int *err;
+};
+template <typename R>
+size_t proposal_smem_bytes(int K, int S);
+template <typename R>
+cudaError_t proposal_occupancy(int K, int S, int *blocks_per_sm);
+template <typename R>
+cudaError_t launch_proposal(const PropArgs<R> &a, int grid, cudaStream_t st);
+
 cudaError_t launch_unrank(const Binom &B, int m, int d, u64 total,
                           const u64 *ranks, long long count, int *tuples,
                           cudaStream_t st);
