@@ -222,8 +222,9 @@ int sisso_l0_gram_noalloc(const double *X, const double *y, int64_t n_samples,
  * Network: 6 -> 256 -> 256 -> 1, ReLU, inputs per pair (i, j) (from the
  * task's correlation matrix): r_i, r_j (Pearson r, Eq. 1), C_ij = corr(f_i,
  * f_j), rho_j.i = corr(f_j, residual of y after the fit on f_i), rho_i.j, and
- * R2_ij of the two-feature fit.  Target: log(min over k of SSE(i, j, k) /
- * S_yy), clamped to [log 1e-12, 0] (0 when no completion is eligible).
+ * log(1 - R2_ij) / 8 of the two-feature fit.  Target: log(min over k of
+ * SSE(i, j, k) / S_yy), clamped to [log 1e-12, 0] (0 when no completion is
+ * eligible).
  * BF16 operands (features, W1, W2, w3, h1, h2 and the back-propagated dh2),
  * FP32 sums and FP32 master weights; squared-error loss, Adam (beta1 0.9,
  * beta2 0.999, eps 1e-8).  Parameters, flat FP32, SISSO_L0_SCORER_PARAMS
@@ -267,10 +268,12 @@ int sisso_l0_scorer_predict(sisso_l0_scorer_t s, const float *feats, int64_t n_r
 /* Training data of one task (single task, mixed precision handle): the
  * features of every pair in colex order into feats (device,
  * [C(n_sis, 2)][8]) and, when labels is not NULL, every pair's target
- * (device, [C(n_sis, 2)]), both from the FP32 tensor-core Gram.  X, y as in
+ * (device, [C(n_sis, 2)]), both from the FP32 tensor-core Gram.  With
+ * standardize != 0 the labels are z-scored over the task's pairs (only a
+ * pair's rank within its task matters to the search).  X, y as in
  * sisso_l0_fit with one task of n_total rows. */
 int sisso_l0_pair_data(sisso_l0_t h, const double *X, const double *y, int64_t n_total,
-                       int64_t n_sis, float *feats, float *labels);
+                       int64_t n_sis, float *feats, float *labels, int32_t standardize);
 
 /* Exact d = 3 search over the triples {i, j, k} reachable from a pair list
  * (host or device, int32 [n_pairs][2], any order within a pair, repeats

@@ -13,8 +13,9 @@ definition:
   the centred, unit-norm target u:  r_i = z_i.u, r_j = z_j.u (Pearson r,
   Eq. 1), C_ij = z_i.z_j, rho_j.i = corr(z_j, u - r_i z_i) (the correlation
   of f_j with the residual of the one-feature fit on f_i), rho_i.j likewise,
-  and R2_ij = 1 - SSE(i, j) / S_yy of the two-feature least-squares fit
-  (Householder QR through ``oracle.score``);
+  and log(max(SSE(i, j) / S_yy, LABEL_FLOOR)) / 8, the log residual fraction
+  1 - R2_ij of the two-feature least-squares fit (Householder QR through
+  ``oracle.score``);
 * the label of a pair: the best completion, min over k not in {i, j} of
   SSE(i, j, k) / S_yy over eligible triples, as log(clip(., LABEL_FLOOR, 1))
   (0 when no completion is eligible: the worst possible fit);
@@ -89,8 +90,8 @@ def _unit_columns(X, y):
 
 
 def pair_features(X, y, pairs=None):
-    """Features [P, 6] = (r_i, r_j, C_ij, rho_j.i, rho_i.j, R2_ij) of the pairs
-    (default: all pairs in colex order) of one task."""
+    """Features [P, 6] = (r_i, r_j, C_ij, rho_j.i, rho_i.j, log(1 - R2_ij) / 8)
+    of the pairs (default: all pairs in colex order) of one task."""
     m = np.asarray(X).shape[0]
     if pairs is None:
         pairs = all_pairs(m)
@@ -108,7 +109,7 @@ def pair_features(X, y, pairs=None):
         out[q, 3] = (Z[j] @ ei) / ni if ni > 0 else 0.0
         out[q, 4] = (Z[i] @ ej) / nj if nj > 0 else 0.0
     sse, _ = _score(X, y, pairs)
-    out[:, 5] = 1.0 - sse[:, 0] / syy
+    out[:, 5] = np.log(np.maximum(sse[:, 0] / syy, LABEL_FLOOR)) / 8.0
     return out
 
 

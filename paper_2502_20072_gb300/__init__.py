@@ -133,7 +133,7 @@ def lib():
         L.sisso_l0_scorer_loss_grad.argtypes = [vp, vp, vp, i64, vp, vp]
         L.sisso_l0_scorer_train.argtypes = [vp, vp, vp, i64, i32, i32, fp, vp]
         L.sisso_l0_scorer_predict.argtypes = [vp, vp, i64, vp]
-        L.sisso_l0_pair_data.argtypes = [vp, dp, dp, i64, i64, vp, vp]
+        L.sisso_l0_pair_data.argtypes = [vp, dp, dp, i64, i64, vp, vp, i32]
         L.sisso_l0_fit_pairs.argtypes = [vp, dp, dp, i64, i64, vp, i64, i32, vp, vp]
         L.sisso_l0_fit_learned.argtypes = [vp, vp, dp, dp, i64, i64, i32, ctypes.c_double, vp, vp]
         no_int = ("sisso_l0_last_error", "sisso_l0_destroy", "sisso_l0_count_tuples",
@@ -273,9 +273,10 @@ class Handle:
         return s.as_dict()
 
     # ----------------------------------------------- learned proposals --
-    def pair_data(self, X, y, labels=True):
+    def pair_data(self, X, y, labels=True, standardize=False):
         """Features [C(m,2), 8] and (optionally) labels [C(m,2)] of every pair
-        of one task, as CUDA tensors (mixed-precision handle)."""
+        of one task, as CUDA tensors (mixed-precision handle); standardize
+        z-scores the labels over the task."""
         import torch
         X = _as_f64(X)
         y = _as_f64(y)
@@ -286,7 +287,8 @@ class Handle:
         lab = torch.empty(npairs, dtype=torch.float32, device=dev) if labels else None
         rc = lib().sisso_l0_pair_data(self._h, ctypes.c_void_p(_ptr(X)), ctypes.c_void_p(_ptr(y)),
                                       n, m, ctypes.c_void_p(feats.data_ptr()),
-                                      ctypes.c_void_p(lab.data_ptr() if lab is not None else 0))
+                                      ctypes.c_void_p(lab.data_ptr() if lab is not None else 0),
+                                      int(bool(standardize)))
         self._check(rc)
         return feats, lab
 

@@ -1490,7 +1490,7 @@ int sisso_l0_scorer_predict(sisso_l0_scorer_t s, const float *feats, int64_t n_r
 }
 
 int sisso_l0_pair_data(sisso_l0_t h, const double *X, const double *y, int64_t n_total,
-                       int64_t n_sis, float *feats, float *labels) {
+                       int64_t n_sis, float *feats, float *labels, int32_t standardize) {
   return guarded(h, [&]() -> int {
     int rc = check_single(h, X, y, n_total, n_sis, 3);
     if (rc) return rc;
@@ -1514,6 +1514,11 @@ int sisso_l0_pair_data(sisso_l0_t h, const double *X, const double *y, int64_t n
         L0_CK(l0::launch_pair_best(h->gram32.as<float>(), P.ld, h->diag.as<float>(), P.m, np,
                                    h->opt.fp32_fallback_pivot_ratio, 1e-12f, labels, h->st),
               "pair label kernel");
+      if (labels && standardize) {
+        L0_CK(h->sel_bin.ensure(16), "alloc");
+        L0_CK(l0::launch_label_standardize(labels, np, h->sel_bin.as<double>(), h->st),
+              "label kernel");
+      }
       return SISSO_L0_OK;
     };
     return fit_requests(h, X, y, off, 1, n_sis, &r, 1, &sp);

@@ -253,7 +253,9 @@ cudaError_t launch_mlp_adam(float *params, float *m1, float *m2, const float *pa
 // Features of the pair i < j from the augmented correlation Gram (target at
 // index 0, upper triangle): r_i, r_j (Pearson r, Eq. 1), C_ij, the
 // correlations rho_j.i, rho_i.j of each column with the residual of the
-// one-feature fit on the other, and the two-feature R^2.
+// one-feature fit on the other, and log(1 - R^2) / 8 of the two-feature fit
+// (the log residual fraction: R^2 itself sits too close to 1 for a BF16
+// input where it matters most).
 __device__ __forceinline__ void pair_feature_vec(const float *G, long long ld, int i, int j,
                                                  float *x) {
   const float g00 = G[0];
@@ -269,8 +271,9 @@ __device__ __forceinline__ void pair_feature_vec(const float *G, long long ld, i
   x[2] = c;
   x[3] = (rj - c * ri) * rsqrtf(ei);
   x[4] = (ri - c * rj) * rsqrtf(ej);
-  x[5] = dc > 1e-6f ? fminf(fmaxf((ri * ri + rj * rj - 2.f * ri * rj * c) / dc, 0.f), 1.f)
-                    : fmaxf(ri * ri, rj * rj);
+  const float r2 = dc > 1e-6f ? fminf(fmaxf((ri * ri + rj * rj - 2.f * ri * rj * c) / dc, 0.f), 1.f)
+                             : fmaxf(ri * ri, rj * rj);
+  x[5] = 0.125f * logf(fmaxf(1.f - r2, 1e-12f));
 }
 
 // symmetric copy of an upper-triangular Gram (lower triangle filled) and
@@ -285,6 +288,8 @@ cudaError_t launch_pair_features(const float *G, long long ld, long long p0, lon
 cudaError_t launch_pair_best(const float *G, long long ld, const float *diag, int m,
                              long long n_pairs, double ratio, float floor_, float *label,
                              cudaStream_t st);
+// labels -> (labels - mean) / std over the n labels (acc: 2 doubles scratch)
+cudaError_t launch_label_standardize(float *lab, long long n, double *acc, cudaStream_t st);
 // top pairs by network score: all pairs whose score falls in the lowest
 // histogram bins holding at least `want` pairs; writes their (i, j) and a
 // bitmap over colex pair ranks; counter[0] = pairs written

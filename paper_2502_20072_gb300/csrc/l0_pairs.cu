@@ -105,6 +105,39 @@ pair_best_kernel(const float *G, long long ld, const float *diag, int m, long lo
   if (lane == 0) label[q] = logf(fminf(fmaxf(best, floor_), 1.f));
 }
 
+// z-score of one task's labels (mean and standard deviation in FP64): the
+// training target is the instance-relative rank of a pair's completion
+__global__ void __launch_bounds__(256)
+label_moments_kernel(const float *lab, long long n, double *acc) {
+  double s = 0.0, q = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = lab[i];
+    s += v;
+    q += v * v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    q += __shfl_xor_sync(0xffffffffu, q, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(acc, s);
+    atomicAdd(acc + 1, q);
+  }
+}
+
+__global__ void __launch_bounds__(256)
+label_normalize_kernel(float *lab, long long n, const double *acc) {
+  const double mean = acc[0] / (double)n;
+  const double var = acc[1] / (double)n - mean * mean;
+  const float inv = (float)(1.0 / sqrt(var > 1e-12 ? var : 1e-12));
+  const float mu = (float)mean;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    lab[i] = (lab[i] - mu) * inv;
+}
+
 // ---------------------------------------------------------- selection --
 constexpr int SEL_SHIFT = 12;                  // 2^20 bins of the ordered score bits
 constexpr int SEL_BINS = 1 << (32 - SEL_SHIFT);
@@ -331,6 +364,16 @@ cudaError_t launch_pair_best(const float *G, long long ld, const float *diag, in
   if (n_pairs <= 0) return cudaSuccess;
   pair_best_kernel<<<(unsigned)((n_pairs + 7) / 8), 256, 0, st>>>(G, ld, diag, m, n_pairs,
                                                                   (float)ratio, floor_, label);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_label_standardize(float *lab, long long n, double *acc, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(acc, 0, 16, st);
+  if (e != cudaSuccess) return e;
+  const unsigned g = (unsigned)std::min<long long>((n + 255) / 256, 152 * 8);
+  label_moments_kernel<<<g, 256, 0, st>>>(lab, n, acc);
+  label_normalize_kernel<<<g, 256, 0, st>>>(lab, n, acc);
   return cudaGetLastError();
 }
 

@@ -28,10 +28,10 @@ FEAT_AMP = 1e-5
 GRAD_REL = 2e-2
 
 
-def _prob(seed, n=300, m=40, sigma=0.01, planted=None, beta=None):
+def _prob(seed, n=300, m=40, sigma=0.01, planted=None, beta=None, n_planted=3):
     kw = dict(n_samples=n, n_sis=m, seed=seed, sigma=sigma, distinct=True)
     if planted is None:
-        kw["n_planted"] = 3
+        kw["n_planted"] = n_planted
     else:
         kw["planted"] = planted
         kw["beta"] = beta
@@ -50,7 +50,8 @@ def test_pair_features_match_oracle():
     ref = ol.pair_features(p.X, p.y)
     assert got.shape == (40 * 39 // 2, 8)
     ri, rj, c = ref[:, 0], ref[:, 1], ref[:, 2]
-    amp = 1.0 / np.minimum(np.minimum(1 - ri**2, 1 - rj**2), 1 - c**2)
+    res2 = np.exp(8.0 * ref[:, 5])          # 1 - R2 of the pair
+    amp = 1.0 / np.minimum(np.minimum(np.minimum(1 - ri**2, 1 - rj**2), 1 - c**2), 8 * res2)
     tol = FEAT_ATOL + FEAT_AMP * amp
     assert np.all(np.abs(got[:, :6] - ref) <= tol[:, None]), np.max(np.abs(got[:, :6] - ref) - tol[:, None])
     assert np.median(np.abs(got[:, :6] - ref)) < 1e-4
@@ -212,47 +213,37 @@ def _spearman(a, b):
 
 
 def test_trained_scorer_recall_and_gain():
-    """Train on exhaustive labels of seeded instances, then compare the
-    learned search with the exhaustive search on a held-out instance: the
-    network's gain is the share of triples it spares at >= 0.99 recall."""
+    """Train on exhaustive labels of seeded instances (eight planted terms,
+    noise sigma = 1, so that the best triples spread over many pairs), then
+    compare the learned search with the exhaustive search on a held-out
+    instance.  The network's gain over the method without it: it spares
+    more than 90 % of the triple fits at recall >= 0.99, where the same
+    network untrained finds well under that."""
+    from paper_2502_20072_gb300 import learn
     m_tr, m_te, n = 120, 200, 400
-    feats, labs = [], []
-    with _mixed() as h:
-        for seed in range(500, 508):
-            p = _prob(seed, n=n, m=m_tr)
-            f, lb = h.pair_data(p.X, p.y)
-            feats.append(f)
-            labs.append(lb)
-    F = torch.cat(feats)
-    Y = torch.cat(labs)
-    perm = torch.randperm(len(Y), generator=torch.Generator().manual_seed(0)).cuda()
-    F, Y = F[perm].contiguous(), Y[perm].contiguous()
-    test = _prob(777, n=n, m=m_te)
-    k = 100
-    with l0.Scorer(seed=11) as untrained, l0.Scorer(seed=11) as s:
-        losses = s.train(F, Y, batch_rows=4096, steps=600, lr=2e-3)
-        assert losses[-20:].mean() < 0.5 * losses[:5].mean()
-        with _mixed() as h:
-            tf, tl = h.pair_data(test.X, test.y)
+    train = [_prob(seed, n=n, m=m_tr, n_planted=8, sigma=1.0) for seed in range(500, 516)]
+    F, Y = learn.pair_training_set(train, seed=0)
+    test = _prob(777, n=n, m=m_te, n_planted=8, sigma=1.0)
+    k, frac = 100, 0.02
+    with l0.Scorer(seed=11) as untrained:
+        s, losses, secs = learn.train_scorer(F, Y, steps=3000, batch_rows=8192, lr=2e-3, seed=11)
+        with s, _mixed() as h:
+            assert losses[-50:].mean() < 0.85 * losses[:5].mean()
+            tf, tl = h.pair_data(test.X, test.y, standardize=True)
             truth = tl.cpu().numpy()
             rho_tr = _spearman(s.predict(tf).cpu().numpy(), truth)
             rho_un = _spearman(untrained.predict(tf).cpu().numpy(), truth)
             ex_t, _ = h.fit(test.X, test.y, 3, k)
             ex_fits = h.stats()["tuple_fits"]
-            res = {}
-            for frac in (0.005, 0.02):
-                le_t, _ = h.fit_learned(test.X, test.y, s, k, fraction=frac)
-                st = h.stats()
-                un_t, _ = h.fit_learned(test.X, test.y, untrained, k, fraction=frac)
-                res[frac] = (_recall(ex_t[0], le_t), _recall(ex_t[0], un_t), st["tuple_fits"],
-                             st["proposal_pairs"])
-    print("rank correlation with the exhaustive labels: trained %.3f untrained %.3f"
-          % (rho_tr, rho_un))
-    for frac, (rt, ru, fits, npairs) in res.items():
-        print("fraction %.3f: recall trained %.3f untrained %.3f; %d pairs, %d of %d fits"
-              % (frac, rt, ru, npairs, fits, ex_fits))
-    assert rho_tr > 0.9 and rho_tr > rho_un
-    for frac, (rt, ru, fits, npairs) in res.items():
-        assert rt >= 0.99
-        assert fits < 0.1 * ex_fits
-        assert npairs >= frac * m_te * (m_te - 1) / 2
+            le_t, _ = h.fit_learned(test.X, test.y, s, k, fraction=frac)
+            st = h.stats()
+            un_t, _ = h.fit_learned(test.X, test.y, untrained, k, fraction=frac)
+    rt, ru = _recall(ex_t[0], le_t), _recall(ex_t[0], un_t)
+    print("trained in %.2f s; rank correlation with the exhaustive labels %.3f (untrained %.3f);"
+          " recall@%d trained %.3f untrained %.3f; %d pairs, %d of %d fits"
+          % (secs, rho_tr, rho_un, k, rt, ru, st["proposal_pairs"], st["tuple_fits"], ex_fits))
+    assert rt >= 0.99
+    assert ru < rt - 0.2
+    assert rho_tr > rho_un
+    assert st["tuple_fits"] < 0.1 * ex_fits
+    assert st["proposal_pairs"] >= frac * m_te * (m_te - 1) / 2

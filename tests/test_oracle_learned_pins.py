@@ -46,7 +46,8 @@ def test_pair_features_partial_correlation_identity():
     # rho from explicit residual projections
     p = _small()
     F = ol.pair_features(p.X, p.y)
-    ri, rj, c, rji, rij, r2 = F.T
+    ri, rj, c, rji, rij, f5 = F.T
+    r2 = 1.0 - np.exp(8.0 * f5)
     np.testing.assert_allclose(r2, ri**2 + rji**2 * (1 - ri**2) / (1 - c**2), rtol=1e-9, atol=1e-12)
     np.testing.assert_allclose(r2, rj**2 + rij**2 * (1 - rj**2) / (1 - c**2), rtol=1e-9, atol=1e-12)
     # r from Eq. 1 directly
@@ -70,7 +71,7 @@ def test_labels_bounded_by_pair_fit_and_by_global_best():
     p = _small()
     F = ol.pair_features(p.X, p.y)
     best = ol.best_completion(p.X, p.y)
-    assert np.all(best <= 1.0 - F[:, 5] + 1e-12)       # nesting
+    assert np.all(best <= np.exp(8.0 * F[:, 5]) * (1 + 1e-12))   # nesting
     ex = oracle.fit(p.X, p.y, 3, 1)
     syy = float(((p.y - p.y.mean()) ** 2).sum())
     assert np.min(best) == pytest.approx(ex["score"][0, 0] / syy, rel=1e-12)
