@@ -6,7 +6,9 @@ recipe:
 
 * primaries x_1..x_8 ~ U(0.5, 2.0) per sample;
 * each candidate column f_j = x_a^p * x_b^q with a, b ~ U{1..8} and
-  p, q ~ U{-2, -1, 0.5, 1, 2, 3};
+  p, q ~ U{-2, -1, 0.5, 1, 2, 3} (with ``factors=3`` a third factor x_c^r
+  drawn the same way: the two-factor family has only 1128 distinct
+  non-constant columns);
 * a column that is the constant 1 (a == b and p + q == 0) is redrawn;
 * with ``distinct=True`` a column whose monomial (exponent vector) was already
   drawn is redrawn too, so no two columns are value duplicates;
@@ -41,7 +43,7 @@ class Problem:
     beta: List[List[float]]       # per task: planted coefficients (same order)
     intercept: float
     sigma: float
-    spec: np.ndarray              # int64 [n_sis, 4]: (a, 2p, b, 2q) per column, a/b 0-based
+    spec: np.ndarray              # int64 [n_sis, 2 * factors]: (a, 2p, b, 2q[, c, 2r]), 0-based
     replaced: np.ndarray          # int64 [n_replaced, 2]: (column, source column)
     seed: int
     name: str = ""
@@ -59,33 +61,34 @@ class Problem:
         return int(self.X.shape[1])
 
 
-def _monomial_key(a: int, p2: int, b: int, q2: int) -> tuple:
+def _monomial_key(idx, e2) -> tuple:
     e = [0] * N_PRIMARIES
-    e[a] += p2
-    e[b] += q2
+    for a, p2 in zip(idx, e2):
+        e[a] += p2
     return tuple(e)
 
 
 def _draw_spec(rng: np.random.Generator, n_sis: int, distinct: bool,
-               forced: Optional[dict] = None) -> np.ndarray:
-    """Draw (a, 2p, b, 2q) for every column; constants always redrawn."""
-    spec = np.zeros((n_sis, 4), dtype=np.int64)
+               factors: int = 2) -> np.ndarray:
+    """Draw (a, 2p, b, 2q[, c, 2r]) for every column (primary indices first,
+    then exponents, from the stream); constants always redrawn."""
+    spec = np.zeros((n_sis, 2 * factors), dtype=np.int64)
     seen = set()
-    forced = forced or {}
     for j in range(n_sis):
         while True:
-            a = int(rng.integers(0, N_PRIMARIES))
-            b = int(rng.integers(0, N_PRIMARIES))
-            p2 = _EXP2[int(rng.integers(0, len(_EXP2)))]
-            q2 = _EXP2[int(rng.integers(0, len(_EXP2)))]
-            key = _monomial_key(a, p2, b, q2)
+            idx = [int(rng.integers(0, N_PRIMARIES)) for _ in range(factors)]
+            e2 = [_EXP2[int(rng.integers(0, len(_EXP2)))] for _ in range(factors)]
+            key = _monomial_key(idx, e2)
             if all(v == 0 for v in key):
                 continue
             if distinct and key in seen:
                 continue
             break
         seen.add(key)
-        spec[j] = (a, p2, b, q2)
+        row = []
+        for a, p2 in zip(idx, e2):
+            row += [a, p2]
+        spec[j] = row
     return spec
 
 
@@ -93,8 +96,10 @@ def _columns(x: np.ndarray, spec: np.ndarray) -> np.ndarray:
     m = spec.shape[0]
     X = np.empty((m, x.shape[1]), dtype=np.float64)
     for j in range(m):
-        a, p2, b, q2 = (int(v) for v in spec[j])
-        X[j] = np.power(x[a], p2 / 2.0) * np.power(x[b], q2 / 2.0)
+        v = np.power(x[int(spec[j, 0])], spec[j, 1] / 2.0)
+        for f in range(1, spec.shape[1] // 2):
+            v = v * np.power(x[int(spec[j, 2 * f])], spec[j, 2 * f + 1] / 2.0)
+        X[j] = v
     return X
 
 
@@ -104,7 +109,7 @@ def make_problem(n_samples: Sequence[int] | int, n_sis: int, seed: int, *,
                  intercept: float = 0.1, sigma: float = 0.01,
                  distinct: bool = True, beta_range: float = 3.0,
                  replace_frac: float = 0.0, replace_rel_noise: float = 1e-4,
-                 name: str = "") -> Problem:
+                 factors: int = 2, name: str = "") -> Problem:
     """Build one seeded problem.
 
     ``n_samples`` is an int (one task) or a list of per-task sample counts.
@@ -118,7 +123,7 @@ def make_problem(n_samples: Sequence[int] | int, n_sis: int, seed: int, *,
     n_total = int(sum(sizes))
     rng = np.random.default_rng(seed)
     x = rng.uniform(0.5, 2.0, size=(N_PRIMARIES, n_total))
-    spec = _draw_spec(rng, n_sis, distinct)
+    spec = _draw_spec(rng, n_sis, distinct, factors)
     X = _columns(x, spec)
 
     n_tasks = len(sizes)
@@ -181,7 +186,15 @@ CONFIGS = {
                sigma=0.01, distinct=True, replace_frac=0.2, replace_rel_noise=1e-4),
     "C5": dict(n_samples=2000, n_sis=20000, n_dim=3, k=100, seed=5, n_planted=3,
                sigma=0.01, distinct=False),
+    # the learned form's workload with distinct columns: three-factor
+    # monomials (the two-factor family repeats each of its 1128 distinct
+    # columns ~18 times at n_sis = 20000); training instances use seeds
+    # 1000..1049 at n_sis = 2000 of the same family
+    "C5L": dict(n_samples=2000, n_sis=20000, n_dim=3, k=100, seed=5, n_planted=3,
+                sigma=0.01, distinct=True, factors=3),
 }
+C5L_TRAIN = dict(n_samples=2000, n_sis=2000, n_planted=3, sigma=0.01, distinct=True, factors=3)
+C5L_TRAIN_SEEDS = tuple(range(1000, 1050))
 
 
 def make_config(name: str, **overrides) -> tuple:
