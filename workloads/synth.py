@@ -6,9 +6,9 @@ recipe:
 
 * primaries x_1..x_8 ~ U(0.5, 2.0) per sample;
 * each candidate column f_j = x_a^p * x_b^q with a, b ~ U{1..8} and
-  p, q ~ U{-2, -1, 0.5, 1, 2, 3} (with ``factors=3`` a third factor x_c^r
-  drawn the same way: the two-factor family has only 1128 distinct
-  non-constant columns);
+  p, q ~ U{-2, -1, 0.5, 1, 2, 3} (with ``factors`` > 2 more factors drawn
+  the same way: the two-factor family has only 1128 distinct non-constant
+  columns, three factors 16,644, four factors 174,056);
 * a column that is the constant 1 (a == b and p + q == 0) is redrawn;
 * with ``distinct=True`` a column whose monomial (exponent vector) was already
   drawn is redrawn too, so no two columns are value duplicates;
@@ -74,8 +74,13 @@ def _draw_spec(rng: np.random.Generator, n_sis: int, distinct: bool,
     then exponents, from the stream); constants always redrawn."""
     spec = np.zeros((n_sis, 2 * factors), dtype=np.int64)
     seen = set()
+    tries = 0
     for j in range(n_sis):
         while True:
+            tries += 1
+            if tries > 200 * n_sis + 100000:
+                raise ValueError("fewer distinct %d-factor monomials than n_sis=%d"
+                                 % (factors, n_sis))
             idx = [int(rng.integers(0, N_PRIMARIES)) for _ in range(factors)]
             e2 = [_EXP2[int(rng.integers(0, len(_EXP2)))] for _ in range(factors)]
             key = _monomial_key(idx, e2)
@@ -186,14 +191,15 @@ CONFIGS = {
                sigma=0.01, distinct=True, replace_frac=0.2, replace_rel_noise=1e-4),
     "C5": dict(n_samples=2000, n_sis=20000, n_dim=3, k=100, seed=5, n_planted=3,
                sigma=0.01, distinct=False),
-    # the learned form's workload with distinct columns: three-factor
+    # the learned form's workload with distinct columns: four-factor
     # monomials (the two-factor family repeats each of its 1128 distinct
-    # columns ~18 times at n_sis = 20000); training instances use seeds
-    # 1000..1049 at n_sis = 2000 of the same family
+    # columns ~18 times at n_sis = 20000, and three factors give only 16,644
+    # distinct columns); training instances use seeds 1000..1049 at
+    # n_sis = 2000 of the same family
     "C5L": dict(n_samples=2000, n_sis=20000, n_dim=3, k=100, seed=5, n_planted=3,
-                sigma=0.01, distinct=True, factors=3),
+                sigma=0.01, distinct=True, factors=4),
 }
-C5L_TRAIN = dict(n_samples=2000, n_sis=2000, n_planted=3, sigma=0.01, distinct=True, factors=3)
+C5L_TRAIN = dict(n_samples=2000, n_sis=2000, n_planted=3, sigma=0.01, distinct=True, factors=4)
 C5L_TRAIN_SEEDS = tuple(range(1000, 1050))
 
 
