@@ -293,6 +293,37 @@ int sisso_l0_fit_learned(sisso_l0_t h, sisso_l0_scorer_t s, const double *X, con
                          int64_t n_total, int64_t n_sis, int32_t k, double fraction,
                          int32_t *out_tuples, double *out_rmse);
 
+/* ---------------------------------------------------------- sharding ----
+ * One search split over n_shards workers (one GPU each).  The tuples are
+ * independent (the paper spreads descriptors over devices and gathers the
+ * selected models at the end, Sec. 3.2.1): shard s searches every n-th work
+ * item (a chunk of prefixes of one tile of the tuple space), so the shards'
+ * tuple sets are disjoint and cover all C(n_sis, n_dim) tuples.  Each shard
+ * returns its FP64 re-fitted candidate pool; the pools are the only data
+ * exchanged (an all-gather of at most SISSO_L0_MAX_POOL candidates per
+ * shard), and sisso_l0_merge_shards ranks their union. */
+#define SISSO_L0_MAX_POOL 2048
+
+/* One shard of a single-task search (n_dim >= 2).  Outputs (host or device):
+ * out_keys / out_sse [SISSO_L0_MAX_POOL], the first *out_count valid: the
+ * lexicographic ranks and exact SSEs (FP64 re-fit; +inf when rank
+ * deficient) of the shard's candidates; *out_bound: every tuple of the shard
+ * outside them has an SSE of at least out_bound - 4 * out_delta. */
+int sisso_l0_fit_shard(sisso_l0_t h, const double *X, const double *y, int64_t n_total,
+                       int64_t n_sis, int32_t n_dim, int32_t k, int32_t shard, int32_t n_shards,
+                       uint64_t *out_keys, double *out_sse, int32_t *out_count,
+                       double *out_bound, double *out_delta);
+
+/* Rank the union of the shards' candidates (host or device arrays, n_cand
+ * entries, any order): the k best by (SSE, lexicographic rank) as tuples and
+ * RMSE = sqrt(SSE / n_total), -1 / +inf padded; *certified = 1 when every
+ * shard's bound - 4 delta clears the k-th SSE (the union then holds the exact
+ * top k of the whole search). */
+int sisso_l0_merge_shards(sisso_l0_t h, int64_t n_sis, int32_t n_dim, int32_t k, int64_t n_total,
+                          const uint64_t *keys, const double *sse, int64_t n_cand,
+                          const double *bounds, const double *deltas, int32_t n_shards,
+                          int32_t *out_tuples, double *out_rmse, int32_t *certified);
+
 #ifdef __cplusplus
 }
 #endif

@@ -85,7 +85,10 @@ EXPORTS = ("sisso_l0_default_options", "sisso_l0_create", "sisso_l0_fit", "sisso
            "sisso_l0_scorer_create", "sisso_l0_scorer_destroy", "sisso_l0_scorer_last_error",
            "sisso_l0_scorer_set_params", "sisso_l0_scorer_get_params",
            "sisso_l0_scorer_loss_grad", "sisso_l0_scorer_train", "sisso_l0_scorer_predict",
-           "sisso_l0_pair_data", "sisso_l0_fit_pairs", "sisso_l0_fit_learned")
+           "sisso_l0_pair_data", "sisso_l0_fit_pairs", "sisso_l0_fit_learned",
+           "sisso_l0_fit_shard", "sisso_l0_merge_shards")
+
+MAX_POOL = 2048
 
 SCORER_PARAMS = 67841
 PAIR_FEATURES_LD = 8
@@ -136,6 +139,10 @@ def lib():
         L.sisso_l0_pair_data.argtypes = [vp, dp, dp, i64, i64, vp, vp, i32]
         L.sisso_l0_fit_pairs.argtypes = [vp, dp, dp, i64, i64, vp, i64, i32, vp, vp]
         L.sisso_l0_fit_learned.argtypes = [vp, vp, dp, dp, i64, i64, i32, ctypes.c_double, vp, vp]
+        L.sisso_l0_fit_shard.argtypes = [vp, dp, dp, i64, i64, i32, i32, i32, i32, vp, vp, vp,
+                                         vp, vp]
+        L.sisso_l0_merge_shards.argtypes = [vp, i64, i32, i32, i64, vp, vp, i64, vp, vp, i32, vp,
+                                            vp, vp]
         no_int = ("sisso_l0_last_error", "sisso_l0_destroy", "sisso_l0_count_tuples",
                   "sisso_l0_scorer_destroy", "sisso_l0_scorer_last_error")
         for name in EXPORTS:
@@ -326,6 +333,49 @@ class Handle:
                                         ctypes.c_void_p(_ptr(out_rmse)))
         self._check(rc)
         return out_tuples, out_rmse
+
+    # -------------------------------------------------------- sharding --
+    def fit_shard(self, X, y, n_dim, k, shard, n_shards):
+        """One shard of a single-task search.  Returns (keys uint64 [c],
+        sse float64 [c], bound, delta)."""
+        X = _as_f64(X)
+        y = _as_f64(y)
+        m, n = int(X.shape[0]), int(X.shape[1])
+        keys = np.empty(MAX_POOL, dtype=np.uint64)
+        sse = np.empty(MAX_POOL, dtype=np.float64)
+        cnt = np.zeros(1, dtype=np.int32)
+        bd = np.zeros(2, dtype=np.float64)
+        rc = lib().sisso_l0_fit_shard(self._h, ctypes.c_void_p(_ptr(X)), ctypes.c_void_p(_ptr(y)),
+                                      n, m, int(n_dim), int(k), int(shard), int(n_shards),
+                                      ctypes.c_void_p(keys.ctypes.data),
+                                      ctypes.c_void_p(sse.ctypes.data),
+                                      ctypes.c_void_p(cnt.ctypes.data),
+                                      ctypes.c_void_p(bd.ctypes.data),
+                                      ctypes.c_void_p(bd.ctypes.data + 8))
+        self._check(rc)
+        c = int(cnt[0])
+        return keys[:c].copy(), sse[:c].copy(), float(bd[0]), float(bd[1])
+
+    def merge_shards(self, n_sis, n_dim, k, n_total, keys, sse, bounds, deltas):
+        """Rank the union of shard candidates.  Returns (tuples [k, n_dim],
+        rmse [k], certified)."""
+        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        sse = np.ascontiguousarray(sse, dtype=np.float64)
+        bounds = np.ascontiguousarray(bounds, dtype=np.float64)
+        deltas = np.ascontiguousarray(deltas, dtype=np.float64)
+        out_t = np.empty((k, n_dim), dtype=np.int32)
+        out_r = np.empty(k, dtype=np.float64)
+        cert = np.zeros(1, dtype=np.int32)
+        rc = lib().sisso_l0_merge_shards(self._h, int(n_sis), int(n_dim), int(k), int(n_total),
+                                         ctypes.c_void_p(keys.ctypes.data),
+                                         ctypes.c_void_p(sse.ctypes.data), len(keys),
+                                         ctypes.c_void_p(bounds.ctypes.data),
+                                         ctypes.c_void_p(deltas.ctypes.data), len(bounds),
+                                         ctypes.c_void_p(out_t.ctypes.data),
+                                         ctypes.c_void_p(out_r.ctypes.data),
+                                         ctypes.c_void_p(cert.ctypes.data))
+        self._check(rc)
+        return out_t, out_r, bool(cert[0])
 
     def debug_unrank(self, m, n, ranks):
         ranks = np.ascontiguousarray(ranks, dtype=np.uint64)

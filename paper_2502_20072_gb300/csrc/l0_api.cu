@@ -188,6 +188,7 @@ struct FitPlan {
   // pair list (proposal); or the call stops after the Gram (prep_only).
   // after_prep runs once the symmetric Gram and its diagonal exist.
   int proposal = 0, prep_only = 0;
+  int shard = 0, n_shards = 1;   // the tuple kernel takes items shard, shard + n_shards, ...
   long long n_pairs = 0;
   u64 prop_fits = 0;
   std::function<int(sisso_l0_t, FitPlan &)> after_prep;
@@ -395,6 +396,8 @@ l0::TileArgs<R> tile_args(sisso_l0_t h, const FitPlan &P, int K, int S, const R 
   a.S = S;
   a.item_counter = h->ctr.as<u64>();
   a.item_limit = item_limit;
+  a.item_stride = P.n_shards;
+  a.item_offset = P.shard;
   a.gthr = h->gthr.as<u64>();
   a.hist = h->hist.as<unsigned>();
   a.out_s = h->lists_s.as<R>();
@@ -748,7 +751,7 @@ std::string graph_key(sisso_l0_t h, const FitPlan &P, int K) {
 template <typename R>
 int run_pass(sisso_l0_t h, FitPlan &P, int K, const R *G, bool with_prep, bool *replayed) {
   *replayed = false;
-  if (!h->opt.use_graph || P.proposal) {
+  if (!h->opt.use_graph || P.proposal || P.n_shards > 1) {
     int rc = with_prep ? prep_pass(h, P) : SISSO_L0_OK;
     if (rc) return rc;
     return search_pass<R>(h, P, K, G);
@@ -784,6 +787,7 @@ int run_pass(sisso_l0_t h, FitPlan &P, int K, const R *G, bool with_prep, bool *
 // the learned forms' additions to a fit (see FitPlan)
 struct Special {
   int proposal = 0, prep_only = 0;
+  int shard = 0, n_shards = 1;
   std::function<int(sisso_l0_t, FitPlan &)> after_prep;
 };
 
@@ -807,6 +811,8 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
   if (sp) {
     P.proposal = sp->proposal;
     P.prep_only = sp->prep_only;
+    P.shard = sp->shard;
+    P.n_shards = sp->n_shards;
     P.after_prep = sp->after_prep;
   }
   int kmax = 0;
@@ -970,7 +976,7 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
       if (host_err != 0) return fail(h, SISSO_L0_ECUDA, "device error flag " + std::to_string(host_err));
       return SISSO_L0_OK;
     }
-  } else if (h->opt.autotune && P.has_tuples) {
+  } else if (h->opt.autotune && P.has_tuples && P.n_shards == 1) {
     rc = prep_pass(h, P);
     if (rc) return rc;
     prep_done = true;
@@ -997,7 +1003,8 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
     prep_done = true;
     rc = finish_pass(h, P, &certified, &delta, &ms_tuple, &ms_merge, &ms_refit);
     if (rc) break;
-    if (certified || K >= Kmax) break;
+    // a shard's pool is certified against the merged result, not its own
+    if (certified || K >= Kmax || P.n_shards > 1) break;
     K = std::min(2 * K, Kmax);
     ++enl;
   }
@@ -1613,6 +1620,103 @@ int sisso_l0_fit_learned(sisso_l0_t h, sisso_l0_scorer_t s, const double *X, con
       return SISSO_L0_OK;
     };
     return fit_requests(h, X, y, off, 1, n_sis, &r, 1, &sp);
+  });
+}
+
+}  // extern "C"
+
+// ============================================================== sharding ==
+// One search split over shards (one per GPU): shard s of n takes every n-th
+// work item (a prefix chunk of one (j, k) tile), so each shard searches a
+// disjoint slice of the tuples; its FP64 re-fitted candidate pool is the only
+// thing exchanged, and the merge ranks the union (cf. the paper's final
+// gather of the selected models, Sec. 3.2.1).
+extern "C" {
+
+int sisso_l0_fit_shard(sisso_l0_t h, const double *X, const double *y, int64_t n_total,
+                       int64_t n_sis, int32_t n_dim, int32_t k, int32_t shard, int32_t n_shards,
+                       uint64_t *out_keys, double *out_sse, int32_t *out_count,
+                       double *out_bound, double *out_delta) {
+  return guarded(h, [&]() -> int {
+    if (!X || !y || !out_keys || !out_sse || !out_count || !out_bound || !out_delta)
+      return fail(h, SISSO_L0_EINVAL, "null pointer argument");
+    if (n_shards < 1 || shard < 0 || shard >= n_shards)
+      return fail(h, SISSO_L0_EINVAL, "shard must be in [0, n_shards)");
+    if (n_dim < 2) return fail(h, SISSO_L0_EINVAL, "sharded searches take n_dim >= 2");
+    if (h->opt.task_mode != SISSO_L0_PER_TASK)
+      return fail(h, SISSO_L0_EUNSUPPORTED, "sharded searches are single-task");
+    const int64_t off[2] = {0, n_total};
+    std::vector<int32_t> tt((size_t)std::max(1, k) * std::max(1, n_dim));
+    std::vector<double> tr((size_t)std::max(1, k));
+    sisso_l0_request r{n_dim, k, tt.data(), tr.data()};
+    Special sp;
+    sp.shard = shard;
+    sp.n_shards = n_shards;
+    int rc = fit_requests(h, X, y, off, 1, n_sis, &r, 1, &sp);
+    if (rc) return rc;
+    const int K = h->stats.candidate_pool;
+    int cnt = 0;
+    l0::CertOut c;
+    L0_CK(cudaMemcpyAsync(&cnt, h->pool_cnt.p, 4, cudaMemcpyDeviceToHost, h->st), "copy");
+    L0_CK(cudaMemcpyAsync(&c, h->cert.p, sizeof(c), cudaMemcpyDeviceToHost, h->st), "copy");
+    L0_CK(cudaMemcpyAsync(out_keys, h->pool_k.p, (size_t)K * 8, cudaMemcpyDefault, h->st), "copy");
+    L0_CK(cudaMemcpyAsync(out_sse, h->refit.p, (size_t)K * 8, cudaMemcpyDefault, h->st), "copy");
+    rc = wait_stream(h);
+    if (rc) return rc;
+    *out_count = cnt;
+    *out_bound = c.pool_worst;
+    *out_delta = c.delta;
+    return SISSO_L0_OK;
+  });
+}
+
+int sisso_l0_merge_shards(sisso_l0_t h, int64_t n_sis, int32_t n_dim, int32_t k, int64_t n_total,
+                          const uint64_t *keys, const double *sse, int64_t n_cand,
+                          const double *bounds, const double *deltas, int32_t n_shards,
+                          int32_t *out_tuples, double *out_rmse, int32_t *certified) {
+  return guarded(h, [&]() -> int {
+    if (!keys || !sse || !bounds || !deltas || !out_tuples || !out_rmse || !certified)
+      return fail(h, SISSO_L0_EINVAL, "null pointer argument");
+    if (n_dim < 1 || n_dim > SISSO_L0_MAX_DIM || k < 1 || n_cand < 0 || n_shards < 1 ||
+        n_total < 1 || n_sis < n_dim)
+      return fail(h, SISSO_L0_EINVAL, "bad arguments");
+    if (n_cand > (1LL << 20)) return fail(h, SISSO_L0_EUNSUPPORTED, "more than 2^20 candidates");
+    const u64 total = binom_host(n_sis, n_dim);
+    if (total >= kSat) return fail(h, SISSO_L0_EUNSUPPORTED, "C(n_sis, n_dim) too large");
+    cudaStream_t st = h->st;
+    int rc = ensure_binom(h, (int)n_sis);
+    if (rc) return rc;
+    long long P = 1;
+    while (P < n_cand || P < k) P <<= 1;
+    const size_t in_bytes = (size_t)std::max<int64_t>(n_cand, 1) * 16 + (size_t)n_shards * 16;
+    L0_CK(h->prop_in.ensure(in_bytes), "alloc");
+    L0_CK(h->scores.ensure((size_t)P * 16), "alloc");
+    L0_CK(h->out_t.ensure((size_t)k * n_dim * 4), "alloc");
+    L0_CK(h->out_r.ensure((size_t)k * 8 + 16), "alloc");
+    unsigned char *in = (unsigned char *)h->prop_in.p;
+    u64 *dk = (u64 *)in;
+    double *ds = (double *)(in + (size_t)std::max<int64_t>(n_cand, 1) * 8);
+    double *db = ds + std::max<int64_t>(n_cand, 1);
+    double *dd = db + n_shards;
+    if (n_cand > 0) {
+      L0_CK(cudaMemcpyAsync(dk, keys, (size_t)n_cand * 8, cudaMemcpyDefault, st), "copy");
+      L0_CK(cudaMemcpyAsync(ds, sse, (size_t)n_cand * 8, cudaMemcpyDefault, st), "copy");
+    }
+    L0_CK(cudaMemcpyAsync(db, bounds, (size_t)n_shards * 8, cudaMemcpyDefault, st), "copy");
+    L0_CK(cudaMemcpyAsync(dd, deltas, (size_t)n_shards * 8, cudaMemcpyDefault, st), "copy");
+    double *ss = h->scores.as<double>();
+    u64 *sk = (u64 *)(ss + P);
+    int *dcert = (int *)(h->out_r.as<double>() + k);
+    l0::Binom B{h->binom.as<u64>(), (int)n_sis + 1};
+    L0_CK(l0::launch_merge_shards(B, (int)n_sis, n_dim, total, k, (double)n_total, dk, ds, n_cand,
+                                  db, dd, n_shards, ss, sk, h->out_t.as<int>(),
+                                  h->out_r.as<double>(), dcert, st),
+          "merge kernel");
+    L0_CK(cudaMemcpyAsync(out_tuples, h->out_t.p, (size_t)k * n_dim * 4, cudaMemcpyDefault, st),
+          "copy");
+    L0_CK(cudaMemcpyAsync(out_rmse, h->out_r.p, (size_t)k * 8, cudaMemcpyDefault, st), "copy");
+    L0_CK(cudaMemcpyAsync(certified, dcert, 4, cudaMemcpyDefault, st), "copy");
+    return wait_stream(h);
   });
 }
 

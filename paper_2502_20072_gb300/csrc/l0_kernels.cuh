@@ -42,6 +42,8 @@ struct TileArgs {
   int K, S;                        // list capacity, staging capacity
   u64 *item_counter;
   long long item_limit;            // items at or past this index are not processed
+  long long item_stride, item_offset;   // the counter's value c stands for item
+                                        // c * stride + offset (a shard's items)
   u64 *gthr;                       // [n_probs] ordered score bits
   unsigned *hist;                  // [n_probs][L0_HIST_WORDS] staged-score counts
   R *out_s; u64 *out_k; int *out_cnt;   // [n_probs][n_slots][K], [n_probs][n_slots]
@@ -319,6 +321,16 @@ template <typename R>
 cudaError_t proposal_occupancy(int K, int S, int *blocks_per_sm);
 template <typename R>
 cudaError_t launch_proposal(const PropArgs<R> &a, int grid, cudaStream_t st);
+
+// final ranking of candidates gathered from shards (one CTA): sort by (SSE,
+// lexicographic rank), unrank the first k, RMSE = sqrt(SSE / n); certified
+// when min over shards of (bound - 4 delta) clears the k-th SSE.  scratch
+// holds 2 P entries (P = n_cand rounded up to a power of two).
+cudaError_t launch_merge_shards(const Binom &B, int m, int d, u64 total, int k, double n_rows,
+                                const u64 *keys, const double *sse, long long n_cand,
+                                const double *bounds, const double *deltas, int n_shards,
+                                double *scratch_s, u64 *scratch_k, int *out_tuples,
+                                double *out_rmse, int *certified, cudaStream_t st);
 
 cudaError_t launch_unrank(const Binom &B, int m, int d, u64 total,
                           const u64 *ranks, long long count, int *tuples,

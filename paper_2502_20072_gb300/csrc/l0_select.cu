@@ -411,7 +411,57 @@ __global__ void unrank_kernel(Binom B, int m, int d, u64 total, const u64 *ranks
   for (int q = 0; q < d; ++q) tuples[i * d + q] = t[q];
 }
 
+__global__ void __launch_bounds__(1024)
+merge_shards_kernel(Binom B, int m, int d, u64 total, int k, double n_rows, const u64 *keys,
+                    const double *sse, long long n_cand, int P, const double *bounds,
+                    const double *deltas, int n_shards, double *ss, u64 *sk, int *out_tuples,
+                    double *out_rmse, int *certified) {
+  const double inf = __longlong_as_double(0x7ff0000000000000ll);
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    ss[i] = (i < n_cand) ? sse[i] : inf;
+    sk[i] = (i < n_cand) ? keys[i] : ~0ull;
+  }
+  __syncthreads();
+  cta_bitonic_sort<double>(ss, sk, P);
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    int *ot = out_tuples + (size_t)i * d;
+    if (i < P && isfinite(ss[i])) {
+      int t[L0_DMAX];
+      lex_unrank(B, m, d, sk[i], total, t);
+      for (int q = 0; q < d; ++q) ot[q] = t[q];
+      out_rmse[i] = sqrt(fmax(ss[i], 0.0) / n_rows);
+    } else {
+      for (int q = 0; q < d; ++q) ot[q] = -1;
+      out_rmse[i] = inf;
+    }
+  }
+  if (threadIdx.x == 0) {
+    // every shard's pool holds all of its tuples whose exact SSE is below
+    // its bound - 4 delta; the merged k-th must clear the smallest of these
+    double worst = inf;
+    for (int q = 0; q < n_shards; ++q) {
+      const double b = bounds[q];
+      if (!isinf(b)) worst = fmin(worst, b - 4.0 * deltas[q]);
+    }
+    const double kth = (k <= P) ? ss[k - 1] : inf;
+    *certified = (isinf(worst) || worst >= kth) ? 1 : 0;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_merge_shards(const Binom &B, int m, int d, u64 total, int k, double n_rows,
+                                const u64 *keys, const double *sse, long long n_cand,
+                                const double *bounds, const double *deltas, int n_shards,
+                                double *scratch_s, u64 *scratch_k, int *out_tuples,
+                                double *out_rmse, int *certified, cudaStream_t st) {
+  int P = 1;
+  while (P < n_cand || P < k) P <<= 1;
+  merge_shards_kernel<<<1, 1024, 0, st>>>(B, m, d, total, k, n_rows, keys, sse, n_cand, P, bounds,
+                                          deltas, n_shards, scratch_s, scratch_k, out_tuples,
+                                          out_rmse, certified);
+  return cudaGetLastError();
+}
 
 template <typename R>
 size_t merge_smem_bytes(int K, int S, int cap) {

@@ -558,7 +558,7 @@ __device__ __forceinline__ void persistent_items(const TileArgs<R> &A, RunItem r
   for (;;) {
     if (tid == 0) s_item = (long long)atomicAdd(A.item_counter, 1ull);
     __syncthreads();
-    const long long item = s_item;
+    const long long item = s_item * A.item_stride + A.item_offset;
     int prob = -1;
     if (item < A.item_limit)
       for (int q = 0; q < A.n_probs; ++q)
