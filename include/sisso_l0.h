@@ -72,6 +72,10 @@ typedef struct {
                                         CUDA graph on the first call of a shape, replay after */
   const char *autotune_cache_path;   /* file that persists autotuner choices (NULL: none) */
   double timeout_seconds;            /* host-side deadline for stream completion (<= 0: none) */
+  int32_t fp64_rerun_uncertified;    /* MIXED: when the candidate pool cannot be certified at
+                                        max_candidate_pool (FP32 score errors as large as the
+                                        gaps between the best scores), redo the fit in FP64
+                                        (1, default) or return the uncertified result (0) */
 } sisso_l0_options;
 
 typedef struct {
@@ -87,7 +91,7 @@ typedef struct {
   int32_t graph_replayed;            /* 1 when the last search pass replayed a CUDA graph */
   int32_t tuned_items_factor;        /* autotuner choice: work items per CTA (x2) */
   int32_t tuned_ctas_per_sm;         /* autotuner choice: resident CTAs per SM */
-  int32_t reserved1;
+  int32_t fp64_rerun;                /* 1: the last fit was redone in FP64 (see options) */
   /* phase times (ms, CUDA events on the handle's stream); 0 when unavailable */
   double ms_prep, ms_gram, ms_tuple, ms_merge, ms_refit, ms_total;
   double ms_tuple_kernel;            /* the tuple kernel alone (last search pass) */

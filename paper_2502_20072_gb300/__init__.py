@@ -50,7 +50,8 @@ class Options(ctypes.Structure):
                 ("rank_deficient_pivot_ratio", ctypes.c_double),
                 ("autotune", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("autotune_cache_path", ctypes.c_char_p),
-                ("timeout_seconds", ctypes.c_double)]
+                ("timeout_seconds", ctypes.c_double),
+                ("fp64_rerun_uncertified", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -65,7 +66,7 @@ class Stats(ctypes.Structure):
                 ("n_eligible_min", ctypes.c_int64), ("max_pool_rel_error", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("graph_replayed", ctypes.c_int32),
                 ("tuned_items_factor", ctypes.c_int32), ("tuned_ctas_per_sm", ctypes.c_int32),
-                ("reserved1", ctypes.c_int32),
+                ("fp64_rerun", ctypes.c_int32),
                 ("ms_prep", ctypes.c_double), ("ms_gram", ctypes.c_double),
                 ("ms_tuple", ctypes.c_double), ("ms_merge", ctypes.c_double),
                 ("ms_refit", ctypes.c_double), ("ms_total", ctypes.c_double),
@@ -176,7 +177,7 @@ class Handle:
     def __init__(self, precision=FP64, task_mode=PER_TASK, device=0, stream=None,
                  candidate_pool=0, max_candidate_pool=2048, timeout_seconds=300.0,
                  fp32_fallback_pivot_ratio=1e-6, rank_deficient_pivot_ratio=1e-12,
-                 autotune=0, use_graph=0, autotune_cache_path=None):
+                 autotune=0, use_graph=0, autotune_cache_path=None, fp64_rerun_uncertified=1):
         L = lib()
         o = Options()
         L.sisso_l0_default_options(ctypes.byref(o))
@@ -191,6 +192,7 @@ class Handle:
         o.rank_deficient_pivot_ratio = float(rank_deficient_pivot_ratio)
         o.autotune = int(autotune)
         o.use_graph = int(use_graph)
+        o.fp64_rerun_uncertified = int(fp64_rerun_uncertified)
         self._cache_path = (autotune_cache_path.encode() if isinstance(autotune_cache_path, str)
                             else autotune_cache_path)
         o.autotune_cache_path = self._cache_path

@@ -76,6 +76,7 @@ struct sisso_l0_handle {
   DevBuf dfr_key, dfr_len, dfr_n, dfr_cnt;
   DevBuf abf, bbf, kmeta, gram32;
   DevBuf prop_in, prop_pairs, prop_bits, prop_ctr, sel_hist, sel_bin, scores, diag;
+  DevBuf col_hash, col_cls;
   int binom_m = -1;
   int done_init_for = 0;
   cudaEvent_t ev[8] = {nullptr};
@@ -354,6 +355,8 @@ int prep_pass(sisso_l0_t h, FitPlan &P) {
   const long long N = P.N;
   L0_CK(cudaMemsetAsync(h->err.p, 0, 16, st), "memset");
   L0_CK(cudaEventRecord(h->ev[0], st), "event");
+  L0_CK(l0::launch_column_classes(P.Xd, N, m, h->col_hash.as<u64>(), h->col_cls.as<int>(), st),
+        "class kernel");
   if (!P.mixed) {
     L0_CK(l0::launch_centre(P.Xd, P.yd, N, m, h->offs.as<long long>(), n_tasks, h->mu.as<double>(),
                             h->inv_s.as<double>(), h->w64.as<double>(), h->err.as<int>(), st),
@@ -414,6 +417,7 @@ l0::TileArgs<R> tile_args(sisso_l0_t h, const FitPlan &P, int K, int S, const R 
   a.inv_s = h->inv_s.as<double>();
   a.mp1 = P.m + 1;
   a.n_total = P.N;
+  a.cls = h->col_cls.as<int>();
   return a;
 }
 
@@ -467,6 +471,7 @@ int search_pass(sisso_l0_t h, FitPlan &P, int K, const R *G) {
       pa.ld = P.ld;
       pa.diag = h->diag.as<R>();
       pa.m = P.m;
+      pa.cls = h->col_cls.as<int>();
       pa.pairs = h->prop_pairs.as<int>();
       pa.n_pairs = P.n_pairs;
       pa.bits = h->prop_bits.as<unsigned>();
@@ -895,6 +900,8 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
   P.ld = ((long long)mp1 + 31) / 32 * 32;
   P.gstride = (long long)mp1 * P.ld;
   L0_CK(h->mu.ensure((size_t)n_tasks * mp1 * 8), "alloc mu");
+  L0_CK(h->col_hash.ensure((size_t)m * 8), "alloc column hashes");
+  L0_CK(h->col_cls.ensure((size_t)m * 4), "alloc column classes");
   L0_CK(h->inv_s.ensure((size_t)n_tasks * mp1 * 8), "alloc inv_s");
   L0_CK(h->w64.ensure((size_t)mp1 * N * 8), "alloc W");
   if (!P.mixed) {
@@ -1040,7 +1047,7 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
   // FP64 Gram + two redo kernels), merge, re-fit, select
   const long long per_pass = 5 + (P.has_singles ? 1 : 0) + (P.mixed && P.has_tuples ? 3 : 0) -
                              (P.has_tuples ? 0 : 1);
-  S.kernel_launches = (P.mixed ? 2 : 1 + n_tasks) + per_pass * (enl + 1);
+  S.kernel_launches = 2 + (P.mixed ? 2 : 1 + n_tasks) + per_pass * (enl + 1);
   S.graph_replayed = replayed ? 1 : 0;
   S.tuned_items_factor = h->opt.autotune ? P.items_factor : tf;
   S.tuned_ctas_per_sm = h->opt.autotune ? P.grid / std::max(1, h->n_sm) : tb;
@@ -1052,6 +1059,24 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
   S.ms_total = t_prep + t_gram + ms_tuple + ms_merge + ms_refit;
   S.ms_tuple_kernel = h->ms_tuple_kernel;
   return SISSO_L0_OK;
+}
+
+// A mixed-precision fit whose pool stays uncertified at the largest K' is
+// one where the FP32 score errors reach the gaps between the best scores;
+// FP64 is what stability needs there, so the fit is redone in FP64.
+int fit_checked(sisso_l0_t h, const double *X, const double *y, const int64_t *task_offsets,
+                int32_t n_tasks, int64_t n_sis, const sisso_l0_request *reqs, int32_t n_reqs) {
+  int rc = fit_requests(h, X, y, task_offsets, n_tasks, n_sis, reqs, n_reqs);
+  if (rc || h->opt.precision != SISSO_L0_MIXED_BF16X3 || h->stats.certified ||
+      !h->opt.fp64_rerun_uncertified)
+    return rc;
+  const double ms_first = h->stats.ms_total;
+  h->opt.precision = SISSO_L0_FP64;
+  rc = fit_requests(h, X, y, task_offsets, n_tasks, n_sis, reqs, n_reqs);
+  h->opt.precision = SISSO_L0_MIXED_BF16X3;
+  h->stats.fp64_rerun = 1;
+  h->stats.ms_total += ms_first;
+  return rc;
 }
 
 }  // namespace
@@ -1074,6 +1099,7 @@ int sisso_l0_default_options(sisso_l0_options *opt) {
   opt->use_graph = 0;
   opt->autotune_cache_path = nullptr;
   opt->timeout_seconds = 0.0;
+  opt->fp64_rerun_uncertified = 1;
   return SISSO_L0_OK;
 }
 
@@ -1119,7 +1145,7 @@ int sisso_l0_fit(sisso_l0_t h, const double *X, const double *y, const int64_t *
     cudaError_t e = cudaSetDevice(h->opt.device);
     if (e != cudaSuccess) return cuda_fail(h, e, "set device");
     sisso_l0_request r{n_dim, k, out_tuples, out_rmse};
-    return fit_requests(h, X, y, task_offsets, n_tasks, n_sis, &r, 1);
+    return fit_checked(h, X, y, task_offsets, n_tasks, n_sis, &r, 1);
   } catch (const std::bad_alloc &) {
     return fail(h, SISSO_L0_ENOMEM, "host allocation failed");
   } catch (...) {
@@ -1134,7 +1160,7 @@ int sisso_l0_fit_multi(sisso_l0_t h, const double *X, const double *y,
   try {
     cudaError_t e = cudaSetDevice(h->opt.device);
     if (e != cudaSuccess) return cuda_fail(h, e, "set device");
-    return fit_requests(h, X, y, task_offsets, n_tasks, n_sis, reqs, n_reqs);
+    return fit_checked(h, X, y, task_offsets, n_tasks, n_sis, reqs, n_reqs);
   } catch (const std::bad_alloc &) {
     return fail(h, SISSO_L0_ENOMEM, "host allocation failed");
   } catch (...) {
@@ -1166,7 +1192,7 @@ void sisso_l0_destroy(sisso_l0_t h) {
                     &h->cert, &h->out_t, &h->out_r, &h->err, &h->dfr_key, &h->dfr_len, &h->dfr_n,
                     &h->dfr_cnt, &h->abf, &h->bbf, &h->kmeta, &h->gram32, &h->prop_in,
                     &h->prop_pairs, &h->prop_bits, &h->prop_ctr, &h->sel_hist, &h->sel_bin,
-                    &h->scores, &h->diag};
+                    &h->scores, &h->diag, &h->col_hash, &h->col_cls};
   for (DevBuf *b : bufs) b->release();
   for (int i = 0; i < 8; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);

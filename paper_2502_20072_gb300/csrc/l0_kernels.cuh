@@ -52,6 +52,8 @@ struct TileArgs {
   // tuple, (problem << 8) | run length (<= 128); dfr_n[0] runs, dfr_n[1] tuples
   u64 *dfr_key; unsigned *dfr_len; u64 *dfr_n; long long dfr_cap;
   int *err;
+  const int *cls;                  // [m] duplicate class of each column (smallest index
+                                   // of the columns equal to it), or null
   // SHARED mode (shared_T > 0): Grams of tasks 0..T-1 at G + t * shared_gstride;
   // task weights S_yy,t / N from inv_s[t * mp1] and n_total
   int shared_T;
@@ -84,6 +86,12 @@ __host__ __device__ inline bool defer_wants_gram(u64 n_tuples, int m, int d) {
 }
 
 // kernels (host launch wrappers)
+// duplicate classes of the columns: cls[j] = the smallest i with column i
+// equal to column j over all rows (relative difference <= 1e-12); a tuple
+// holding two columns of one class is exactly rank deficient
+cudaError_t launch_column_classes(const double *X, long long n_total, int m, u64 *hash, int *cls,
+                                  cudaStream_t st);
+
 cudaError_t launch_centre(const double *X, const double *y, long long n_total,
                           int m, const long long *offsets_dev, int T,
                           double *mu, double *inv_s, double *W64, int *err,
@@ -305,6 +313,7 @@ cudaError_t launch_pairs_from_list(const int *in, long long n, int m, int *pairs
 template <typename R>
 struct PropArgs {
   const R *G; long long ld; const R *diag; int m;
+  const int *cls;
   const int *pairs; long long n_pairs; const unsigned *bits;
   u64 *pair_ctr; u64 *fits;
   Binom B; u64 total;

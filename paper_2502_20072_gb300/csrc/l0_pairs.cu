@@ -276,6 +276,8 @@ proposal_kernel(PropArgs<R> A) {
     const R l11 = sqrt(gii > R(0) ? gii : R(1)), il11 = R(1) / l11;
     const R l21 = gij * il11, d2 = gjj - l21 * l21;
     const bool pair_ok = gii > R(0) && gjj > R(0) && d2 >= (R)A.ratio * gjj;
+    // a pair of one duplicate class: all its triples are rank deficient
+    const bool pair_dup = A.cls && A.cls[pi] == A.cls[pj];
     const R il22 = R(1) / sqrt(d2 > R(0) ? d2 : R(1));
     const R z1 = cy[pi] * il11, z2 = (cy[pj] - l21 * z1) * il22;
     const R pP = g00 - z1 * z1 - z2 * z2;
@@ -304,6 +306,10 @@ proposal_kernel(PropArgs<R> A) {
           }
           if (!eval) { done |= bit; continue; }
           if (pass == 0) ++fits;
+          if (pair_dup || (A.cls && (A.cls[k] == A.cls[pi] || A.cls[k] == A.cls[pj]))) {
+            done |= bit;   // two columns of one duplicate class: ineligible
+            continue;
+          }
           const R gkk = A.diag[k];
           const R g1 = Gi[k] * il11, g2 = (Gj[k] - l21 * g1) * il22;
           const R pk = gkk - g1 * g1 - g2 * g2;

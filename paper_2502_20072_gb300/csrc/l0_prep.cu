@@ -61,6 +61,59 @@ centre_kernel(const double *__restrict__ X, const double *__restrict__ y,
   }
 }
 
+// ---------------------------------------------------- duplicate classes --
+// Column hash: XOR over rows of a mix of the row index and the value rounded
+// to 36 mantissa bits (values that differ in the last bits hash alike).
+__device__ __forceinline__ u64 mix64(u64 z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void __launch_bounds__(256)
+column_hash_kernel(const double *__restrict__ X, long long n_total, int m, u64 *hash) {
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (c >= m) return;
+  const double *src = X + (long long)c * n_total;
+  u64 h = 0;
+  for (long long i = lane; i < n_total; i += 32) {
+    const u64 b = ((u64)__double_as_longlong(src[i]) + 0x8000ull) & ~0xFFFFull;
+    h ^= mix64(b ^ ((u64)i * 0x9E3779B97F4A7C15ull));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) h ^= __shfl_xor_sync(0xffffffffu, h, o);
+  if (lane == 0) hash[c] = h;
+}
+
+__global__ void __launch_bounds__(256)
+column_class_kernel(const double *__restrict__ X, long long n_total, int m, const u64 *hash,
+                    int *cls) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  const u64 hj = hash[j];
+  const double *xj = X + (long long)j * n_total;
+  int c = j;
+  for (int i = 0; i < j; ++i) {
+    if (hash[i] != hj) continue;
+    const double *xi = X + (long long)i * n_total;
+    bool same = true;
+    for (long long r = 0; r < n_total && same; ++r) {
+      const double a = xi[r], b = xj[r];
+      same = fabs(a - b) <= 1e-12 * fmax(fabs(a), fabs(b));
+    }
+    if (same) { c = i; break; }
+  }
+  cls[j] = c;
+}
+
+cudaError_t launch_column_classes(const double *X, long long n_total, int m, u64 *hash, int *cls,
+                                  cudaStream_t st) {
+  column_hash_kernel<<<(m + 7) / 8, 256, 0, st>>>(X, n_total, m, hash);
+  column_class_kernel<<<(m + 255) / 256, 256, 0, st>>>(X, n_total, m, hash, cls);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_centre(const double *X, const double *y, long long n_total,
                           int m, const long long *offsets_dev, int T,
                           double *mu, double *inv_s, double *W64, int *err,

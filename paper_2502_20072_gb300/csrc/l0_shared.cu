@@ -39,6 +39,7 @@ __device__ void run_item_shared(const TileArgs<R> &A, const ProbDesc &pd, int pr
   c.total = pd.total;
   c.B = A.B;
   c.ratio = (R)A.ratio;
+  c.cls = A.cls;
   int pidx[DPM];
   {
     const int jend = min(c.j0 + TJ, c.m);
@@ -109,7 +110,7 @@ __device__ void run_item_shared(const TileArgs<R> &A, const ProbDesc &pd, int pr
           const R pp = -fma(g2, g2, kpn);
           const R wn = fma(g2, z2, rb.kw1[kk]);
           if (!(pp >= R(0))) {
-            if (MIXED) dfr |= bit; else bad |= bit;
+            if (MIXED && !same_class(c.cls, c.j0 + jl, c.k0 + kk)) dfr |= bit; else bad |= bit;
             continue;
           }
           score[u][v] += wt * (pP - wn * wn / (pp + rb.kpt[kk]));

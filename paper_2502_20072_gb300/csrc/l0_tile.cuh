@@ -79,7 +79,12 @@ struct ItemCtx {
   u64 total;
   Binom B;
   R ratio;
+  const int *cls;   // duplicate classes (or null)
 };
+
+__device__ __forceinline__ bool same_class(const int *cls, int a, int b) {
+  return cls && __ldg(cls + a) == __ldg(cls + b);
+}
 
 template <typename R, int DP>
 __device__ __forceinline__ void defer_run(const TileArgs<R> &A, const ItemCtx<R> &c,
@@ -205,12 +210,23 @@ __device__ __forceinline__ void make_record(const ItemCtx<R> &c, const int *pidx
     for (int p = 0; p < DP; ++p) g[p] = R(0);
   }
   const bool elig = (cdiag > R(0)) && (piv >= (R)c.ratio * cdiag);
+  // two columns of one duplicate class: exactly rank deficient, ineligible
+  // (never worth an FP64 redo)
+  bool dup = false;
+  if (c.cls && col < c.m) {
+#pragma unroll
+    for (int a = 0; a < DP; ++a) {
+      dup = dup || same_class(c.cls, pidx[a], col);
+#pragma unroll
+      for (int b = 0; b < a; ++b) dup = dup || same_class(c.cls, pidx[a], pidx[b]);
+    }
+  }
   if (isj) {
     const int j = col;
     const bool shape = (j < c.m) && (DP == 0 || pidx[DP > 0 ? DP - 1 : 0] < j);
     int flag;
     R invl = R(0), z2 = R(0), pPj = R(0), e = R(0);
-    if (!shape) {
+    if (!shape || dup) {
       flag = 0;
     } else if (!pok || !elig) {
       flag = MIXED ? 3 : 0;
@@ -239,7 +255,7 @@ __device__ __forceinline__ void make_record(const ItemCtx<R> &c, const int *pidx
       kpt = R(0);
     } else {
       kpt = (R)c.ratio * cdiag;
-      kp1 = elig ? (kpt - piv) : (MIXED ? r_inf<R>() : -r_inf<R>());
+      kp1 = dup ? -r_inf<R>() : elig ? (kpt - piv) : (MIXED ? r_inf<R>() : -r_inf<R>());
       kw1 = -w1;
     }
 #pragma unroll
@@ -286,7 +302,7 @@ __device__ __noinline__ int slow_tuple(const TileArgs<R> &A, const ItemCtx<R> &c
   const R pp = -fma(g2, g2, kpn);
   const R wn = fma(g2, rb.jz2[jl], kv.kw);
   if (!(pp >= R(0))) {           // pivot of k below the cut
-    if (MIXED) defer_run<R, DP>(A, c, rb.pidx, j, k, 1);
+    if (MIXED && !same_class(c.cls, j, k)) defer_run<R, DP>(A, c, rb.pidx, j, k, 1);
     return 1;
   }
   const R p = pp + rb.kpt[kk];

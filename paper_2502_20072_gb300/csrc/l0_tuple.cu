@@ -54,6 +54,7 @@ __device__ void run_item(const TileArgs<R> &A, const ProbDesc &pd, int prob, int
   c.total = pd.total;
   c.B = A.B;
   c.ratio = (R)A.ratio;
+  c.cls = A.cls;
   const R *G = c.G;
   const long long ld = c.ld;
   R creg[UJ][UK];
