@@ -249,9 +249,11 @@ class Handle:
         self._check(rc)
         return (out_tuples, out_rmse) if ret_np else (out_tuples, out_rmse)
 
-    def fit_multi(self, X, y, requests, offsets=None):
+    def fit_multi(self, X, y, requests, offsets=None, outs=None):
         """Several searches in one pass.  requests: list of (n_dim, k).
-        Returns a list of (tuples [n_out, k, n_dim], rmse [n_out, k])."""
+        Returns a list of (tuples [n_out, k, n_dim], rmse [n_out, k]) (numpy,
+        or the given output buffers `outs`, torch or numpy, one pair per
+        request)."""
         X = _as_f64(X)
         y = _as_f64(y)
         n_sis, n_total = int(X.shape[0]), int(X.shape[1])
@@ -260,15 +262,14 @@ class Handle:
         off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
         n_tasks = len(off) - 1
         n_out = 1 if self.task_mode == SHARED else n_tasks
-        outs = []
+        if outs is None:
+            outs = [(np.empty((n_out, k, d), dtype=np.int32), np.empty((n_out, k), dtype=np.float64))
+                    for d, k in requests]
         reqs = (Request * len(requests))()
-        for i, (d, k) in enumerate(requests):
-            t = np.empty((n_out, k, d), dtype=np.int32)
-            r = np.empty((n_out, k), dtype=np.float64)
-            outs.append((t, r))
+        for i, ((d, k), (t, r)) in enumerate(zip(requests, outs)):
             reqs[i].n_dim, reqs[i].k = int(d), int(k)
-            reqs[i].out_tuples = t.ctypes.data
-            reqs[i].out_rmse = r.ctypes.data
+            reqs[i].out_tuples = _ptr(t)
+            reqs[i].out_rmse = _ptr(r)
         rc = lib().sisso_l0_fit_multi(self._h, ctypes.c_void_p(_ptr(X)), ctypes.c_void_p(_ptr(y)),
                                       off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n_tasks,
                                       n_sis, reqs, len(requests))

@@ -594,7 +594,7 @@ int search_pass(sisso_l0_t h, FitPlan &P, int K, const R *G) {
 
 // after a pass: error word, certificate, statistics (host sync)
 int finish_pass(sisso_l0_t h, FitPlan &P, int *certified, double *delta_max, float *ms_tuple,
-                float *ms_merge, float *ms_refit) {
+                float *ms_merge, float *ms_refit, int *hopeless) {
   cudaStream_t st = h->st;
   const int n_probs = (int)P.pd.size();
   std::vector<l0::CertOut> cert(n_probs);
@@ -620,8 +620,14 @@ int finish_pass(sisso_l0_t h, FitPlan &P, int *certified, double *delta_max, flo
   P.prop_fits += pfits[1];
   *certified = 1;
   *delta_max = 0;
+  *hopeless = 0;
   for (auto &c : cert) {
-    if (!c.certified) *certified = 0;
+    if (!c.certified) {
+      *certified = 0;
+      // search-score errors of a quarter of the k-th score itself: a larger
+      // pool cannot separate the best tuples
+      if (4.0 * c.delta >= c.kth_refit) *hopeless = 1;
+    }
     *delta_max = std::max(*delta_max, c.delta);
   }
   // phase timings are statistics only: a failed read (e.g. events recorded
@@ -1008,8 +1014,10 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
                  : run_pass<double>(h, P, K, h->gram.as<double>(), with_prep, &replayed);
     if (rc) break;
     prep_done = true;
-    rc = finish_pass(h, P, &certified, &delta, &ms_tuple, &ms_merge, &ms_refit);
+    int hopeless = 0;
+    rc = finish_pass(h, P, &certified, &delta, &ms_tuple, &ms_merge, &ms_refit, &hopeless);
     if (rc) break;
+    if (!certified && hopeless && P.mixed && h->opt.fp64_rerun_uncertified) break;
     // a shard's pool is certified against the merged result, not its own
     if (certified || K >= Kmax || P.n_shards > 1) break;
     K = std::min(2 * K, Kmax);

@@ -86,31 +86,39 @@ column_hash_kernel(const double *__restrict__ X, long long n_total, int m, u64 *
   if (lane == 0) hash[c] = h;
 }
 
+// one warp per column j: lanes scan the hashes of the columns before it, 32
+// at a time; each hash match is verified by the whole warp (coalesced rows)
 __global__ void __launch_bounds__(256)
 column_class_kernel(const double *__restrict__ X, long long n_total, int m, const u64 *hash,
                     int *cls) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (j >= m) return;
   const u64 hj = hash[j];
   const double *xj = X + (long long)j * n_total;
   int c = j;
-  for (int i = 0; i < j; ++i) {
-    if (hash[i] != hj) continue;
-    const double *xi = X + (long long)i * n_total;
-    bool same = true;
-    for (long long r = 0; r < n_total && same; ++r) {
-      const double a = xi[r], b = xj[r];
-      same = fabs(a - b) <= 1e-12 * fmax(fabs(a), fabs(b));
+  for (int i0 = 0; i0 < j && c == j; i0 += 32) {
+    const int i = i0 + lane;
+    unsigned hit = __ballot_sync(0xffffffffu, i < j && hash[i] == hj);
+    while (hit && c == j) {
+      const int q = i0 + __ffs(hit) - 1;
+      hit &= hit - 1;
+      const double *xi = X + (long long)q * n_total;
+      bool same = true;
+      for (long long r = lane; r < n_total; r += 32) {
+        const double a = xi[r], b = xj[r];
+        same = same && fabs(a - b) <= 1e-12 * fmax(fabs(a), fabs(b));
+      }
+      if (__all_sync(0xffffffffu, same)) c = q;
     }
-    if (same) { c = i; break; }
   }
-  cls[j] = c;
+  if (lane == 0) cls[j] = c;
 }
 
 cudaError_t launch_column_classes(const double *X, long long n_total, int m, u64 *hash, int *cls,
                                   cudaStream_t st) {
   column_hash_kernel<<<(m + 7) / 8, 256, 0, st>>>(X, n_total, m, hash);
-  column_class_kernel<<<(m + 255) / 256, 256, 0, st>>>(X, n_total, m, hash, cls);
+  column_class_kernel<<<(m + 7) / 8, 256, 0, st>>>(X, n_total, m, hash, cls);
   return cudaGetLastError();
 }
 
