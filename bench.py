@@ -391,7 +391,7 @@ def run_learned(args):
                                                 lr=2e-3, seed=0, device=local)
     del F, Y
     torch.cuda.empty_cache()
-    prob, d, k = make_config("C5L")
+    prob, d, k = make_config("C5L", n_sis=args.learned_sis)
     m = prob.n_sis
     X = torch.from_numpy(prob.X).cuda()
     y = torch.from_numpy(prob.y).cuda()
@@ -468,6 +468,8 @@ def main():
     ap.add_argument("--fraction", type=float, default=0.01)
     ap.add_argument("--train-steps", type=int, default=4000)
     ap.add_argument("--train-instances", type=int, default=50)
+    ap.add_argument("--learned-sis", type=int, default=20000,
+                    help="columns of the learned workload (smaller for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -133,6 +133,23 @@ __device__ __forceinline__ void colex_unrank_arith(int p, u64 r, int xmax, int *
   }
 }
 
+// lexicographic unrank with arithmetic binomials: no table loads, so no
+// chain of dependent memory reads (the inverse of lex_rank)
+__device__ __forceinline__ void lex_unrank_arith(int m, int d, u64 r, u64 total, int *t) {
+  u64 q = total - 1ull - r;
+  int hi = m - 1;
+  for (int i = d; i >= 1; --i) {
+    int lo = i - 1, h = hi;
+    while (lo < h) {
+      const int mid = (lo + h + 1) >> 1;
+      if (binom_arith(mid, i) <= q) lo = mid; else h = mid - 1;
+    }
+    q -= binom_arith(lo, i);
+    t[d - i] = m - 1 - lo;
+    hi = lo - 1;
+  }
+}
+
 // next p-combination in colex order
 template <int P>
 __device__ __forceinline__ void colex_next(int *a) {

@@ -165,22 +165,33 @@ centre_split_kernel(const double *__restrict__ X, const double *__restrict__ y,
   const long long lo = offsets[t], hi = offsets[t + 1];
   const long long n = hi - lo;
   const double *src = (c == 0) ? (y + lo) : (X + (long long)(c - 1) * n_total + lo);
-  double s = 0.0;
+  // four independent partial sums per lane keep four loads in flight
+  double s4[4] = {0.0, 0.0, 0.0, 0.0};
   bool finite = true;
-  for (long long i = lane; i < n; i += 32) {
-    const double v = src[i];
-    finite &= isfinite(v);
-    s += v;
+  for (long long i0 = lane; i0 < n; i0 += 128) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long i = i0 + 32 * u;
+      const double v = (i < n) ? src[i] : 0.0;
+      finite &= isfinite(v);
+      s4[u] += v;
+    }
   }
+  double s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
   if (__any_sync(0xffffffffu, !finite) && lane == 0) set_err(err, 5);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   const double mean = s / (double)n;
-  double ss = 0.0;
-  for (long long i = lane; i < n; i += 32) {
-    const double v = src[i] - mean;
-    ss += v * v;
+  double q4[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long long i0 = lane; i0 < n; i0 += 128) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long i = i0 + 32 * u;
+      const double v = (i < n) ? src[i] - mean : 0.0;
+      q4[u] = fma(v, v, q4[u]);
+    }
   }
+  double ss = (q4[0] + q4[1]) + (q4[2] + q4[3]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
   const double nrm = sqrt(ss);
@@ -193,6 +204,7 @@ centre_split_kernel(const double *__restrict__ X, const double *__restrict__ y,
   const long long np = npad[t];
   __nv_bfloat16 *Ar = A + (long long)c * ldk + kb;
   __nv_bfloat16 *Br = B + (long long)c * ldk + kb;
+#pragma unroll 4
   for (long long i = lane; i < n; i += 32) {
     const double z = (src[i] - mean) * is;
     if (W) W[(long long)c * n_total + lo + i] = z;

@@ -188,8 +188,26 @@ __device__ void block_reduce(double *v, int nv, bool take_max, double (*red)[L0_
 // Householder least squares of one task's rows (paper Sec. 2.4: QR by
 // Householder reflections, least-squares fit, squared deviation) by one CTA.
 // A holds the d centred columns and the centred target as column d, each of
-// length n; row i is owned by thread i mod REFIT_THREADS.  Norms are scaled
-// two-pass sums of squares.  Returns SSE; *rho = min_j |R_jj| / ||a_j||.
+// length n; row i is owned by thread i mod REFIT_THREADS.  Each reflection
+// takes one pass over the rows for the norm of its column and the dot
+// products with the later columns, and one pass for the update.  Norms are
+// plain sums of squares (FP64 holds the squares of any centred value below
+// 1e150; a column whose sum overflows is rescaled by its maximum first).
+// Returns SSE; *rho = min_j |R_jj| / ||a_j||.
+__device__ double norm_scaled(const double *a, long long lo, long long n,
+                              double (*red)[L0_DMAX + 1]) {
+  double v[1] = {0.0};
+  for (long long i = lo + threadIdx.x; i < n; i += REFIT_THREADS) v[0] = fmax(v[0], fabs(a[i]));
+  block_reduce(v, 1, true, red);
+  const double m1 = v[0];
+  if (!(m1 > 0.0)) return 0.0;
+  const double im1 = 1.0 / m1;
+  v[0] = 0.0;
+  for (long long i = lo + threadIdx.x; i < n; i += REFIT_THREADS) { const double q = a[i] * im1; v[0] += q * q; }
+  block_reduce(v, 1, false, red);
+  return m1 * sqrt(v[0]);
+}
+
 __device__ double householder_cta(double *A, long long n, int d,
                                   double (*red)[L0_DMAX + 1], double *rho) {
   const int tid = threadIdx.x;
@@ -197,30 +215,30 @@ __device__ double householder_cta(double *A, long long n, int d,
   // norms of the original centred columns
   for (int j = 0; j < d; ++j) v[j] = 0.0;
   for (long long i = tid; i < n; i += REFIT_THREADS)
-    for (int j = 0; j < d; ++j) v[j] = fmax(v[j], fabs(A[(long long)j * n + i]));
-  block_reduce(v, d, true, red);
-  double mx[L0_DMAX];
-  for (int j = 0; j < d; ++j) { mx[j] = v[j]; v[j] = 0.0; }
-  for (long long i = tid; i < n; i += REFIT_THREADS)
-    for (int j = 0; j < d; ++j)
-      if (mx[j] > 0.0) { const double r = A[(long long)j * n + i] / mx[j]; v[j] += r * r; }
+    for (int j = 0; j < d; ++j) {
+      const double x = A[(long long)j * n + i];
+      v[j] = fma(x, x, v[j]);
+    }
   block_reduce(v, d, false, red);
-  for (int j = 0; j < d; ++j) cn[j] = mx[j] > 0.0 ? mx[j] * sqrt(v[j]) : 0.0;
+  for (int j = 0; j < d; ++j) {
+    cn[j] = sqrt(v[j]);
+    if (!isfinite(v[j])) cn[j] = norm_scaled(A + (long long)j * n, 0, n, red);
+  }
   double r = DBL_MAX;
   for (int j = 0; j < d; ++j) {
     double *aj = A + (long long)j * n;
-    // sigma = ||aj[j..n)||, scaled two-pass
-    v[0] = 0.0;
-    for (long long i = j + tid; i < n; i += REFIT_THREADS) v[0] = fmax(v[0], fabs(aj[i]));
-    block_reduce(v, 1, true, red);
-    const double m1 = v[0];
-    double sigma = 0.0;
-    if (m1 > 0.0) {
-      v[0] = 0.0;
-      for (long long i = j + tid; i < n; i += REFIT_THREADS) { const double q = aj[i] / m1; v[0] += q * q; }
-      block_reduce(v, 1, false, red);
-      sigma = m1 * sqrt(v[0]);
+    const int nc = d - j;   // columns j+1 .. d (the target is column d)
+    // one pass: ||aj[j..n)||^2 and aj[j+1..n) . ac[j+1..n) for the later columns
+    for (int c = 0; c <= nc; ++c) v[c] = 0.0;
+    for (long long i = j + tid; i < n; i += REFIT_THREADS) {
+      const double ai = aj[i];
+      v[nc] = fma(ai, ai, v[nc]);
+      if (i > j)
+        for (int c = 0; c < nc; ++c) v[c] = fma(ai, A[(long long)(j + 1 + c) * n + i], v[c]);
     }
+    block_reduce(v, nc + 1, false, red);
+    double sigma = sqrt(v[nc]);
+    if (!isfinite(v[nc])) sigma = norm_scaled(aj, j, n, red);
     if (sigma == 0.0) {
       r = 0.0;
       continue;
@@ -229,13 +247,6 @@ __device__ double householder_cta(double *A, long long n, int d,
     const double alpha = (x0 >= 0.0) ? -sigma : sigma;
     const double v0 = x0 - alpha;
     const double beta = 1.0 / (sigma * (sigma + fabs(x0)));
-    const int nc = d - j;   // columns j+1 .. d (the target is column d)
-    for (int c = 0; c < nc; ++c) v[c] = 0.0;
-    for (long long i = j + 1 + tid; i < n; i += REFIT_THREADS) {
-      const double ai = aj[i];
-      for (int c = 0; c < nc; ++c) v[c] += ai * A[(long long)(j + 1 + c) * n + i];
-    }
-    block_reduce(v, nc, false, red);
     for (int c = 0; c < nc; ++c) {
       double *ac = A + (long long)(j + 1 + c) * n;
       const double sdot = (v[c] + v0 * ac[j]) * beta;
@@ -271,7 +282,7 @@ refit_kernel(RefitArgs a) {
   const int d = pd.d;
   if (threadIdx.x == 0) {
     int t[L0_DMAX];
-    lex_unrank(a.B, pd.m, d, a.pool_k[(size_t)prob * a.K + cidx], pd.total, t);
+    lex_unrank_arith(pd.m, d, a.pool_k[(size_t)prob * a.K + cidx], pd.total, t);
     for (int q = 0; q < d; ++q) s_t[q] = t[q];
   }
   __syncthreads();
@@ -284,11 +295,24 @@ refit_kernel(RefitArgs a) {
   for (int tk = t_lo; tk < t_hi; ++tk) {
     const long long lo = a.offsets[tk], hi = a.offsets[tk + 1], n = hi - lo;
     const double *mu = a.mu + (size_t)tk * (a.m + 1);
+    // centred columns into A: eight loads in flight per thread per column
     for (int q = 0; q <= d; ++q) {
       const double *src = (q < d) ? a.X + (long long)s_t[q] * a.n_total + lo : a.y + lo;
       const double mean = (q < d) ? mu[s_t[q] + 1] : mu[0];
       double *dst = A + (long long)q * n;
-      for (long long i = threadIdx.x; i < n; i += REFIT_THREADS) dst[i] = src[i] - mean;
+      for (long long i0 = threadIdx.x; i0 < n; i0 += 8 * REFIT_THREADS) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const long long i = i0 + (long long)u * REFIT_THREADS;
+          v[u] = (i < n) ? __ldg(src + i) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const long long i = i0 + (long long)u * REFIT_THREADS;
+          if (i < n) dst[i] = v[u] - mean;
+        }
+      }
     }
     __syncthreads();
     double rho;
@@ -369,7 +393,7 @@ select_kernel(SelectArgs<R> a) {
     double *orr = a.out_rmse + pd.out_r_off + i;
     if (i < nvalid) {
       int t[L0_DMAX];
-      lex_unrank(a.B, pd.m, d, sk[i], pd.total, t);
+      lex_unrank_arith(pd.m, d, sk[i], pd.total, t);
       for (int q = 0; q < d; ++q) ot[q] = t[q];
       *orr = sqrt(fmax(ss[i], 0.0) / div);
     } else {
@@ -407,7 +431,7 @@ __global__ void unrank_kernel(Binom B, int m, int d, u64 total, const u64 *ranks
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
   int t[L0_DMAX];
-  lex_unrank(B, m, d, ranks[i], total, t);
+  lex_unrank_arith(m, d, ranks[i], total, t);
   for (int q = 0; q < d; ++q) tuples[i * d + q] = t[q];
 }
 
@@ -427,7 +451,7 @@ merge_shards_kernel(Binom B, int m, int d, u64 total, int k, double n_rows, cons
     int *ot = out_tuples + (size_t)i * d;
     if (i < P && isfinite(ss[i])) {
       int t[L0_DMAX];
-      lex_unrank(B, m, d, sk[i], total, t);
+      lex_unrank_arith(m, d, sk[i], total, t);
       for (int q = 0; q < d; ++q) ot[q] = t[q];
       out_rmse[i] = sqrt(fmax(ss[i], 0.0) / n_rows);
     } else {
