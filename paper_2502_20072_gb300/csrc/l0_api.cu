@@ -449,7 +449,7 @@ int search_pass(sisso_l0_t h, FitPlan &P, int K, const R *G) {
     // tuples outside them
     L0_CK(l0::launch_seed<R>(G, h->probs.as<l0::ProbDesc>(), n_probs, K, S,
                              (P.shared || P.proposal) ? 0 : 1, ratio, B, h->gthr.as<u64>(),
-                             h->hist.as<unsigned>(), st),
+                             h->hist.as<unsigned>(), std::max(P.m, 2 * K + 64), st),
           "seed kernel");
   }
   if (P.has_singles) {
@@ -712,7 +712,8 @@ int autotune(sisso_l0_t h, FitPlan &P, int K, const R *G) {
       L0_CK(l0::launch_seed<R>(G, h->probs.as<l0::ProbDesc>(), n_probs, K, S, P.shared ? 0 : 1,
                                P.mixed ? h->opt.fp32_fallback_pivot_ratio
                                        : h->opt.rank_deficient_pivot_ratio,
-                               B, h->gthr.as<u64>(), h->hist.as<unsigned>(), st),
+                               B, h->gthr.as<u64>(), h->hist.as<unsigned>(),
+                             std::max(P.m, 2 * K + 64), st),
             "seed kernel");
       L0_CK(cudaMemsetAsync(h->ctr.p, 0, 8, st), "memset");
       if (P.mixed) L0_CK(cudaMemsetAsync(h->dfr_n.p, 0, 24, st), "memset");

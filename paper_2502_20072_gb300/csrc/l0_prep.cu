@@ -99,7 +99,7 @@ column_class_kernel(const double *__restrict__ X, long long n_total, int m, cons
   int c = j;
   for (int i0 = 0; i0 < j && c == j; i0 += 32) {
     const int i = i0 + lane;
-    unsigned hit = __ballot_sync(0xffffffffu, i < j && hash[i] == hj);
+    unsigned hit = __ballot_sync(0xffffffffu, i < j && __ldg(hash + i) == hj);
     while (hit && c == j) {
       const int q = i0 + __ffs(hit) - 1;
       hit &= hit - 1;

@@ -29,15 +29,42 @@ __device__ __forceinline__ R gram_at(const R *G, long long ld, int a, int b) {
 // one CTA per problem
 constexpr int SEED_THREADS = 1024;
 
+__device__ __forceinline__ unsigned ord32f(float x) {
+  const unsigned b = __float_as_uint(x);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float f32_up(float x) { return x; }
+__device__ __forceinline__ float f32_up(double x) { return __double2float_ru(x); }
+
+// smallest key T with #{keys <= T} >= want (keys[0..n) in shared memory; all
+// threads; binary search over the 32-bit key space, one block count each)
+__device__ unsigned select_key(const unsigned *keys, int n, int want, int *s_cnt) {
+  unsigned lo = 0u, hi = 0xffffffffu;
+  while (lo < hi) {
+    const unsigned mid = lo + ((hi - lo) >> 1);
+    int c = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) c += keys[i] <= mid ? 1 : 0;
+    if (threadIdx.x == 0) *s_cnt = 0;
+    __syncthreads();
+    if (c) atomicAdd(s_cnt, c);
+    __syncthreads();
+    const int tot = *s_cnt;
+    __syncthreads();
+    if (tot >= want) hi = mid; else lo = mid + 1u;
+  }
+  return lo;
+}
+
+// The K'-th best score of all d-tuples of the M columns with the best
+// single-column fits: two order-statistic searches (no sorting).
 template <typename R>
 __global__ void __launch_bounds__(SEED_THREADS)
 seed_kernel(const R *Gbase, const ProbDesc *probs, int K, int S, int seed, double ratio,
-            Binom B, u64 *gthr, unsigned *hist) {
+            Binom B, u64 *gthr, unsigned *hist, int max_keys) {
   extern __shared__ __align__(16) unsigned char smem[];
+  unsigned *keys = (unsigned *)smem;            // [max(m, tuples)]
   __shared__ int cols[64];
-  __shared__ u64 s_total;
-  unsigned char *p = smem;
-  CtaList<R> L = cta_list_carve<R>(p, K, S);
+  __shared__ int s_cnt, s_n;
   const int prob = blockIdx.x;
   const ProbDesc pd = probs[prob];
   if (threadIdx.x == 0) gthr[prob] = ord_inf<R>();
@@ -52,128 +79,125 @@ seed_kernel(const R *Gbase, const ProbDesc *probs, int K, int S, int seed, doubl
     if (small_binom(q, pd.d) >= 2ull * (u64)K) { M = q; break; }
   const R *G = Gbase + pd.g_off;
   const long long ld = pd.ld;
-  const int m = pd.m, d = pd.d;
+  const int d = pd.d;
+  const int m = min(pd.m, max_keys);   // a prefix of the columns when n_sis is huge
   const R G00 = G[0];
-  // 1. the M best single columns
-  L.K = M;
-  cta_list_reset<R>(L, nullptr);
-  __syncthreads();
-  for (int base = 0; base < m; base += blockDim.x) {
-    const int k = base + threadIdx.x;
-    R rel = R(0);
-    bool ok = false;
-    if (k < m) {
-      const R ckk = G[(long long)(k + 1) * (ld + 1)];
-      const R ck = G[k + 1];
-      ok = ckk > R(0);
-      rel = G00 - ck * ck / ckk;
-    }
-    int redo = 0;
-    do {
-      if (ok && cta_list_admits<R>(L, rel, (u64)k)) cta_list_push<R>(L, rel, (u64)k);
-      __syncthreads();
-      if (++redo > L0_MAX_REDO) break;
-    } while (cta_list_fold<R>(L, nullptr));
+  // 1. the M best single columns: 1 - r_j^2 as ordered keys
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    const R ckk = G[(long long)(k + 1) * (ld + 1)];
+    const R ck = G[k + 1];
+    keys[k] = (ckk > R(0)) ? ord32f(f32_up(G00 - ck * ck / ckk)) : 0xffffffffu;
   }
-  const int Mr = *(volatile int *)L.n_list;
+  __syncthreads();
+  const unsigned t1 = select_key(keys, m, M, &s_cnt);
+  if (threadIdx.x == 0) s_n = 0;
+  __syncthreads();
+  for (int k = threadIdx.x; k < m; k += blockDim.x)
+    if (keys[k] < t1) cols[atomicAdd(&s_n, 1)] = k;   // fewer than M by construction
+  __syncthreads();
+  for (int k = threadIdx.x; k < m; k += blockDim.x)
+    if (keys[k] == t1) {
+      const int slot = atomicAdd(&s_n, 1);
+      if (slot < M) cols[slot] = k;
+    }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    for (int i = 0; i < Mr; ++i) cols[i] = (int)L.lk[i];
+    const int Mr = min(s_n, M);
+    s_n = Mr;
     for (int i = 1; i < Mr; ++i) {     // ascending column order
       int v = cols[i], q = i - 1;
       while (q >= 0 && cols[q] > v) { cols[q + 1] = cols[q]; --q; }
       cols[q + 1] = v;
     }
-    s_total = small_binom(Mr, d);
   }
   __syncthreads();
-  const u64 total = s_total;
+  const int Mr = s_n;
+  const u64 total = small_binom(Mr, d);
   if (total < (u64)K) return;     // too few tuples to bound the K'-th
-  // 2. every d-tuple of those columns, exact augmented Cholesky
-  L.K = K;
-  cta_list_reset<R>(L, nullptr);
-  __syncthreads();
-  for (u64 base = 0; base < total; base += blockDim.x) {
-    const u64 r = base + threadIdx.x;
-    R rel = R(0);
-    bool ok = false;
-    u64 key = 0;
-    if (r < total) {
-      int a[L0_DMAX];
-      {  // colex unrank over the Mr seed columns
-        u64 q = r;
-        int hi = Mr - 1;
-        for (int i = d; i >= 1; --i) {
-          int lo = i - 1, h = hi;
-          while (lo < h) {
-            const int mid = (lo + h + 1) >> 1;
-            if (small_binom(mid, i) <= q) lo = mid; else h = mid - 1;
-          }
-          q -= small_binom(lo, i);
-          a[i - 1] = lo;
-          hi = lo - 1;
+  // 2. every d-tuple of those columns (at most the key capacity; a subset of
+  // real tuples bounds the K'-th best just as well), exact augmented Cholesky
+  const int nt = (int)(total < (u64)max_keys ? total : (u64)max_keys);
+  for (int r = threadIdx.x; r < nt; r += blockDim.x) {
+    int a[L0_DMAX];
+    {  // colex unrank over the Mr seed columns
+      u64 q = (u64)r;
+      int hi = Mr - 1;
+      for (int i = d; i >= 1; --i) {
+        int lo = i - 1, h = hi;
+        while (lo < h) {
+          const int mid = (lo + h + 1) >> 1;
+          if (small_binom(mid, i) <= q) lo = mid; else h = mid - 1;
         }
+        q -= small_binom(lo, i);
+        a[i - 1] = lo;
+        hi = lo - 1;
       }
-      int t[L0_DMAX];
-      for (int i = 0; i < d; ++i) t[i] = cols[a[i]];
-      // Cholesky of (t_1 .. t_d, target): pivots of the features checked,
-      // the last pivot is rel = SSE / S_yy
-      R Lm[L0_DMAX + 1][L0_DMAX + 1];
-      ok = true;
-      for (int i = 0; i <= d; ++i) {
-        const int ia = (i < d) ? t[i] + 1 : 0;
-        for (int j = 0; j <= i; ++j) {
-          const int ib = (j < d) ? t[j] + 1 : 0;
-          R c = gram_at<R>(G, ld, ia, ib);
-          const R orig = c;
-          for (int q = 0; q < j; ++q) c -= Lm[i][q] * Lm[j][q];
-          if (j < i) {
-            Lm[i][j] = c / Lm[j][j];
-          } else if (i < d) {
-            ok = ok && orig > R(0) && c >= (R)ratio * orig;
-            Lm[i][i] = sqrt(c > R(0) ? c : R(1));
-          } else {
-            rel = c;
-          }
-        }
-      }
-      key = lex_rank(B, m, d, t, pd.total);
     }
-    int redo = 0;
-    do {
-      if (ok && cta_list_admits<R>(L, rel, key)) cta_list_push<R>(L, rel, key);
-      __syncthreads();
-      if (++redo > L0_MAX_REDO) break;
-    } while (cta_list_fold<R>(L, nullptr));
+    int t[L0_DMAX];
+    for (int i = 0; i < d; ++i) t[i] = cols[a[i]];
+    // Cholesky of (t_1 .. t_d, target): pivots of the features checked,
+    // the last pivot is rel = SSE / S_yy
+    R Lm[L0_DMAX + 1][L0_DMAX + 1];
+    R rel = R(0);
+    bool ok = true;
+    for (int i = 0; i <= d; ++i) {
+      const int ia = (i < d) ? t[i] + 1 : 0;
+      for (int j = 0; j <= i; ++j) {
+        const int ib = (j < d) ? t[j] + 1 : 0;
+        R c = gram_at<R>(G, ld, ia, ib);
+        const R orig = c;
+        for (int q = 0; q < j; ++q) c -= Lm[i][q] * Lm[j][q];
+        if (j < i) {
+          Lm[i][j] = c / Lm[j][j];
+        } else if (i < d) {
+          ok = ok && orig > R(0) && c >= (R)ratio * orig;
+          Lm[i][i] = sqrt(c > R(0) ? c : R(1));
+        } else {
+          rel = c;
+        }
+      }
+    }
+    keys[r] = ok ? ord32f(f32_up(rel)) : 0xffffffffu;
   }
-  if (threadIdx.x == 0 && *(volatile int *)L.n_list >= K)
-    atomicMin(gthr + prob, ord_of(L.ls[K - 1]));
+  __syncthreads();
+  // the K'-th smallest score (rounded up to FP32): K' real tuples lie at or
+  // below it, so it bounds the search's K'-th best
+  const unsigned t2 = select_key(keys, nt, K, &s_cnt);
+  if (threadIdx.x == 0 && t2 != 0xffffffffu) {
+    const unsigned b = (t2 & 0x80000000u) ? (t2 & 0x7fffffffu) : ~t2;
+    atomicMin(gthr + prob, ord_of((R)__uint_as_float(b)));
+  }
 }
 
 }  // namespace
 
 template <typename R>
 size_t seed_smem_bytes(int K, int S) {
-  return cta_list_bytes<R>(K, S) + 16;
+  (void)S;
+  return 0;   // the key array is sized per launch (n_sis, 2 K' + 64 tuples)
 }
 
 template <typename R>
 cudaError_t launch_seed(const R *G, const ProbDesc *probs_dev, int n_probs, int K, int S,
                         int seed, double ratio, const Binom &B, u64 *gthr, unsigned *hist,
-                        cudaStream_t st) {
-  const size_t smem = seed_smem_bytes<R>(K, S);
+                        int max_keys, cudaStream_t st) {
+  if (max_keys > 50000) max_keys = 50000;   // 200 KB of keys
+  const size_t smem = (size_t)4 * (size_t)max_keys;
   cudaError_t e =
       cudaFuncSetAttribute(seed_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   seed_kernel<R><<<n_probs, SEED_THREADS, smem, st>>>(G, probs_dev, K, S, seed, ratio, B, gthr,
-                                                                hist);
+                                                                hist, max_keys);
   return cudaGetLastError();
 }
 
 template size_t seed_smem_bytes<double>(int, int);
 template size_t seed_smem_bytes<float>(int, int);
 template cudaError_t launch_seed<double>(const double *, const ProbDesc *, int, int, int, int,
-                                         double, const Binom &, u64 *, unsigned *, cudaStream_t);
+                                         double, const Binom &, u64 *, unsigned *, int,
+                                         cudaStream_t);
 template cudaError_t launch_seed<float>(const float *, const ProbDesc *, int, int, int, int,
-                                        double, const Binom &, u64 *, unsigned *, cudaStream_t);
+                                        double, const Binom &, u64 *, unsigned *, int,
+                                        cudaStream_t);
 
 }  // namespace l0

@@ -344,7 +344,7 @@ __device__ double block_max(double v, double *red) {
 // One CTA per problem: sort the pool by (refit score, key), emit the best k,
 // and evaluate the certificate.
 template <typename R>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(256)
 select_kernel(SelectArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int prob = blockIdx.x;
@@ -531,7 +531,7 @@ cudaError_t launch_select(const SelectArgs<R> &a, cudaStream_t st) {
   size_t smem = (size_t)P * 16;
   cudaError_t e = cudaFuncSetAttribute(select_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  select_kernel<R><<<a.n_probs, 1024, smem, st>>>(a);
+  select_kernel<R><<<a.n_probs, 256, smem, st>>>(a);
   return cudaGetLastError();
 }
 
