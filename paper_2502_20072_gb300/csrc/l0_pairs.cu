@@ -243,7 +243,7 @@ constexpr int PROP_THREADS = 256;
 constexpr int PROP_U = 8;   // third columns per lane per round
 
 template <typename R>
-__global__ void __launch_bounds__(PROP_THREADS)
+__global__ void __launch_bounds__(PROP_THREADS, 2)
 proposal_kernel(PropArgs<R> A) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char *p = smem;
@@ -285,6 +285,28 @@ proposal_kernel(PropArgs<R> A) {
       const u64 gprev = gnext;
       if (tid < 32) gnext = ld_relaxed(A.gthr);
       unsigned done = 0u;
+      // all loads of the round first (no branches between them), so that the
+      // lane has its 8 columns' Gram entries and bitmap words in flight at once
+      R ld_gi[PROP_U], ld_gj[PROP_U], ld_gk[PROP_U], ld_cy[PROP_U];
+      unsigned ld_w1[PROP_U], ld_w2[PROP_U];
+      int ld_cl[PROP_U];
+#pragma unroll
+      for (int u = 0; u < PROP_U; ++u) {
+        const int k = k0 + u * 32 + lane;
+        const int kc = k < A.m ? k : A.m - 1;
+        ld_gi[u] = Gi[kc];
+        ld_gj[u] = Gj[kc];
+        ld_gk[u] = A.diag[kc];
+        ld_cy[u] = cy[kc];
+        ld_cl[u] = A.cls ? __ldg(A.cls + kc) : kc;
+        // bitmap words: (k, pi) and (k, pj) when k < pi; (pi, k) when pi < k < pj
+        const int a1 = kc < pi ? kc : pi, b1 = kc < pi ? pi : (kc > pi ? kc : pi + 1);
+        const long long r1 = (long long)b1 * (b1 - 1) / 2 + a1;
+        const long long r2 = (long long)pj * (pj - 1) / 2 + (kc < pj ? kc : 0);
+        ld_w1[u] = __ldg(A.bits + (r1 >> 5)) >> (r1 & 31);
+        ld_w2[u] = __ldg(A.bits + (r2 >> 5)) >> (r2 & 31);
+      }
+      const int cpi = A.cls ? __ldg(A.cls + pi) : pi, cpj = A.cls ? __ldg(A.cls + pj) : pj;
       for (int pass = 0;; ++pass) {
         const R cut = cta_cut<R>(L);
 #pragma unroll
@@ -295,10 +317,10 @@ proposal_kernel(PropArgs<R> A) {
           int t[3];
           bool eval;
           if (k < pi) {
-            eval = !selected(A.bits, k, pi) && !selected(A.bits, k, pj);
+            eval = !(ld_w1[u] & 1u) && !(ld_w2[u] & 1u);
             t[0] = k; t[1] = pi; t[2] = pj;
           } else if (k < pj) {
-            eval = !selected(A.bits, pi, k);
+            eval = !(ld_w1[u] & 1u);
             t[0] = pi; t[1] = k; t[2] = pj;
           } else {
             eval = true;
@@ -306,12 +328,12 @@ proposal_kernel(PropArgs<R> A) {
           }
           if (!eval) { done |= bit; continue; }
           if (pass == 0) ++fits;
-          if (pair_dup || (A.cls && (A.cls[k] == A.cls[pi] || A.cls[k] == A.cls[pj]))) {
+          if (pair_dup || ld_cl[u] == cpi || ld_cl[u] == cpj) {
             done |= bit;   // two columns of one duplicate class: ineligible
             continue;
           }
-          const R gkk = A.diag[k];
-          const R g1 = Gi[k] * il11, g2 = (Gj[k] - l21 * g1) * il22;
+          const R gkk = ld_gk[u];
+          const R g1 = ld_gi[u] * il11, g2 = (ld_gj[u] - l21 * g1) * il22;
           const R pk = gkk - g1 * g1 - g2 * g2;
           if (!pair_ok || !(gkk > R(0)) || !(pk >= (R)A.ratio * gkk)) {
             // near-singular in FP32: exact FP64 redo; in FP64: ineligible
@@ -319,7 +341,7 @@ proposal_kernel(PropArgs<R> A) {
             done |= bit;
             continue;
           }
-          const R wv = cy[k] - g1 * z1 - g2 * z2;
+          const R wv = ld_cy[u] - g1 * z1 - g2 * z2;
           const R rel = pP - wv * wv / pk;
           if (rel > cut) { done |= bit; continue; }
           const u64 key = lex_rank(A.B, A.m, 3, t, A.total);
