@@ -318,12 +318,12 @@ def run_ours(args):
         stage = {s: statistics.mean(v) for s, v in acc.items()}
     t_tuple = statistics.mean(tuple_ms) / 1000.0
     achieved = fl_all / t_tuple / 1e12
+    pk = l0.measure_peaks(local)
     if precision == l0.FP64 or st["fp64_rerun"]:
         # an uncertified mixed fit is redone in FP64: its last tuple kernel is the FP64 one
-        peak, peak_note = FP64_PEAK_TFLOPS, "GB300 FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"
+        peak, peak_note = pk["fp64_tflops"], "measured FP64 FMA rate (sisso_l0_measure_peaks)"
     else:
-        peak = fp32_peak_tflops(2070.0)
-        peak_note = "152 SM x 128 FP32 lanes x 2 flop x 2070 MHz"
+        peak, peak_note = pk["fp32_tflops"], "measured FP32 FMA rate (sisso_l0_measure_peaks)"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
@@ -352,6 +352,7 @@ def run_ours(args):
                      "kernel": "tile_kernel (tuple search)", "peak_source": peak_note,
                      "flops_per_tuple": {str(dd): flops_per_tuple(dd) for dd in dims}},
         "clocks": clk,
+        "measured_peaks": {kk: round(v, 1) for kk, v in pk.items()},
     }
     if fp64_line is not None:
         line["fp64_path"] = fp64_line

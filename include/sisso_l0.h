@@ -328,6 +328,13 @@ int sisso_l0_merge_shards(sisso_l0_t h, int64_t n_sis, int32_t n_dim, int32_t k,
                           const double *bounds, const double *deltas, int32_t n_shards,
                           int32_t *out_tuples, double *out_rmse, int32_t *certified);
 
+/* Measured rates of the units the l0 kernels are bound by, on `device`
+ * (microbenchmarks, CUDA events, a few tens of milliseconds; no paper
+ * counterpart): out[0] FP32 FMA TFLOP/s, out[1] FP64 FMA TFLOP/s, out[2]
+ * MUFU rsqrt Gop/s, out[3] shared-memory load GB/s, out[4] L2 load GB/s.
+ * Allocates 33 MB of scratch for the call.  Errors: EINVAL, ENOMEM, ECUDA. */
+int sisso_l0_measure_peaks(int32_t device, double *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,7 +87,7 @@ EXPORTS = ("sisso_l0_default_options", "sisso_l0_create", "sisso_l0_fit", "sisso
            "sisso_l0_scorer_set_params", "sisso_l0_scorer_get_params",
            "sisso_l0_scorer_loss_grad", "sisso_l0_scorer_train", "sisso_l0_scorer_predict",
            "sisso_l0_pair_data", "sisso_l0_fit_pairs", "sisso_l0_fit_learned",
-           "sisso_l0_fit_shard", "sisso_l0_merge_shards")
+           "sisso_l0_fit_shard", "sisso_l0_merge_shards", "sisso_l0_measure_peaks")
 
 MAX_POOL = 2048
 
@@ -144,6 +144,7 @@ def lib():
                                          vp, vp]
         L.sisso_l0_merge_shards.argtypes = [vp, i64, i32, i32, i64, vp, vp, i64, vp, vp, i32, vp,
                                             vp, vp]
+        L.sisso_l0_measure_peaks.argtypes = [i32, vp]
         no_int = ("sisso_l0_last_error", "sisso_l0_destroy", "sisso_l0_count_tuples",
                   "sisso_l0_scorer_destroy", "sisso_l0_scorer_last_error")
         for name in EXPORTS:
@@ -151,6 +152,16 @@ def lib():
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
+
+
+def measure_peaks(device=0) -> dict:
+    """Measured unit rates of the device (see sisso_l0_measure_peaks)."""
+    out = np.zeros(5, dtype=np.float64)
+    rc = lib().sisso_l0_measure_peaks(int(device), ctypes.c_void_p(out.ctypes.data))
+    if rc != OK:
+        raise L0Error(rc, "sisso_l0_measure_peaks failed")
+    return {"fp32_tflops": out[0], "fp64_tflops": out[1], "rsqrt_gops": out[2],
+            "smem_gbs": out[3], "l2_gbs": out[4]}
 
 
 def count_tuples(m: int, n: int) -> int:

@@ -187,3 +187,13 @@ def test_c2_full_size_fp64_sampled_against_oracle():
     for tup, s in zip(samp, ssamp[:, 0]):
         if tuple(tup) not in listed:
             assert s >= kth * (1 - TIE_GAP)
+
+
+def test_measured_peaks_are_plausible():
+    pk = l0.measure_peaks(0)
+    # nominal: FP32 152 SM x 128 lanes x 2 x ~2.07 GHz = 80 TFLOP/s; FP64 a small
+    # fraction of it; shared memory and L2 in the tens of TB/s
+    assert 20 < pk["fp32_tflops"] < 100, pk
+    assert 0.1 < pk["fp64_tflops"] < 20, pk
+    assert pk["rsqrt_gops"] > 1000, pk
+    assert pk["smem_gbs"] > 5000 and pk["l2_gbs"] > 3000, pk
