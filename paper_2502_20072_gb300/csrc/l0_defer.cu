@@ -235,8 +235,15 @@ defer_dot_kernel(DeferArgs a) {
         }
         const double *x = a.W64 + (long long)ra * a.n_total + lo;
         const double *z = a.W64 + (long long)cb * a.n_total + lo;
-        double sacc = 0.0;
-        for (long long i = lane; i < n; i += 32) sacc = fma(x[i], z[i], sacc);
+        double s4[4] = {0.0, 0.0, 0.0, 0.0};
+        for (long long i0 = lane; i0 < n; i0 += 128) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const long long i = i0 + 32 * u;
+            if (i < n) s4[u] = fma(x[i], z[i], s4[u]);
+          }
+        }
+        double sacc = (s4[0] + s4[1]) + (s4[2] + s4[3]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
         if (lane == 0) {
