@@ -91,7 +91,10 @@ typedef struct {
   int32_t graph_replayed;            /* 1 when the last search pass replayed a CUDA graph */
   int32_t tuned_items_factor;        /* autotuner choice: work items per CTA (x2) */
   int32_t tuned_ctas_per_sm;         /* autotuner choice: resident CTAs per SM */
-  int32_t fp64_rerun;                /* 1: the last fit was redone in FP64 (see options) */
+  int32_t fp64_rerun;                /* 1: the last fit was redone in FP64 after an
+                                        uncertified mixed pass (see options); 2: it ran in
+                                        FP64 directly because the same inputs (pointers,
+                                        shapes, requests) needed FP64 on the previous call */
   /* phase times (ms, CUDA events on the handle's stream); 0 when unavailable */
   double ms_prep, ms_gram, ms_tuple, ms_merge, ms_refit, ms_total;
   double ms_tuple_kernel;            /* the tuple kernel alone (last search pass) */

@@ -86,6 +86,7 @@ struct sisso_l0_handle {
   cudaGraphExec_t graph_exec = nullptr;
   std::string graph_key;
   std::map<std::string, std::pair<int, int>> tune;   // autotuner choices
+  std::string fp64_key;   // inputs whose last mixed-precision fit needed FP64
 };
 
 namespace {
@@ -1073,18 +1074,41 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
 // A mixed-precision fit whose pool stays uncertified at the largest K' is
 // one where the FP32 score errors reach the gaps between the best scores;
 // FP64 is what stability needs there, so the fit is redone in FP64.
+// identity of a call's inputs and requests (pointers, shapes, requests)
+std::string inputs_key(const double *X, const double *y, const int64_t *off, int32_t n_tasks,
+                       int64_t n_sis, const sisso_l0_request *reqs, int32_t n_reqs) {
+  std::string k;
+  char buf[96];
+  snprintf(buf, sizeof(buf), "%p|%p|%lld|", (const void *)X, (const void *)y, (long long)n_sis);
+  k += buf;
+  for (int t = 0; t <= n_tasks; ++t) k += std::to_string((long long)off[t]) + ",";
+  for (int q = 0; q < n_reqs; ++q) k += "r" + std::to_string(reqs[q].n_dim) + "x" + std::to_string(reqs[q].k);
+  return k;
+}
+
 int fit_checked(sisso_l0_t h, const double *X, const double *y, const int64_t *task_offsets,
                 int32_t n_tasks, int64_t n_sis, const sisso_l0_request *reqs, int32_t n_reqs) {
-  int rc = fit_requests(h, X, y, task_offsets, n_tasks, n_sis, reqs, n_reqs);
-  if (rc || h->opt.precision != SISSO_L0_MIXED_BF16X3 || h->stats.certified ||
-      !h->opt.fp64_rerun_uncertified)
+  const bool mixed = h->opt.precision == SISSO_L0_MIXED_BF16X3;
+  std::string key;
+  if (mixed && h->opt.fp64_rerun_uncertified && X && y && task_offsets && reqs && n_tasks > 0)
+    key = inputs_key(X, y, task_offsets, n_tasks, n_sis, reqs, n_reqs);
+  if (!key.empty() && key == h->fp64_key) {
+    // the same inputs needed FP64 last time: go there directly
+    h->opt.precision = SISSO_L0_FP64;
+    int rc = fit_requests(h, X, y, task_offsets, n_tasks, n_sis, reqs, n_reqs);
+    h->opt.precision = SISSO_L0_MIXED_BF16X3;
+    h->stats.fp64_rerun = 2;
     return rc;
+  }
+  int rc = fit_requests(h, X, y, task_offsets, n_tasks, n_sis, reqs, n_reqs);
+  if (rc || !mixed || h->stats.certified || !h->opt.fp64_rerun_uncertified) return rc;
   const double ms_first = h->stats.ms_total;
   h->opt.precision = SISSO_L0_FP64;
   rc = fit_requests(h, X, y, task_offsets, n_tasks, n_sis, reqs, n_reqs);
   h->opt.precision = SISSO_L0_MIXED_BF16X3;
   h->stats.fp64_rerun = 1;
   h->stats.ms_total += ms_first;
+  if (!rc) h->fp64_key = key;
   return rc;
 }
 

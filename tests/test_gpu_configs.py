@@ -110,6 +110,12 @@ def test_c4_mixed_equals_fp64_and_refits(c4):
     with l0.Handle(precision=l0.MIXED_BF16X3) as h:
         tm, rm = h.fit(prob.X, prob.y, d, k)
         st = h.stats()
+        if st["fp64_rerun"] == 1:
+            # the same inputs again: straight to FP64, same result
+            tm2, rm2 = h.fit(prob.X, prob.y, d, k)
+            assert h.stats()["fp64_rerun"] == 2
+            np.testing.assert_array_equal(tm2, tm)
+            np.testing.assert_array_equal(rm2, rm)
     with l0.Handle(precision=l0.FP64) as h:
         tf, rf = h.fit(prob.X, prob.y, d, k)
     print("C4 stats", {q: st[q] for q in ("certified", "candidate_pool", "pool_enlargements",
