@@ -63,12 +63,21 @@ struct TileArgs {
   long long n_total;
 };
 
-// work items of one j-tile row: (#k tiles reaching past j0) x (#prefix chunks)
+// k tiles of j-tile row bj: they start right after the row block's first
+// column, k0 = j0 + 1 + bk * TILE_TK, so only the first one crosses the
+// diagonal (a quarter of its slots have k <= j)
+__host__ __device__ inline int tile_k_count(int bj, int m) {
+  const int first = bj * TILE_TJ + 1;
+  return first < m ? (m - first + TILE_TK - 1) / TILE_TK : 0;
+}
+__host__ __device__ inline int tile_k0(int bj, int bk) { return bj * TILE_TJ + 1 + bk * TILE_TK; }
+
+// work items of one j-tile row: (#k tiles) x (#prefix chunks)
 __host__ __device__ inline long long tile_row_items(int bj, int m, int dp, int L,
                                                     int n_kt, u64 nprefix) {
-  int j0 = bj * TILE_TJ;
-  int bk_min = (j0 + 1) / TILE_TK;
-  long long nk = (long long)n_kt - bk_min;
+  (void)dp;
+  (void)n_kt;
+  const long long nk = tile_k_count(bj, m);
   if (nk <= 0) return 0;
   long long nch = (long long)((nprefix + (u64)L - 1) / (u64)L);
   return nk * nch;

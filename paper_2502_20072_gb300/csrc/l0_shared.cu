@@ -34,7 +34,7 @@ __device__ void run_item_shared(const TileArgs<R> &A, const ProbDesc &pd, int pr
   c.m = pd.m;
   c.d = pd.d;
   c.j0 = bj * TJ;
-  c.k0 = bk * TK;
+  c.k0 = tile_k0(bj, bk);
   c.diag = (c.k0 <= c.j0 + TJ - 1);
   c.total = pd.total;
   c.B = A.B;

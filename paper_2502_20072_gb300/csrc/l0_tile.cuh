@@ -606,11 +606,10 @@ __device__ __forceinline__ void persistent_items(const TileArgs<R> &A, RunItem r
     const int jend = min((bj + 1) * TJ, pd.m);
     const u64 np = binom_arith(jend - 1, pd.dp);
     const long long nch = (long long)((np + (u64)pd.L - 1) / (u64)pd.L);
-    const int bk_min = (bj * TJ + 1) / TK;
-    const int bk = bk_min + (int)(rem / nch);
+    const int bk = (int)(rem / nch);
     const u64 r0 = (u64)(rem % nch) * (u64)pd.L;
     const u64 r1 = (r0 + (u64)pd.L < np) ? r0 + (u64)pd.L : np;
-    if (bk >= pd.n_kt || r1 <= r0 || r1 - r0 > (u64)pd.L) {   // inconsistent plan
+    if (bk >= tile_k_count(bj, pd.m) || r1 <= r0 || r1 - r0 > (u64)pd.L) {   // inconsistent plan
       set_err(A.err, 9);
       break;
     }
