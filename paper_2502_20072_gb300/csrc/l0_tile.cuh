@@ -152,18 +152,24 @@ __device__ __forceinline__ void load_raw(const ItemCtx<R> &c, const int *pidx, i
   }
 }
 
+// Values of one record (row j or column k) for one prefix.
+template <typename R, int DPM>
+struct RecOut {
+  R g[DPM];
+  R invl, z2, e, pPj;       // row record
+  int flag;
+  R kp1, kw1, kpt;          // column record
+};
+
+// Arithmetic of a record, free of branches on data (selects instead), then
+// stored by rec_store.
 template <typename R, int DP>
-__device__ __forceinline__ void make_record(const ItemCtx<R> &c, const int *pidx,
-                                            const RecRaw<R, DP> &raw, bool isj, bool isk,
-                                            int idx, int col, R cdiag, R cy, R G00, R thr_s,
-                                            const RecBuf<R, (DP > 0 ? DP : 1)> &rb) {
+__device__ __forceinline__ void rec_compute(const ItemCtx<R> &c, const int *pidx,
+                                            const RecRaw<R, DP> &raw, int col, R cdiag, R cy,
+                                            R G00, R thr_s,
+                                            RecOut<R, (DP > 0 ? DP : 1)> &o) {
   constexpr int DPM = DP > 0 ? DP : 1;
   constexpr bool MIXED = sizeof(R) == 4;
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int p = 0; p < DP; ++p) rb.pidx[p] = pidx[p];
-  }
-  if (!isj && !isk) return;
   // Cholesky of the prefix block C[P][P] and z_P = L_P^{-1} c_P
   R Lp[DPM][DPM];
   R invd[DPM];
@@ -194,26 +200,24 @@ __device__ __forceinline__ void make_record(const ItemCtx<R> &c, const int *pidx
     zP[a] = za * invd[a];
     pPb -= zP[a] * zP[a];
   }
-  R g[DPM];
   R piv = cdiag, w1 = cy;
 #pragma unroll
   for (int p = 0; p < DP; ++p) {
     R gp = raw.cpc[p];
 #pragma unroll
-    for (int t = 0; t < p; ++t) gp -= Lp[p][t] * g[t];
-    g[p] = gp * invd[p];
-    piv -= g[p] * g[p];
-    w1 -= g[p] * zP[p];
+    for (int t = 0; t < p; ++t) gp -= Lp[p][t] * o.g[t];
+    o.g[p] = gp * invd[p];
+    piv -= o.g[p] * o.g[p];
+    w1 -= o.g[p] * zP[p];
   }
-  if (col >= c.m) {
+  const bool inm = col < c.m;
 #pragma unroll
-    for (int p = 0; p < DP; ++p) g[p] = R(0);
-  }
+  for (int p = 0; p < DPM; ++p) o.g[p] = (p < DP && inm) ? o.g[p] : R(0);
   const bool elig = (cdiag > R(0)) && (piv >= (R)c.ratio * cdiag);
   // two columns of one duplicate class: exactly rank deficient, ineligible
   // (never worth an FP64 redo)
   bool dup = false;
-  if (c.cls && col < c.m) {
+  if (c.cls && inm) {
 #pragma unroll
     for (int a = 0; a < DP; ++a) {
       dup = dup || same_class(c.cls, pidx[a], col);
@@ -221,49 +225,61 @@ __device__ __forceinline__ void make_record(const ItemCtx<R> &c, const int *pidx
       for (int b = 0; b < a; ++b) dup = dup || same_class(c.cls, pidx[a], pidx[b]);
     }
   }
+  // row record
+  const bool shape = inm && (DP == 0 || pidx[DP > 0 ? DP - 1 : 0] < col);
+  const R invl = inv_sqrt(piv > R(0) ? piv : R(1));
+  const R z2 = w1 * invl;
+  const R pPj = pPb - z2 * z2;
+  const R e = pPj - (thr_s + (R)(16.0 * Eps<R>::v));
+  const bool fast_ok = shape && !dup && pok && elig;
+  o.flag = (!shape || dup) ? 0 : (!pok || !elig) ? (MIXED ? 3 : 0) : (e > R(0) ? 1 : 2);
+  o.invl = fast_ok ? invl : R(0);
+  o.z2 = fast_ok ? z2 : R(0);
+  o.pPj = fast_ok ? pPj : R(0);
+  o.e = fast_ok ? e : R(0);
+  // column record: kp1 = pthr - p1 (negated); past m or ineligible: -inf
+  // skips the column (FP64), +inf flags it for the FP64 redo (FP32)
+  const R kpt = (R)c.ratio * cdiag;
+  o.kpt = inm ? kpt : R(0);
+  o.kw1 = inm ? -w1 : R(0);
+  o.kp1 = !inm ? -r_inf<R>()
+               : dup ? -r_inf<R>() : elig ? (kpt - piv) : (MIXED ? r_inf<R>() : -r_inf<R>());
+}
+
+template <typename R, int DPM>
+__device__ __forceinline__ void rec_store(const RecOut<R, DPM> &o, bool isj, int idx,
+                                          const RecBuf<R, DPM> &rb) {
   if (isj) {
-    const int j = col;
-    const bool shape = (j < c.m) && (DP == 0 || pidx[DP > 0 ? DP - 1 : 0] < j);
-    int flag;
-    R invl = R(0), z2 = R(0), pPj = R(0), e = R(0);
-    if (!shape || dup) {
-      flag = 0;
-    } else if (!pok || !elig) {
-      flag = MIXED ? 3 : 0;
-    } else {
-      invl = inv_sqrt(piv);
-      z2 = w1 * invl;
-      pPj = pPb - z2 * z2;
-      R tl = thr_s + (R)(16.0 * Eps<R>::v);
-      e = pPj - tl;
-      flag = (e > R(0)) ? 1 : 2;
-    }
 #pragma unroll
-    for (int p = 0; p < DPM; ++p) rb.jg[p * TJ + idx] = (p < DP) ? -g[p] : R(0);
-    rb.jinvl[idx] = invl;
-    rb.jz2[idx] = z2;
-    rb.je[idx] = e;
-    rb.jpP[idx] = pPj;
-    rb.jflag[idx] = flag;
+    for (int p = 0; p < DPM; ++p) rb.jg[p * TJ + idx] = -o.g[p];
+    rb.jinvl[idx] = o.invl;
+    rb.jz2[idx] = o.z2;
+    rb.je[idx] = o.e;
+    rb.jpP[idx] = o.pPj;
+    rb.jflag[idx] = o.flag;
   } else {
-    // kp1 = pthr - p1 (negated); past m or ineligible: -inf skips the
-    // column (FP64), +inf flags it for the FP64 redo (FP32)
-    R kp1, kw1, kpt;
-    if (col >= c.m) {
-      kp1 = -r_inf<R>();
-      kw1 = R(0);
-      kpt = R(0);
-    } else {
-      kpt = (R)c.ratio * cdiag;
-      kp1 = dup ? -r_inf<R>() : elig ? (kpt - piv) : (MIXED ? r_inf<R>() : -r_inf<R>());
-      kw1 = -w1;
-    }
 #pragma unroll
-    for (int p = 0; p < DPM; ++p) rb.kg[p * TK + idx] = (p < DP) ? g[p] : R(0);
-    rb.kp1[idx] = kp1;
-    rb.kw1[idx] = kw1;
-    rb.kpt[idx] = kpt;
+    for (int p = 0; p < DPM; ++p) rb.kg[p * TK + idx] = o.g[p];
+    rb.kp1[idx] = o.kp1;
+    rb.kw1[idx] = o.kw1;
+    rb.kpt[idx] = o.kpt;
   }
+}
+
+template <typename R, int DP>
+__device__ __forceinline__ void make_record(const ItemCtx<R> &c, const int *pidx,
+                                            const RecRaw<R, DP> &raw, bool isj, bool isk,
+                                            int idx, int col, R cdiag, R cy, R G00, R thr_s,
+                                            const RecBuf<R, (DP > 0 ? DP : 1)> &rb) {
+  constexpr int DPM = DP > 0 ? DP : 1;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int p = 0; p < DP; ++p) rb.pidx[p] = pidx[p];
+  }
+  if (!isj && !isk) return;
+  RecOut<R, DPM> o;
+  rec_compute<R, DP>(c, pidx, raw, col, cdiag, cy, G00, thr_s, o);
+  rec_store<R, DPM>(o, isj, idx, rb);
 }
 
 // ------------------------------------------------------------------ tuples --
