@@ -753,7 +753,8 @@ std::string graph_key(sisso_l0_t h, const FitPlan &P, int K) {
                           &h->lists_k, &h->lists_cnt, &h->part_s, &h->part_k, &h->part_cnt,
                           &h->done, &h->pool_s, &h->pool_k, &h->pool_cnt, &h->scratch, &h->refit,
                           &h->rdiv, &h->cert, &h->out_t, &h->out_r, &h->err, &h->dfr_key,
-                          &h->dfr_len, &h->dfr_n, &h->abf, &h->bbf, &h->kmeta, &h->gram32};
+                          &h->dfr_len, &h->dfr_n, &h->abf, &h->bbf, &h->kmeta, &h->gram32,
+                          &h->col_hash, &h->col_cls};
   for (const DevBuf *b : bufs) {
     snprintf(buf, sizeof(buf), "|%p", b->p);
     k += buf;
