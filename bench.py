@@ -454,6 +454,70 @@ def run_learned(args):
         print(json.dumps(line))
 
 
+def run_sis(args):
+    """SIS screening (the step before l0): Pearson r of n_feat seeded
+    candidate features with y and the top m, device-resident inputs."""
+    import torch
+    import paper_2502_20072_gb300 as l0
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    n_feat, n, m = args.sis_features, 1000, 20000
+    g = torch.Generator(device="cuda").manual_seed(7)
+    X = torch.randn((n_feat, n), generator=g, device="cuda", dtype=torch.float64)
+    w = torch.randn((8,), generator=g, device="cuda", dtype=torch.float64)
+    y = (X[:8].T @ w) + 0.1 * torch.randn((n,), generator=g, device="cuda", dtype=torch.float64)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    prec = {"fp64": l0.FP64, "mixed": l0.MIXED_BF16X3}[args.precision]
+    h = l0.Handle(precision=prec, device=local, stream=stream.cuda_stream)
+    idx = torch.empty(m, dtype=torch.int32, device="cuda")
+    r = torch.empty(m, dtype=torch.float64, device="cuda")
+    lib = l0.lib()
+    import ctypes
+
+    def step():
+        rc = lib.sisso_l0_sis(h._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                              n, n_feat, m, ctypes.c_void_p(idx.data_ptr()),
+                              ctypes.c_void_p(r.data_ptr()))
+        h._check(rc)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    clocks = Clocks(local)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        step()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    pk_hbm = None
+    mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(mp):
+        pk_hbm = json.load(open(mp)).get("hbm_gbs")
+    gbs = n_feat * n * 8 / (ms * 1e-3) / 1e9
+    line = {"metric": "SIS screening features/sec (Pearson r + top-m)",
+            "value": n_feat / (ms * 1e-3), "unit": "features/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == l0.FP64 else "f64 in, f32 products",
+            "data": "synthetic (seeded normal features on the device)",
+            "config": {"workload": "SIS: n_feat=%d n_samples=%d m=%d" % (n_feat, n, m),
+                       "inputs": "larger than L2 (%.1f GB)" % (n_feat * n * 8 / 1e9)},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk_hbm, "unit": "GB/s",
+                         "frac": gbs / pk_hbm if pk_hbm else None, "traffic": None,
+                         "kernel": "sis_score_kernel + selection",
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy)"},
+            "clocks": clk}
+    h.close()
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -469,6 +533,7 @@ def main():
     ap.add_argument("--fraction", type=float, default=0.01)
     ap.add_argument("--train-steps", type=int, default=4000)
     ap.add_argument("--train-instances", type=int, default=50)
+    ap.add_argument("--sis-features", type=int, default=4000000)
     ap.add_argument("--learned-sis", type=int, default=20000,
                     help="columns of the learned workload (smaller for profiling)")
     args = ap.parse_args()
@@ -476,6 +541,8 @@ def main():
         run_reference(args)
     elif args.workload == "C5L":
         run_learned(args)
+    elif args.workload == "SIS":
+        run_sis(args)
     else:
         run_ours(args)
 

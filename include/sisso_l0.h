@@ -331,6 +331,19 @@ int sisso_l0_merge_shards(sisso_l0_t h, int64_t n_sis, int32_t n_dim, int32_t k,
                           const double *bounds, const double *deltas, int32_t n_shards,
                           int32_t *out_tuples, double *out_rmse, int32_t *certified);
 
+/* SIS screening, the step before l0 (paper Sec. 2.3): the Pearson r (Eq. 1)
+ * of every candidate feature with y and the m features of largest |r|
+ * (ties: the smaller index), in that order.  X: FP64 feature-major
+ * [n_feat][n_total] (host or device), y: [n_total]; outputs out_idx int32
+ * [m] and out_r (the signed r) [m], host or device.  One pass over X.  An
+ * FP64 handle computes every sum in FP64 (bound by the FP64 pipe on this
+ * part); a mixed-precision handle takes the centred products in FP32
+ * (r within ~1e-6 relative; one FP64 operation per sample).  Errors: EINVAL (n_total < 2, m outside
+ * [1, n_feat]), EUNSUPPORTED (m > 65536, n_feat >= 2^32, or more than 2^22
+ * features tied at the selection cut), ENONFINITE, ENOMEM, ECUDA. */
+int sisso_l0_sis(sisso_l0_t h, const double *X, const double *y, int64_t n_total,
+                 int64_t n_feat, int32_t m, int32_t *out_idx, double *out_r);
+
 /* Measured rates of the units the l0 kernels are bound by, on `device`
  * (microbenchmarks, CUDA events, a few tens of milliseconds; no paper
  * counterpart): out[0] FP32 FMA TFLOP/s, out[1] FP64 FMA TFLOP/s, out[2]

@@ -87,7 +87,8 @@ EXPORTS = ("sisso_l0_default_options", "sisso_l0_create", "sisso_l0_fit", "sisso
            "sisso_l0_scorer_set_params", "sisso_l0_scorer_get_params",
            "sisso_l0_scorer_loss_grad", "sisso_l0_scorer_train", "sisso_l0_scorer_predict",
            "sisso_l0_pair_data", "sisso_l0_fit_pairs", "sisso_l0_fit_learned",
-           "sisso_l0_fit_shard", "sisso_l0_merge_shards", "sisso_l0_measure_peaks")
+           "sisso_l0_fit_shard", "sisso_l0_merge_shards", "sisso_l0_measure_peaks",
+           "sisso_l0_sis")
 
 MAX_POOL = 2048
 
@@ -145,6 +146,7 @@ def lib():
         L.sisso_l0_merge_shards.argtypes = [vp, i64, i32, i32, i64, vp, vp, i64, vp, vp, i32, vp,
                                             vp, vp]
         L.sisso_l0_measure_peaks.argtypes = [i32, vp]
+        L.sisso_l0_sis.argtypes = [vp, dp, dp, i64, i64, i32, vp, vp]
         no_int = ("sisso_l0_last_error", "sisso_l0_destroy", "sisso_l0_count_tuples",
                   "sisso_l0_scorer_destroy", "sisso_l0_scorer_last_error")
         for name in EXPORTS:
@@ -390,6 +392,19 @@ class Handle:
                                          ctypes.c_void_p(cert.ctypes.data))
         self._check(rc)
         return out_t, out_r, bool(cert[0])
+
+    def sis(self, X, y, m):
+        """SIS screening: (indices [m], r [m]) of the m features of largest
+        |r| with y (X feature-major [n_feat, n_total])."""
+        X = _as_f64(X)
+        y = _as_f64(y)
+        nf, n = int(X.shape[0]), int(X.shape[1])
+        idx = np.empty(m, dtype=np.int32)
+        r = np.empty(m, dtype=np.float64)
+        self._check(lib().sisso_l0_sis(self._h, ctypes.c_void_p(_ptr(X)), ctypes.c_void_p(_ptr(y)),
+                                       n, nf, int(m), ctypes.c_void_p(idx.ctypes.data),
+                                       ctypes.c_void_p(r.ctypes.data)))
+        return idx, r
 
     def debug_unrank(self, m, n, ranks):
         ranks = np.ascontiguousarray(ranks, dtype=np.uint64)

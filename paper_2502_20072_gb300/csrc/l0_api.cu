@@ -1781,3 +1781,48 @@ int sisso_l0_merge_shards(sisso_l0_t h, int64_t n_sis, int32_t n_dim, int32_t k,
 }
 
 }  // extern "C"
+
+// ============================================================ screening ==
+extern "C" int sisso_l0_sis(sisso_l0_t h, const double *X, const double *y, int64_t n_total,
+                            int64_t n_feat, int32_t m, int32_t *out_idx, double *out_r) {
+  return guarded(h, [&]() -> int {
+    if (!X || !y || !out_idx || !out_r) return fail(h, SISSO_L0_EINVAL, "null pointer argument");
+    if (n_total < 2 || n_feat < 1 || m < 1 || m > n_feat)
+      return fail(h, SISSO_L0_EINVAL, "need n_total >= 2 and 1 <= m <= n_feat");
+    if (m > 65536 || n_feat >= (1ll << 32))
+      return fail(h, SISSO_L0_EUNSUPPORTED, "m above 65536 or n_feat above 2^32");
+    cudaStream_t st = h->st;
+    const double *Xd = X, *yd = y;
+    if (!is_device_ptr(X)) {
+      const size_t xb = (size_t)n_feat * (size_t)n_total * 8;
+      L0_CK(h->xin.ensure(xb), "alloc X");
+      L0_CK(cudaMemcpyAsync(h->xin.p, X, xb, cudaMemcpyHostToDevice, st), "copy X");
+      Xd = h->xin.as<double>();
+    }
+    if (!is_device_ptr(y)) {
+      L0_CK(h->yin.ensure((size_t)n_total * 8), "alloc y");
+      L0_CK(cudaMemcpyAsync(h->yin.p, y, (size_t)n_total * 8, cudaMemcpyHostToDevice, st), "copy y");
+      yd = h->yin.as<double>();
+    }
+    L0_CK(h->scores.ensure(l0::sis_scratch_bytes(n_feat, m, n_total)), "alloc screening scratch");
+    L0_CK(h->out_t.ensure((size_t)m * 4), "alloc");
+    L0_CK(h->out_r.ensure((size_t)m * 8), "alloc");
+    L0_CK(h->err.ensure(16), "alloc");
+    L0_CK(cudaMemsetAsync(h->err.p, 0, 16, st), "memset");
+    L0_CK(l0::launch_sis(Xd, yd, n_total, n_feat, m,
+                         h->opt.precision == SISSO_L0_MIXED_BF16X3 ? 1 : 0, h->scores.p,
+                         h->out_t.as<int>(),
+                         h->out_r.as<double>(), h->err.as<int>(), st),
+          "screening kernels");
+    L0_CK(cudaMemcpyAsync(out_idx, h->out_t.p, (size_t)m * 4, cudaMemcpyDefault, st), "copy");
+    L0_CK(cudaMemcpyAsync(out_r, h->out_r.p, (size_t)m * 8, cudaMemcpyDefault, st), "copy");
+    int herr = 0;
+    L0_CK(cudaMemcpyAsync(&herr, h->err.p, 4, cudaMemcpyDeviceToHost, st), "copy");
+    int rc = wait_stream(h);
+    if (rc) return rc;
+    if (herr == 5) return fail(h, SISSO_L0_ENONFINITE, "NaN or Inf in X or y");
+    if (herr == 12) return fail(h, SISSO_L0_EUNSUPPORTED, "more than 2^22 features tie at the cut");
+    if (herr) return fail(h, SISSO_L0_ECUDA, "device error flag " + std::to_string(herr));
+    return SISSO_L0_OK;
+  });
+}

@@ -350,6 +350,14 @@ cudaError_t launch_merge_shards(const Binom &B, int m, int d, u64 total, int k, 
                                 double *scratch_s, u64 *scratch_k, int *out_tuples,
                                 double *out_rmse, int *certified, cudaStream_t st);
 
+// SIS screening: Pearson r of every feature with y, the m largest |r|
+// (ties: smaller index) into out_idx / out_r (device); err 5 on NaN/Inf,
+// 12 when more than 2^22 candidates tie at the cut
+size_t sis_scratch_bytes(long long n_feat, int m, long long n);
+cudaError_t launch_sis(const double *X, const double *y, long long n, long long n_feat, int m,
+                       int fp32_products, void *scratch, int *out_idx, double *out_r, int *err,
+                       cudaStream_t st);
+
 cudaError_t launch_unrank(const Binom &B, int m, int d, u64 total,
                           const u64 *ranks, long long count, int *tuples,
                           cudaStream_t st);
