@@ -336,9 +336,13 @@ int sisso_l0_merge_shards(sisso_l0_t h, int64_t n_sis, int32_t n_dim, int32_t k,
  * (ties: the smaller index), in that order.  X: FP64 feature-major
  * [n_feat][n_total] (host or device), y: [n_total]; outputs out_idx int32
  * [m] and out_r (the signed r) [m], host or device.  One pass over X.  An
- * FP64 handle computes every sum in FP64 (bound by the FP64 pipe on this
- * part); a mixed-precision handle takes the centred products in FP32
- * (r within ~1e-6 relative; one FP64 operation per sample).  Errors: EINVAL (n_total < 2, m outside
+ * FP64 handle computes every r in FP64.  A mixed-precision handle gives the
+ * same output with a pre-screen: each sample truncated to FP32 by integer
+ * operations, FP32 sums, and a rigorous interval around each |r|; only the
+ * features whose interval reaches the m-th largest lower bound are re-scored
+ * by the FP64 routine (no FP64 operation per sample elsewhere).  get_stats
+ * then reports fp64_fallback_tuples = features scored in FP64, ms_total and
+ * kernel_launches.  Errors: EINVAL (n_total < 2, m outside
  * [1, n_feat]), EUNSUPPORTED (m > 65536, n_feat >= 2^32, or more than 2^22
  * features tied at the selection cut), ENONFINITE, ENOMEM, ECUDA. */
 int sisso_l0_sis(sisso_l0_t h, const double *X, const double *y, int64_t n_total,

@@ -1809,17 +1809,33 @@ extern "C" int sisso_l0_sis(sisso_l0_t h, const double *X, const double *y, int6
     L0_CK(h->out_r.ensure((size_t)m * 8), "alloc");
     L0_CK(h->err.ensure(16), "alloc");
     L0_CK(cudaMemsetAsync(h->err.p, 0, 16, st), "memset");
-    L0_CK(l0::launch_sis(Xd, yd, n_total, n_feat, m,
-                         h->opt.precision == SISSO_L0_MIXED_BF16X3 ? 1 : 0, h->scores.p,
-                         h->out_t.as<int>(),
-                         h->out_r.as<double>(), h->err.as<int>(), st),
+    const bool pre = h->opt.precision == SISSO_L0_MIXED_BF16X3;
+    L0_CK(cudaEventRecord(h->ev[0], st), "event");
+    L0_CK(l0::launch_sis(Xd, yd, n_total, n_feat, m, pre ? 1 : 0, h->scores.p,
+                         h->out_t.as<int>(), h->out_r.as<double>(), h->err.as<int>(), st),
           "screening kernels");
+    L0_CK(cudaEventRecord(h->ev[1], st), "event");
     L0_CK(cudaMemcpyAsync(out_idx, h->out_t.p, (size_t)m * 4, cudaMemcpyDefault, st), "copy");
     L0_CK(cudaMemcpyAsync(out_r, h->out_r.p, (size_t)m * 8, cudaMemcpyDefault, st), "copy");
     int herr = 0;
+    unsigned long long rescored = 0;
     L0_CK(cudaMemcpyAsync(&herr, h->err.p, 4, cudaMemcpyDeviceToHost, st), "copy");
+    L0_CK(cudaMemcpyAsync(&rescored, (char *)h->scores.p + 40, 8, cudaMemcpyDeviceToHost, st),
+          "copy");
     int rc = wait_stream(h);
     if (rc) return rc;
+    sisso_l0_stats &S = h->stats;
+    S = sisso_l0_stats{};
+    S.struct_size = (int32_t)sizeof(sisso_l0_stats);
+    S.certified = 1;
+    S.fp64_fallback_tuples = pre ? rescored : (uint64_t)n_feat;
+    S.kernel_launches = pre ? 17 : 10;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]) != cudaSuccess) {
+      cudaGetLastError();
+      ms = 0.f;
+    }
+    S.ms_total = ms;
     if (herr == 5) return fail(h, SISSO_L0_ENONFINITE, "NaN or Inf in X or y");
     if (herr == 12) return fail(h, SISSO_L0_EUNSUPPORTED, "more than 2^22 features tie at the cut");
     if (herr) return fail(h, SISSO_L0_ECUDA, "device error flag " + std::to_string(herr));

@@ -355,7 +355,7 @@ cudaError_t launch_merge_shards(const Binom &B, int m, int d, u64 total, int k, 
 // 12 when more than 2^22 candidates tie at the cut
 size_t sis_scratch_bytes(long long n_feat, int m, long long n);
 cudaError_t launch_sis(const double *X, const double *y, long long n, long long n_feat, int m,
-                       int fp32_products, void *scratch, int *out_idx, double *out_r, int *err,
+                       int prescreen, void *scratch, int *out_idx, double *out_r, int *err,
                        cudaStream_t st);
 
 cudaError_t launch_unrank(const Binom &B, int m, int d, u64 total,

@@ -18,13 +18,14 @@
 #include <algorithm>
 
 #include "l0_kernels.cuh"
+#include "l0_tc.cuh"
 
 namespace l0 {
 
 namespace {
 
 __global__ void __launch_bounds__(1024)
-sis_target_kernel(const double *y, long long n, double *out) {
+sis_target_kernel(const double *y, long long n, double *out, int *err) {
   __shared__ double red[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   auto block_sum = [&](double v) {
@@ -52,7 +53,45 @@ sis_target_kernel(const double *y, long long n, double *out) {
     out[0] = mean;
     out[1] = syy;
     out[2] = sy0;
+    if (!isfinite(syy)) set_err(err, 5);
   }
+}
+
+// Pearson r of one feature by one warp, in FP64 (all lanes take part; the
+// value is valid in every lane): shifted-data sums over 16 samples per lane
+// in flight.  `finite` is cleared when a sample is NaN or Inf.
+__device__ __forceinline__ double sis_r64_warp(const double *__restrict__ x, long long n,
+                                               const double *__restrict__ y, double my,
+                                               double syy, double sy0, int lane, bool &finite) {
+  const double c = __ldg(x);
+  double S1 = 0.0, S2 = 0.0, S3 = 0.0;
+  constexpr int U = 16;
+  for (long long i0 = lane; i0 < n; i0 += 32 * U) {
+    double v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long i = i0 + 32 * u;
+      v[u] = (i < n) ? __ldcs(x + i) : c;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long i = i0 + 32 * u;
+      finite &= isfinite(v[u]);
+      const double d = v[u] - c;            // 0 past the end
+      S1 += d;
+      S2 = fma(d, d, S2);
+      S3 = fma(d, (i < n) ? __ldg(y + i) - my : 0.0, S3);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    S1 += __shfl_xor_sync(0xffffffffu, S1, o);
+    S2 += __shfl_xor_sync(0xffffffffu, S2, o);
+    S3 += __shfl_xor_sync(0xffffffffu, S3, o);
+  }
+  const double sxx = S2 - S1 * S1 / (double)n;
+  const double sxy = S3 - S1 * sy0 / (double)n;
+  return (sxx > 0.0 && syy > 0.0) ? sxy / sqrt(sxx * syy) : 0.0;
 }
 
 __global__ void __launch_bounds__(256)
@@ -64,135 +103,444 @@ sis_score_kernel(const double *__restrict__ X, long long n, long long n_feat,
   const double my = tgt[0], syy = tgt[1], sy0 = tgt[2];
   for (long long f = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); f < n_feat;
        f += warps) {
-    const double *x = X + f * n;
-    const double c = __ldg(x);
-    double S1 = 0.0, S2 = 0.0, S3 = 0.0;
     bool finite = true;
-    // 16 loads per lane in flight per chunk of 512 samples
-    constexpr int U = 16;
-    for (long long i0 = lane; i0 < n; i0 += 32 * U) {
-      double v[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const long long i = i0 + 32 * u;
-        v[u] = (i < n) ? __ldcs(x + i) : c;
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const long long i = i0 + 32 * u;
-        finite &= isfinite(v[u]);
-        const double d = v[u] - c;            // 0 past the end
-        S1 += d;
-        S2 = fma(d, d, S2);
-        S3 = fma(d, (i < n) ? __ldg(y + i) - my : 0.0, S3);
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      S1 += __shfl_xor_sync(0xffffffffu, S1, o);
-      S2 += __shfl_xor_sync(0xffffffffu, S2, o);
-      S3 += __shfl_xor_sync(0xffffffffu, S3, o);
-    }
+    const double r = sis_r64_warp(X + f * n, n, y, my, syy, sy0, lane, finite);
     if (__any_sync(0xffffffffu, !finite) && lane == 0) set_err(err, 5);
-    if (lane == 0) {
-      const double sxx = S2 - S1 * S1 / (double)n;
-      const double sxy = S3 - S1 * sy0 / (double)n;
-      r_out[f] = (sxx > 0.0 && syy > 0.0) ? sxy / sqrt(sxx * syy) : 0.0;
-    }
+    if (lane == 0) r_out[f] = r;
   }
 }
 
-// The same sums with the products in FP32: each sample costs one FP64
-// subtraction (x - c) and one conversion; the centred value, the centred
-// target and their products are FP32, summed in FP32 over 16 samples per
-// lane and then in FP64.  GB300's FP64 pipe (~1 TFLOP/s) cannot keep up
-// with HBM at five FP64 operations per sample; at one it nearly can.
-// r carries ~1e-6 relative error (FP32 rounding of x - c).
-__global__ void __launch_bounds__(256)
-sis_score32_kernel(const double *__restrict__ X, long long n, long long n_feat,
-                   const float *__restrict__ yc, const double *__restrict__ tgt,
-                   double *__restrict__ r_out, int *err) {
-  const int lane = threadIdx.x & 31;
-  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-  const double syy = tgt[1], sy0 = tgt[2];
-  for (long long f = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); f < n_feat;
-       f += warps) {
-    const double *x = X + f * n;
-    const double c = __ldg(x);
-    double S1 = 0.0, S2 = 0.0, S3 = 0.0;
-    bool finite = true;
-    constexpr int U = 16;
-    for (long long i0 = lane; i0 < n; i0 += 32 * U) {
-      double v[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const long long i = i0 + 32 * u;
-        v[u] = (i < n) ? __ldcs(x + i) : c;
-      }
-      float a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const long long i = i0 + 32 * u;
-        finite &= isfinite(v[u]);
-        const float d = (float)(v[u] - c);
-        a1 += d;
-        a2 = fmaf(d, d, a2);
-        a3 = fmaf(d, (i < n) ? __ldg(yc + i) : 0.f, a3);
-      }
-      S1 += (double)a1;
-      S2 += (double)a2;
-      S3 += (double)a3;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      S1 += __shfl_xor_sync(0xffffffffu, S1, o);
-      S2 += __shfl_xor_sync(0xffffffffu, S2, o);
-      S3 += __shfl_xor_sync(0xffffffffu, S3, o);
-    }
-    if (__any_sync(0xffffffffu, !finite) && lane == 0) set_err(err, 5);
-    if (lane == 0) {
-      const double sxx = S2 - S1 * S1 / (double)n;
-      const double sxy = S3 - S1 * sy0 / (double)n;
-      r_out[f] = (sxx > 0.0 && syy > 0.0) ? sxy / sqrt(sxx * syy) : 0.0;
-    }
-  }
+// ---------------------------------------------------------- pre-screen --
+// GB300's FP64 pipe retires ~1.7 FMA per clock per SM, so a scan with even
+// one FP64 operation per sample falls far behind HBM.  The pre-screen does
+// none: each sample is truncated to FP32 with integer operations, the sums
+// run in FP32, and every feature gets an interval [lo, hi] that holds its
+// exact |r|.  Only features whose interval reaches the m-th largest lower
+// bound are re-scored by sis_r64_warp; the others cannot be selected.  The
+// selection that follows is therefore the one the FP64 scan makes.
+constexpr double SIS_U = 5.9604644775390625e-8;   // 2^-24, FP32 unit roundoff
+
+// x with its 29 low mantissa bits cleared, as a float (exact), by integer
+// operations: the exponent is re-biased by adding 128 to its low 8 bits
+// (1023 - 127 = 896 = 128 mod 256).  Exact to |f - x| <= 2^-23 |x| for
+// 2^-60 <= |x| < 2^61; |x| < 2^-60 (zero and subnormals included) gives 0,
+// off by less than 2^-60.  mx keeps the largest |x| bit pattern (high word):
+// SIS_MX_BAD or above (|x| >= 2^61, Inf, NaN) sends the feature to FP64.
+constexpr unsigned SIS_MX_LO = 963u << 20;    // 2^-60
+constexpr unsigned SIS_MX_BAD = 1084u << 20;  // 2^61
+__device__ __forceinline__ float sis_trunc32(double v, unsigned &mx) {
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  const unsigned a = hi & 0x7fffffffu;
+  mx = max(mx, a);
+  const unsigned t = __funnelshift_l(lo, hi, 3);          // (hi << 3) | (lo >> 29)
+  const unsigned f = ((t + 0x40000000u) & 0x7fffffffu) | (hi & 0x80000000u);
+  return a < SIS_MX_LO ? 0.f : __uint_as_float(f);
 }
 
-// centred target in FP32 (the FP64 sum of its rounded values goes to sy0)
+// Centred target in FP32, scaled by a power of two 2^-k with 2^-k sqrt(S_yy/n)
+// in [0.5, 1): yc[i] = fl32((y_i - mean) 2^-k).  tgt[3] = S_yy 4^-k (exact),
+// tgt[4] = sum yc^2, tgt[5] = sum yc (both FP64 over the rounded values).
 __global__ void __launch_bounds__(1024)
 sis_target32_kernel(const double *y, long long n, double *tgt, float *yc) {
-  __shared__ double red[32];
-  const double mean = tgt[0];
-  double t = 0.0;
+  __shared__ double red[2][32];
+  const double mean = tgt[0], syy = tgt[1];
+  int k = 0;
+  if (syy > 0.0 && isfinite(syy)) frexp(sqrt(syy / (double)n), &k);
+  double t = 0.0, q = 0.0;
   for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-    const float v = (float)(y[i] - mean);
+    const float v = (float)ldexp(y[i] - mean, -k);
     yc[i] = v;
     t += (double)v;
+    q = fma((double)v, (double)v, q);
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  for (int o = 16; o > 0; o >>= 1) {
+    t += __shfl_xor_sync(0xffffffffu, t, o);
+    q += __shfl_xor_sync(0xffffffffu, q, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = t;
+    red[1][threadIdx.x >> 5] = q;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-    tgt[2] = s;
+    double st = 0.0, sq = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      st += red[0][i];
+      sq += red[1][i];
+    }
+    tgt[3] = ldexp(syy, -2 * k);
+    tgt[4] = sq;
+    tgt[5] = st;
+  }
+}
+
+// [lo, hi] around |r| from the FP32 sums S1, S2, S3 of a feature whose
+// first sample is c (error model below)
+__device__ __forceinline__ void sis_bounds(double S1, double S2, double S3, double c, bool bad,
+                                           const double *tgt, long long n, double &lo,
+                                           double &hi) {
+  // |d_i - (x_i - c)| <= 2^-22 (|x_i| + |c|) + 2^-59 (two flushes below 2^-60)
+  const double syy_s = tgt[3], syc2 = tgt[4], sy0 = tgt[5];
+  const double nn = (double)n;
+  const double g = 80.0 * SIS_U + nn * 2.220446049250313e-16;
+  const double sxx = S2 - S1 * S1 / nn;
+  const double sxy = S3 - S1 * sy0 / nn;
+  const double sxx_lo = sxx - 3.0 * g * S2;
+  const double E = (2.384185791015625e-7 * (sqrt(fmax(S2, 0.0) * (1.0 + g)) + 2.0 * sqrt(nn) * fabs(c)) +
+                    1.7347234759768071e-18 * sqrt(nn)) *
+                   (1.0 + 4.8e-7);
+  lo = 0.0;
+  hi = INFINITY;
+  if (!bad && isfinite(S1) && isfinite(S2) && isfinite(S3) && syy_s > 0.0 && sxx_lo > 0.0 &&
+      9.0 * E * E < sxx_lo && 30.0 * g * S2 < sxx_lo) {
+    const double a = fabs(sxy / sqrt(sxx * syy_s));
+    const double nx = sqrt(sxx_lo);
+    const double eps =
+        1.01 * (1.05 * E / (nx - E) + SIS_U + 2.0 * g * sqrt(S2 * syc2 / (sxx_lo * syy_s)) +
+                a * 1.65 * g * S2 / sxx_lo) +
+        1e-10;
+    lo = fmax(a - eps, 0.0);
+    hi = a + eps;
+  }
+}
+
+// One warp per group of 32 features; writes lo_out[f] = max(|r~| - eps, 0)
+// and hi_out[f] = |r~| + eps, eps bounding |r~ - r| for the exact r (and
+// for the FP64 scan's r, which lies within n 2^-52 of it in the same terms).
+// The warp streams the features of its group one after the other, leaving
+// feature t's sums in lane t; the FP64 epilogue then runs once for all 32
+// (a masked FP64 instruction costs the pipe as much as a full one).
+//
+// Error model, with d_i = fl32(t(x_i) - t(c)), t the truncation above and c
+// the first sample: |d_i - (x_i - c)| <= (2^-22 (|d_i| + 2|c|) + 2^-59) / (1 - 2^-22),
+// so the error vector e has
+// ||e|| <= E = (2^-22 (sqrt(S2) + 2 sqrt(n)|c|) + 2^-59 sqrt(n)) (1 + 2^-21).
+// The angle between the centred sample vector and its computed image is
+// at most asin(||e|| / ||a||) <= 1.05 E / (||a~|| - E) while 3E < ||a~||.
+// The FP32 partial sums (<= 64 terms per lane, then a 5-level tree) carry
+// at most g sum|terms| with g = 80 u; by Cauchy-Schwarz this moves S_xx by
+// <= 3 g S2 and S_xy by <= 2 g sqrt(S2 sum yc^2).  Rounding yc moves r by <= u.
+__global__ void __launch_bounds__(256, 4)
+sis_prescreen_kernel(const double *__restrict__ X, long long n, long long n_feat,
+                     const float *__restrict__ yc, const double *__restrict__ tgt,
+                     double *__restrict__ lo_out, double *__restrict__ hi_out) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  constexpr int U = 16;
+  constexpr long long CHUNK = 32 * U;
+  for (long long g0 = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
+       g0 < n_feat; g0 += warps * 32) {
+    const int G = (int)min(32ll, n_feat - g0);
+    // lane t: sums of feature g0 + t (earlier chunks in FP64, the last in FP32)
+    double D1 = 0.0, D2 = 0.0, D3 = 0.0, cm = 0.0;
+    float F1 = 0.f, F2 = 0.f, F3 = 0.f;
+    bool badm = false;
+    for (int t = 0; t < G; ++t) {
+      const double *x = X + (g0 + t) * n;
+      const double c = __ldg(x);
+      unsigned mx = 0;
+      const float fc = sis_trunc32(c, mx);
+      float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      int pending = 0;
+      for (long long b0 = 0; b0 < n; b0 += CHUNK) {    // same trip count in every lane
+        double v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const long long i = b0 + lane + 32 * u;
+          v[u] = (i < n) ? __ldcs(x + i) : c;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const long long i = b0 + lane + 32 * u;
+          const float d = sis_trunc32(v[u], mx) - fc;      // 0 past the end
+          a1 += d;
+          a2 = fmaf(d, d, a2);
+          a3 = fmaf(d, (i < n) ? __ldg(yc + i) : 0.f, a3);
+        }
+        const bool last = b0 + CHUNK >= n;
+        if (++pending == 4 || last) {                      // <= 64 terms per lane
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+            a3 += __shfl_xor_sync(0xffffffffu, a3, o);
+          }
+          if (lane == t) {
+            if (last) {
+              F1 = a1;
+              F2 = a2;
+              F3 = a3;
+            } else {                                      // n > 2048 only
+              D1 += (double)a1;
+              D2 += (double)a2;
+              D3 += (double)a3;
+            }
+          }
+          a1 = a2 = a3 = 0.f;
+          pending = 0;
+        }
+      }
+      const bool bad = __any_sync(0xffffffffu, mx >= SIS_MX_BAD);
+      if (lane == t) {
+        cm = c;
+        badm = bad;
+      }
+    }
+    if (lane < G) {
+      double lo, hi;
+      sis_bounds(D1 + (double)F1, D2 + (double)F2, D3 + (double)F3, cm, badm, tgt, n, lo, hi);
+      lo_out[g0 + lane] = lo;
+      hi_out[g0 + lane] = hi;
+    }
+  }
+}
+
+// The same pre-screen with the rows staged in shared memory by the TMA
+// unit: each warp owns a ring of PB_STAGES buffers; lane 0 keeps
+// PB_STAGES - 1 bulk copies (one segment of up to PB_SEG samples each) in
+// flight while the warp reduces the oldest.  Feature-major rows are
+// contiguous, so a segment is one copy; its start is rounded down to 16
+// bytes (off = 1 when it falls on an odd sample) and its length up.  A copy
+// that would end past the last sample of X stops one sample short and that
+// sample is read directly.  Requires X 16-byte aligned.  With n <= 2 PB_SEG
+// (YREG) every lane keeps the centred target of its sample positions in
+// registers: the same positions recur in every row.
+constexpr int PB_WARPS = 16, PB_STAGES = 3, PB_SEG = 512, PB_K = PB_SEG / 32;
+constexpr int PB_STAGE_BYTES = PB_SEG * 8 + 16;
+constexpr size_t PB_SMEM = (size_t)PB_WARPS * PB_STAGES * PB_STAGE_BYTES + PB_WARPS * PB_STAGES * 8;
+
+struct PbJob {
+  long long f, e0;      // feature, first sample (flat index into X)
+  int s, len, off;      // segment, samples, offset in the stage (0 or 1)
+  bool tail;            // last sample read from global
+  bool valid;
+};
+
+__device__ __forceinline__ PbJob pb_job(long long q, long long warp, long long warps, int nseg,
+                                        long long n, long long n_feat) {
+  PbJob j;
+  const long long per_group = 32ll * nseg;
+  const long long k = q / per_group, rem = q - k * per_group;
+  const int t = (int)(rem / nseg);
+  j.s = (int)(rem - (long long)t * nseg);
+  j.f = (warp + k * warps) * 32 + t;
+  j.valid = j.f < n_feat;
+  j.len = (int)min((long long)PB_SEG, n - (long long)j.s * PB_SEG);
+  j.e0 = j.f * n + (long long)j.s * PB_SEG;
+  j.off = (int)(j.e0 & 1);
+  j.tail = ((j.off + j.len) & 1) && (j.e0 + j.len == n_feat * n);
+  return j;
+}
+
+__device__ __forceinline__ void pb_issue(const PbJob &j, const double *X, uint32_t stage,
+                                         uint32_t bar) {
+  const uint32_t bytes = (uint32_t)(((j.off + j.len - (j.tail ? 1 : 0)) * 8 + 15) & ~15);
+  tc::fence_proxy_async_smem();
+  tc::mbar_expect_tx(bar, bytes);      // bytes = 0 (a lone tail sample): a plain arrive
+  if (bytes) tc::bulk_load(stage, X + (j.e0 - j.off), bytes, bar);
+}
+
+template <bool YREG>
+__global__ void __launch_bounds__(PB_WARPS * 32, 1)
+sis_prescreen_bulk_kernel(const double *__restrict__ X, long long n, long long n_feat,
+                          const float *__restrict__ yc, const double *__restrict__ tgt,
+                          double *__restrict__ lo_out, double *__restrict__ hi_out, int *err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long warp = (long long)blockIdx.x * PB_WARPS + w;
+  const long long warps = (long long)gridDim.x * PB_WARPS;
+  unsigned char *ring = smem + (size_t)w * PB_STAGES * PB_STAGE_BYTES;
+  const uint32_t bar0 =
+      tc::smem_u32(smem + (size_t)PB_WARPS * PB_STAGES * PB_STAGE_BYTES) + w * PB_STAGES * 8;
+  const uint32_t ring0 = tc::smem_u32(ring);
+  const int nseg = (int)((n + PB_SEG - 1) / PB_SEG);
+  if (lane == 0) {
+    for (int b = 0; b < PB_STAGES; ++b) tc::mbar_init(bar0 + 8 * b, 1);
+    tc::fence_proxy_async_smem();
+  }
+  __syncwarp();
+  if (lane == 0)
+    for (int q = 0; q < PB_STAGES; ++q) {
+      const PbJob j = pb_job(q, warp, warps, nseg, n, n_feat);
+      if (j.valid) pb_issue(j, X, ring0 + q * PB_STAGE_BYTES, bar0 + 8 * q);
+    }
+  float yr0[PB_K], yr1[PB_K];
+#pragma unroll
+  for (int k = 0; k < PB_K; ++k) {
+    const long long i = lane + 32 * k;
+    yr0[k] = (YREG && i < n) ? yc[i] : 0.f;
+    yr1[k] = (YREG && i + PB_SEG < n) ? yc[i + PB_SEG] : 0.f;
+  }
+  double D1 = 0.0, D2 = 0.0, D3 = 0.0, cm = 0.0;   // lane t: feature t of the group
+  float F1 = 0.f, F2 = 0.f, F3 = 0.f;
+  bool badm = false;
+  float a1 = 0.f, a2 = 0.f, a3 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;
+  double c = 0.0;
+  float fc = 0.f;
+  unsigned mx = 0;
+  long long q = 0;
+  for (;; ++q) {
+    const PbJob j = pb_job(q, warp, warps, nseg, n, n_feat);
+    if (!j.valid) break;
+    const int st = (int)(q % PB_STAGES);
+    if (!__all_sync(0xffffffffu,
+                    tc::mbar_wait(bar0 + 8 * st, (uint32_t)((q / PB_STAGES) & 1), err))) {
+      ++q;            // this copy and the later ones may still be in flight
+      break;
+    }
+    const double *sv = (const double *)(ring + (size_t)st * PB_STAGE_BYTES) + j.off;
+    const int t = (int)((j.f) & 31);
+    if (j.s == 0) {
+      c = sv[0];
+      mx = 0;
+      fc = sis_trunc32(c, mx);
+    }
+    const long long ib = (long long)j.s * PB_SEG;
+    // one segment; yv: this lane's centred target values (YREG), by constant index
+    auto segment = [&](const float (&yv)[PB_K]) {
+      if (j.len == PB_SEG && !j.tail) {
+#pragma unroll
+        for (int k = 0; k < PB_K; k += 2) {
+          const float d0 = sis_trunc32(sv[lane + 32 * k], mx) - fc;
+          const float d1 = sis_trunc32(sv[lane + 32 * (k + 1)], mx) - fc;
+          const float y0 = YREG ? yv[k] : __ldg(yc + ib + lane + 32 * k);
+          const float y1 = YREG ? yv[k + 1] : __ldg(yc + ib + lane + 32 * (k + 1));
+          a1 += d0;
+          a2 = fmaf(d0, d0, a2);
+          a3 = fmaf(d0, y0, a3);
+          b1 += d1;
+          b2 = fmaf(d1, d1, b2);
+          b3 = fmaf(d1, y1, b3);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < PB_K; ++k) {
+          const int i = lane + 32 * k;
+          if (i < j.len) {
+            const double v = (j.tail && i == j.len - 1) ? __ldg(X + j.e0 + i) : sv[i];
+            const float d = sis_trunc32(v, mx) - fc;
+            const float y0 = YREG ? yv[k] : __ldg(yc + ib + i);
+            a1 += d;
+            a2 = fmaf(d, d, a2);
+            a3 = fmaf(d, y0, a3);
+          }
+        }
+      }
+    };
+    if (j.s == 0)
+      segment(yr0);
+    else
+      segment(yr1);
+    const bool last = j.s == nseg - 1;
+    if (last || (j.s & 3) == 3) {                   // <= 64 terms per lane
+      a1 += b1;
+      a2 += b2;
+      a3 += b3;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        a3 += __shfl_xor_sync(0xffffffffu, a3, o);
+      }
+      if (lane == t) {
+        if (last) {
+          F1 = a1;
+          F2 = a2;
+          F3 = a3;
+        } else {                                    // n > 4 PB_SEG only
+          D1 += (double)a1;
+          D2 += (double)a2;
+          D3 += (double)a3;
+        }
+      }
+      a1 = a2 = a3 = b1 = b2 = b3 = 0.f;
+    }
+    if (last) {
+      const bool bad = __any_sync(0xffffffffu, mx >= SIS_MX_BAD);
+      if (lane == t) {
+        cm = c;
+        badm = bad;
+      }
+    }
+    // the stage is free once every lane has read it: refill it
+    __syncwarp();
+    if (lane == 0) {
+      const PbJob jn = pb_job(q + PB_STAGES, warp, warps, nseg, n, n_feat);
+      if (jn.valid) pb_issue(jn, X, ring0 + st * PB_STAGE_BYTES, bar0 + 8 * st);
+    }
+    const long long g0 = j.f - t;
+    if (last && (t == 31 || j.f == n_feat - 1)) {   // group done: bounds of its features
+      if (g0 + lane < n_feat) {
+        double lo, hi;
+        sis_bounds(D1 + (double)F1, D2 + (double)F2, D3 + (double)F3, cm, badm, tgt, n, lo, hi);
+        lo_out[g0 + lane] = lo;
+        hi_out[g0 + lane] = hi;
+      }
+      D1 = D2 = D3 = 0.0;
+      F1 = F2 = F3 = 0.f;
+      badm = false;
+    }
+  }
+  // drain: after an expired wait, give copies still in flight their time
+  for (long long r = q; r < q + PB_STAGES - 1; ++r) {
+    const PbJob j = pb_job(r, warp, warps, nseg, n, n_feat);
+    if (!j.valid) break;
+    if (!__all_sync(0xffffffffu,
+                    tc::mbar_wait(bar0 + 8 * (int)(r % PB_STAGES), (uint32_t)((r / PB_STAGES) & 1), err)))
+      break;
   }
 }
 
 // ordered image of -|r| (ascending = best first)
 __device__ __forceinline__ u64 sis_key(double r) { return ord_of(-fabs(r)); }
 
+// Level-0 histogram privatised per block: 65536 16-bit counters packed two
+// to a word in shared memory (a block takes at most 65535 features), then
+// one global atomic per non-empty bin and block.
+constexpr int H0_THREADS = 1024;
+constexpr long long H0_MAX_PER_BLOCK = 65535;
+__global__ void __launch_bounds__(H0_THREADS)
+sis_hist0_kernel(const double *r, long long n_feat, long long per, unsigned *hist) {
+  extern __shared__ unsigned sh[];          // 32768 words
+  for (int i = threadIdx.x; i < 32768; i += H0_THREADS) sh[i] = 0u;
+  __syncthreads();
+  const long long f0 = (long long)blockIdx.x * per;
+  const long long f1 = min(n_feat, f0 + per);
+  for (long long f = f0 + threadIdx.x; f < f0 + (per + 31) / 32 * 32; f += H0_THREADS) {
+    unsigned bin = 0xffffffffu;
+    if (f < f1) bin = (unsigned)(sis_key(r[f]) >> 48);
+    const unsigned peers = __match_any_sync(0xffffffffu, bin);
+    if (bin != 0xffffffffu && (threadIdx.x & 31) == __ffs(peers) - 1)
+      atomicAdd(sh + (bin >> 1), (unsigned)__popc(peers) << (16 * (bin & 1)));
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 32768; i += H0_THREADS) {
+    const unsigned v = sh[i];
+    if (v & 0xffffu) atomicAdd(hist + 2 * i, v & 0xffffu);
+    if (v >> 16) atomicAdd(hist + 2 * i + 1, v >> 16);
+  }
+}
+
+// level 0: bins of the top 16 bits of the key; level 1: the next 16 bits
+// within the level-0 bin *cut1.  Lanes that hit the same bin add once.
 __global__ void __launch_bounds__(256)
 sis_hist_kernel(const double *r, long long n_feat, int level, const unsigned *cut1,
                 unsigned *hist) {
   const unsigned c1 = level ? *cut1 : 0u;
-  for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < n_feat;
-       f += (long long)gridDim.x * blockDim.x) {
-    const u64 k = sis_key(r[f]);
-    const unsigned b1 = (unsigned)(k >> 48);
-    if (level == 0) atomicAdd(hist + b1, 1u);
-    else if (b1 == c1) atomicAdd(hist + ((unsigned)(k >> 32) & 0xffffu), 1u);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long end = (n_feat + 31) / 32 * 32;         // whole warps stay in the loop
+  for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < end; f += stride) {
+    unsigned bin = 0xffffffffu;
+    if (f < n_feat) {
+      const u64 k = sis_key(r[f]);
+      const unsigned b1 = (unsigned)(k >> 48);
+      if (level == 0) bin = b1;
+      else if (b1 == c1) bin = (unsigned)(k >> 32) & 0xffffu;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, bin);
+    if (bin != 0xffffffffu && (threadIdx.x & 31) == __ffs(peers) - 1)
+      atomicAdd(hist + bin, (unsigned)__popc(peers));
   }
 }
 
@@ -235,16 +583,30 @@ sis_cut_kernel(const unsigned *hist, long long want, unsigned long long *below, 
   }
 }
 
+// append (key, index) of every feature at or before the cut bin; one
+// atomic per warp
 __global__ void __launch_bounds__(256)
 sis_compact_kernel(const double *r, long long n_feat, const unsigned *cut1, const unsigned *cut2,
                    u64 *keys, unsigned *idx, unsigned long long *count, long long cap) {
   const unsigned c1 = *cut1, c2 = *cut2;
-  for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < n_feat;
-       f += (long long)gridDim.x * blockDim.x) {
-    const u64 k = sis_key(r[f]);
-    const unsigned b1 = (unsigned)(k >> 48), b2 = (unsigned)(k >> 32) & 0xffffu;
-    if (b1 < c1 || (b1 == c1 && b2 <= c2)) {
-      const unsigned long long s = atomicAdd(count, 1ull);
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long end = (n_feat + 31) / 32 * 32;
+  for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < end; f += stride) {
+    bool take = false;
+    u64 k = 0;
+    if (f < n_feat) {
+      k = sis_key(r[f]);
+      const unsigned b1 = (unsigned)(k >> 48), b2 = (unsigned)(k >> 32) & 0xffffu;
+      take = b1 < c1 || (b1 == c1 && b2 <= c2);
+    }
+    const unsigned ball = __ballot_sync(0xffffffffu, take);
+    if (!ball) continue;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(count, (unsigned long long)__popc(ball));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (take) {
+      const unsigned long long s = base + __popc(ball & ((1u << lane) - 1u));
       if ((long long)s < cap) {
         keys[s] = k;
         idx[s] = (unsigned)f;
@@ -253,11 +615,130 @@ sis_compact_kernel(const double *r, long long n_feat, const unsigned *cut1, cons
   }
 }
 
+// Pre-screen candidates: a feature whose upper bound hi reaches the cut bin
+// of the lower bounds (key prefix <= (cut1, cut2)) is listed for the FP64
+// re-score; any other feature has |r| below the m-th largest |r| and its
+// entry of r becomes 0.
+__global__ void __launch_bounds__(256)
+sis_candidates_kernel(const double *hi, long long n_feat, const unsigned *cut1,
+                      const unsigned *cut2, double *r, unsigned *list,
+                      unsigned long long *count) {
+  const unsigned long long P = ((unsigned long long)*cut1 << 16) | *cut2;
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long end = (n_feat + 31) / 32 * 32;
+  for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < end; f += stride) {
+    bool take = false;
+    if (f < n_feat) {
+      take = (sis_key(hi[f]) >> 32) <= P;
+      if (!take) r[f] = 0.0;
+    }
+    const unsigned ball = __ballot_sync(0xffffffffu, take);
+    if (!ball) continue;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(count, (unsigned long long)__popc(ball));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (take) list[base + __popc(ball & ((1u << lane) - 1u))] = (unsigned)f;
+  }
+}
+
+// FP64 r of the listed candidates, one warp each
+__global__ void __launch_bounds__(256)
+sis_rescore_kernel(const double *__restrict__ X, long long n, const unsigned *list,
+                   const unsigned long long *count, const double *__restrict__ y,
+                   const double *__restrict__ tgt, double *__restrict__ r_out, int *err) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  const long long nc = (long long)*count;
+  const double my = tgt[0], syy = tgt[1], sy0 = tgt[2];
+  for (long long t = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < nc;
+       t += warps) {
+    const long long f = list[t];
+    bool finite = true;
+    const double r = sis_r64_warp(X + f * n, n, y, my, syy, sy0, lane, finite);
+    if (__any_sync(0xffffffffu, !finite) && lane == 0) set_err(err, 5);
+    if (lane == 0) r_out[f] = r;
+  }
+}
+
 __device__ __forceinline__ bool sis_less(u64 ka, unsigned ia, u64 kb, unsigned ib) {
   return ka < kb || (ka == kb && ia < ib);
 }
 
-// one block: sort the candidates by (key, index), emit the first m
+// Exact order of up to SIS_RANK_MAX compacted candidates: the rank of each
+// (key, index) pair is the number of pairs before it (all pairs differ in
+// the index, so the ranks are a permutation).  blockIdx.y splits the pairs
+// compared against; the counts meet by atomicAdd in rank[] (zeroed).
+constexpr long long SIS_RANK_MAX = 65536;
+constexpr int SIS_RANK_SPLIT = 32;
+constexpr int SIS_RANK_PER = 4;          // elements ranked per thread
+
+__global__ void __launch_bounds__(256)
+sis_rank_kernel(const u64 *keys, const unsigned *idx, const unsigned long long *count,
+                long long cap, unsigned *rank) {
+  __shared__ u64 sk[256];
+  __shared__ unsigned si[256];
+  const long long c = min((long long)*count, cap);
+  if (c > SIS_RANK_MAX) return;                 // sis_sort_kernel orders these
+  const long long i0 = (long long)blockIdx.x * 256 * SIS_RANK_PER;
+  if (i0 >= c) return;
+  u64 ki[SIS_RANK_PER];
+  unsigned ii[SIS_RANK_PER], cnt[SIS_RANK_PER];
+#pragma unroll
+  for (int q = 0; q < SIS_RANK_PER; ++q) {
+    const long long i = i0 + threadIdx.x + 256 * q;
+    ki[q] = (i < c) ? keys[i] : ~0ull;
+    ii[q] = (i < c) ? idx[i] : 0xffffffffu;
+    cnt[q] = 0;
+  }
+  const long long per = (c + SIS_RANK_SPLIT - 1) / SIS_RANK_SPLIT;
+  const long long j0 = (long long)blockIdx.y * per, j1 = min(c, j0 + per);
+  for (long long jb = j0; jb < j1; jb += 256) {
+    __syncthreads();
+    const long long j = jb + threadIdx.x;
+    if (j < j1) {
+      sk[threadIdx.x] = keys[j];
+      si[threadIdx.x] = idx[j];
+    }
+    __syncthreads();
+    const int nb = (int)min((long long)256, j1 - jb);
+    for (int t = 0; t < nb; ++t) {
+      const u64 kj = sk[t];
+      const unsigned sj = si[t];
+#pragma unroll
+      for (int q = 0; q < SIS_RANK_PER; ++q)
+        cnt[q] += (kj < ki[q] || (kj == ki[q] && sj < ii[q])) ? 1u : 0u;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < SIS_RANK_PER; ++q) {
+    const long long i = i0 + threadIdx.x + 256 * q;
+    if (i < c && cnt[q]) atomicAdd(rank + i, cnt[q]);
+  }
+}
+
+__global__ void __launch_bounds__(256)
+sis_scatter_kernel(const unsigned *idx, const unsigned *rank, const unsigned long long *count,
+                   long long cap, int m, const double *r, int *out_idx, double *out_r) {
+  const long long c = min((long long)*count, cap);
+  if (c > SIS_RANK_MAX) return;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < max(c, (long long)m);
+       i += (long long)gridDim.x * blockDim.x) {
+    if (i < c) {
+      const unsigned q = rank[i];
+      if (q < (unsigned)m) {
+        out_idx[q] = (int)idx[i];
+        out_r[q] = r[idx[i]];
+      }
+    } else {
+      out_idx[i] = -1;
+      out_r[i] = 0.0;
+    }
+  }
+}
+
+// Above SIS_RANK_MAX candidates (many features tied near the cut): one
+// block sorts them by (key, index) and emits the first m.
 __global__ void __launch_bounds__(1024)
 sis_sort_kernel(u64 *keys, unsigned *idx, const unsigned long long *count, long long cap,
                 int m, const double *r, int *out_idx, double *out_r, int *err) {
@@ -266,6 +747,7 @@ sis_sort_kernel(u64 *keys, unsigned *idx, const unsigned long long *count, long 
     if (threadIdx.x == 0) set_err(err, 12);
     n = cap;
   }
+  if (n <= SIS_RANK_MAX) return;
   long long P = 1;
   while (P < n) P <<= 1;
   for (long long i = n + threadIdx.x; i < P; i += blockDim.x) {
@@ -310,50 +792,109 @@ namespace l0 {
 
 size_t sis_scratch_bytes(long long n_feat, int m, long long n) {
   const long long cap = std::min<long long>(n_feat, 1ll << 22);
-  return (size_t)n_feat * 8 + 64 + 65536 * 4 + 64 + (size_t)cap * 16 * 2 + (size_t)cap * 8 * 2 +
-         (size_t)m * 16 + (size_t)n * 4 + 2048;
+  return 256 + (size_t)n_feat * (8 + 8 + 4) + 256 + 65536 * 4 + (size_t)cap * (16 + 8) +
+         (size_t)std::min<long long>(cap, SIS_RANK_MAX) * 4 + (size_t)n * 4 + (size_t)m * 0 +
+         16 * 256;
 }
 
-// scratch: sis_scratch_bytes; out_idx / out_r device [m]; err: device int
+// scratch: sis_scratch_bytes, its first 64 bytes the counters (bytes
+// [40, 48): features re-scored in FP64 by the pre-screen path);
+// out_idx / out_r device [m]; err: device int
 cudaError_t launch_sis(const double *X, const double *y, long long n, long long n_feat, int m,
-                       int fp32_products, void *scratch, int *out_idx, double *out_r, int *err,
+                       int prescreen, void *scratch, int *out_idx, double *out_r, int *err,
                        cudaStream_t st) {
   const long long cap = std::min<long long>(n_feat, 1ll << 22);
+  const long long rcap = std::min<long long>(cap, SIS_RANK_MAX);
   char *p = (char *)scratch;
   auto take = [&](size_t bytes) {
     char *q = p;
     p += (bytes + 255) / 256 * 256;
     return q;
   };
+  char *small = take(64);
+  unsigned *cuts = (unsigned *)small;                                 // selection cut1, cut2
+  unsigned *pcuts = cuts + 2;                                         // pre-screen cut1, cut2
+  unsigned long long *cnt = (unsigned long long *)(small + 16);       // below, count
+  unsigned long long *pcnt = cnt + 2;                                 // below, candidates
   double *r = (double *)take((size_t)n_feat * 8);
+  double *hi = (double *)take((size_t)n_feat * 8);
+  unsigned *list = (unsigned *)take((size_t)n_feat * 4);
   double *tgt = (double *)take(64);
   unsigned *hist = (unsigned *)take(65536 * 4);
-  char *small = take(64);
-  unsigned *cuts = (unsigned *)small;                                   // cut1, cut2
-  unsigned long long *cnt = (unsigned long long *)(small + 16);         // below, count
   u64 *keys = (u64 *)take((size_t)cap * 16);
   unsigned *idx = (unsigned *)take((size_t)cap * 8);
+  unsigned *rank = (unsigned *)take((size_t)rcap * 4);
   float *yc = (float *)take((size_t)n * 4);
   const unsigned g = (unsigned)std::min<long long>((n_feat + 255) / 256, 152 * 16);
   const unsigned gw = (unsigned)std::min<long long>((n_feat + 7) / 8, 152 * 32);
   cudaError_t e = cudaMemsetAsync(small, 0, 64, st);
   if (e != cudaSuccess) return e;
-  sis_target_kernel<<<1, 1024, 0, st>>>(y, n, tgt);
-  if (fp32_products) {
+  int dev = 0, n_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(sis_hist0_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                32768 * 4)) != cudaSuccess)
+    return e;
+  const long long h0_per =
+      std::min<long long>(H0_MAX_PER_BLOCK, std::max<long long>(1024, (n_feat + n_sm - 1) / n_sm));
+  // the m-th smallest key of r: two 16-bit levels
+  auto cut_of = [&](const double *v, unsigned *c2, unsigned long long *below) -> cudaError_t {
+    cudaError_t e2 = cudaMemsetAsync(hist, 0, 65536 * 4, st);
+    if (e2 != cudaSuccess) return e2;
+    sis_hist0_kernel<<<(unsigned)((n_feat + h0_per - 1) / h0_per), H0_THREADS, 32768 * 4, st>>>(
+        v, n_feat, h0_per, hist);
+    sis_cut_kernel<<<1, 1024, 0, st>>>(hist, m, below, c2);
+    e2 = cudaMemsetAsync(hist, 0, 65536 * 4, st);
+    if (e2 != cudaSuccess) return e2;
+    sis_hist_kernel<<<g, 256, 0, st>>>(v, n_feat, 1, c2, hist);
+    sis_cut_kernel<<<1, 1024, 0, st>>>(hist, m, below, c2 + 1);
+    return cudaSuccess;
+  };
+  sis_target_kernel<<<1, 1024, 0, st>>>(y, n, tgt, err);
+  if (prescreen) {
     sis_target32_kernel<<<1, 1024, 0, st>>>(y, n, tgt, yc);
-    sis_score32_kernel<<<gw, 256, 0, st>>>(X, n, n_feat, yc, tgt, r, err);
+    // one wave of resident blocks: every warp takes groups of 32 features
+    int per_sm = 0;
+    if (((uintptr_t)X & 15) == 0) {
+      const bool yreg = n <= 2 * PB_SEG;
+      const void *fn = yreg ? (const void *)sis_prescreen_bulk_kernel<true>
+                            : (const void *)sis_prescreen_bulk_kernel<false>;
+      if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)PB_SMEM)) != cudaSuccess)
+        return e;
+      const long long groups = (n_feat + 31) / 32;
+      const unsigned grid = (unsigned)std::min<long long>((groups + PB_WARPS - 1) / PB_WARPS, n_sm);
+      if (yreg)
+        sis_prescreen_bulk_kernel<true><<<grid, PB_WARPS * 32, PB_SMEM, st>>>(X, n, n_feat, yc, tgt,
+                                                                             r, hi, err);
+      else
+        sis_prescreen_bulk_kernel<false><<<grid, PB_WARPS * 32, PB_SMEM, st>>>(X, n, n_feat, yc,
+                                                                              tgt, r, hi, err);
+    } else {
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sis_prescreen_kernel, 256,
+                                                             0)) != cudaSuccess)
+        return e;
+      const long long waves = (long long)n_sm * std::max(per_sm, 1);
+      sis_prescreen_kernel<<<(unsigned)std::min<long long>((n_feat + 255) / 256, waves), 256, 0,
+                             st>>>(X, n, n_feat, yc, tgt, r, hi);
+    }
+    if ((e = cut_of(r, pcuts, pcnt)) != cudaSuccess) return e;
+    sis_candidates_kernel<<<g, 256, 0, st>>>(hi, n_feat, pcuts, pcuts + 1, r, list, pcnt + 1);
+    sis_rescore_kernel<<<gw, 256, 0, st>>>(X, n, list, pcnt + 1, y, tgt, r, err);
   } else {
     sis_score_kernel<<<gw, 256, 0, st>>>(X, n, n_feat, y, tgt, r, err);
   }
-  e = cudaMemsetAsync(hist, 0, 65536 * 4, st);
-  if (e != cudaSuccess) return e;
-  sis_hist_kernel<<<g, 256, 0, st>>>(r, n_feat, 0, cuts, hist);
-  sis_cut_kernel<<<1, 1024, 0, st>>>(hist, m, cnt, cuts);
-  e = cudaMemsetAsync(hist, 0, 65536 * 4, st);
-  if (e != cudaSuccess) return e;
-  sis_hist_kernel<<<g, 256, 0, st>>>(r, n_feat, 1, cuts, hist);
-  sis_cut_kernel<<<1, 1024, 0, st>>>(hist, m, cnt, cuts + 1);
+  if ((e = cut_of(r, cuts, cnt)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(rank, 0, (size_t)rcap * 4, st)) != cudaSuccess) return e;
   sis_compact_kernel<<<g, 256, 0, st>>>(r, n_feat, cuts, cuts + 1, keys, idx, cnt + 1, cap);
+  sis_rank_kernel<<<dim3((unsigned)((rcap + 256 * SIS_RANK_PER - 1) / (256 * SIS_RANK_PER)),
+                       SIS_RANK_SPLIT),
+                    256, 0, st>>>(
+      keys, idx, cnt + 1, cap, rank);
+  sis_scatter_kernel<<<(unsigned)std::min<long long>((std::max<long long>(rcap, m) + 255) / 256,
+                                                     152 * 8),
+                       256, 0, st>>>(idx, rank, cnt + 1, cap, m, r, out_idx, out_r);
   sis_sort_kernel<<<1, 1024, 0, st>>>(keys, idx, cnt + 1, cap, m, r, out_idx, out_r, err);
   return cudaGetLastError();
 }
