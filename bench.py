@@ -60,6 +60,26 @@ def tile_traffic(workload, precision):
     return rec[0] if h.hexdigest()[:16] == rec[1] else None
 
 
+# DRAM bytes of one pre-screen launch per feature of n_samples=1000, from the
+# ncu capture in profiles/sis_prescreen_n1000.md (500000 features: 4000108800
+# read + 11160832 written), scaled by the features of a launch (the kernel
+# reads each row once).  Tied to the sources it was taken from, as above.
+SIS_TRAFFIC_SOURCES = ("l0_sis.cu", "l0_tc.cuh")
+SIS_TRAFFIC_CAPTURED = {1000: ((4000108800 + 11160832) / 500000, None)}
+
+
+def sis_traffic(fp64, n_feat, n):
+    import hashlib
+    rec = SIS_TRAFFIC_CAPTURED.get(n)
+    if fp64 or rec is None or rec[1] is None:
+        return None
+    h = hashlib.sha256()
+    for f in SIS_TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2502_20072_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return rec[0] * n_feat if h.hexdigest()[:16] == rec[1] else None
+
+
 def flops_per_tuple(d):
     # hoisted per-tuple work of the tuple kernel's fast path:
     # (d-2) FMA for h, MUL g2, FMA pp, FMA w, MUL w^2, FMA t  ->  d+1 FMA + 2 MUL
@@ -424,6 +444,7 @@ def run_learned(args):
     clk = clocks.stop()
     ms = ev[0].elapsed_time(ev[1]) / args.steps
     st = h.stats()
+    ms_scan = st["ms_tuple_kernel"]          # the scan kernel of the last step
     got = set(map(tuple, out_t.cpu().numpy().tolist()))
     ref = set(map(tuple, ex_t[0].tolist()))
     recall = len(got & ref) / len(ref)
@@ -496,11 +517,13 @@ def run_sis(args):
     clk = clocks.stop()
     ms = ev[0].elapsed_time(ev[1]) / args.steps
     st = h.stats()
+    ms_scan = st["ms_tuple_kernel"]          # the scan kernel of the last step
     pk_hbm = None
     mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(mp):
         pk_hbm = json.load(open(mp)).get("hbm_gbs")
     gbs = n_feat * n * 8 / (ms * 1e-3) / 1e9
+    gbs_scan = n_feat * n * 8 / (ms_scan * 1e-3) / 1e9 if ms_scan > 0 else None
     # end to end through the C entry with host buffers (pinned), copies timed:
     # a 1/8 slice of the features so the host copy stays a few GB
     ne = max(m, n_feat // 8)
@@ -548,9 +571,12 @@ def run_sis(args):
                     "h2d_bytes_per_step": ne * n * 8 + n * 8, "d2h_bytes_per_step": m * 12,
                     "sample": "%d features from pinned host memory" % ne},
             "gpu_launches": int(st["kernel_launches"]) * args.steps,
-            "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk_hbm, "unit": "GB/s",
-                         "frac": gbs / pk_hbm if pk_hbm else None, "traffic": None,
-                         "kernel": "whole screening pass (X bytes / step time)",
+            "roofline": {"bound": "hbm", "achieved": gbs_scan, "peak": pk_hbm, "unit": "GB/s",
+                         "frac": gbs_scan / pk_hbm if (pk_hbm and gbs_scan) else None,
+                         "traffic": sis_traffic(prec == l0.FP64, n_feat, n),
+                         "kernel": "sis_score_kernel" if prec == l0.FP64 else
+                                   "sis_prescreen_bulk_kernel",
+                         "kernel_ms": ms_scan, "whole_pass_gbs": gbs,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy)"},
             "cpu_baseline": cpu,
             "clocks": clk}

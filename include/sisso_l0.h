@@ -341,7 +341,8 @@ int sisso_l0_merge_shards(sisso_l0_t h, int64_t n_sis, int32_t n_dim, int32_t k,
  * operations, FP32 sums, and a rigorous interval around each |r|; only the
  * features whose interval reaches the m-th largest lower bound are re-scored
  * by the FP64 routine (no FP64 operation per sample elsewhere).  get_stats
- * then reports fp64_fallback_tuples = features scored in FP64, ms_total and
+ * then reports fp64_fallback_tuples = features scored in FP64, ms_total,
+ * ms_tuple_kernel = the scan kernel alone (pre-screen or FP64 score) and
  * kernel_launches.  Errors: EINVAL (n_total < 2, m outside
  * [1, n_feat]), EUNSUPPORTED (m > 65536, n_feat >= 2^32, or more than 2^22
  * features tied at the selection cut), ENONFINITE, ENOMEM, ECUDA. */

@@ -1812,7 +1812,8 @@ extern "C" int sisso_l0_sis(sisso_l0_t h, const double *X, const double *y, int6
     const bool pre = h->opt.precision == SISSO_L0_MIXED_BF16X3;
     L0_CK(cudaEventRecord(h->ev[0], st), "event");
     L0_CK(l0::launch_sis(Xd, yd, n_total, n_feat, m, pre ? 1 : 0, h->scores.p,
-                         h->out_t.as<int>(), h->out_r.as<double>(), h->err.as<int>(), st),
+                         h->out_t.as<int>(), h->out_r.as<double>(), h->err.as<int>(), st,
+                         h->ev_k[0], h->ev_k[1]),
           "screening kernels");
     L0_CK(cudaEventRecord(h->ev[1], st), "event");
     L0_CK(cudaMemcpyAsync(out_idx, h->out_t.p, (size_t)m * 4, cudaMemcpyDefault, st), "copy");
@@ -1829,13 +1830,18 @@ extern "C" int sisso_l0_sis(sisso_l0_t h, const double *X, const double *y, int6
     S.struct_size = (int32_t)sizeof(sisso_l0_stats);
     S.certified = 1;
     S.fp64_fallback_tuples = pre ? rescored : (uint64_t)n_feat;
-    S.kernel_launches = pre ? 17 : 10;
+    S.kernel_launches = pre ? 20 : 13;
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]) != cudaSuccess) {
       cudaGetLastError();
       ms = 0.f;
     }
     S.ms_total = ms;
+    if (cudaEventElapsedTime(&ms, h->ev_k[0], h->ev_k[1]) != cudaSuccess) {
+      cudaGetLastError();
+      ms = 0.f;
+    }
+    S.ms_tuple_kernel = ms;
     if (herr == 5) return fail(h, SISSO_L0_ENONFINITE, "NaN or Inf in X or y");
     if (herr == 12) return fail(h, SISSO_L0_EUNSUPPORTED, "more than 2^22 features tie at the cut");
     if (herr) return fail(h, SISSO_L0_ECUDA, "device error flag " + std::to_string(herr));

@@ -356,7 +356,7 @@ cudaError_t launch_merge_shards(const Binom &B, int m, int d, u64 total, int k, 
 size_t sis_scratch_bytes(long long n_feat, int m, long long n);
 cudaError_t launch_sis(const double *X, const double *y, long long n, long long n_feat, int m,
                        int prescreen, void *scratch, int *out_idx, double *out_r, int *err,
-                       cudaStream_t st);
+                       cudaStream_t st, cudaEvent_t scan0, cudaEvent_t scan1);
 
 cudaError_t launch_unrank(const Binom &B, int m, int d, u64 total,
                           const u64 *ranks, long long count, int *tuples,

@@ -310,6 +310,23 @@ constexpr int PB_WARPS = 16, PB_STAGES = 3, PB_SEG = 512, PB_K = PB_SEG / 32;
 constexpr int PB_STAGE_BYTES = PB_SEG * 8 + 16;
 constexpr size_t PB_SMEM = (size_t)PB_WARPS * PB_STAGES * PB_STAGE_BYTES + PB_WARPS * PB_STAGES * 8;
 
+// A warp's jobs in order: group kg (features (warp + kg warps) 32 + t),
+// feature t of the group, segment s of the feature; advanced one job at a
+// time (no divisions in the loop).
+struct PbCursor {
+  long long kg = 0;
+  int t = 0, s = 0;
+  __device__ __forceinline__ void advance(int nseg) {
+    if (++s == nseg) {
+      s = 0;
+      if (++t == 32) {
+        t = 0;
+        ++kg;
+      }
+    }
+  }
+};
+
 struct PbJob {
   long long f, e0;      // feature, first sample (flat index into X)
   int s, len, off;      // segment, samples, offset in the stage (0 or 1)
@@ -317,14 +334,11 @@ struct PbJob {
   bool valid;
 };
 
-__device__ __forceinline__ PbJob pb_job(long long q, long long warp, long long warps, int nseg,
+__device__ __forceinline__ PbJob pb_job(const PbCursor &cur, long long warp, long long warps,
                                         long long n, long long n_feat) {
   PbJob j;
-  const long long per_group = 32ll * nseg;
-  const long long k = q / per_group, rem = q - k * per_group;
-  const int t = (int)(rem / nseg);
-  j.s = (int)(rem - (long long)t * nseg);
-  j.f = (warp + k * warps) * 32 + t;
+  j.s = cur.s;
+  j.f = (warp + cur.kg * warps) * 32 + cur.t;
   j.valid = j.f < n_feat;
   j.len = (int)min((long long)PB_SEG, n - (long long)j.s * PB_SEG);
   j.e0 = j.f * n + (long long)j.s * PB_SEG;
@@ -360,11 +374,13 @@ sis_prescreen_bulk_kernel(const double *__restrict__ X, long long n, long long n
     tc::fence_proxy_async_smem();
   }
   __syncwarp();
-  if (lane == 0)
-    for (int q = 0; q < PB_STAGES; ++q) {
-      const PbJob j = pb_job(q, warp, warps, nseg, n, n_feat);
-      if (j.valid) pb_issue(j, X, ring0 + q * PB_STAGE_BYTES, bar0 + 8 * q);
-    }
+  // producer cursor: PB_STAGES jobs ahead of the consumer once the ring is full
+  PbCursor pc;
+  for (int q = 0; q < PB_STAGES; ++q) {
+    const PbJob j = pb_job(pc, warp, warps, n, n_feat);
+    if (lane == 0 && j.valid) pb_issue(j, X, ring0 + q * PB_STAGE_BYTES, bar0 + 8 * q);
+    pc.advance(nseg);
+  }
   float yr0[PB_K], yr1[PB_K];
 #pragma unroll
   for (int k = 0; k < PB_K; ++k) {
@@ -379,18 +395,19 @@ sis_prescreen_bulk_kernel(const double *__restrict__ X, long long n, long long n
   double c = 0.0;
   float fc = 0.f;
   unsigned mx = 0;
-  long long q = 0;
-  for (;; ++q) {
-    const PbJob j = pb_job(q, warp, warps, nseg, n, n_feat);
+  PbCursor cc;
+  int st = 0;
+  uint32_t phase = 0;
+  int inflight = 0;      // copies issued and not yet waited on (for the drain)
+  for (;;) {
+    const PbJob j = pb_job(cc, warp, warps, n, n_feat);
     if (!j.valid) break;
-    const int st = (int)(q % PB_STAGES);
-    if (!__all_sync(0xffffffffu,
-                    tc::mbar_wait(bar0 + 8 * st, (uint32_t)((q / PB_STAGES) & 1), err))) {
-      ++q;            // this copy and the later ones may still be in flight
+    if (!__all_sync(0xffffffffu, tc::mbar_wait(bar0 + 8 * st, phase, err))) {
+      inflight = PB_STAGES - 1;     // the later copies may still be in flight
       break;
     }
     const double *sv = (const double *)(ring + (size_t)st * PB_STAGE_BYTES) + j.off;
-    const int t = (int)((j.f) & 31);
+    const int t = cc.t;
     if (j.s == 0) {
       c = sv[0];
       mx = 0;
@@ -399,7 +416,7 @@ sis_prescreen_bulk_kernel(const double *__restrict__ X, long long n, long long n
     const long long ib = (long long)j.s * PB_SEG;
     // one segment; yv: this lane's centred target values (YREG), by constant index
     auto segment = [&](const float (&yv)[PB_K]) {
-      if (j.len == PB_SEG && !j.tail) {
+      if (j.len == PB_SEG) {
 #pragma unroll
         for (int k = 0; k < PB_K; k += 2) {
           const float d0 = sis_trunc32(sv[lane + 32 * k], mx) - fc;
@@ -418,8 +435,7 @@ sis_prescreen_bulk_kernel(const double *__restrict__ X, long long n, long long n
         for (int k = 0; k < PB_K; ++k) {
           const int i = lane + 32 * k;
           if (i < j.len) {
-            const double v = (j.tail && i == j.len - 1) ? __ldg(X + j.e0 + i) : sv[i];
-            const float d = sis_trunc32(v, mx) - fc;
+            const float d = sis_trunc32(sv[i], mx) - fc;
             const float y0 = YREG ? yv[k] : __ldg(yc + ib + i);
             a1 += d;
             a2 = fmaf(d, d, a2);
@@ -428,6 +444,13 @@ sis_prescreen_bulk_kernel(const double *__restrict__ X, long long n, long long n
         }
       }
     };
+    if (j.tail) {
+      // the last sample of X came through a global load: stage it in place
+      // (the stage holds PB_SEG + 2 samples, so the slot exists)
+      __syncwarp();
+      if (lane == 0) ((double *)sv)[j.len - 1] = __ldg(X + j.e0 + j.len - 1);
+      __syncwarp();
+    }
     if (j.s == 0)
       segment(yr0);
     else
@@ -465,9 +488,10 @@ sis_prescreen_bulk_kernel(const double *__restrict__ X, long long n, long long n
     }
     // the stage is free once every lane has read it: refill it
     __syncwarp();
-    if (lane == 0) {
-      const PbJob jn = pb_job(q + PB_STAGES, warp, warps, nseg, n, n_feat);
-      if (jn.valid) pb_issue(jn, X, ring0 + st * PB_STAGE_BYTES, bar0 + 8 * st);
+    {
+      const PbJob jn = pb_job(pc, warp, warps, n, n_feat);
+      if (lane == 0 && jn.valid) pb_issue(jn, X, ring0 + st * PB_STAGE_BYTES, bar0 + 8 * st);
+      pc.advance(nseg);
     }
     const long long g0 = j.f - t;
     if (last && (t == 31 || j.f == n_feat - 1)) {   // group done: bounds of its features
@@ -481,14 +505,21 @@ sis_prescreen_bulk_kernel(const double *__restrict__ X, long long n, long long n
       F1 = F2 = F3 = 0.f;
       badm = false;
     }
+    cc.advance(nseg);
+    if (++st == PB_STAGES) {
+      st = 0;
+      phase ^= 1u;
+    }
   }
-  // drain: after an expired wait, give copies still in flight their time
-  for (long long r = q; r < q + PB_STAGES - 1; ++r) {
-    const PbJob j = pb_job(r, warp, warps, nseg, n, n_feat);
-    if (!j.valid) break;
-    if (!__all_sync(0xffffffffu,
-                    tc::mbar_wait(bar0 + 8 * (int)(r % PB_STAGES), (uint32_t)((r / PB_STAGES) & 1), err)))
-      break;
+  // drain after an expired wait: give the copies still in flight their time
+  for (int r = 0; r < inflight; ++r) {
+    cc.advance(nseg);
+    if (++st == PB_STAGES) {
+      st = 0;
+      phase ^= 1u;
+    }
+    if (!pb_job(cc, warp, warps, n, n_feat).valid) break;
+    if (!__all_sync(0xffffffffu, tc::mbar_wait(bar0 + 8 * st, phase, err))) break;
   }
 }
 
@@ -544,36 +575,63 @@ sis_hist_kernel(const double *r, long long n_feat, int level, const unsigned *cu
   }
 }
 
-// one block of 1024: the smallest bin b with before + count(bins <= b) >= want
+// one block of 1024: the smallest bin b with before + count(bins <= b) >= want.
+// Each thread holds 64 bins in registers (16 vector loads issued together);
+// a warp-shuffle scan gives every thread the count before its bins.
 __global__ void __launch_bounds__(1024)
 sis_cut_kernel(const unsigned *hist, long long want, unsigned long long *below, unsigned *cut) {
-  __shared__ unsigned long long part[1024];
+  __shared__ unsigned long long wsum[32];
   __shared__ unsigned s_bin;
   __shared__ unsigned long long s_before;
-  const int tid = threadIdx.x;
-  constexpr int PER = 65536 / 1024;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const unsigned long long base = below ? *below : 0ull;
+  const uint4 *h4 = (const uint4 *)hist + tid * 16;
+  uint4 v[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = h4[k];
   unsigned long long s = 0;
-  for (int b = 0; b < PER; ++b) s += hist[tid * PER + b];
-  part[tid] = s;
-  if (tid == 0) { s_bin = 0xffffu; s_before = base; }
-  __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    const unsigned long long v = (tid >= o) ? part[tid - o] : 0ull;
-    __syncthreads();
-    part[tid] += v;
-    __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 16; ++k) s += (unsigned long long)v[k].x + v[k].y + v[k].z + v[k].w;
+  if (tid == 0) {
+    s_bin = 0xffffu;
+    s_before = base;
   }
-  const unsigned long long before = base + (tid ? part[tid - 1] : 0ull);
-  if (before < (unsigned long long)want && base + part[tid] >= (unsigned long long)want) {
+  unsigned long long inc = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) wsum[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    unsigned long long t = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long u = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += u;
+    }
+    wsum[lane] = t;
+  }
+  __syncthreads();
+  inc += w ? wsum[w - 1] : 0ull;
+  const unsigned long long before = base + inc - s;
+  const unsigned long long W = (unsigned long long)want;
+  if (before < W && base + inc >= W) {
     unsigned long long acc = before;
-    for (int b = 0; b < PER; ++b) {
-      if (acc + hist[tid * PER + b] >= (unsigned long long)want) {
-        s_bin = tid * PER + b;
-        s_before = acc;
-        break;
+    bool found = false;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const unsigned c4[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (!found && acc + c4[q] >= W) {
+          found = true;
+          s_bin = tid * 64 + 4 * k + q;
+          s_before = acc;
+        }
+        if (!found) acc += c4[q];
       }
-      acc += hist[tid * PER + b];
     }
   }
   __syncthreads();
@@ -587,7 +645,8 @@ sis_cut_kernel(const unsigned *hist, long long want, unsigned long long *below, 
 // atomic per warp
 __global__ void __launch_bounds__(256)
 sis_compact_kernel(const double *r, long long n_feat, const unsigned *cut1, const unsigned *cut2,
-                   u64 *keys, unsigned *idx, unsigned long long *count, long long cap) {
+                   u64 *keys, unsigned *idx, unsigned long long *count, long long cap,
+                   unsigned long long *krange) {
   const unsigned c1 = *cut1, c2 = *cut2;
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -605,6 +664,17 @@ sis_compact_kernel(const double *r, long long n_feat, const unsigned *cut1, cons
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(count, (unsigned long long)__popc(ball));
     base = __shfl_sync(0xffffffffu, base, 0);
+    // key range of the taken: krange[0] = max ~key, krange[1] = max key
+    unsigned long long kn = take ? ~k : 0ull, kx = take ? k : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      kn = max(kn, __shfl_xor_sync(0xffffffffu, kn, o));
+      kx = max(kx, __shfl_xor_sync(0xffffffffu, kx, o));
+    }
+    if (lane == 0) {
+      atomicMax(krange, kn);
+      atomicMax(krange + 1, kx);
+    }
     if (take) {
       const unsigned long long s = base + __popc(ball & ((1u << lane) - 1u));
       if ((long long)s < cap) {
@@ -665,55 +735,98 @@ __device__ __forceinline__ bool sis_less(u64 ka, unsigned ia, u64 kb, unsigned i
   return ka < kb || (ka == kb && ia < ib);
 }
 
-// Exact order of up to SIS_RANK_MAX compacted candidates: the rank of each
-// (key, index) pair is the number of pairs before it (all pairs differ in
-// the index, so the ranks are a permutation).  blockIdx.y splits the pairs
-// compared against; the counts meet by atomicAdd in rank[] (zeroed).
+// Exact order of up to SIS_RANK_MAX compacted candidates.  The key range
+// [kmin, kmax] is cut into SIS_NB buckets by the leading bits of key - kmin
+// (monotone in the key); a pair's rank is the count of the buckets before
+// its own plus the pairs of its bucket that precede it by (key, index).
+// All pairs differ in the index, so the ranks are a permutation.
 constexpr long long SIS_RANK_MAX = 65536;
-constexpr int SIS_RANK_SPLIT = 32;
-constexpr int SIS_RANK_PER = 4;          // elements ranked per thread
+constexpr int SIS_NB = 4096;
+
+__device__ __forceinline__ unsigned sis_bucket(u64 k, const unsigned long long *krange) {
+  const u64 kmin = ~krange[0], span = krange[1] - kmin;
+  const int shift = max(0, 64 - __clzll((long long)span) - 12);   // span >> shift < 4096
+  return (unsigned)((k - kmin) >> shift);
+}
+
+__global__ void __launch_bounds__(256)
+sis_bucket_kernel(const u64 *keys, const unsigned long long *count, long long cap,
+                  const unsigned long long *krange, unsigned *bidx, unsigned *bcount) {
+  const long long c = min((long long)*count, cap);
+  if (c > SIS_RANK_MAX) return;                 // sis_sort_kernel orders these
+  const long long end = (c + 31) / 32 * 32;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < end;
+       i += (long long)gridDim.x * blockDim.x) {
+    unsigned b = 0xffffffffu;
+    if (i < c) {
+      b = sis_bucket(keys[i], krange);
+      bidx[i] = b;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    if (b != 0xffffffffu && (threadIdx.x & 31) == __ffs(peers) - 1)
+      atomicAdd(bcount + b, (unsigned)__popc(peers));
+  }
+}
+
+// one block of 1024: exclusive scan of the SIS_NB bucket counts
+__global__ void __launch_bounds__(1024)
+sis_bucket_scan_kernel(const unsigned *bcount, unsigned *bstart) {
+  __shared__ unsigned wsum[32];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const uint4 v = ((const uint4 *)bcount)[tid];
+  const unsigned s = v.x + v.y + v.z + v.w;
+  unsigned inc = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) wsum[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    unsigned t = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned u = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += u;
+    }
+    wsum[lane] = t;
+  }
+  __syncthreads();
+  const unsigned ex = inc - s + (w ? wsum[w - 1] : 0u);
+  ((uint4 *)bstart)[tid] = make_uint4(ex, ex + v.x, ex + v.x + v.y, ex + v.x + v.y + v.z);
+}
+
+__global__ void __launch_bounds__(256)
+sis_bucket_place_kernel(const unsigned long long *count, long long cap, const unsigned *bidx,
+                        const unsigned *bstart, unsigned *bfill, unsigned *order) {
+  const long long c = min((long long)*count, cap);
+  if (c > SIS_RANK_MAX) return;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < c;
+       i += (long long)gridDim.x * blockDim.x) {
+    const unsigned b = bidx[i];
+    order[bstart[b] + atomicAdd(bfill + b, 1u)] = (unsigned)i;
+  }
+}
 
 __global__ void __launch_bounds__(256)
 sis_rank_kernel(const u64 *keys, const unsigned *idx, const unsigned long long *count,
-                long long cap, unsigned *rank) {
-  __shared__ u64 sk[256];
-  __shared__ unsigned si[256];
+                long long cap, const unsigned *bidx, const unsigned *bstart,
+                const unsigned *bcount, const unsigned *order, unsigned *rank) {
   const long long c = min((long long)*count, cap);
-  if (c > SIS_RANK_MAX) return;                 // sis_sort_kernel orders these
-  const long long i0 = (long long)blockIdx.x * 256 * SIS_RANK_PER;
-  if (i0 >= c) return;
-  u64 ki[SIS_RANK_PER];
-  unsigned ii[SIS_RANK_PER], cnt[SIS_RANK_PER];
-#pragma unroll
-  for (int q = 0; q < SIS_RANK_PER; ++q) {
-    const long long i = i0 + threadIdx.x + 256 * q;
-    ki[q] = (i < c) ? keys[i] : ~0ull;
-    ii[q] = (i < c) ? idx[i] : 0xffffffffu;
-    cnt[q] = 0;
-  }
-  const long long per = (c + SIS_RANK_SPLIT - 1) / SIS_RANK_SPLIT;
-  const long long j0 = (long long)blockIdx.y * per, j1 = min(c, j0 + per);
-  for (long long jb = j0; jb < j1; jb += 256) {
-    __syncthreads();
-    const long long j = jb + threadIdx.x;
-    if (j < j1) {
-      sk[threadIdx.x] = keys[j];
-      si[threadIdx.x] = idx[j];
+  if (c > SIS_RANK_MAX) return;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < c;
+       i += (long long)gridDim.x * blockDim.x) {
+    const u64 ki = keys[i];
+    const unsigned ii = idx[i], b = bidx[i];
+    const unsigned s0 = bstart[b], nb = bcount[b];
+    unsigned cnt = s0;
+    for (unsigned t = s0; t < s0 + nb; ++t) {
+      const unsigned jx = order[t];
+      const u64 kj = keys[jx];
+      cnt += (kj < ki || (kj == ki && idx[jx] < ii)) ? 1u : 0u;
     }
-    __syncthreads();
-    const int nb = (int)min((long long)256, j1 - jb);
-    for (int t = 0; t < nb; ++t) {
-      const u64 kj = sk[t];
-      const unsigned sj = si[t];
-#pragma unroll
-      for (int q = 0; q < SIS_RANK_PER; ++q)
-        cnt[q] += (kj < ki[q] || (kj == ki[q] && sj < ii[q])) ? 1u : 0u;
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < SIS_RANK_PER; ++q) {
-    const long long i = i0 + threadIdx.x + 256 * q;
-    if (i < c && cnt[q]) atomicAdd(rank + i, cnt[q]);
+    rank[i] = cnt;
   }
 }
 
@@ -792,17 +905,19 @@ namespace l0 {
 
 size_t sis_scratch_bytes(long long n_feat, int m, long long n) {
   const long long cap = std::min<long long>(n_feat, 1ll << 22);
-  return 256 + (size_t)n_feat * (8 + 8 + 4) + 256 + 65536 * 4 + (size_t)cap * (16 + 8) +
-         (size_t)std::min<long long>(cap, SIS_RANK_MAX) * 4 + (size_t)n * 4 + (size_t)m * 0 +
-         16 * 256;
+  const long long rcap = std::min<long long>(cap, SIS_RANK_MAX);
+  (void)m;
+  return 256 * 2 + (size_t)n_feat * (8 + 8 + 4) + 256 + 65536 * 4 + (size_t)cap * (16 + 8) +
+         (size_t)rcap * 12 + (size_t)SIS_NB * 12 + (size_t)n * 4 + 20 * 256;
 }
 
 // scratch: sis_scratch_bytes, its first 64 bytes the counters (bytes
 // [40, 48): features re-scored in FP64 by the pre-screen path);
-// out_idx / out_r device [m]; err: device int
+// out_idx / out_r device [m]; err: device int; scan0 / scan1 (optional):
+// events recorded around the scan kernel (pre-screen or FP64 score)
 cudaError_t launch_sis(const double *X, const double *y, long long n, long long n_feat, int m,
                        int prescreen, void *scratch, int *out_idx, double *out_r, int *err,
-                       cudaStream_t st) {
+                       cudaStream_t st, cudaEvent_t scan0, cudaEvent_t scan1) {
   const long long cap = std::min<long long>(n_feat, 1ll << 22);
   const long long rcap = std::min<long long>(cap, SIS_RANK_MAX);
   char *p = (char *)scratch;
@@ -816,6 +931,7 @@ cudaError_t launch_sis(const double *X, const double *y, long long n, long long 
   unsigned *pcuts = cuts + 2;                                         // pre-screen cut1, cut2
   unsigned long long *cnt = (unsigned long long *)(small + 16);       // below, count
   unsigned long long *pcnt = cnt + 2;                                 // below, candidates
+  unsigned long long *krange = (unsigned long long *)take(64);        // max ~key, max key
   double *r = (double *)take((size_t)n_feat * 8);
   double *hi = (double *)take((size_t)n_feat * 8);
   unsigned *list = (unsigned *)take((size_t)n_feat * 4);
@@ -824,11 +940,17 @@ cudaError_t launch_sis(const double *X, const double *y, long long n, long long 
   u64 *keys = (u64 *)take((size_t)cap * 16);
   unsigned *idx = (unsigned *)take((size_t)cap * 8);
   unsigned *rank = (unsigned *)take((size_t)rcap * 4);
+  unsigned *bidx = (unsigned *)take((size_t)rcap * 4);
+  unsigned *order = (unsigned *)take((size_t)rcap * 4);
+  unsigned *bcount = (unsigned *)take((size_t)SIS_NB * 4 * 2);   // counts, fill cursors
+  unsigned *bfill = bcount + SIS_NB;
+  unsigned *bstart = (unsigned *)take((size_t)SIS_NB * 4);
   float *yc = (float *)take((size_t)n * 4);
   const unsigned g = (unsigned)std::min<long long>((n_feat + 255) / 256, 152 * 16);
   const unsigned gw = (unsigned)std::min<long long>((n_feat + 7) / 8, 152 * 32);
   cudaError_t e = cudaMemsetAsync(small, 0, 64, st);
   if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(krange, 0, 16, st)) != cudaSuccess) return e;
   int dev = 0, n_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
@@ -854,6 +976,7 @@ cudaError_t launch_sis(const double *X, const double *y, long long n, long long 
   sis_target_kernel<<<1, 1024, 0, st>>>(y, n, tgt, err);
   if (prescreen) {
     sis_target32_kernel<<<1, 1024, 0, st>>>(y, n, tgt, yc);
+    if (scan0 && (e = cudaEventRecord(scan0, st)) != cudaSuccess) return e;
     // one wave of resident blocks: every warp takes groups of 32 features
     int per_sm = 0;
     if (((uintptr_t)X & 15) == 0) {
@@ -879,19 +1002,24 @@ cudaError_t launch_sis(const double *X, const double *y, long long n, long long 
       sis_prescreen_kernel<<<(unsigned)std::min<long long>((n_feat + 255) / 256, waves), 256, 0,
                              st>>>(X, n, n_feat, yc, tgt, r, hi);
     }
+    if (scan1 && (e = cudaEventRecord(scan1, st)) != cudaSuccess) return e;
     if ((e = cut_of(r, pcuts, pcnt)) != cudaSuccess) return e;
     sis_candidates_kernel<<<g, 256, 0, st>>>(hi, n_feat, pcuts, pcuts + 1, r, list, pcnt + 1);
     sis_rescore_kernel<<<gw, 256, 0, st>>>(X, n, list, pcnt + 1, y, tgt, r, err);
   } else {
+    if (scan0 && (e = cudaEventRecord(scan0, st)) != cudaSuccess) return e;
     sis_score_kernel<<<gw, 256, 0, st>>>(X, n, n_feat, y, tgt, r, err);
+    if (scan1 && (e = cudaEventRecord(scan1, st)) != cudaSuccess) return e;
   }
   if ((e = cut_of(r, cuts, cnt)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(rank, 0, (size_t)rcap * 4, st)) != cudaSuccess) return e;
-  sis_compact_kernel<<<g, 256, 0, st>>>(r, n_feat, cuts, cuts + 1, keys, idx, cnt + 1, cap);
-  sis_rank_kernel<<<dim3((unsigned)((rcap + 256 * SIS_RANK_PER - 1) / (256 * SIS_RANK_PER)),
-                       SIS_RANK_SPLIT),
-                    256, 0, st>>>(
-      keys, idx, cnt + 1, cap, rank);
+  if ((e = cudaMemsetAsync(bcount, 0, (size_t)SIS_NB * 8, st)) != cudaSuccess) return e;
+  sis_compact_kernel<<<g, 256, 0, st>>>(r, n_feat, cuts, cuts + 1, keys, idx, cnt + 1, cap,
+                                        krange);
+  const unsigned gr = (unsigned)((rcap + 255) / 256);
+  sis_bucket_kernel<<<gr, 256, 0, st>>>(keys, cnt + 1, cap, krange, bidx, bcount);
+  sis_bucket_scan_kernel<<<1, 1024, 0, st>>>(bcount, bstart);
+  sis_bucket_place_kernel<<<gr, 256, 0, st>>>(cnt + 1, cap, bidx, bstart, bfill, order);
+  sis_rank_kernel<<<gr, 256, 0, st>>>(keys, idx, cnt + 1, cap, bidx, bstart, bcount, order, rank);
   sis_scatter_kernel<<<(unsigned)std::min<long long>((std::max<long long>(rcap, m) + 255) / 256,
                                                      152 * 8),
                        256, 0, st>>>(idx, rank, cnt + 1, cap, m, r, out_idx, out_r);
