@@ -25,7 +25,7 @@ namespace l0 {
 namespace {
 
 __global__ void __launch_bounds__(1024)
-sis_target_kernel(const double *y, long long n, double *out, int *err) {
+sis_target_kernel(const double *y, long long n, double *out, double *yd, int *err) {
   __shared__ double red[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   auto block_sum = [&](double v) {
@@ -44,6 +44,7 @@ sis_target_kernel(const double *y, long long n, double *out, int *err) {
   double q = 0.0, t = 0.0;
   for (long long i = threadIdx.x; i < n; i += blockDim.x) {
     const double d = y[i] - mean;
+    yd[i] = d;
     q = fma(d, d, q);
     t += d;
   }
@@ -59,10 +60,12 @@ sis_target_kernel(const double *y, long long n, double *out, int *err) {
 
 // Pearson r of one feature by one warp, in FP64 (all lanes take part; the
 // value is valid in every lane): shifted-data sums over 16 samples per lane
-// in flight.  `finite` is cleared when a sample is NaN or Inf.
+// in flight; yd = y - mean(y) (computed once, the same rounding as inline).
+// `finite` is cleared when a sample is NaN or Inf (exponent field all ones,
+// tested on the high word so that the FP64 pipe only does the four sums).
 __device__ __forceinline__ double sis_r64_warp(const double *__restrict__ x, long long n,
-                                               const double *__restrict__ y, double my,
-                                               double syy, double sy0, int lane, bool &finite) {
+                                               const double *__restrict__ yd, double syy,
+                                               double sy0, int lane, bool &finite) {
   const double c = __ldg(x);
   double S1 = 0.0, S2 = 0.0, S3 = 0.0;
   constexpr int U = 16;
@@ -76,11 +79,11 @@ __device__ __forceinline__ double sis_r64_warp(const double *__restrict__ x, lon
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const long long i = i0 + 32 * u;
-      finite &= isfinite(v[u]);
+      finite &= ((unsigned)__double2hiint(v[u]) & 0x7ff00000u) != 0x7ff00000u;
       const double d = v[u] - c;            // 0 past the end
       S1 += d;
       S2 = fma(d, d, S2);
-      S3 = fma(d, (i < n) ? __ldg(y + i) - my : 0.0, S3);
+      S3 = fma(d, (i < n) ? __ldg(yd + i) : 0.0, S3);
     }
   }
 #pragma unroll
@@ -96,15 +99,15 @@ __device__ __forceinline__ double sis_r64_warp(const double *__restrict__ x, lon
 
 __global__ void __launch_bounds__(256)
 sis_score_kernel(const double *__restrict__ X, long long n, long long n_feat,
-                 const double *__restrict__ y, const double *__restrict__ tgt,
+                 const double *__restrict__ yd, const double *__restrict__ tgt,
                  double *__restrict__ r_out, int *err) {
   const int lane = threadIdx.x & 31;
   const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-  const double my = tgt[0], syy = tgt[1], sy0 = tgt[2];
+  const double syy = tgt[1], sy0 = tgt[2];
   for (long long f = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); f < n_feat;
        f += warps) {
     bool finite = true;
-    const double r = sis_r64_warp(X + f * n, n, y, my, syy, sy0, lane, finite);
+    const double r = sis_r64_warp(X + f * n, n, yd, syy, sy0, lane, finite);
     if (__any_sync(0xffffffffu, !finite) && lane == 0) set_err(err, 5);
     if (lane == 0) r_out[f] = r;
   }
@@ -715,17 +718,17 @@ sis_candidates_kernel(const double *hi, long long n_feat, const unsigned *cut1,
 // FP64 r of the listed candidates, one warp each
 __global__ void __launch_bounds__(256)
 sis_rescore_kernel(const double *__restrict__ X, long long n, const unsigned *list,
-                   const unsigned long long *count, const double *__restrict__ y,
+                   const unsigned long long *count, const double *__restrict__ yd,
                    const double *__restrict__ tgt, double *__restrict__ r_out, int *err) {
   const int lane = threadIdx.x & 31;
   const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
   const long long nc = (long long)*count;
-  const double my = tgt[0], syy = tgt[1], sy0 = tgt[2];
+  const double syy = tgt[1], sy0 = tgt[2];
   for (long long t = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < nc;
        t += warps) {
     const long long f = list[t];
     bool finite = true;
-    const double r = sis_r64_warp(X + f * n, n, y, my, syy, sy0, lane, finite);
+    const double r = sis_r64_warp(X + f * n, n, yd, syy, sy0, lane, finite);
     if (__any_sync(0xffffffffu, !finite) && lane == 0) set_err(err, 5);
     if (lane == 0) r_out[f] = r;
   }
@@ -908,7 +911,7 @@ size_t sis_scratch_bytes(long long n_feat, int m, long long n) {
   const long long rcap = std::min<long long>(cap, SIS_RANK_MAX);
   (void)m;
   return 256 * 2 + (size_t)n_feat * (8 + 8 + 4) + 256 + 65536 * 4 + (size_t)cap * (16 + 8) +
-         (size_t)rcap * 12 + (size_t)SIS_NB * 12 + (size_t)n * 4 + 20 * 256;
+         (size_t)rcap * 12 + (size_t)SIS_NB * 12 + (size_t)n * 12 + 21 * 256;
 }
 
 // scratch: sis_scratch_bytes, its first 64 bytes the counters (bytes
@@ -946,6 +949,7 @@ cudaError_t launch_sis(const double *X, const double *y, long long n, long long 
   unsigned *bfill = bcount + SIS_NB;
   unsigned *bstart = (unsigned *)take((size_t)SIS_NB * 4);
   float *yc = (float *)take((size_t)n * 4);
+  double *yd = (double *)take((size_t)n * 8);
   const unsigned g = (unsigned)std::min<long long>((n_feat + 255) / 256, 152 * 16);
   const unsigned gw = (unsigned)std::min<long long>((n_feat + 7) / 8, 152 * 32);
   cudaError_t e = cudaMemsetAsync(small, 0, 64, st);
@@ -973,7 +977,7 @@ cudaError_t launch_sis(const double *X, const double *y, long long n, long long 
     sis_cut_kernel<<<1, 1024, 0, st>>>(hist, m, below, c2 + 1);
     return cudaSuccess;
   };
-  sis_target_kernel<<<1, 1024, 0, st>>>(y, n, tgt, err);
+  sis_target_kernel<<<1, 1024, 0, st>>>(y, n, tgt, yd, err);
   if (prescreen) {
     sis_target32_kernel<<<1, 1024, 0, st>>>(y, n, tgt, yc);
     if (scan0 && (e = cudaEventRecord(scan0, st)) != cudaSuccess) return e;
@@ -1005,10 +1009,10 @@ cudaError_t launch_sis(const double *X, const double *y, long long n, long long 
     if (scan1 && (e = cudaEventRecord(scan1, st)) != cudaSuccess) return e;
     if ((e = cut_of(r, pcuts, pcnt)) != cudaSuccess) return e;
     sis_candidates_kernel<<<g, 256, 0, st>>>(hi, n_feat, pcuts, pcuts + 1, r, list, pcnt + 1);
-    sis_rescore_kernel<<<gw, 256, 0, st>>>(X, n, list, pcnt + 1, y, tgt, r, err);
+    sis_rescore_kernel<<<gw, 256, 0, st>>>(X, n, list, pcnt + 1, yd, tgt, r, err);
   } else {
     if (scan0 && (e = cudaEventRecord(scan0, st)) != cudaSuccess) return e;
-    sis_score_kernel<<<gw, 256, 0, st>>>(X, n, n_feat, y, tgt, r, err);
+    sis_score_kernel<<<gw, 256, 0, st>>>(X, n, n_feat, yd, tgt, r, err);
     if (scan1 && (e = cudaEventRecord(scan1, st)) != cudaSuccess) return e;
   }
   if ((e = cut_of(r, cuts, cnt)) != cudaSuccess) return e;
