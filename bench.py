@@ -44,8 +44,8 @@ def fp32_peak_tflops(sm_mhz):
 # They describe the kernel built from sources with this hash; once the sources
 # change the figure no longer applies and the bench reports null.
 TRAFFIC_SOURCES = ("l0_common.cuh", "l0_tile.cuh", "l0_tuple.cu", "l0_kernels.cuh")
-TRAFFIC_CAPTURED = {("C2", "mixed"): (2416384 + 2304, "293c3cbe19100b15"),
-                    ("C2", "fp64"): (4533248 + 16896, "293c3cbe19100b15")}
+TRAFFIC_CAPTURED = {("C2", "mixed"): (2421504 + 2048, "6c86dcb0dd5668e2"),
+                    ("C2", "fp64"): (4539904 + 8448, "6c86dcb0dd5668e2")}
 
 
 def tile_traffic(workload, precision):
@@ -61,11 +61,11 @@ def tile_traffic(workload, precision):
 
 
 # DRAM bytes of one pre-screen launch per feature of n_samples=1000, from the
-# ncu capture in profiles/sis_prescreen_n1000.md (500000 features: 4000115968
-# read + 11180288 written), scaled by the features of a launch (the kernel
+# ncu capture in profiles/sis_prescreen_n1000.md (500000 features: 4000093952
+# read + 10153984 written), scaled by the features of a launch (the kernel
 # reads each row once).  Tied to the sources it was taken from, as above.
 SIS_TRAFFIC_SOURCES = ("l0_sis.cu", "l0_tc.cuh")
-SIS_TRAFFIC_CAPTURED = {1000: ((4000115968 + 11180288) / 500000, "e9eb83e24b937094")}
+SIS_TRAFFIC_CAPTURED = {1000: ((4000093952 + 10153984) / 500000, "750ba56b3dbc9719")}
 
 
 def sis_traffic(fp64, n_feat, n):
