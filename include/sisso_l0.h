@@ -349,6 +349,52 @@ int sisso_l0_merge_shards(sisso_l0_t h, int64_t n_sis, int32_t n_dim, int32_t k,
 int sisso_l0_sis(sisso_l0_t h, const double *X, const double *y, int64_t n_total,
                  int64_t n_feat, int32_t m, int32_t *out_idx, double *out_r);
 
+/* SIS against several targets (paper Sec. 2: from the second dimension on,
+ * the projection score is taken against the residuals of the previous
+ * models; Sec. 3 uses ten residuals per SIS iteration).  A feature's score
+ * is max_t |r(x, Y[t])| (Eq. 1); out_r holds the signed r of the first
+ * target reaching it.  The n_exclude features listed in `exclude` (distinct
+ * indices, host or device int32) are never selected.  Y: FP64
+ * [n_targets][n_total], host or device, 1 <= n_targets <= 16; the rest as in
+ * sisso_l0_sis.  The pre-screen (mixed handle) makes one pass over X per
+ * target and takes the largest bounds; the FP64 re-score reads each
+ * candidate once for all targets.  Errors: EINVAL (also m > n_feat -
+ * n_exclude, repeated or out-of-range exclusions), as sisso_l0_sis. */
+int sisso_l0_sis_multi(sisso_l0_t h, const double *X, const double *Y, int32_t n_targets,
+                       int64_t n_total, int64_t n_feat, int32_t m, const int32_t *exclude,
+                       int64_t n_exclude, int32_t *out_idx, double *out_r);
+
+/* Residuals y - (b_0 + sum_a b_a x_{t_a}) of the least-squares fits with
+ * intercept (Sec. 2.4) of n_models models of n_dim features each.
+ * tuples: int32 [n_models][n_dim] feature indices into X (host or device);
+ * X as in sisso_l0_sis; out: FP64 [n_models][n_total], host or device.  FP64
+ * Gram-Schmidt with a second orthogonalisation pass; a column dependent on
+ * the earlier ones (norm below 1e-12 of its centred norm after projection)
+ * is dropped, which leaves the residual of the minimum-norm fit.  Errors:
+ * EINVAL (1 <= n_dim <= 8, indices in range), ENOMEM, ECUDA. */
+int sisso_l0_residuals(sisso_l0_t h, const double *X, const double *y, int64_t n_total,
+                       int64_t n_feat, const int32_t *tuples, int32_t n_dim, int32_t n_models,
+                       double *out);
+
+/* The dimension loop of descriptor identification (Sec. 2, Fig. 1b): for
+ * n = 1 .. n_dim_max, screen m new features (n = 1: against y; n > 1:
+ * against the residuals of the min(n_res, eligible) best (n-1)-dimensional
+ * models, never re-selecting a feature), append them to the subspace S, and
+ * run the exhaustive l0 search of every n-tuple of S (single task, the
+ * handle's precision).  Outputs (host arrays): out_S int32 [n_dim_max * m],
+ * the features in selection order; out_tuples int32
+ * [n_dim_max][k][n_dim_max], row n-1 holding the k best n-tuples as
+ * ascending global feature indices (entries past n and unfilled slots -1);
+ * out_rmse FP64 [n_dim_max][k] (+inf where unfilled).  X, y host or device
+ * (host inputs are copied to the device once).  Errors: EINVAL
+ * (1 <= n_dim_max <= 6, 1 <= n_res <= 16, m n_dim_max <= n_feat,
+ * n_total >= n_dim_max + 2), and those of sisso_l0_sis_multi and
+ * sisso_l0_fit. */
+int sisso_l0_dimension_loop(sisso_l0_t h, const double *X, const double *y, int64_t n_total,
+                            int64_t n_feat, int32_t m, int32_t n_dim_max, int32_t k,
+                            int32_t n_res, int32_t *out_S, int32_t *out_tuples,
+                            double *out_rmse);
+
 /* Measured rates of the units the l0 kernels are bound by, on `device`
  * (microbenchmarks, CUDA events, a few tens of milliseconds; no paper
  * counterpart): out[0] FP32 FMA TFLOP/s, out[1] FP64 FMA TFLOP/s, out[2]

@@ -88,7 +88,8 @@ EXPORTS = ("sisso_l0_default_options", "sisso_l0_create", "sisso_l0_fit", "sisso
            "sisso_l0_scorer_loss_grad", "sisso_l0_scorer_train", "sisso_l0_scorer_predict",
            "sisso_l0_pair_data", "sisso_l0_fit_pairs", "sisso_l0_fit_learned",
            "sisso_l0_fit_shard", "sisso_l0_merge_shards", "sisso_l0_measure_peaks",
-           "sisso_l0_sis")
+           "sisso_l0_sis", "sisso_l0_sis_multi", "sisso_l0_residuals",
+           "sisso_l0_dimension_loop")
 
 MAX_POOL = 2048
 
@@ -147,6 +148,10 @@ def lib():
                                             vp, vp]
         L.sisso_l0_measure_peaks.argtypes = [i32, vp]
         L.sisso_l0_sis.argtypes = [vp, dp, dp, i64, i64, i32, vp, vp]
+        L.sisso_l0_sis_multi.argtypes = [vp, dp, dp, i32, i64, i64, i32, vp, i64, vp, vp]
+        L.sisso_l0_residuals.argtypes = [vp, dp, dp, i64, i64, vp, i32, i32, vp]
+        L.sisso_l0_dimension_loop.argtypes = [vp, dp, dp, i64, i64, i32, i32, i32, i32, vp, vp,
+                                              vp]
         no_int = ("sisso_l0_last_error", "sisso_l0_destroy", "sisso_l0_count_tuples",
                   "sisso_l0_scorer_destroy", "sisso_l0_scorer_last_error")
         for name in EXPORTS:
@@ -405,6 +410,55 @@ class Handle:
                                        n, nf, int(m), ctypes.c_void_p(idx.ctypes.data),
                                        ctypes.c_void_p(r.ctypes.data)))
         return idx, r
+
+    def sis_multi(self, X, Y, m, exclude=()):
+        """SIS against several targets Y [R, n_total] (max |r| over them),
+        never selecting the features in ``exclude``: (indices [m], r [m])."""
+        X = _as_f64(X)
+        Y = _as_f64(Y)
+        if len(Y.shape) == 1:
+            Y = Y.reshape(1, -1)
+        nf, n = int(X.shape[0]), int(X.shape[1])
+        ex = np.ascontiguousarray(np.asarray(exclude, dtype=np.int32).reshape(-1))
+        idx = np.empty(m, dtype=np.int32)
+        r = np.empty(m, dtype=np.float64)
+        self._check(lib().sisso_l0_sis_multi(
+            self._h, ctypes.c_void_p(_ptr(X)), ctypes.c_void_p(_ptr(Y)), int(Y.shape[0]), n, nf,
+            int(m), ctypes.c_void_p(ex.ctypes.data if len(ex) else None), len(ex),
+            ctypes.c_void_p(idx.ctypes.data), ctypes.c_void_p(r.ctypes.data)))
+        return idx, r
+
+    def residuals(self, X, y, tuples):
+        """Residuals [R, n_total] of the least-squares fits (with intercept)
+        of the R models ``tuples`` [R, d] (feature indices into X)."""
+        X = _as_f64(X)
+        y = _as_f64(y)
+        t = np.ascontiguousarray(np.atleast_2d(np.asarray(tuples, dtype=np.int32)))
+        nf, n = int(X.shape[0]), int(X.shape[1])
+        out = np.empty((t.shape[0], n), dtype=np.float64)
+        self._check(lib().sisso_l0_residuals(
+            self._h, ctypes.c_void_p(_ptr(X)), ctypes.c_void_p(_ptr(y)), n, nf,
+            ctypes.c_void_p(t.ctypes.data), int(t.shape[1]), int(t.shape[0]),
+            ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def dimension_loop(self, X, y, m, n_dim_max, k, n_res):
+        """SIS + l0 per dimension 1..n_dim_max.  Returns a list of dicts per
+        dimension: S (global indices in selection order, cumulative), tuples
+        [k, n] (ascending global indices; -1 unfilled), rmse [k]."""
+        X = _as_f64(X)
+        y = _as_f64(y)
+        nf, n = int(X.shape[0]), int(X.shape[1])
+        D = int(n_dim_max)
+        S = np.empty(D * m, dtype=np.int32)
+        T = np.empty((D, k, D), dtype=np.int32)
+        R = np.empty((D, k), dtype=np.float64)
+        self._check(lib().sisso_l0_dimension_loop(
+            self._h, ctypes.c_void_p(_ptr(X)), ctypes.c_void_p(_ptr(y)), n, nf, int(m), D, int(k),
+            int(n_res), ctypes.c_void_p(S.ctypes.data), ctypes.c_void_p(T.ctypes.data),
+            ctypes.c_void_p(R.ctypes.data)))
+        return [dict(S=S[:(d + 1) * m].copy(), tuples=T[d, :, :d + 1].copy(), rmse=R[d].copy())
+                for d in range(D)]
 
     def debug_unrank(self, m, n, ranks):
         ranks = np.ascontiguousarray(ranks, dtype=np.uint64)

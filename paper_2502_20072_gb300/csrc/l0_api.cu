@@ -77,6 +77,8 @@ struct sisso_l0_handle {
   DevBuf abf, bbf, kmeta, gram32;
   DevBuf prop_in, prop_pairs, prop_bits, prop_ctr, sel_hist, sel_bin, scores, diag;
   DevBuf col_hash, col_cls;
+  DevBuf sis_ex, sis_y;                               // screening: exclusions, targets
+  DevBuf loop_x, loop_y, loop_xs, loop_res, loop_q, loop_tup, loop_rows;   // dimension loop
   int binom_m = -1;
   int done_init_for = 0;
   cudaEvent_t ev[8] = {nullptr};
@@ -1783,15 +1785,134 @@ int sisso_l0_merge_shards(sisso_l0_t h, int64_t n_sis, int32_t n_dim, int32_t k,
 }  // extern "C"
 
 // ============================================================ screening ==
+namespace {
+
+// Screening against R targets [R][n_total] (host or device), never selecting
+// the n_ex features in ex (host or device int32).
+int sis_impl(sisso_l0_t h, const double *X, const double *Y, int R, int64_t n_total,
+             int64_t n_feat, int32_t m, const int32_t *ex, int64_t n_ex, int32_t *out_idx,
+             double *out_r) {
+  if (!X || !Y || !out_idx || !out_r || (n_ex > 0 && !ex))
+    return fail(h, SISSO_L0_EINVAL, "null pointer argument");
+  if (R < 1 || R > l0::SIS_MAX_TARGETS)
+    return fail(h, SISSO_L0_EINVAL, "n_targets outside [1, 16]");
+  if (n_total < 2 || n_feat < 1 || m < 1 || n_ex < 0 || m > n_feat - n_ex)
+    return fail(h, SISSO_L0_EINVAL, "need n_total >= 2 and 1 <= m <= n_feat - n_exclude");
+  if (m > 65536 || n_feat >= (1ll << 32))
+    return fail(h, SISSO_L0_EUNSUPPORTED, "m above 65536 or n_feat above 2^32");
+  cudaStream_t st = h->st;
+  const double *Xd = X, *Yd = Y;
+  if (!is_device_ptr(X)) {
+    const size_t xb = (size_t)n_feat * (size_t)n_total * 8;
+    L0_CK(h->xin.ensure(xb), "alloc X");
+    L0_CK(cudaMemcpyAsync(h->xin.p, X, xb, cudaMemcpyHostToDevice, st), "copy X");
+    Xd = h->xin.as<double>();
+  }
+  if (!is_device_ptr(Y)) {
+    L0_CK(h->sis_y.ensure((size_t)R * n_total * 8), "alloc targets");
+    L0_CK(cudaMemcpyAsync(h->sis_y.p, Y, (size_t)R * n_total * 8, cudaMemcpyHostToDevice, st),
+          "copy targets");
+    Yd = h->sis_y.as<double>();
+  }
+  const int *exd = nullptr;
+  if (n_ex > 0) {
+    // distinct, in range (the device marks each listed feature)
+    std::vector<int32_t> hx((size_t)n_ex);
+    if (is_device_ptr(ex)) {
+      L0_CK(cudaMemcpyAsync(hx.data(), ex, (size_t)n_ex * 4, cudaMemcpyDeviceToHost, st), "copy");
+      L0_CK(cudaStreamSynchronize(st), "sync");
+    } else {
+      std::copy(ex, ex + n_ex, hx.begin());
+    }
+    std::sort(hx.begin(), hx.end());
+    for (size_t i = 0; i < hx.size(); ++i)
+      if (hx[i] < 0 || hx[i] >= n_feat || (i && hx[i] == hx[i - 1]))
+        return fail(h, SISSO_L0_EINVAL, "exclusions must be distinct indices in [0, n_feat)");
+    L0_CK(h->sis_ex.ensure((size_t)n_ex * 4), "alloc exclusions");
+    L0_CK(cudaMemcpyAsync(h->sis_ex.p, hx.data(), (size_t)n_ex * 4, cudaMemcpyHostToDevice, st),
+          "copy exclusions");
+    L0_CK(cudaStreamSynchronize(st), "sync");   // hx leaves scope
+    exd = h->sis_ex.as<int>();
+  }
+  L0_CK(h->scores.ensure(l0::sis_scratch_bytes(n_feat, m, n_total, R)), "alloc screening scratch");
+  L0_CK(h->out_t.ensure((size_t)m * 4), "alloc");
+  L0_CK(h->out_r.ensure((size_t)m * 8), "alloc");
+  L0_CK(h->err.ensure(16), "alloc");
+  L0_CK(cudaMemsetAsync(h->err.p, 0, 16, st), "memset");
+  const bool pre = h->opt.precision == SISSO_L0_MIXED_BF16X3;
+  L0_CK(cudaEventRecord(h->ev[0], st), "event");
+  L0_CK(l0::launch_sis(Xd, Yd, R, n_total, n_feat, m, exd, n_ex, pre ? 1 : 0, h->scores.p,
+                       h->out_t.as<int>(), h->out_r.as<double>(), h->err.as<int>(), st,
+                       h->ev_k[0], h->ev_k[1]),
+        "screening kernels");
+  L0_CK(cudaEventRecord(h->ev[1], st), "event");
+  L0_CK(cudaMemcpyAsync(out_idx, h->out_t.p, (size_t)m * 4, cudaMemcpyDefault, st), "copy");
+  L0_CK(cudaMemcpyAsync(out_r, h->out_r.p, (size_t)m * 8, cudaMemcpyDefault, st), "copy");
+  int herr = 0;
+  unsigned long long rescored = 0;
+  L0_CK(cudaMemcpyAsync(&herr, h->err.p, 4, cudaMemcpyDeviceToHost, st), "copy");
+  L0_CK(cudaMemcpyAsync(&rescored, (char *)h->scores.p + 40, 8, cudaMemcpyDeviceToHost, st),
+        "copy");
+  int rc = wait_stream(h);
+  if (rc) return rc;
+  sisso_l0_stats &S = h->stats;
+  S = sisso_l0_stats{};
+  S.struct_size = (int32_t)sizeof(sisso_l0_stats);
+  S.certified = 1;
+  S.fp64_fallback_tuples = pre ? rescored : (uint64_t)n_feat;
+  S.kernel_launches = (pre ? 19 + R : 13) + (n_ex > 0 ? 1 : 0);
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]) != cudaSuccess) {
+    cudaGetLastError();
+    ms = 0.f;
+  }
+  S.ms_total = ms;
+  if (cudaEventElapsedTime(&ms, h->ev_k[0], h->ev_k[1]) != cudaSuccess) {
+    cudaGetLastError();
+    ms = 0.f;
+  }
+  S.ms_tuple_kernel = ms;
+  if (herr == 5) return fail(h, SISSO_L0_ENONFINITE, "NaN or Inf in X or the targets");
+  if (herr == 12) return fail(h, SISSO_L0_EUNSUPPORTED, "more than 2^22 features tie at the cut");
+  if (herr) return fail(h, SISSO_L0_ECUDA, "device error flag " + std::to_string(herr));
+  return SISSO_L0_OK;
+}
+
+}  // namespace
+
 extern "C" int sisso_l0_sis(sisso_l0_t h, const double *X, const double *y, int64_t n_total,
                             int64_t n_feat, int32_t m, int32_t *out_idx, double *out_r) {
   return guarded(h, [&]() -> int {
-    if (!X || !y || !out_idx || !out_r) return fail(h, SISSO_L0_EINVAL, "null pointer argument");
-    if (n_total < 2 || n_feat < 1 || m < 1 || m > n_feat)
-      return fail(h, SISSO_L0_EINVAL, "need n_total >= 2 and 1 <= m <= n_feat");
-    if (m > 65536 || n_feat >= (1ll << 32))
-      return fail(h, SISSO_L0_EUNSUPPORTED, "m above 65536 or n_feat above 2^32");
+    return sis_impl(h, X, y, 1, n_total, n_feat, m, nullptr, 0, out_idx, out_r);
+  });
+}
+
+extern "C" int sisso_l0_sis_multi(sisso_l0_t h, const double *X, const double *Y,
+                                  int32_t n_targets, int64_t n_total, int64_t n_feat, int32_t m,
+                                  const int32_t *exclude, int64_t n_exclude, int32_t *out_idx,
+                                  double *out_r) {
+  return guarded(h, [&]() -> int {
+    return sis_impl(h, X, Y, n_targets, n_total, n_feat, m, exclude, n_exclude, out_idx, out_r);
+  });
+}
+
+extern "C" int sisso_l0_residuals(sisso_l0_t h, const double *X, const double *y,
+                                  int64_t n_total, int64_t n_feat, const int32_t *tuples,
+                                  int32_t n_dim, int32_t n_models, double *out) {
+  return guarded(h, [&]() -> int {
+    if (!X || !y || !tuples || !out) return fail(h, SISSO_L0_EINVAL, "null pointer argument");
+    if (n_total < 2 || n_feat < 1 || n_dim < 1 || n_dim > 8 || n_models < 1)
+      return fail(h, SISSO_L0_EINVAL, "need n_total >= 2, 1 <= n_dim <= 8, n_models >= 1");
     cudaStream_t st = h->st;
+    std::vector<int32_t> ht((size_t)n_models * n_dim);
+    if (is_device_ptr(tuples)) {
+      L0_CK(cudaMemcpyAsync(ht.data(), tuples, ht.size() * 4, cudaMemcpyDeviceToHost, st), "copy");
+      L0_CK(cudaStreamSynchronize(st), "sync");
+    } else {
+      std::copy(tuples, tuples + ht.size(), ht.begin());
+    }
+    for (int32_t v : ht)
+      if (v < 0 || v >= n_feat) return fail(h, SISSO_L0_EINVAL, "tuple index outside [0, n_feat)");
     const double *Xd = X, *yd = y;
     if (!is_device_ptr(X)) {
       const size_t xb = (size_t)n_feat * (size_t)n_total * 8;
@@ -1804,47 +1925,114 @@ extern "C" int sisso_l0_sis(sisso_l0_t h, const double *X, const double *y, int6
       L0_CK(cudaMemcpyAsync(h->yin.p, y, (size_t)n_total * 8, cudaMemcpyHostToDevice, st), "copy y");
       yd = h->yin.as<double>();
     }
-    L0_CK(h->scores.ensure(l0::sis_scratch_bytes(n_feat, m, n_total)), "alloc screening scratch");
-    L0_CK(h->out_t.ensure((size_t)m * 4), "alloc");
-    L0_CK(h->out_r.ensure((size_t)m * 8), "alloc");
-    L0_CK(h->err.ensure(16), "alloc");
-    L0_CK(cudaMemsetAsync(h->err.p, 0, 16, st), "memset");
-    const bool pre = h->opt.precision == SISSO_L0_MIXED_BF16X3;
-    L0_CK(cudaEventRecord(h->ev[0], st), "event");
-    L0_CK(l0::launch_sis(Xd, yd, n_total, n_feat, m, pre ? 1 : 0, h->scores.p,
-                         h->out_t.as<int>(), h->out_r.as<double>(), h->err.as<int>(), st,
-                         h->ev_k[0], h->ev_k[1]),
-          "screening kernels");
-    L0_CK(cudaEventRecord(h->ev[1], st), "event");
-    L0_CK(cudaMemcpyAsync(out_idx, h->out_t.p, (size_t)m * 4, cudaMemcpyDefault, st), "copy");
-    L0_CK(cudaMemcpyAsync(out_r, h->out_r.p, (size_t)m * 8, cudaMemcpyDefault, st), "copy");
-    int herr = 0;
-    unsigned long long rescored = 0;
-    L0_CK(cudaMemcpyAsync(&herr, h->err.p, 4, cudaMemcpyDeviceToHost, st), "copy");
-    L0_CK(cudaMemcpyAsync(&rescored, (char *)h->scores.p + 40, 8, cudaMemcpyDeviceToHost, st),
-          "copy");
-    int rc = wait_stream(h);
-    if (rc) return rc;
-    sisso_l0_stats &S = h->stats;
-    S = sisso_l0_stats{};
-    S.struct_size = (int32_t)sizeof(sisso_l0_stats);
-    S.certified = 1;
-    S.fp64_fallback_tuples = pre ? rescored : (uint64_t)n_feat;
-    S.kernel_launches = pre ? 20 : 13;
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]) != cudaSuccess) {
-      cudaGetLastError();
-      ms = 0.f;
+    L0_CK(h->loop_tup.ensure(ht.size() * 4), "alloc");
+    L0_CK(cudaMemcpyAsync(h->loop_tup.p, ht.data(), ht.size() * 4, cudaMemcpyHostToDevice, st),
+          "copy tuples");
+    L0_CK(h->loop_q.ensure((size_t)n_models * n_dim * n_total * 8), "alloc");
+    double *od = out;
+    if (!is_device_ptr(out)) {
+      L0_CK(h->loop_res.ensure((size_t)n_models * n_total * 8), "alloc");
+      od = h->loop_res.as<double>();
     }
-    S.ms_total = ms;
-    if (cudaEventElapsedTime(&ms, h->ev_k[0], h->ev_k[1]) != cudaSuccess) {
-      cudaGetLastError();
-      ms = 0.f;
+    L0_CK(l0::launch_residuals(Xd, yd, n_total, h->loop_tup.as<int>(), n_dim, n_models,
+                               h->loop_q.as<double>(), od, st),
+          "residual kernel");
+    if (od != out)
+      L0_CK(cudaMemcpyAsync(out, od, (size_t)n_models * n_total * 8, cudaMemcpyDeviceToHost, st),
+            "copy residuals");
+    return wait_stream(h);
+  });
+}
+
+extern "C" int sisso_l0_dimension_loop(sisso_l0_t h, const double *X, const double *y,
+                                       int64_t n_total, int64_t n_feat, int32_t m, int32_t n_dim_max,
+                                       int32_t k, int32_t n_res, int32_t *out_S,
+                                       int32_t *out_tuples, double *out_rmse) {
+  return guarded(h, [&]() -> int {
+    if (!X || !y || !out_S || !out_tuples || !out_rmse)
+      return fail(h, SISSO_L0_EINVAL, "null pointer argument");
+    if (is_device_ptr(out_S) || is_device_ptr(out_tuples) || is_device_ptr(out_rmse))
+      return fail(h, SISSO_L0_EINVAL, "the loop's outputs are host arrays");
+    if (n_dim_max < 1 || n_dim_max > 6 || m < 1 || k < 1 || n_res < 1 ||
+        n_res > l0::SIS_MAX_TARGETS || (int64_t)m * n_dim_max > n_feat)
+      return fail(h, SISSO_L0_EINVAL,
+                  "need 1 <= n_dim_max <= 6, m, k >= 1, 1 <= n_res <= 16, m n_dim_max <= n_feat");
+    if (n_total < n_dim_max + 2) return fail(h, SISSO_L0_EINVAL, "too few samples");
+    cudaStream_t st = h->st;
+    // X and y resident on the device for the whole loop
+    const double *Xd = X, *yd = y;
+    if (!is_device_ptr(X)) {
+      const size_t xb = (size_t)n_feat * (size_t)n_total * 8;
+      L0_CK(h->loop_x.ensure(xb), "alloc X");
+      L0_CK(cudaMemcpyAsync(h->loop_x.p, X, xb, cudaMemcpyHostToDevice, st), "copy X");
+      Xd = h->loop_x.as<double>();
     }
-    S.ms_tuple_kernel = ms;
-    if (herr == 5) return fail(h, SISSO_L0_ENONFINITE, "NaN or Inf in X or y");
-    if (herr == 12) return fail(h, SISSO_L0_EUNSUPPORTED, "more than 2^22 features tie at the cut");
-    if (herr) return fail(h, SISSO_L0_ECUDA, "device error flag " + std::to_string(herr));
+    if (!is_device_ptr(y)) {
+      L0_CK(h->loop_y.ensure((size_t)n_total * 8), "alloc y");
+      L0_CK(cudaMemcpyAsync(h->loop_y.p, y, (size_t)n_total * 8, cudaMemcpyHostToDevice, st),
+            "copy y");
+      yd = h->loop_y.as<double>();
+    }
+    const int D = n_dim_max;
+    for (size_t i = 0; i < (size_t)D * k * D; ++i) out_tuples[i] = -1;
+    for (size_t i = 0; i < (size_t)D * k; ++i) out_rmse[i] = INFINITY;
+    std::vector<int32_t> S;
+    std::vector<int32_t> prev;      // best models of the previous dimension, [n_prev][n - 1]
+    int n_prev = 0;
+    const int64_t offs[2] = {0, n_total};
+    for (int n = 1; n <= D; ++n) {
+      // screening: against y, then against the residuals of the best models
+      std::vector<int32_t> idx(m);
+      std::vector<double> rr(m);
+      int rc;
+      if (n == 1) {
+        rc = sis_impl(h, Xd, yd, 1, n_total, n_feat, m, nullptr, 0, idx.data(), rr.data());
+      } else {
+        const int R = std::min(n_prev, (int)n_res);
+        if (R < 1) return fail(h, SISSO_L0_EINVAL, "no eligible model to take residuals from");
+        L0_CK(h->loop_tup.ensure((size_t)R * (n - 1) * 4), "alloc");
+        L0_CK(cudaMemcpyAsync(h->loop_tup.p, prev.data(), (size_t)R * (n - 1) * 4,
+                              cudaMemcpyHostToDevice, st),
+              "copy models");
+        L0_CK(h->loop_q.ensure((size_t)R * (n - 1) * n_total * 8), "alloc");
+        L0_CK(h->loop_res.ensure((size_t)R * n_total * 8), "alloc");
+        L0_CK(l0::launch_residuals(Xd, yd, n_total, h->loop_tup.as<int>(), n - 1, R,
+                                   h->loop_q.as<double>(), h->loop_res.as<double>(), st),
+              "residual kernel");
+        rc = sis_impl(h, Xd, h->loop_res.as<double>(), R, n_total, n_feat, m, S.data(),
+                      (int64_t)S.size(), idx.data(), rr.data());
+      }
+      if (rc) return rc;
+      S.insert(S.end(), idx.begin(), idx.end());
+      // the l0 search over every n-tuple of S
+      L0_CK(h->loop_rows.ensure(S.size() * 4), "alloc");
+      L0_CK(cudaMemcpyAsync(h->loop_rows.p, S.data(), S.size() * 4, cudaMemcpyHostToDevice, st),
+            "copy S");
+      L0_CK(h->loop_xs.ensure(S.size() * (size_t)n_total * 8), "alloc");
+      L0_CK(l0::launch_gather_rows(Xd, n_total, h->loop_rows.as<int>(), (int)S.size(),
+                                   h->loop_xs.as<double>(), st),
+            "gather S");
+      std::vector<int32_t> tl((size_t)k * n);
+      std::vector<double> rm(k);
+      sisso_l0_request req{n, k, tl.data(), rm.data()};
+      rc = fit_checked(h, h->loop_xs.as<double>(), yd, offs, 1, (int64_t)S.size(), &req, 1);
+      if (rc) return rc;
+      prev.clear();
+      n_prev = 0;
+      for (int q = 0; q < k; ++q) {
+        if (tl[(size_t)q * n] < 0) break;
+        std::vector<int32_t> g(n);
+        for (int a = 0; a < n; ++a) g[a] = S[tl[(size_t)q * n + a]];
+        std::sort(g.begin(), g.end());
+        for (int a = 0; a < n; ++a) out_tuples[((size_t)(n - 1) * k + q) * D + a] = g[a];
+        out_rmse[(size_t)(n - 1) * k + q] = rm[q];
+        if (n_prev < n_res) {
+          prev.insert(prev.end(), g.begin(), g.end());
+          ++n_prev;
+        }
+      }
+    }
+    std::copy(S.begin(), S.end(), out_S);
     return SISSO_L0_OK;
   });
 }

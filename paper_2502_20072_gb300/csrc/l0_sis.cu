@@ -26,6 +26,9 @@ namespace {
 
 __global__ void __launch_bounds__(1024)
 sis_target_kernel(const double *y, long long n, double *out, double *yd, int *err) {
+  y += (long long)blockIdx.x * n;            // one block per target
+  yd += (long long)blockIdx.x * n;
+  out += 8 * blockIdx.x;
   __shared__ double red[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   auto block_sum = [&](double v) {
@@ -97,9 +100,67 @@ __device__ __forceinline__ double sis_r64_warp(const double *__restrict__ x, lon
   return (sxx > 0.0 && syy > 0.0) ? sxy / sqrt(sxx * syy) : 0.0;
 }
 
+// The same for R targets at once (R <= SIS_MAX_TARGETS): the row is read
+// once and S3 accumulated against every target's centred values yd[t][.];
+// returns the signed r of the first target with the largest |r| (the
+// projection score against several residuals).
+__device__ __forceinline__ double sis_r64_multi_warp(const double *__restrict__ x, long long n,
+                                                     const double *__restrict__ yd,
+                                                     const double *__restrict__ tgt, int R,
+                                                     int lane, bool &finite) {
+  const double c = __ldg(x);
+  double S1 = 0.0, S2 = 0.0, S3[SIS_MAX_TARGETS];
+#pragma unroll
+  for (int t = 0; t < SIS_MAX_TARGETS; ++t) S3[t] = 0.0;
+  constexpr int U = 8;
+  for (long long i0 = lane; i0 < n; i0 += 32 * U) {
+    double v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long i = i0 + 32 * u;
+      v[u] = (i < n) ? __ldcs(x + i) : c;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long i = i0 + 32 * u;
+      finite &= ((unsigned)__double2hiint(v[u]) & 0x7ff00000u) != 0x7ff00000u;
+      const double d = v[u] - c;
+      S1 += d;
+      S2 = fma(d, d, S2);
+      if (i < n) {
+#pragma unroll
+        for (int t = 0; t < SIS_MAX_TARGETS; ++t)
+          if (t < R) S3[t] = fma(d, __ldg(yd + (long long)t * n + i), S3[t]);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    S1 += __shfl_xor_sync(0xffffffffu, S1, o);
+    S2 += __shfl_xor_sync(0xffffffffu, S2, o);
+#pragma unroll
+    for (int t = 0; t < SIS_MAX_TARGETS; ++t)
+      if (t < R) S3[t] += __shfl_xor_sync(0xffffffffu, S3[t], o);
+  }
+  const double sxx = S2 - S1 * S1 / (double)n;
+  double best = 0.0, babs = -1.0;
+#pragma unroll
+  for (int t = 0; t < SIS_MAX_TARGETS; ++t)
+    if (t < R) {
+      const double syy = tgt[8 * t + 1], sy0 = tgt[8 * t + 2];
+      const double sxy = S3[t] - S1 * sy0 / (double)n;
+      const double rt = (sxx > 0.0 && syy > 0.0) ? sxy / sqrt(sxx * syy) : 0.0;
+      if (fabs(rt) > babs) {
+        babs = fabs(rt);
+        best = rt;
+      }
+    }
+  return best;
+}
+
 __global__ void __launch_bounds__(256)
 sis_score_kernel(const double *__restrict__ X, long long n, long long n_feat,
-                 const double *__restrict__ yd, const double *__restrict__ tgt,
+                 const double *__restrict__ yd, const double *__restrict__ tgt, int R,
                  double *__restrict__ r_out, int *err) {
   const int lane = threadIdx.x & 31;
   const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
@@ -107,7 +168,8 @@ sis_score_kernel(const double *__restrict__ X, long long n, long long n_feat,
   for (long long f = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); f < n_feat;
        f += warps) {
     bool finite = true;
-    const double r = sis_r64_warp(X + f * n, n, yd, syy, sy0, lane, finite);
+    const double r = R == 1 ? sis_r64_warp(X + f * n, n, yd, syy, sy0, lane, finite)
+                            : sis_r64_multi_warp(X + f * n, n, yd, tgt, R, lane, finite);
     if (__any_sync(0xffffffffu, !finite) && lane == 0) set_err(err, 5);
     if (lane == 0) r_out[f] = r;
   }
@@ -146,6 +208,9 @@ __device__ __forceinline__ float sis_trunc32(double v, unsigned &mx) {
 __global__ void __launch_bounds__(1024)
 sis_target32_kernel(const double *y, long long n, double *tgt, float *yc) {
   __shared__ double red[2][32];
+  y += (long long)blockIdx.x * n;            // one block per target
+  yc += (long long)blockIdx.x * n;
+  tgt += 8 * blockIdx.x;
   const double mean = tgt[0], syy = tgt[1];
   int k = 0;
   if (syy > 0.0 && isfinite(syy)) frexp(sqrt(syy / (double)n), &k);
@@ -226,7 +291,7 @@ __device__ __forceinline__ void sis_bounds(double S1, double S2, double S3, doub
 // <= 3 g S2 and S_xy by <= 2 g sqrt(S2 sum yc^2).  Rounding yc moves r by <= u.
 __global__ void __launch_bounds__(256, 4)
 sis_prescreen_kernel(const double *__restrict__ X, long long n, long long n_feat,
-                     const float *__restrict__ yc, const double *__restrict__ tgt,
+                     const float *__restrict__ yc, const double *__restrict__ tgt, int accum,
                      double *__restrict__ lo_out, double *__restrict__ hi_out) {
   const int lane = threadIdx.x & 31;
   const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
@@ -293,6 +358,10 @@ sis_prescreen_kernel(const double *__restrict__ X, long long n, long long n_feat
     if (lane < G) {
       double lo, hi;
       sis_bounds(D1 + (double)F1, D2 + (double)F2, D3 + (double)F3, cm, badm, tgt, n, lo, hi);
+      if (accum) {                        // several targets: the largest bounds
+        lo = fmax(lo, lo_out[g0 + lane]);
+        hi = fmax(hi, hi_out[g0 + lane]);
+      }
       lo_out[g0 + lane] = lo;
       hi_out[g0 + lane] = hi;
     }
@@ -361,7 +430,7 @@ __device__ __forceinline__ void pb_issue(const PbJob &j, const double *X, uint32
 template <bool YREG>
 __global__ void __launch_bounds__(PB_WARPS * 32, 1)
 sis_prescreen_bulk_kernel(const double *__restrict__ X, long long n, long long n_feat,
-                          const float *__restrict__ yc, const double *__restrict__ tgt,
+                          const float *__restrict__ yc, const double *__restrict__ tgt, int accum,
                           double *__restrict__ lo_out, double *__restrict__ hi_out, int *err) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -501,6 +570,10 @@ sis_prescreen_bulk_kernel(const double *__restrict__ X, long long n, long long n
       if (g0 + lane < n_feat) {
         double lo, hi;
         sis_bounds(D1 + (double)F1, D2 + (double)F2, D3 + (double)F3, cm, badm, tgt, n, lo, hi);
+        if (accum) {                      // several targets: the largest bounds
+          lo = fmax(lo, lo_out[g0 + lane]);
+          hi = fmax(hi, hi_out[g0 + lane]);
+        }
         lo_out[g0 + lane] = lo;
         hi_out[g0 + lane] = hi;
       }
@@ -527,7 +600,7 @@ sis_prescreen_bulk_kernel(const double *__restrict__ X, long long n, long long n
 }
 
 // ordered image of -|r| (ascending = best first)
-__device__ __forceinline__ u64 sis_key(double r) { return ord_of(-fabs(r)); }
+__device__ __forceinline__ u64 sis_key(double r) { return r != r ? ~0ull : ord_of(-fabs(r)); }
 
 // Level-0 histogram privatised per block: 65536 16-bit counters packed two
 // to a word in shared memory (a block takes at most 65535 features), then
@@ -703,8 +776,9 @@ sis_candidates_kernel(const double *hi, long long n_feat, const unsigned *cut1,
   for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < end; f += stride) {
     bool take = false;
     if (f < n_feat) {
-      take = (sis_key(hi[f]) >> 32) <= P;
-      if (!take) r[f] = 0.0;
+      const double h = hi[f];
+      take = (sis_key(h) >> 32) <= P;
+      if (!take) r[f] = (h != h) ? h : 0.0;      // excluded stay NaN
     }
     const unsigned ball = __ballot_sync(0xffffffffu, take);
     if (!ball) continue;
@@ -719,7 +793,7 @@ sis_candidates_kernel(const double *hi, long long n_feat, const unsigned *cut1,
 __global__ void __launch_bounds__(256)
 sis_rescore_kernel(const double *__restrict__ X, long long n, const unsigned *list,
                    const unsigned long long *count, const double *__restrict__ yd,
-                   const double *__restrict__ tgt, double *__restrict__ r_out, int *err) {
+                   const double *__restrict__ tgt, int R, double *__restrict__ r_out, int *err) {
   const int lane = threadIdx.x & 31;
   const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
   const long long nc = (long long)*count;
@@ -728,9 +802,23 @@ sis_rescore_kernel(const double *__restrict__ X, long long n, const unsigned *li
        t += warps) {
     const long long f = list[t];
     bool finite = true;
-    const double r = sis_r64_warp(X + f * n, n, yd, syy, sy0, lane, finite);
+    const double r = R == 1 ? sis_r64_warp(X + f * n, n, yd, syy, sy0, lane, finite)
+                            : sis_r64_multi_warp(X + f * n, n, yd, tgt, R, lane, finite);
     if (__any_sync(0xffffffffu, !finite) && lane == 0) set_err(err, 5);
     if (lane == 0) r_out[f] = r;
+  }
+}
+
+// Excluded features (already selected): NaN in the given arrays, whose key
+// sorts after every score, so that no cut, candidate list or compaction
+// takes them.
+__global__ void __launch_bounds__(256)
+sis_exclude_kernel(const int *ex, long long n_ex, double *a, double *b) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_ex;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long j = ex[i];
+    a[j] = __longlong_as_double(0x7ff8000000000000ll);
+    if (b) b[j] = __longlong_as_double(0x7ff8000000000000ll);
   }
 }
 
@@ -906,21 +994,24 @@ sis_sort_kernel(u64 *keys, unsigned *idx, const unsigned long long *count, long 
 // ------------------------------------------------------------- launcher --
 namespace l0 {
 
-size_t sis_scratch_bytes(long long n_feat, int m, long long n) {
+size_t sis_scratch_bytes(long long n_feat, int m, long long n, int R) {
   const long long cap = std::min<long long>(n_feat, 1ll << 22);
   const long long rcap = std::min<long long>(cap, SIS_RANK_MAX);
   (void)m;
   return 256 * 2 + (size_t)n_feat * (8 + 8 + 4) + 256 + 65536 * 4 + (size_t)cap * (16 + 8) +
-         (size_t)rcap * 12 + (size_t)SIS_NB * 12 + (size_t)n * 12 + 21 * 256;
+         (size_t)rcap * 12 + (size_t)SIS_NB * 12 + (size_t)n * 12 * R + 64 * (size_t)R + 22 * 256;
 }
 
+// y: R targets [R][n] (R <= SIS_RMAX); ex: n_ex distinct feature indices
+// never selected (device; may be null when n_ex = 0).
 // scratch: sis_scratch_bytes, its first 64 bytes the counters (bytes
 // [40, 48): features re-scored in FP64 by the pre-screen path);
 // out_idx / out_r device [m]; err: device int; scan0 / scan1 (optional):
 // events recorded around the scan kernel (pre-screen or FP64 score)
-cudaError_t launch_sis(const double *X, const double *y, long long n, long long n_feat, int m,
-                       int prescreen, void *scratch, int *out_idx, double *out_r, int *err,
-                       cudaStream_t st, cudaEvent_t scan0, cudaEvent_t scan1) {
+cudaError_t launch_sis(const double *X, const double *y, int R, long long n, long long n_feat,
+                       int m, const int *ex, long long n_ex, int prescreen, void *scratch,
+                       int *out_idx, double *out_r, int *err, cudaStream_t st, cudaEvent_t scan0,
+                       cudaEvent_t scan1) {
   const long long cap = std::min<long long>(n_feat, 1ll << 22);
   const long long rcap = std::min<long long>(cap, SIS_RANK_MAX);
   char *p = (char *)scratch;
@@ -938,7 +1029,7 @@ cudaError_t launch_sis(const double *X, const double *y, long long n, long long 
   double *r = (double *)take((size_t)n_feat * 8);
   double *hi = (double *)take((size_t)n_feat * 8);
   unsigned *list = (unsigned *)take((size_t)n_feat * 4);
-  double *tgt = (double *)take(64);
+  double *tgt = (double *)take((size_t)64 * R);          // [R][8]
   unsigned *hist = (unsigned *)take(65536 * 4);
   u64 *keys = (u64 *)take((size_t)cap * 16);
   unsigned *idx = (unsigned *)take((size_t)cap * 8);
@@ -948,8 +1039,8 @@ cudaError_t launch_sis(const double *X, const double *y, long long n, long long 
   unsigned *bcount = (unsigned *)take((size_t)SIS_NB * 4 * 2);   // counts, fill cursors
   unsigned *bfill = bcount + SIS_NB;
   unsigned *bstart = (unsigned *)take((size_t)SIS_NB * 4);
-  float *yc = (float *)take((size_t)n * 4);
-  double *yd = (double *)take((size_t)n * 8);
+  float *yc = (float *)take((size_t)n * 4 * R);          // [R][n]
+  double *yd = (double *)take((size_t)n * 8 * R);        // [R][n]
   const unsigned g = (unsigned)std::min<long long>((n_feat + 255) / 256, 152 * 16);
   const unsigned gw = (unsigned)std::min<long long>((n_feat + 7) / 8, 152 * 32);
   cudaError_t e = cudaMemsetAsync(small, 0, 64, st);
@@ -977,9 +1068,10 @@ cudaError_t launch_sis(const double *X, const double *y, long long n, long long 
     sis_cut_kernel<<<1, 1024, 0, st>>>(hist, m, below, c2 + 1);
     return cudaSuccess;
   };
-  sis_target_kernel<<<1, 1024, 0, st>>>(y, n, tgt, yd, err);
+  const unsigned gx = (unsigned)std::min<long long>((n_ex + 255) / 256, 1024);
+  sis_target_kernel<<<R, 1024, 0, st>>>(y, n, tgt, yd, err);
   if (prescreen) {
-    sis_target32_kernel<<<1, 1024, 0, st>>>(y, n, tgt, yc);
+    sis_target32_kernel<<<R, 1024, 0, st>>>(y, n, tgt, yc);
     if (scan0 && (e = cudaEventRecord(scan0, st)) != cudaSuccess) return e;
     // one wave of resident blocks: every warp takes groups of 32 features
     int per_sm = 0;
@@ -992,28 +1084,33 @@ cudaError_t launch_sis(const double *X, const double *y, long long n, long long 
         return e;
       const long long groups = (n_feat + 31) / 32;
       const unsigned grid = (unsigned)std::min<long long>((groups + PB_WARPS - 1) / PB_WARPS, n_sm);
-      if (yreg)
-        sis_prescreen_bulk_kernel<true><<<grid, PB_WARPS * 32, PB_SMEM, st>>>(X, n, n_feat, yc, tgt,
-                                                                             r, hi, err);
-      else
-        sis_prescreen_bulk_kernel<false><<<grid, PB_WARPS * 32, PB_SMEM, st>>>(X, n, n_feat, yc,
-                                                                              tgt, r, hi, err);
+      for (int t = 0; t < R; ++t) {      // one pass over X per target
+        if (yreg)
+          sis_prescreen_bulk_kernel<true><<<grid, PB_WARPS * 32, PB_SMEM, st>>>(
+              X, n, n_feat, yc + (size_t)t * n, tgt + 8 * t, t > 0, r, hi, err);
+        else
+          sis_prescreen_bulk_kernel<false><<<grid, PB_WARPS * 32, PB_SMEM, st>>>(
+              X, n, n_feat, yc + (size_t)t * n, tgt + 8 * t, t > 0, r, hi, err);
+      }
     } else {
       if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sis_prescreen_kernel, 256,
                                                              0)) != cudaSuccess)
         return e;
       const long long waves = (long long)n_sm * std::max(per_sm, 1);
-      sis_prescreen_kernel<<<(unsigned)std::min<long long>((n_feat + 255) / 256, waves), 256, 0,
-                             st>>>(X, n, n_feat, yc, tgt, r, hi);
+      for (int t = 0; t < R; ++t)
+        sis_prescreen_kernel<<<(unsigned)std::min<long long>((n_feat + 255) / 256, waves), 256, 0,
+                               st>>>(X, n, n_feat, yc + (size_t)t * n, tgt + 8 * t, t > 0, r, hi);
     }
     if (scan1 && (e = cudaEventRecord(scan1, st)) != cudaSuccess) return e;
+    if (n_ex) sis_exclude_kernel<<<gx, 256, 0, st>>>(ex, n_ex, r, hi);
     if ((e = cut_of(r, pcuts, pcnt)) != cudaSuccess) return e;
     sis_candidates_kernel<<<g, 256, 0, st>>>(hi, n_feat, pcuts, pcuts + 1, r, list, pcnt + 1);
-    sis_rescore_kernel<<<gw, 256, 0, st>>>(X, n, list, pcnt + 1, yd, tgt, r, err);
+    sis_rescore_kernel<<<gw, 256, 0, st>>>(X, n, list, pcnt + 1, yd, tgt, R, r, err);
   } else {
     if (scan0 && (e = cudaEventRecord(scan0, st)) != cudaSuccess) return e;
-    sis_score_kernel<<<gw, 256, 0, st>>>(X, n, n_feat, yd, tgt, r, err);
+    sis_score_kernel<<<gw, 256, 0, st>>>(X, n, n_feat, yd, tgt, R, r, err);
     if (scan1 && (e = cudaEventRecord(scan1, st)) != cudaSuccess) return e;
+    if (n_ex) sis_exclude_kernel<<<gx, 256, 0, st>>>(ex, n_ex, r, nullptr);
   }
   if ((e = cut_of(r, cuts, cnt)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(bcount, 0, (size_t)SIS_NB * 8, st)) != cudaSuccess) return e;
