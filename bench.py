@@ -64,7 +64,7 @@ def tile_traffic(workload, precision):
 # ncu capture in profiles/sis_prescreen_n1000.md (500000 features: 4000093952
 # read + 10153984 written), scaled by the features of a launch (the kernel
 # reads each row once).  Tied to the sources it was taken from, as above.
-SIS_TRAFFIC_SOURCES = ("l0_sis.cu", "l0_tc.cuh")
+SIS_TRAFFIC_SOURCES = ("l0_sis.cu", "l0_tc.cuh", "l0_screen.cuh")
 SIS_TRAFFIC_CAPTURED = {1000: ((4000093952 + 10153984) / 500000, "750ba56b3dbc9719")}
 
 
@@ -585,6 +585,89 @@ def run_sis(args):
         print(json.dumps(line))
 
 
+def run_loop(args):
+    """The dimension loop (SIS -> l0 -> residuals -> multi-residual SIS ...):
+    n_feat seeded candidate features resident on the device, one planted
+    three-term descriptor among decoys."""
+    import torch
+    import paper_2502_20072_gb300 as l0
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    n_feat, n, m, D, k, n_res = args.loop_features, 1000, args.loop_m, 3, 10, 10
+    g = torch.Generator(device="cuda").manual_seed(11)
+    X = torch.randn((n_feat, n), generator=g, device="cuda", dtype=torch.float64)
+    a, b, c = 11, n_feat // 2, (7 * n_feat) // 9
+    X[:64] = X[a] + 0.4 * torch.randn((64, n), generator=g, device="cuda", dtype=torch.float64)
+    y = 2.0 * X[a] + 0.6 * X[b] - 0.4 * X[c] + 0.02 * torch.randn((n,), generator=g, device="cuda",
+                                                                  dtype=torch.float64)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    prec = {"fp64": l0.FP64, "mixed": l0.MIXED_BF16X3}[args.precision]
+    h = l0.Handle(precision=prec, device=local, stream=stream.cuda_stream)
+    out = None
+
+    def step():
+        nonlocal out
+        out = h.dimension_loop(X, y, m, D, k, n_res)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    clocks = Clocks(local)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        step()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    found = tuple(int(t) for t in out[2]["tuples"][0]) == tuple(sorted((a, b, c)))
+    # screening passes over X: one per dimension (all residuals in one pass)
+    passes = D
+    xbytes = passes * n_feat * n * 8
+    tuples = sum(math.comb(m * d, d) for d in range(1, D + 1))
+    pk_hbm = None
+    mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(mp):
+        pk_hbm = json.load(open(mp)).get("hbm_gbs")
+    gbs = xbytes / (ms * 1e-3) / 1e9
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        sys.path.insert(0, ROOT)
+        from oracle import loop as oloop
+        ns, ms_s = 20000, 20
+        Xs = X[:ns].cpu().numpy()
+        ys = y.cpu().numpy()
+        t0 = time.perf_counter()
+        oloop.dimension_loop(Xs, ys, ms_s, 2, k, n_res)
+        dt = time.perf_counter() - t0
+        cpu = {"value": dt * 1e3, "unit": "ms per loop", "cores": 16, "kind": "oracle",
+               "sample": "%d of the features, m=%d, dimensions 1-2 (not comparable in size: "
+                         "context only)" % (ns, ms_s)}
+    line = {"metric": "dimension loop (SIS + l0 per dimension, 3 dimensions) ms per loop",
+            "value": ms, "unit": "ms", "n_gpus": ws, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == l0.FP64 else "f32 pre-screen + f64; FP32 l0 search + FP64 re-fit",
+            "data": "synthetic (seeded normal features on the device, planted 3-term descriptor)",
+            "config": {"workload": "LOOP: n_feat=%d n_samples=%d m=%d per dimension D=%d k=%d "
+                                   "residuals=%d" % (n_feat, n, m, D, k, n_res),
+                       "inputs": "larger than L2 (%.1f GB)" % (n_feat * n * 8 / 1e9),
+                       "planted_found": found, "l0_tuples": tuples,
+                       "screening_passes": passes},
+            "gpu_launches": int(h.stats()["kernel_launches"]) * args.steps,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk_hbm, "unit": "GB/s",
+                         "frac": gbs / pk_hbm if pk_hbm else None, "traffic": None,
+                         "kernel": "whole loop: X bytes of the screening passes / loop time"},
+            "cpu_baseline": cpu, "clocks": clk}
+    h.close()
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -601,6 +684,8 @@ def main():
     ap.add_argument("--train-steps", type=int, default=4000)
     ap.add_argument("--train-instances", type=int, default=50)
     ap.add_argument("--sis-features", type=int, default=4000000)
+    ap.add_argument("--loop-features", type=int, default=1000000)
+    ap.add_argument("--loop-m", type=int, default=500)
     ap.add_argument("--learned-sis", type=int, default=20000,
                     help="columns of the learned workload (smaller for profiling)")
     args = ap.parse_args()
@@ -610,6 +695,8 @@ def main():
         run_learned(args)
     elif args.workload == "SIS":
         run_sis(args)
+    elif args.workload == "LOOP":
+        run_loop(args)
     else:
         run_ours(args)
 

@@ -389,7 +389,8 @@ int sisso_l0_residuals(sisso_l0_t h, const double *X, const double *y, int64_t n
  * (host inputs are copied to the device once).  Errors: EINVAL
  * (1 <= n_dim_max <= 6, 1 <= n_res <= 16, m n_dim_max <= n_feat,
  * n_total >= n_dim_max + 2), and those of sisso_l0_sis_multi and
- * sisso_l0_fit. */
+ * sisso_l0_fit.  get_stats then reports the last l0 search, except
+ * kernel_launches, which counts the whole loop. */
 int sisso_l0_dimension_loop(sisso_l0_t h, const double *X, const double *y, int64_t n_total,
                             int64_t n_feat, int32_t m, int32_t n_dim_max, int32_t k,
                             int32_t n_res, int32_t *out_S, int32_t *out_tuples,

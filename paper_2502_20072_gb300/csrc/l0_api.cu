@@ -22,6 +22,7 @@
 
 #include "../../include/sisso_l0.h"
 #include "l0_kernels.cuh"
+#include "l0_screen.cuh"
 
 using l0::u64;
 
@@ -1979,6 +1980,7 @@ extern "C" int sisso_l0_dimension_loop(sisso_l0_t h, const double *X, const doub
     std::vector<int32_t> S;
     std::vector<int32_t> prev;      // best models of the previous dimension, [n_prev][n - 1]
     int n_prev = 0;
+    int64_t launches = 0;           // library kernels of the whole loop
     const int64_t offs[2] = {0, n_total};
     for (int n = 1; n <= D; ++n) {
       // screening: against y, then against the residuals of the best models
@@ -2001,8 +2003,10 @@ extern "C" int sisso_l0_dimension_loop(sisso_l0_t h, const double *X, const doub
               "residual kernel");
         rc = sis_impl(h, Xd, h->loop_res.as<double>(), R, n_total, n_feat, m, S.data(),
                       (int64_t)S.size(), idx.data(), rr.data());
+        launches += 1;              // residual kernel
       }
       if (rc) return rc;
+      launches += h->stats.kernel_launches + 1;    // screening, gather
       S.insert(S.end(), idx.begin(), idx.end());
       // the l0 search over every n-tuple of S
       L0_CK(h->loop_rows.ensure(S.size() * 4), "alloc");
@@ -2017,6 +2021,7 @@ extern "C" int sisso_l0_dimension_loop(sisso_l0_t h, const double *X, const doub
       sisso_l0_request req{n, k, tl.data(), rm.data()};
       rc = fit_checked(h, h->loop_xs.as<double>(), yd, offs, 1, (int64_t)S.size(), &req, 1);
       if (rc) return rc;
+      launches += h->stats.kernel_launches;
       prev.clear();
       n_prev = 0;
       for (int q = 0; q < k; ++q) {
@@ -2033,6 +2038,7 @@ extern "C" int sisso_l0_dimension_loop(sisso_l0_t h, const double *X, const doub
       }
     }
     std::copy(S.begin(), S.end(), out_S);
+    h->stats.kernel_launches = launches;   // the last fit's stats, launches of the whole loop
     return SISSO_L0_OK;
   });
 }

@@ -13,6 +13,7 @@
 // two passes.  All in FP64.
 #include "../../include/sisso_l0.h"
 #include "l0_kernels.cuh"
+#include "l0_screen.cuh"
 
 namespace l0 {
 

@@ -18,6 +18,7 @@
 #include <algorithm>
 
 #include "l0_kernels.cuh"
+#include "l0_screen.cuh"
 #include "l0_tc.cuh"
 
 namespace l0 {
@@ -599,6 +600,154 @@ sis_prescreen_bulk_kernel(const double *__restrict__ X, long long n, long long n
   }
 }
 
+// Several targets in one pass over X (the residual screening of the
+// dimension loop): the FP32 centred values of all R targets sit in shared
+// memory ([R][n], n <= PM_NMAX), each lane accumulates S3 for every target,
+// and the epilogue takes, per feature, the largest lower and upper bounds
+// over the targets -- an interval around max_t |r_t|.  Same staging, error
+// model and cursors as sis_prescreen_bulk_kernel; 12 warps so that the
+// targets fit beside the rings.
+constexpr int PM_WARPS = 12;
+constexpr int PM_NMAX = 2 * PB_SEG;
+constexpr size_t PM_RING_BYTES = (size_t)PM_WARPS * PB_STAGES * PB_STAGE_BYTES;
+constexpr size_t pm_smem(int R, long long n) {
+  return PM_RING_BYTES + (size_t)PM_WARPS * PB_STAGES * 8 + (size_t)R * n * 4;
+}
+
+__global__ void __launch_bounds__(PM_WARPS * 32, 1)
+sis_prescreen_multi_kernel(const double *__restrict__ X, long long n, long long n_feat,
+                           const float *__restrict__ yc, const double *__restrict__ tgt, int R,
+                           double *__restrict__ lo_out, double *__restrict__ hi_out, int *err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long warp = (long long)blockIdx.x * PM_WARPS + w;
+  const long long warps = (long long)gridDim.x * PM_WARPS;
+  unsigned char *ring = smem + (size_t)w * PB_STAGES * PB_STAGE_BYTES;
+  const uint32_t bar0 = tc::smem_u32(smem + PM_RING_BYTES) + w * PB_STAGES * 8;
+  float *ys = (float *)(smem + PM_RING_BYTES + (size_t)PM_WARPS * PB_STAGES * 8);
+  const uint32_t ring0 = tc::smem_u32(ring);
+  const int nseg = (int)((n + PB_SEG - 1) / PB_SEG);    // 1 or 2
+  if (lane == 0) {
+    for (int b = 0; b < PB_STAGES; ++b) tc::mbar_init(bar0 + 8 * b, 1);
+    tc::fence_proxy_async_smem();
+  }
+  __syncwarp();
+  PbCursor pc;
+  for (int q = 0; q < PB_STAGES; ++q) {
+    const PbJob j = pb_job(pc, warp, warps, n, n_feat);
+    if (lane == 0 && j.valid) pb_issue(j, X, ring0 + q * PB_STAGE_BYTES, bar0 + 8 * q);
+    pc.advance(nseg);
+  }
+  for (long long i = threadIdx.x; i < (long long)R * n; i += blockDim.x) ys[i] = yc[i];
+  __syncthreads();
+  float F1 = 0.f, F2 = 0.f, F3[SIS_MAX_TARGETS];      // lane t: feature t of the group
+  double cm = 0.0;
+  bool badm = false;
+  float a1 = 0.f, a2 = 0.f, a3[SIS_MAX_TARGETS];
+#pragma unroll
+  for (int t = 0; t < SIS_MAX_TARGETS; ++t) a3[t] = F3[t] = 0.f;
+  double c = 0.0;
+  float fc = 0.f;
+  unsigned mx = 0;
+  PbCursor cc;
+  int st = 0;
+  uint32_t phase = 0;
+  int inflight = 0;
+  for (;;) {
+    const PbJob j = pb_job(cc, warp, warps, n, n_feat);
+    if (!j.valid) break;
+    if (!__all_sync(0xffffffffu, tc::mbar_wait(bar0 + 8 * st, phase, err))) {
+      inflight = PB_STAGES - 1;
+      break;
+    }
+    const double *sv = (const double *)(ring + (size_t)st * PB_STAGE_BYTES) + j.off;
+    const int t = cc.t;
+    if (j.s == 0) {
+      c = sv[0];
+      mx = 0;
+      fc = sis_trunc32(c, mx);
+    }
+    if (j.tail) {
+      __syncwarp();
+      if (lane == 0) ((double *)sv)[j.len - 1] = __ldg(X + j.e0 + j.len - 1);
+      __syncwarp();
+    }
+    const float *yb = ys + (long long)j.s * PB_SEG;
+#pragma unroll 4
+    for (int k = 0; k < PB_K; ++k) {
+      const int i = lane + 32 * k;
+      if (i < j.len) {
+        const float d = sis_trunc32(sv[i], mx) - fc;
+        a1 += d;
+        a2 = fmaf(d, d, a2);
+#pragma unroll
+        for (int u = 0; u < SIS_MAX_TARGETS; ++u)
+          if (u < R) a3[u] = fmaf(d, yb[(long long)u * n + i], a3[u]);
+      }
+    }
+    const bool last = j.s == nseg - 1;
+    if (last) {                                     // <= 32 terms per lane
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+#pragma unroll
+        for (int u = 0; u < SIS_MAX_TARGETS; ++u)
+          if (u < R) a3[u] += __shfl_xor_sync(0xffffffffu, a3[u], o);
+      }
+      const bool bad = __any_sync(0xffffffffu, mx >= SIS_MX_BAD);
+      if (lane == t) {
+        F1 = a1;
+        F2 = a2;
+#pragma unroll
+        for (int u = 0; u < SIS_MAX_TARGETS; ++u) F3[u] = a3[u];
+        cm = c;
+        badm = bad;
+      }
+      a1 = a2 = 0.f;
+#pragma unroll
+      for (int u = 0; u < SIS_MAX_TARGETS; ++u) a3[u] = 0.f;
+    }
+    __syncwarp();
+    {
+      const PbJob jn = pb_job(pc, warp, warps, n, n_feat);
+      if (lane == 0 && jn.valid) pb_issue(jn, X, ring0 + st * PB_STAGE_BYTES, bar0 + 8 * st);
+      pc.advance(nseg);
+    }
+    const long long g0 = j.f - t;
+    if (last && (t == 31 || j.f == n_feat - 1)) {
+      if (g0 + lane < n_feat) {
+        double lo = 0.0, hi = 0.0;
+#pragma unroll
+        for (int u = 0; u < SIS_MAX_TARGETS; ++u)
+          if (u < R) {
+            double l1, h1;
+            sis_bounds((double)F1, (double)F2, (double)F3[u], cm, badm, tgt + 8 * u, n, l1, h1);
+            lo = fmax(lo, l1);
+            hi = fmax(hi, h1);
+          }
+        lo_out[g0 + lane] = lo;
+        hi_out[g0 + lane] = hi;
+      }
+      badm = false;
+    }
+    cc.advance(nseg);
+    if (++st == PB_STAGES) {
+      st = 0;
+      phase ^= 1u;
+    }
+  }
+  for (int r = 0; r < inflight; ++r) {
+    cc.advance(nseg);
+    if (++st == PB_STAGES) {
+      st = 0;
+      phase ^= 1u;
+    }
+    if (!pb_job(cc, warp, warps, n, n_feat).valid) break;
+    if (!__all_sync(0xffffffffu, tc::mbar_wait(bar0 + 8 * st, phase, err))) break;
+  }
+}
+
 // ordered image of -|r| (ascending = best first)
 __device__ __forceinline__ u64 sis_key(double r) { return r != r ? ~0ull : ord_of(-fabs(r)); }
 
@@ -1084,6 +1233,17 @@ cudaError_t launch_sis(const double *X, const double *y, int R, long long n, lon
         return e;
       const long long groups = (n_feat + 31) / 32;
       const unsigned grid = (unsigned)std::min<long long>((groups + PB_WARPS - 1) / PB_WARPS, n_sm);
+      if (R > 1 && n <= PM_NMAX && pm_smem(R, n) <= 227 * 1024) {   // one pass for all targets
+        const size_t sm = pm_smem(R, n);
+        if ((e = cudaFuncSetAttribute(sis_prescreen_multi_kernel,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
+            cudaSuccess)
+          return e;
+        const unsigned gm =
+            (unsigned)std::min<long long>((groups + PM_WARPS - 1) / PM_WARPS, n_sm);
+        sis_prescreen_multi_kernel<<<gm, PM_WARPS * 32, sm, st>>>(X, n, n_feat, yc, tgt, R, r, hi,
+                                                                  err);
+      } else
       for (int t = 0; t < R; ++t) {      // one pass over X per target
         if (yreg)
           sis_prescreen_bulk_kernel<true><<<grid, PB_WARPS * 32, PB_SMEM, st>>>(

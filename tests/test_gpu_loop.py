@@ -60,6 +60,22 @@ def test_sis_multi_matches_oracle_and_paths_agree(R):
     assert m <= st["fp64_fallback_tuples"] <= 8 * m
 
 
+def test_sis_multi_long_rows():
+    """Rows longer than the fused multi-target pre-screen takes (one pass
+    per target): same selection as the FP64 scan and the oracle."""
+    X, y, _ = _planted(6, n=1500)
+    Y = oloop.residuals(X, y, [[123], [2001], [40], [7]])
+    with l0.Handle(precision=l0.FP64) as h:
+        i64, r64 = h.sis_multi(X, Y, 30, exclude=[123])
+    with l0.Handle(precision=l0.MIXED_BF16X3) as h:
+        i32, r32 = h.sis_multi(X, Y, 30, exclude=[123])
+    np.testing.assert_array_equal(i32, i64)
+    np.testing.assert_array_equal(r32, r64)
+    ref_i, ref_r = oloop.sis_multi(X, Y, 30, exclude=[123])
+    np.testing.assert_array_equal(i64, ref_i)
+    np.testing.assert_allclose(r64, ref_r, rtol=1e-11, atol=1e-13)
+
+
 def test_sis_multi_errors():
     X, y, _ = _planted(3)
     nf = X.shape[0]
