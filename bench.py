@@ -668,6 +668,111 @@ def run_loop(args):
         print(json.dumps(line))
 
 
+def run_generated(args):
+    """SIS over generated features (operators on child pairs, value rules,
+    Pearson in one pass, nothing stored): every pair of n_child children for
+    the five binary operators (both orders for - and /) and the nine unary
+    operators on every child."""
+    import torch
+    import paper_2502_20072_gb300 as l0
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    nc, n, m = args.gen_children, 200, 5000
+    g = torch.Generator(device="cuda").manual_seed(13)
+    C = (0.3 + 2.7 * torch.rand((nc, n), generator=g, device="cuda", dtype=torch.float64))
+    y = torch.log(C[4]) * C[7] + 0.05 * torch.randn((n,), generator=g, device="cuda",
+                                                    dtype=torch.float64)
+    i, j = torch.triu_indices(nc, nc, 1, device="cuda")
+    parts = []
+    for op, both in ((0, False), (1, True), (2, False), (3, True), (4, False)):
+        parts.append((torch.full_like(i, op), i, j))
+        if both:
+            parts.append((torch.full_like(i, op), j, i))
+    ar = torch.arange(nc, device="cuda")
+    for op in range(5, 14):
+        parts.append((torch.full_like(ar, op), ar, torch.zeros_like(ar)))
+    ops = torch.cat([p[0] for p in parts]).to(torch.int32)
+    c1 = torch.cat([p[1] for p in parts]).to(torch.int32)
+    c2 = torch.cat([p[2] for p in parts]).to(torch.int32)
+    n_cand = int(ops.shape[0])
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    h = l0.Handle(precision=l0.FP64, device=local, stream=stream.cuda_stream)
+    idx = torch.empty(m, dtype=torch.int32, device="cuda")
+    r = torch.empty(m, dtype=torch.float64, device="cuda")
+    lib = l0.lib()
+    import ctypes
+
+    def step():
+        rc = lib.sisso_l0_sis_generated(
+            h._h, ctypes.c_void_p(C.data_ptr()), nc, n, ctypes.c_void_p(ops.data_ptr()),
+            ctypes.c_void_p(c1.data_ptr()), ctypes.c_void_p(c2.data_ptr()), n_cand,
+            ctypes.c_void_p(y.data_ptr()), m, 1e-5, 1e8, ctypes.c_void_p(idx.data_ptr()),
+            ctypes.c_void_p(r.data_ptr()), None)
+        h._check(rc)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    clocks = Clocks(local)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        step()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    st = h.stats()
+    ms_k = st["ms_tuple_kernel"]
+    # FP64 operations per sample of the arithmetic operators: the value, the
+    # shift, S1, and the FMAs of S2 and S3
+    flop = n_cand * n * 7
+    tf = flop / (ms_k * 1e-3) / 1e12 if ms_k > 0 else None
+    peaks = {}
+    try:
+        peaks = l0.measure_peaks(local)
+    except Exception:
+        pass
+    pk = peaks.get("fp64_tflops")
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        sys.path.insert(0, ROOT)
+        from oracle import generate as og
+        ns = 20000
+        Cs = C.cpu().numpy()
+        ys = y.cpu().numpy()
+        sel = torch.randperm(n_cand, generator=torch.Generator().manual_seed(0))[:ns].numpy()
+        o_h, a_h, b_h = ops.cpu().numpy()[sel], c1.cpu().numpy()[sel], c2.cpu().numpy()[sel]
+        t0 = time.perf_counter()
+        og.sis_generated(Cs, o_h, a_h, b_h, ys, 100)
+        dt = time.perf_counter() - t0
+        cpu = {"value": ns / dt, "unit": "candidates/s", "cores": 1, "kind": "oracle",
+               "sample": "%d random candidates of the %d" % (ns, n_cand)}
+    line = {"metric": "generated-feature SIS candidates/sec (operator values + rules + Pearson "
+                      "+ top-m)",
+            "value": n_cand / (ms * 1e-3), "unit": "candidates/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded uniform children on the device)",
+            "config": {"workload": "GEN: n_child=%d n_samples=%d candidates=%d m=%d"
+                                   % (nc, n, n_cand, m),
+                       "inputs": "children %.1f MB (L2-resident), candidate lists %.0f MB"
+                                 % (nc * n * 8 / 1e6, n_cand * 12 / 1e6)},
+            "gpu_launches": int(st["kernel_launches"]) * args.steps,
+            "roofline": {"bound": "alu", "achieved": tf, "peak": pk, "unit": "TFLOP/s",
+                         "frac": tf / pk if (tf and pk) else None, "traffic": None,
+                         "kernel": "gen_score_kernel (FP64)", "kernel_ms": ms_k,
+                         "peak_source": "measured FP64 FMA rate (sisso_l0_measure_peaks)",
+                         "flop_per_sample": 7},
+            "cpu_baseline": cpu, "clocks": clk}
+    h.close()
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -685,6 +790,7 @@ def main():
     ap.add_argument("--train-instances", type=int, default=50)
     ap.add_argument("--sis-features", type=int, default=4000000)
     ap.add_argument("--loop-features", type=int, default=1000000)
+    ap.add_argument("--gen-children", type=int, default=3000)
     ap.add_argument("--loop-m", type=int, default=500)
     ap.add_argument("--learned-sis", type=int, default=20000,
                     help="columns of the learned workload (smaller for profiling)")
@@ -697,6 +803,8 @@ def main():
         run_sis(args)
     elif args.workload == "LOOP":
         run_loop(args)
+    elif args.workload == "GEN":
+        run_generated(args)
     else:
         run_ours(args)
 

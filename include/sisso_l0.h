@@ -364,6 +364,37 @@ int sisso_l0_sis_multi(sisso_l0_t h, const double *X, const double *Y, int32_t n
                        int64_t n_total, int64_t n_feat, int32_t m, const int32_t *exclude,
                        int64_t n_exclude, int32_t *out_idx, double *out_r);
 
+/* Operators of on-the-fly feature generation (paper Sec. 3's set). */
+enum {
+  SISSO_L0_OP_ADD = 0, SISSO_L0_OP_SUB = 1, SISSO_L0_OP_MUL = 2, SISSO_L0_OP_DIV = 3,
+  SISSO_L0_OP_ABS_DIFF = 4, SISSO_L0_OP_LOG = 5, SISSO_L0_OP_EXP = 6, SISSO_L0_OP_NEG_EXP = 7,
+  SISSO_L0_OP_ABS = 8, SISSO_L0_OP_SQRT = 9, SISSO_L0_OP_CBRT = 10, SISSO_L0_OP_SQ = 11,
+  SISSO_L0_OP_CUBE = 12, SISSO_L0_OP_INV = 13
+};
+
+/* SIS over generated features that are never stored (paper Sec. 2: the
+ * operators applied to child features, their values evaluated and checked
+ * on the GPU; the last rung evaluated inside SIS, Sec. 2.3, Sec. 3).
+ * Candidate t is ops[t](C[c1[t]], C[c2[t]]) -- codes 0-4 binary, 5-13
+ * unary on c1[t] (c2[t] ignored) -- evaluated in FP64.  A candidate is valid
+ * when every value is finite, max |value| lies in [l_bound, u_bound], the
+ * values are not all equal and not equal sample by sample to a child; the m
+ * valid candidates of largest |r| with y (Eq. 1) are returned, ties to the
+ * smaller candidate index, -1 (and r = 0) past the valid count.
+ *   C     FP64 [n_child][n_total] child values (host or device)
+ *   ops, c1, c2  int32 [n_cand] (host or device)
+ *   y     FP64 [n_total]
+ *   out_idx int32 [m], out_r FP64 [m] (host or device)
+ *   out_valid uint8 [n_cand] (optional, host or device): 1 valid, 0 not
+ * Errors: EINVAL (also an operator code or child index out of range,
+ * detected on the device), ENONFINITE (y), EUNSUPPORTED (m > 65536,
+ * n_cand >= 2^32), ENOMEM, ECUDA. */
+int sisso_l0_sis_generated(sisso_l0_t h, const double *C, int64_t n_child, int64_t n_total,
+                           const int32_t *ops, const int32_t *c1, const int32_t *c2,
+                           int64_t n_cand, const double *y, int32_t m, double l_bound,
+                           double u_bound, int32_t *out_idx, double *out_r,
+                           uint8_t *out_valid);
+
 /* Residuals y - (b_0 + sum_a b_a x_{t_a}) of the least-squares fits with
  * intercept (Sec. 2.4) of n_models models of n_dim features each.
  * tuples: int32 [n_models][n_dim] feature indices into X (host or device);

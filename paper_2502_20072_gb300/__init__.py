@@ -89,7 +89,7 @@ EXPORTS = ("sisso_l0_default_options", "sisso_l0_create", "sisso_l0_fit", "sisso
            "sisso_l0_pair_data", "sisso_l0_fit_pairs", "sisso_l0_fit_learned",
            "sisso_l0_fit_shard", "sisso_l0_merge_shards", "sisso_l0_measure_peaks",
            "sisso_l0_sis", "sisso_l0_sis_multi", "sisso_l0_residuals",
-           "sisso_l0_dimension_loop")
+           "sisso_l0_dimension_loop", "sisso_l0_sis_generated")
 
 MAX_POOL = 2048
 
@@ -150,6 +150,8 @@ def lib():
         L.sisso_l0_sis.argtypes = [vp, dp, dp, i64, i64, i32, vp, vp]
         L.sisso_l0_sis_multi.argtypes = [vp, dp, dp, i32, i64, i64, i32, vp, i64, vp, vp]
         L.sisso_l0_residuals.argtypes = [vp, dp, dp, i64, i64, vp, i32, i32, vp]
+        L.sisso_l0_sis_generated.argtypes = [vp, dp, i64, i64, vp, vp, vp, i64, dp, i32,
+                                             ctypes.c_double, ctypes.c_double, vp, vp, vp]
         L.sisso_l0_dimension_loop.argtypes = [vp, dp, dp, i64, i64, i32, i32, i32, i32, vp, vp,
                                               vp]
         no_int = ("sisso_l0_last_error", "sisso_l0_destroy", "sisso_l0_count_tuples",
@@ -427,6 +429,32 @@ class Handle:
             int(m), ctypes.c_void_p(ex.ctypes.data if len(ex) else None), len(ex),
             ctypes.c_void_p(idx.ctypes.data), ctypes.c_void_p(r.ctypes.data)))
         return idx, r
+
+    def sis_generated(self, C, ops, c1, c2, y, m, l_bound=1e-5, u_bound=1e8, want_valid=True):
+        """SIS over the generated candidates ops[t](C[c1[t]], C[c2[t]]):
+        (candidate indices [m] (-1 past the valid count), r [m], valid
+        [n_cand] uint8 or None)."""
+        C = _as_f64(C)
+        y = _as_f64(y)
+        ints = []
+        for a in (ops, c1, c2):
+            if hasattr(a, "data_ptr"):
+                import torch
+                ints.append(a.to(torch.int32).contiguous())
+            else:
+                ints.append(np.ascontiguousarray(a, dtype=np.int32))
+        nc, n = int(C.shape[0]), int(C.shape[1])
+        n_cand = int(ints[0].shape[0])
+        idx = np.empty(m, dtype=np.int32)
+        r = np.empty(m, dtype=np.float64)
+        valid = np.empty(n_cand, dtype=np.uint8) if want_valid else None
+        self._check(lib().sisso_l0_sis_generated(
+            self._h, ctypes.c_void_p(_ptr(C)), nc, n, ctypes.c_void_p(_ptr(ints[0])),
+            ctypes.c_void_p(_ptr(ints[1])), ctypes.c_void_p(_ptr(ints[2])), n_cand,
+            ctypes.c_void_p(_ptr(y)), int(m), float(l_bound), float(u_bound),
+            ctypes.c_void_p(idx.ctypes.data), ctypes.c_void_p(r.ctypes.data),
+            ctypes.c_void_p(valid.ctypes.data if valid is not None else None)))
+        return idx, r, valid
 
     def residuals(self, X, y, tuples):
         """Residuals [R, n_total] of the least-squares fits (with intercept)

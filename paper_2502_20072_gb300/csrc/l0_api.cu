@@ -79,6 +79,7 @@ struct sisso_l0_handle {
   DevBuf prop_in, prop_pairs, prop_bits, prop_ctr, sel_hist, sel_bin, scores, diag;
   DevBuf col_hash, col_cls;
   DevBuf sis_ex, sis_y;                               // screening: exclusions, targets
+  DevBuf gen_ops, gen_c1, gen_c2, gen_valid;          // generated candidates
   DevBuf loop_x, loop_y, loop_xs, loop_res, loop_q, loop_tup, loop_rows;   // dimension loop
   int binom_m = -1;
   int done_init_for = 0;
@@ -1894,6 +1895,103 @@ extern "C" int sisso_l0_sis_multi(sisso_l0_t h, const double *X, const double *Y
                                   double *out_r) {
   return guarded(h, [&]() -> int {
     return sis_impl(h, X, Y, n_targets, n_total, n_feat, m, exclude, n_exclude, out_idx, out_r);
+  });
+}
+
+extern "C" int sisso_l0_sis_generated(sisso_l0_t h, const double *C, int64_t n_child,
+                                      int64_t n_total, const int32_t *ops, const int32_t *c1,
+                                      const int32_t *c2, int64_t n_cand, const double *y,
+                                      int32_t m, double l_bound, double u_bound,
+                                      int32_t *out_idx, double *out_r, uint8_t *out_valid) {
+  return guarded(h, [&]() -> int {
+    if (!C || !ops || !c1 || !c2 || !y || !out_idx || !out_r)
+      return fail(h, SISSO_L0_EINVAL, "null pointer argument");
+    if (n_total < 2 || n_child < 1 || n_cand < 1 || m < 1 || m > n_cand)
+      return fail(h, SISSO_L0_EINVAL, "need n_total >= 2, n_child >= 1, 1 <= m <= n_cand");
+    if (!(l_bound >= 0.0) || !(u_bound >= l_bound))
+      return fail(h, SISSO_L0_EINVAL, "need 0 <= l_bound <= u_bound");
+    if (m > 65536 || n_cand >= (1ll << 32))
+      return fail(h, SISSO_L0_EUNSUPPORTED, "m above 65536 or n_cand above 2^32");
+    cudaStream_t st = h->st;
+    const double *Cd = C, *yd = y;
+    if (!is_device_ptr(C)) {
+      const size_t cb = (size_t)n_child * (size_t)n_total * 8;
+      L0_CK(h->xin.ensure(cb), "alloc children");
+      L0_CK(cudaMemcpyAsync(h->xin.p, C, cb, cudaMemcpyHostToDevice, st), "copy children");
+      Cd = h->xin.as<double>();
+    }
+    if (!is_device_ptr(y)) {
+      L0_CK(h->sis_y.ensure((size_t)n_total * 8), "alloc y");
+      L0_CK(cudaMemcpyAsync(h->sis_y.p, y, (size_t)n_total * 8, cudaMemcpyHostToDevice, st),
+            "copy y");
+      yd = h->sis_y.as<double>();
+    }
+    auto dev_ints = [&](const int32_t *a, DevBuf &b) -> const int * {
+      if (is_device_ptr(a)) return (const int *)a;
+      if (b.ensure((size_t)n_cand * 4) != cudaSuccess) return nullptr;
+      if (cudaMemcpyAsync(b.p, a, (size_t)n_cand * 4, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return nullptr;
+      return b.as<int>();
+    };
+    l0::SisGen g;
+    g.n_child = n_child;
+    g.ops = dev_ints(ops, h->gen_ops);
+    g.c1 = dev_ints(c1, h->gen_c1);
+    g.c2 = dev_ints(c2, h->gen_c2);
+    if (!g.ops || !g.c1 || !g.c2) return fail(h, SISSO_L0_ENOMEM, "candidate lists");
+    g.lb = l_bound;
+    g.ub = u_bound;
+    g.valid = nullptr;
+    if (out_valid) {
+      if (is_device_ptr(out_valid)) {
+        g.valid = out_valid;
+      } else {
+        L0_CK(h->gen_valid.ensure((size_t)n_cand), "alloc");
+        g.valid = (unsigned char *)h->gen_valid.p;
+      }
+    }
+    L0_CK(h->scores.ensure(l0::sis_scratch_bytes(n_cand, m, n_total, 1)), "alloc screening scratch");
+    L0_CK(h->out_t.ensure((size_t)m * 4), "alloc");
+    L0_CK(h->out_r.ensure((size_t)m * 8), "alloc");
+    L0_CK(h->err.ensure(16), "alloc");
+    L0_CK(cudaMemsetAsync(h->err.p, 0, 16, st), "memset");
+    L0_CK(cudaEventRecord(h->ev[0], st), "event");
+    L0_CK(l0::launch_sis(Cd, yd, 1, n_total, n_cand, m, nullptr, 0, 0, h->scores.p,
+                         h->out_t.as<int>(), h->out_r.as<double>(), h->err.as<int>(), st,
+                         h->ev_k[0], h->ev_k[1], &g),
+          "generated screening kernels");
+    L0_CK(cudaEventRecord(h->ev[1], st), "event");
+    L0_CK(cudaMemcpyAsync(out_idx, h->out_t.p, (size_t)m * 4, cudaMemcpyDefault, st), "copy");
+    L0_CK(cudaMemcpyAsync(out_r, h->out_r.p, (size_t)m * 8, cudaMemcpyDefault, st), "copy");
+    if (out_valid && (void *)g.valid != (void *)out_valid)
+      L0_CK(cudaMemcpyAsync(out_valid, g.valid, (size_t)n_cand, cudaMemcpyDeviceToHost, st),
+            "copy validity");
+    int herr = 0;
+    L0_CK(cudaMemcpyAsync(&herr, h->err.p, 4, cudaMemcpyDeviceToHost, st), "copy");
+    int rc = wait_stream(h);
+    if (rc) return rc;
+    sisso_l0_stats &S = h->stats;
+    S = sisso_l0_stats{};
+    S.struct_size = (int32_t)sizeof(sisso_l0_stats);
+    S.certified = 1;
+    S.fp64_fallback_tuples = (uint64_t)n_cand;
+    S.kernel_launches = 13;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]) != cudaSuccess) {
+      cudaGetLastError();
+      ms = 0.f;
+    }
+    S.ms_total = ms;
+    if (cudaEventElapsedTime(&ms, h->ev_k[0], h->ev_k[1]) != cudaSuccess) {
+      cudaGetLastError();
+      ms = 0.f;
+    }
+    S.ms_tuple_kernel = ms;
+    if (herr == 14) return fail(h, SISSO_L0_EINVAL, "operator code or child index out of range");
+    if (herr == 5) return fail(h, SISSO_L0_ENONFINITE, "NaN or Inf in y");
+    if (herr == 12) return fail(h, SISSO_L0_EUNSUPPORTED, "more than 2^22 candidates tie at the cut");
+    if (herr) return fail(h, SISSO_L0_ECUDA, "device error flag " + std::to_string(herr));
+    return SISSO_L0_OK;
   });
 }
 

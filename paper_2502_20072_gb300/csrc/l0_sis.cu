@@ -748,6 +748,96 @@ sis_prescreen_multi_kernel(const double *__restrict__ X, long long n, long long 
   }
 }
 
+// --------------------------------------------------- generated features --
+// On-the-fly feature values (paper Sec. 2: operators applied to child
+// features; the last rung is evaluated inside SIS, Sec. 2.3 and Sec. 3).
+// Candidate t is ops[t](C[c1[t]], C[c2[t]]) (unary operators read c1 only),
+// evaluated in FP64 sample by sample and screened in the same pass: one warp
+// per candidate, shifted-data sums as in sis_r64_warp.  Value rules: every
+// value finite, the largest |value| in [lb, ub], not constant, not equal
+// sample by sample to a child.  An invalid candidate's r is NaN (its key
+// sorts after every score, so the selection never takes it).
+__device__ __forceinline__ double gen_apply(int op, double a, double b) {
+  switch (op) {
+    case 0: return a + b;
+    case 1: return a - b;
+    case 2: return a * b;
+    case 3: return a / b;
+    case 4: return fabs(a - b);
+    case 5: return log(a);
+    case 6: return exp(a);
+    case 7: return exp(-a);
+    case 8: return fabs(a);
+    case 9: return sqrt(a);
+    case 10: return cbrt(a);
+    case 11: return a * a;
+    case 12: return a * a * a;
+    default: return 1.0 / a;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+gen_score_kernel(const double *__restrict__ C, long long n, long long n_child,
+                 const int *__restrict__ ops, const int *__restrict__ c1,
+                 const int *__restrict__ c2, long long n_cand, const double *__restrict__ yd,
+                 const double *__restrict__ tgt, double lb, double ub,
+                 double *__restrict__ r_out, unsigned char *__restrict__ valid_out, int *err) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  const double syy = tgt[1], sy0 = tgt[2];
+  for (long long t = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < n_cand;
+       t += warps) {
+    const int op = ops[t];
+    const bool binary = op <= 4;
+    // a malformed candidate is reported and never read
+    if (op < 0 || op > 13 || c1[t] < 0 || c1[t] >= n_child ||
+        (binary && (c2[t] < 0 || c2[t] >= n_child))) {
+      if (lane == 0) {
+        set_err(err, 14);
+        r_out[t] = __longlong_as_double(0x7ff8000000000000ll);
+        if (valid_out) valid_out[t] = 0;
+      }
+      continue;
+    }
+    const double *xa = C + (long long)c1[t] * n;
+    const double *xb = C + (long long)(binary ? c2[t] : c1[t]) * n;
+    const double v0 = gen_apply(op, __ldg(xa), __ldg(xb));
+    double S1 = 0.0, S2 = 0.0, S3 = 0.0, mx = 0.0;
+    bool finite = true, same = true, eqa = true, eqb = binary;
+    for (long long i = lane; i < n; i += 32) {
+      const double a = __ldg(xa + i), b = __ldg(xb + i);
+      const double v = gen_apply(op, a, b);
+      finite &= ((unsigned)__double2hiint(v) & 0x7ff00000u) != 0x7ff00000u;
+      mx = fmax(mx, fabs(v));
+      same &= v == v0;
+      eqa &= v == a;
+      eqb &= v == b;
+      const double d = v - v0;
+      S1 += d;
+      S2 = fma(d, d, S2);
+      S3 = fma(d, __ldg(yd + i), S3);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      S1 += __shfl_xor_sync(0xffffffffu, S1, o);
+      S2 += __shfl_xor_sync(0xffffffffu, S2, o);
+      S3 += __shfl_xor_sync(0xffffffffu, S3, o);
+      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    const bool ok = __all_sync(0xffffffffu, finite) && !__all_sync(0xffffffffu, same) &&
+                    !__all_sync(0xffffffffu, eqa) && !(binary && __all_sync(0xffffffffu, eqb)) &&
+                    mx <= ub && mx >= lb;
+    if (lane == 0) {
+      const double sxx = S2 - S1 * S1 / (double)n;
+      const double sxy = S3 - S1 * sy0 / (double)n;
+      double r = (sxx > 0.0 && syy > 0.0) ? sxy / sqrt(sxx * syy) : 0.0;
+      if (!ok) r = __longlong_as_double(0x7ff8000000000000ll);
+      r_out[t] = r;
+      if (valid_out) valid_out[t] = ok ? 1 : 0;
+    }
+  }
+}
+
 // ordered image of -|r| (ascending = best first)
 __device__ __forceinline__ u64 sis_key(double r) { return r != r ? ~0ull : ord_of(-fabs(r)); }
 
@@ -882,7 +972,7 @@ sis_compact_kernel(const double *r, long long n_feat, const unsigned *cut1, cons
     if (f < n_feat) {
       k = sis_key(r[f]);
       const unsigned b1 = (unsigned)(k >> 48), b2 = (unsigned)(k >> 32) & 0xffffu;
-      take = b1 < c1 || (b1 == c1 && b2 <= c2);
+      take = (b1 < c1 || (b1 == c1 && b2 <= c2)) && k != ~0ull;   // never a NaN (excluded, invalid)
     }
     const unsigned ball = __ballot_sync(0xffffffffu, take);
     if (!ball) continue;
@@ -1156,11 +1246,13 @@ size_t sis_scratch_bytes(long long n_feat, int m, long long n, int R) {
 // scratch: sis_scratch_bytes, its first 64 bytes the counters (bytes
 // [40, 48): features re-scored in FP64 by the pre-screen path);
 // out_idx / out_r device [m]; err: device int; scan0 / scan1 (optional):
-// events recorded around the scan kernel (pre-screen or FP64 score)
+// events recorded around the scan kernel (pre-screen or FP64 score); gen
+// (optional): the candidates are generated features of the children X
+// (n_feat = candidates, R = 1)
 cudaError_t launch_sis(const double *X, const double *y, int R, long long n, long long n_feat,
                        int m, const int *ex, long long n_ex, int prescreen, void *scratch,
                        int *out_idx, double *out_r, int *err, cudaStream_t st, cudaEvent_t scan0,
-                       cudaEvent_t scan1) {
+                       cudaEvent_t scan1, const SisGen *gen) {
   const long long cap = std::min<long long>(n_feat, 1ll << 22);
   const long long rcap = std::min<long long>(cap, SIS_RANK_MAX);
   char *p = (char *)scratch;
@@ -1219,7 +1311,12 @@ cudaError_t launch_sis(const double *X, const double *y, int R, long long n, lon
   };
   const unsigned gx = (unsigned)std::min<long long>((n_ex + 255) / 256, 1024);
   sis_target_kernel<<<R, 1024, 0, st>>>(y, n, tgt, yd, err);
-  if (prescreen) {
+  if (gen) {                           // generated candidates, FP64 (R = 1)
+    if (scan0 && (e = cudaEventRecord(scan0, st)) != cudaSuccess) return e;
+    gen_score_kernel<<<gw, 256, 0, st>>>(X, n, gen->n_child, gen->ops, gen->c1, gen->c2, n_feat,
+                                         yd, tgt, gen->lb, gen->ub, r, gen->valid, err);
+    if (scan1 && (e = cudaEventRecord(scan1, st)) != cudaSuccess) return e;
+  } else if (prescreen) {
     sis_target32_kernel<<<R, 1024, 0, st>>>(y, n, tgt, yc);
     if (scan0 && (e = cudaEventRecord(scan0, st)) != cudaSuccess) return e;
     // one wave of resident blocks: every warp takes groups of 32 features
