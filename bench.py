@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -97,8 +98,9 @@ class Clocks:
 
     def __init__(self, gpu_index):
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv") \
-            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_bench.csv"
+        # raw samples (the JSON line carries their summary); CLOCKS_CSV moves them
+        self.path = os.environ.get("CLOCKS_CSV") or os.path.join(tempfile.gettempdir(),
+                                                                 "clocks_bench.csv")
         self.idx = gpu_index
 
     def start(self):
@@ -388,7 +390,7 @@ def run_ours(args):
 def run_learned(args):
     """The learned d = 3 search on the 20000-column workload: train the pair
     scorer on the exhaustive labels of 50 seeded 2000-column instances, run the
-    exhaustive search once as the judge, then time the learned search."""
+    exhaustive search once as the reference, then time the learned search."""
     import numpy as np
     import torch
     import paper_2502_20072_gb300 as l0
@@ -419,7 +421,7 @@ def run_learned(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     h = l0.Handle(precision=l0.MIXED_BF16X3, device=local, stream=stream.cuda_stream)
-    # the judge: exhaustive FP32 search with FP64 re-fit
+    # the reference: exhaustive FP32 search with FP64 re-fit
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)

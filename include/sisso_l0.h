@@ -222,7 +222,7 @@ int sisso_l0_gram_noalloc(const double *X, const double *y, int64_t n_samples,
  * learned form of the d = 3 search ranks the (d-1)-subsets -- pairs of
  * features -- with a small network trained on the exhaustive search's own
  * results, and fits exactly only the triples reachable from the best pairs;
- * the exhaustive search stays the reference and judges the network's
+ * the exhaustive search stays the reference and measures the network's
  * recall.  Pairs are ranked in colex order: rank(i, j) = j (j - 1) / 2 + i,
  * i < j.
  *

@@ -2,7 +2,7 @@
 
 The learned d = 3 search ranks feature pairs with a small network and fits
 only the triples reachable from the best pairs (the paper's search is
-exhaustive, Sec. 2.4; the exhaustive search stays the judge).  The network
+exhaustive, Sec. 2.4; the exhaustive search stays the reference).  The network
 learns from the exhaustive search's own results: for every pair of a
 training task, the log of its best completion min_k SSE(i, j, k) / S_yy,
 z-scored within the task (only a pair's rank inside its task matters).
