@@ -100,3 +100,22 @@ def test_fewer_valid_than_m():
     idx, r, ok = og.sis_generated(C, [og.SQ, og.SQ, og.LOG], [0, 1, 1], [0, 0, 0], y, 3)
     assert list(ok) == [True, False, False]
     assert list(idx) == [0, -1, -1]
+
+
+def test_bounds_are_inclusive():
+    """max |value| equal to either bound is valid; just beyond is not."""
+    a = np.array([1.0, 2.0, 4.0])
+    for lb, ub, ok in ((4.0, 8.0, True), (1.0, 4.0, True), (np.nextafter(4.0, 5.0), 8.0, False),
+                       (1.0, np.nextafter(4.0, 0.0), False)):
+        assert og.valid(a, a + 1.0, None, lb, ub) is ok
+
+
+def test_unary_operators_ignore_the_second_child():
+    rng = np.random.default_rng(3)
+    C = rng.uniform(0.5, 2.0, size=(4, 30))
+    y = rng.normal(size=30)
+    unary = [op for op in range(14) if op not in og.BINARY]
+    i1, r1, v1 = og.sis_generated(C, unary, [1] * len(unary), [0] * len(unary), y, 5)
+    i2, r2, v2 = og.sis_generated(C, unary, [1] * len(unary), [3] * len(unary), y, 5)
+    assert list(i1) == list(i2) and list(v1) == list(v2)
+    np.testing.assert_array_equal(r1, r2)

@@ -94,3 +94,17 @@ def test_residual_screening_finds_planted_second_term():
         if best is None or sse < best[0]:
             best = (sse, tuple(sorted((int(S[i]), int(S[j])))))
     assert best[1] == (a, b)
+
+
+def test_loop_never_reselects_and_takes_all_models_when_fewer_than_n_res():
+    X, y = _data(5, n=50, nf=30)
+    out = oloop.dimension_loop(X, y, m=4, D=3, k=2, n_res=10)
+    S = out[-1]["S"].tolist()
+    assert len(S) == 12 and len(set(S)) == 12
+    # each dimension's S extends the previous one
+    for a, b in zip(out, out[1:]):
+        assert b["S"][:len(a["S"])].tolist() == a["S"].tolist()
+    # dimension 2 screens against the residuals of both (k = 2 < n_res) 1-D models
+    res = oloop.residuals(X, y, out[0]["tuples"])
+    idx, _ = oloop.sis_multi(X, res, 4, exclude=out[0]["S"])
+    assert out[1]["S"][4:].tolist() == idx.tolist()
