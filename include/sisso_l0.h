@@ -201,13 +201,15 @@ int sisso_l0_debug_gram(sisso_l0_t h, const double *X, const double *y,
  *   out_gram  device FP64, row-major with leading dimension ld_out >= n_sis+1;
  *             entries (a, b), a <= b < n_sis+1, receive what
  *             sisso_l0_debug_gram returns for the same data (index 0 the
- *             target, j+1 feature j); other entries are left untouched
+ *             target, j+1 feature j); every other entry (a > b, and the
+ *             columns past n_sis) is left untouched
  *   stream    cudaStream_t (NULL = legacy stream); the call returns after
  *             the stream has finished its work
  * Scratch lives in a fixed 16 MiB array inside the library (held by every
  * GPU that loads the library until the process exits), so
  * (n_sis+1) * n_samples + 2 (n_sis+1) + 3 must not exceed 2^21 doubles;
- * larger inputs return SISSO_L0_EUNSUPPORTED.  The first call on a device
+ * larger inputs (including sizes whose product would overflow 64 bits)
+ * return SISSO_L0_EUNSUPPORTED before any work is queued.  The first call on a device
  * looks up the array's device address for that device (the current device).
  * All calls share the array: calls that overlap on the GPU race and must be
  * serialised by the caller.  Calls no cudaMalloc, cudaFree or other

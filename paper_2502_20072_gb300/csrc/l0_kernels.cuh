@@ -109,7 +109,8 @@ cudaError_t launch_centre(const double *X, const double *y, long long n_total,
 cudaError_t launch_gram64(const double *W64, long long n_total, int m,
                           const long long *offsets_host, int T, double *G,
                           long long ld, long long g_stride, cudaStream_t st,
-                          const u64 *gate = nullptr, int gate_d = 0);
+                          const u64 *gate = nullptr, int gate_d = 0,
+                          int upper_only = 0);
 
 template <typename R>
 cudaError_t launch_tile(const TileArgs<R> &a, int dp_lo, int dp_hi, int grid,

@@ -47,11 +47,14 @@ extern "C" int sisso_l0_gram_noalloc(const double *X, const double *y, int64_t n
                                      void *stream) {
   if (!X || !y || !out_gram || n_samples < 2 || n_sis < 1 || ld_out < n_sis + 1)
     return SISSO_L0_EINVAL;
-  const int64_t mp1 = n_sis + 1;
   // scratch layout (in doubles): W [(m+1) * n] | mu [m+1] | inv_s [m+1] |
-  // offsets (2 x int64) | error word
-  const uint64_t need = (uint64_t)mp1 * (uint64_t)n_samples + 2ull * (uint64_t)mp1 + 3ull;
-  if (need > L0_NOALLOC_SCRATCH_DOUBLES) return SISSO_L0_EUNSUPPORTED;
+  // offsets (2 x int64) | error word; it fits when (m+1)(n+2) + 3 <= the
+  // array's size.  Both factors are bounded before they are multiplied, so
+  // no size can wrap the product.
+  const uint64_t cap = L0_NOALLOC_SCRATCH_DOUBLES - 3ull;
+  if ((uint64_t)n_sis >= cap || (uint64_t)n_samples >= cap) return SISSO_L0_EUNSUPPORTED;
+  const int64_t mp1 = n_sis + 1;
+  if ((uint64_t)n_samples + 2ull > cap / (uint64_t)mp1) return SISSO_L0_EUNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= L0_NOALLOC_MAX_DEVICES)
     return SISSO_L0_ECUDA;
@@ -83,7 +86,7 @@ extern "C" int sisso_l0_gram_noalloc(const double *X, const double *y, int64_t n
     return SISSO_L0_ECUDA;
   const long long off_host[2] = {0, (long long)n_samples};
   if (l0::launch_gram64(W, (long long)n_samples, (int)n_sis, off_host, 1, out_gram,
-                        (long long)ld_out, 0, st) != cudaSuccess)
+                        (long long)ld_out, 0, st, nullptr, 0, /*upper_only=*/1) != cudaSuccess)
     return SISSO_L0_ECUDA;
   int herr = 0;
   if (cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||

@@ -134,10 +134,13 @@ cudaError_t launch_centre(const double *X, const double *y, long long n_total,
 
 // FP64 Gram of the scaled columns of one task: G = W_t^T W_t over the task's
 // rows, upper-triangular 64x64 tiles only (FFMA64, 4x4 outputs per thread).
+// A diagonal tile stores its full 64x64 block (the entries below the diagonal
+// are the mirrored values) unless upper_only is set, in which case only
+// entries (r, c) with r <= c are stored.
 __global__ void __launch_bounds__(256)
 gram64_kernel(const double *__restrict__ W, long long n_total, int mp1,
               long long lo, long long hi, double *__restrict__ G, long long ld,
-              int nb, const u64 *gate, int gate_d) {
+              int nb, const u64 *gate, int gate_d, int upper_only) {
   if (gate && !defer_wants_gram(gate[1], mp1 - 1, gate_d)) return;
   // decode the upper-triangular tile index (bi <= bj)
   int idx = blockIdx.x;
@@ -190,7 +193,7 @@ gram64_kernel(const double *__restrict__ W, long long n_total, int mp1,
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int c = bj * 64 + tx + 16 * j;
-      if (c < mp1) G[(long long)r * ld + c] = acc[i][j];
+      if (c < mp1 && (!upper_only || c >= r)) G[(long long)r * ld + c] = acc[i][j];
     }
   }
 }
@@ -198,14 +201,15 @@ gram64_kernel(const double *__restrict__ W, long long n_total, int mp1,
 cudaError_t launch_gram64(const double *W64, long long n_total, int m,
                           const long long *offsets_host, int T, double *G,
                           long long ld, long long g_stride, cudaStream_t st,
-                          const u64 *gate, int gate_d) {
+                          const u64 *gate, int gate_d, int upper_only) {
   const int mp1 = m + 1;
   const int nb = (mp1 + 63) / 64;
   const int ntiles = nb * (nb + 1) / 2;
   for (int t = 0; t < T; ++t) {
     gram64_kernel<<<ntiles, 256, 0, st>>>(W64, n_total, mp1, offsets_host[t],
                                           offsets_host[t + 1],
-                                          G + (long long)t * g_stride, ld, nb, gate, gate_d);
+                                          G + (long long)t * g_stride, ld, nb, gate, gate_d,
+                                          upper_only);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -46,9 +46,15 @@ def test_noalloc_gram_matches_allocating_entry_point_twice():
             out = torch.full((m + 1, ld), float("nan"), dtype=torch.float64, device="cuda")
             rc = _noalloc(Xd, yd, n, m, out, ld)
             assert rc == l0.OK
-            got = out[:, : m + 1].cpu().numpy()
+            full = out.cpu().numpy()
+            got = full[:, : m + 1]
             iu = np.triu_indices(m + 1)
             np.testing.assert_allclose(got[iu], ref[iu], rtol=0, atol=GRAM_ATOL)
+            # the entry point writes only the upper triangle: the strict lower
+            # triangle and the padding columns keep the caller's NaN fill
+            il = np.tril_indices(m + 1, -1)
+            assert np.isnan(got[il]).all()
+            assert np.isnan(full[:, m + 1:]).all()
 
 
 def test_noalloc_rejects_inputs_beyond_its_scratch():
@@ -59,3 +65,7 @@ def test_noalloc_rejects_inputs_beyond_its_scratch():
     out = torch.zeros((m + 1, m + 1), dtype=torch.float64, device="cuda")
     assert _noalloc(Xd, yd, n, m, out, m + 1) == l0.EUNSUPPORTED
     assert _noalloc(Xd, yd, n, m, out, m) == l0.EINVAL
+    # sizes whose (n_sis + 1) * n_samples product wraps 64 bits are refused
+    # on the host before anything is launched (no kernel sees these sizes)
+    assert _noalloc(Xd, yd, 2 ** 62, 3, out, 2 ** 40) == l0.EUNSUPPORTED
+    assert _noalloc(Xd, yd, 4, 2 ** 62, out, 2 ** 62 + 1) == l0.EUNSUPPORTED
