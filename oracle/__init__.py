@@ -157,10 +157,17 @@ def agreement(ref_tuples, ref_score, got_tuples, rel_gap=1e-9, score_fn=None):
     k = len(ref_t)
     if len(got_t) != k:
         return False, "length %d != %d" % (len(got_t), k)
+    def tied(a, b):
+        # padding positions carry +inf: two equal non-finite scores are one
+        # tie group; a finite score never ties a non-finite one
+        if not (np.isfinite(a) and np.isfinite(b)):
+            return bool(a == b)
+        return abs(a - b) <= rel_gap * max(abs(a), abs(b))
+
     groups = []
     start = 0
     for i in range(1, k + 1):
-        if i == k or not (abs(s[i] - s[i - 1]) <= rel_gap * max(abs(s[i]), abs(s[i - 1]))):
+        if i == k or not tied(s[i], s[i - 1]):
             groups.append((start, i))
             start = i
     for (a, b) in groups:

@@ -119,6 +119,84 @@ def test_rounded_forward_equals_exact_forward_on_bf16_values():
     np.testing.assert_array_equal(a, b)
 
 
+def _torch_net(torch, flat):
+    """A 6-256-256-1 ReLU network of torch.nn modules in FP64 holding the
+    same parameters as the flat vector (W1 [256,6] | b1 | W2 [256,256] with
+    rows = output units | b2 | w3 | b3)."""
+    p = ol.unpack(flat)
+    net = torch.nn.Sequential(torch.nn.Linear(6, 256), torch.nn.ReLU(),
+                              torch.nn.Linear(256, 256), torch.nn.ReLU(),
+                              torch.nn.Linear(256, 1)).double()
+    with torch.no_grad():
+        net[0].weight.copy_(torch.from_numpy(p["W1"]))
+        net[0].bias.copy_(torch.from_numpy(p["b1"]))
+        net[2].weight.copy_(torch.from_numpy(p["W2"]))
+        net[2].bias.copy_(torch.from_numpy(p["b2"]))
+        net[4].weight.copy_(torch.from_numpy(p["w3"][None, :]))
+        net[4].bias.copy_(torch.from_numpy(p["b3"]))
+    return net
+
+
+def _dense_params(rng):
+    # every tensor non-zero, biases of both signs so some units are off
+    p = dict(W1=rng.normal(size=(256, 6)) * 0.6, b1=rng.normal(size=256) * 0.3,
+             W2=rng.normal(size=(256, 256)) / 16.0, b2=rng.normal(size=256) * 0.2,
+             w3=rng.normal(size=256) / 16.0, b3=np.array([0.37]))
+    return ol.pack(p)
+
+
+def test_unrounded_forward_matches_torch_nn_fp64():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(21)
+    flat = _dense_params(rng)
+    feats = rng.normal(size=(300, 6))
+    out, c = ol.forward(flat, feats, round_bf16=False)
+    net = _torch_net(torch, flat)
+    with torch.no_grad():
+        ref = net(torch.from_numpy(feats))[:, 0].numpy()
+        h1 = net[1](net[0](torch.from_numpy(feats))).numpy()
+    np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(c["h1"], h1, rtol=1e-12, atol=1e-14)
+    # both ReLUs cut something on this input, so a dropped ReLU would show
+    assert 0.1 < np.mean(c["pre1"] > 0) < 0.9
+    assert 0.1 < np.mean(c["pre2"] > 0) < 0.9
+
+
+def test_unrounded_gradient_matches_torch_autograd_fp64():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(22)
+    flat = _dense_params(rng)
+    feats = rng.normal(size=(64, 6))
+    target = rng.normal(size=64)
+    loss, g = ol.loss_and_grad(flat, feats, target, round_bf16=False)
+    net = _torch_net(torch, flat)
+    out = net(torch.from_numpy(feats))[:, 0]
+    tl = torch.mean((out - torch.from_numpy(target)) ** 2)
+    tl.backward()
+    assert loss == pytest.approx(float(tl.detach()), rel=1e-12)
+    ref = ol.pack(dict(W1=net[0].weight.grad.numpy(), b1=net[0].bias.grad.numpy(),
+                       W2=net[2].weight.grad.numpy(), b2=net[2].bias.grad.numpy(),
+                       w3=net[4].weight.grad.numpy()[0], b3=net[4].bias.grad.numpy()))
+    np.testing.assert_allclose(g, ref, rtol=1e-10, atol=1e-14)
+
+
+def test_adam_matches_torch_optim_over_several_steps():
+    """Eight Adam steps with changing gradients against torch.optim.Adam in
+    FP64: the bias corrections 1 - beta^t past the first step are checked."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(23)
+    w0 = rng.normal(size=50)
+    grads = [rng.normal(size=50) * (1.0 + 3.0 * t) for t in range(8)]
+    w, m1, m2 = w0.copy(), np.zeros(50), np.zeros(50)
+    tw = torch.nn.Parameter(torch.from_numpy(w0.copy()))
+    opt = torch.optim.Adam([tw], lr=3e-2, betas=(0.8, 0.95), eps=1e-6)
+    for t, g in enumerate(grads, start=1):
+        w, m1, m2 = ol.adam_step(w, g, m1, m2, t, 3e-2, beta1=0.8, beta2=0.95, eps=1e-6)
+        tw.grad = torch.from_numpy(g.copy())
+        opt.step()
+        np.testing.assert_allclose(w, tw.detach().numpy(), rtol=1e-13, atol=1e-15)
+
+
 def test_first_adam_step_is_sign_step():
     rng = np.random.default_rng(5)
     w = rng.normal(size=100)

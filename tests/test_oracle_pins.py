@@ -262,6 +262,86 @@ def test_shared_mode_two_identical_tasks():
     np.testing.assert_allclose(shared["rmse"][0], single["rmse"][0], rtol=1e-15)
 
 
+def test_shared_mode_pools_sse_over_unequal_tasks():
+    """SHARED score = sum_t SSE_t / sum_t n_t, each task with its own
+    intercept and coefficients (Sec. 3.1), against LAPACK per task.  The
+    tasks differ in size and in data, so the pooled mean differs from the
+    mean of the per-task MSEs (a wrong weighting fails here)."""
+    rng = _rng(93)
+    sizes = [12, 31, 57]
+    m, d = 8, 2
+    X = rng.normal(1.0, 2.0, size=(m, sum(sizes)))
+    y = np.empty(sum(sizes))
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    for t in range(3):
+        lo, hi = off[t], off[t + 1]
+        # a different descriptor per task and a task-dependent noise level
+        y[lo:hi] = (t + 1.0) * X[t, lo:hi] - 0.5 * X[t + 3, lo:hi] \
+            + (0.3 + 0.7 * t) * rng.standard_normal(hi - lo)
+    k = math.comb(m, d)
+    res = oracle.fit(X, y, d, k, offsets=off, mode=oracle.SHARED)
+    assert res["tuples"].shape[0] == 1
+    expect = {}
+    mean_of_mse = {}
+    for tup in itertools.combinations(range(m), d):
+        sse = []
+        for t in range(3):
+            lo, hi = off[t], off[t + 1]
+            A = np.column_stack([np.ones(hi - lo)] + [X[j, lo:hi] for j in tup])
+            beta, *_ = np.linalg.lstsq(A, y[lo:hi], rcond=None)
+            r = y[lo:hi] - A @ beta
+            sse.append(float(r @ r))
+        expect[tup] = sum(sse) / float(sum(sizes))
+        mean_of_mse[tup] = sum(e / n for e, n in zip(sse, sizes)) / 3.0
+    got = {tuple(int(v) for v in t): sc for t, sc in zip(res["tuples"][0], res["score"][0])}
+    assert set(got) == set(expect)
+    for tup, v in expect.items():
+        assert abs(got[tup] - v) <= 1e-11 * v, (tup, got[tup], v)
+        # the two weightings really differ on this input
+        assert abs(mean_of_mse[tup] - v) > 1e-3 * v
+    order = sorted(expect, key=lambda t: (expect[t], t))
+    assert [tuple(int(v) for v in t) for t in res["tuples"][0]] == order
+    np.testing.assert_allclose(res["rmse"][0], np.sqrt([expect[t] for t in order]), rtol=1e-11)
+
+
+def test_shared_mode_ineligible_in_any_task():
+    """A tuple rank deficient in one task only is ineligible for the pooled
+    ranking (the shared descriptor must be fitted in every task)."""
+    rng = _rng(94)
+    sizes = [20, 25]
+    m = 6
+    X = rng.normal(size=(m, sum(sizes)))
+    X[4, :20] = 3.0 * X[1, :20] - 2.0          # columns 1 and 4 collinear in task 0 only
+    y = rng.normal(size=sum(sizes))
+    off = np.array([0, 20, 45], dtype=np.int64)
+    res = oracle.fit(X, y, 2, math.comb(m, 2), offsets=off, mode=oracle.SHARED)
+    got = [tuple(int(v) for v in t) for t in res["tuples"][0] if t[0] >= 0]
+    assert (1, 4) not in got
+    assert len(got) == math.comb(m, 2) - 1
+    per_task = oracle.fit(X, y, 2, math.comb(m, 2), offsets=off)
+    t1 = [tuple(int(v) for v in t) for t in per_task["tuples"][1] if t[0] >= 0]
+    assert (1, 4) in t1
+
+
+def test_agreement_handles_padding():
+    """Padded positions (+inf scores) form one tie group; a list that agrees
+    on its finite part and pads the rest agrees, and no NaN is formed."""
+    ref_t = np.array([[0, 1], [0, 2], [-1, -1], [-1, -1]])
+    ref_s = np.array([1.0, 2.0, np.inf, np.inf])
+    import warnings
+    with warnings.catch_warnings():
+        warnings.simplefilter("error")
+        ok, msg = oracle.agreement(ref_t, ref_s, ref_t.copy())
+        assert ok, msg
+        bad = ref_t.copy()
+        bad[2] = [1, 2]
+        ok, _ = oracle.agreement(ref_t, ref_s, bad)
+        assert not ok
+        # a finite score next to an infinite one is never a tie
+        ok, _ = oracle.agreement(ref_t[:3], ref_s[:3], np.array([[0, 1], [-1, -1], [0, 2]]))
+        assert not ok
+
+
 # ------------------------------------------------- rank deficiency, ties --
 def test_exact_duplicate_is_ineligible_near_duplicate_is_not():
     X, y = _random_problem(101, n=40, m=8)
