@@ -52,6 +52,9 @@ struct TileArgs {
   // tuple, (problem << 8) | run length (<= 128); dfr_n[0] runs, dfr_n[1] tuples
   u64 *dfr_key; unsigned *dfr_len; u64 *dfr_n; long long dfr_cap;
   int *err;
+  // FP32 band pass: every tuple scoring below the (fixed) cut is queued for
+  // the FP64 redo instead of entering the FP32 lists
+  int band;
   const int *cls;                  // [m] duplicate class of each column (smallest index
                                    // of the columns equal to it), or null
   // SHARED mode (shared_T > 0): Grams of tasks 0..T-1 at G + t * shared_gstride;
@@ -93,6 +96,18 @@ __host__ __device__ inline bool defer_wants_gram(u64 n_tuples, int m, int d) {
   return (double)n_tuples * (double)((d + 1) * (d + 2) / 2) * 8.0 >
          (double)(m + 1) * (double)(m + 1);
 }
+
+// The FP32 tuple kernel for d = 2 and 3 (l0_tile32.cu), PER_TASK exhaustive
+// searches on the same work items as tile_kernel.  Shapes: 1 = 256 threads,
+// one CTA per SM; 2 = 256 threads, two CTAs per SM; 3 = 512 threads (four
+// rows per warp).  The Gram's leading dimension and per-task stride must be
+// multiples of 4 floats (its rows are copied by the TMA unit).
+bool tile32_supports(int variant, int dp_lo, int dp_hi);
+size_t tile32_smem_bytes(int K, int S);
+int tile32_threads(int variant);
+cudaError_t tile32_occupancy(int variant, int dp_lo, int dp_hi, size_t smem, int *blocks_per_sm);
+cudaError_t launch_tile32(const TileArgs<float> &a, int variant, int dp_lo, int dp_hi, int grid,
+                          size_t smem, cudaStream_t st);
 
 // kernels (host launch wrappers)
 // duplicate classes of the columns: cls[j] = the smallest i with column i
@@ -161,7 +176,16 @@ struct RefitArgs {
   int dmax;                   // largest d over the problems
   int smem_rows;              // set by launch_refit: columns in shared memory
   double *refit;              // [n_probs][K] score (SSE or pooled mean SSE), +inf if ineligible
+  int refit_all;              // 0: only the first refit_count(k, K, cnt) pool entries
 };
+// Pool entries re-fitted in FP64: the pool is sorted by search score, and the
+// first max(2k, K'/2) of it are re-fitted (all of it when the caller needs
+// every entry's exact score); the rest are bounded by the certificate
+// through the first search score left out.
+__host__ __device__ inline int refit_count(int k, int K, int cnt, int all) {
+  const int r = all ? cnt : (2 * k > K / 2 ? 2 * k : K / 2);
+  return r < cnt ? r : cnt;
+}
 cudaError_t launch_refit(const RefitArgs &a, cudaStream_t st);
 
 struct CertOut {
@@ -185,7 +209,17 @@ struct SelectArgs {
   CertOut *cert;
   double cert_safety;
   const u64 *gthr;             // [n_probs] final search threshold (ordered bits of R)
+  int refit_all;               // as RefitArgs::refit_all
+  const double *delta_floor;   // [n_probs] band pass: the previous pass's search-score
+                               // error (null: not a band pass)
+  const u64 *band_thr;         // [n_probs] band pass: the fixed FP32 cut it started from
 };
+// Band pass set-up: from the previous pass's certificate of each problem, the
+// cut (k-th re-fitted score + margin * delta, as ordered bits of the FP32
+// relative score) into band_thr and delta into delta_floor.
+cudaError_t launch_band_cut(const CertOut *cert, const ProbDesc *probs, int n_probs,
+                            const double *inv_s, int mp1, int shared, double margin,
+                            u64 *band_thr, double *delta_floor, cudaStream_t st);
 template <typename R>
 cudaError_t launch_select(const SelectArgs<R> &a, cudaStream_t st);
 

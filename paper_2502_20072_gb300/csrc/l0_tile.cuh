@@ -324,6 +324,10 @@ __device__ __noinline__ int slow_tuple(const TileArgs<R> &A, const ItemCtx<R> &c
   const R p = pp + rb.kpt[kk];
   const R rel = rb.jpP[jl] - wn * wn / p;
   if (rel > cta_cut<R>(L)) return 1;
+  if (MIXED && A.band) {   // band pass: scored again in FP64
+    defer_run<R, DP>(A, c, rb.pidx, j, k, 1);
+    return 1;
+  }
   int t[L0_DMAX];
 #pragma unroll
   for (int q = 0; q < DP; ++q) t[q] = rb.pidx[q];

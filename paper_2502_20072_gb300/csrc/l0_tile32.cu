@@ -1,0 +1,624 @@
+// l0_tile32.cu -- the FP32 tuple kernel for d = 2 and d = 3.
+//
+// The same search as tile_kernel (l0_tuple.cu; paper Sec. 2.4: every tuple
+// fitted by least squares, the best kept), on the same work items, CTA lists,
+// global cut, FP64 redo queue and merge, written for the two tuple sizes the
+// FP32 form runs most: one prefix index i (d = 3) or none (d = 2).  A CTA owns
+// a 64 (j) x 128 (k) tile of the Gram in registers and walks prefixes i < j;
+// per prefix ("step") it needs only row i of the Gram:
+//
+//   row record j    g_j = C_ij / l_i, 1/l_j, z2_j, e_j = pP_j - cut
+//   column record k g_k = C_ik / l_i, pthr_k - p1_k, -w1_k
+//
+// (l_i = sqrt(C_ii), l_j the pivot of j after i, z2_j and pP_j the target
+// column of the Cholesky factor after (i, j)).  Each tuple then costs the
+// five packed operations of the fast test
+//
+//   h = C_jk - g_j g_k,  g2 = h / l_j,  -p = g2^2 + (pthr_k - p1_k),
+//   -w = g2 z2_j - w1_k,  t = w^2 - e_j p      (flagged when t >= 0),
+//
+// two tuples per fma.rn.f32x2.  What differs from tile_kernel:
+//  * the two row segments of G[i+1] a step needs (64 + 128 entries) are
+//    copied into shared memory by the TMA unit (cp.async.bulk) through a
+//    ring of four stages with mbarrier completion, three steps ahead;
+//  * records are stored duplicated ((x, x) pairs) so that every operand of
+//    the packed test comes from one 64- or 128-bit shared load, with no
+//    register moves; each lane holds adjacent column pairs (2 lane, 2 lane+1)
+//    so the column records load as pairs too;
+//  * the row state (skip, exact, redo in FP64) is folded into e: +inf never
+//    flags, a positive NaN always flags (and the exact path reads the
+//    state); no flag loads or masks in the test;
+//  * the diagonal tile masks k <= j with the sign of (2 lane - j), one
+//    integer add per row; every other tile runs the bare test;
+//  * <= 128 registers, so two 256-thread CTAs share an SM (or one 512-thread
+//    CTA with four rows per warp): barrier waits of one CTA hide behind the
+//    other's work.
+// Flagged tuples take the same exact path as tile_kernel (FP32 relative
+// score, composite admission with the lexicographic rank, FP64 redo of
+// near-singular tuples), so both kernels produce the same candidate lists.
+#include "l0_tile.cuh"
+#include "l0_tc.cuh"
+
+namespace l0 {
+
+namespace {
+
+using namespace tile;
+
+constexpr int T32_NS = 4;          // stages of the Gram-row ring
+constexpr int T32_JSEG = 68;       // floats of G[i+1][j0 .. j0 + 68)
+constexpr int T32_KSEG = 132;      // floats of G[i+1][k0 - 1 .. k0 + 131)
+constexpr int T32_SEG = T32_JSEG + T32_KSEG;
+constexpr int T32_MAXL = 256;      // prefix steps per item (plan_problems caps L)
+
+// Shared memory beyond the CTA list, at fixed offsets from one base pointer
+// (one register addresses all of it):
+//   two record buffers, each
+//     row   [TJ] x 32 B: {(-g, -g), (1/l, 1/l)}, {(z2, z2), (e, e)}
+//     jpP   [TJ] floats (pP_j, exact path), jflag [TJ] ints (0 skip, 1 fast,
+//           2 exact, 3 redo in FP64)
+//     kg, kp, kw, kpt [TK] floats
+//   the ring [NS][SEG] floats, the item's prefix scalars C_ii, r_i and class
+//   [MAXL] each, the ring's mbarriers [NS]
+constexpr int R_ROW = 0;
+constexpr int R_JPP = R_ROW + TJ * 32;
+constexpr int R_JFLAG = R_JPP + TJ * 4;
+constexpr int R_KG = R_JFLAG + TJ * 4;
+constexpr int R_KP = R_KG + TK * 4;
+constexpr int R_KW = R_KP + TK * 4;
+constexpr int R_KPT = R_KW + TK * 4;
+constexpr int T32_REC_BYTES = R_KPT + TK * 4;
+constexpr int O_STAGE = 2 * T32_REC_BYTES;
+constexpr int O_PDG = O_STAGE + T32_NS * T32_SEG * 4;
+constexpr int O_PRY = O_PDG + T32_MAXL * 4;
+constexpr int O_PCLS = O_PRY + T32_MAXL * 4;
+constexpr int O_BAR = O_PCLS + T32_MAXL * 4;
+constexpr int O_HC = O_BAR + 64;                      // histogram octave counts [256]
+constexpr int O_HF = O_HC + L0_HIST_COARSE * 4;       // one octave's fine counts [16]
+constexpr size_t T32_EXTRA_BYTES = (size_t)O_HF + 64;
+static_assert(O_HC % 16 == 0 && O_HF % 16 == 0, "cp.async destinations are 16-byte aligned");
+static_assert(O_STAGE % 16 == 0 && (T32_JSEG * 4) % 16 == 0 && (T32_SEG * 4) % 16 == 0,
+              "TMA destinations must be 16-byte aligned");
+static_assert(O_BAR % 8 == 0, "mbarriers are 8-byte aligned");
+
+// one record buffer
+struct Rec32 {
+  unsigned char *p;
+  __device__ __forceinline__ ulonglong2 *row() const { return (ulonglong2 *)(p + R_ROW); }
+  __device__ __forceinline__ float *jpP() const { return (float *)(p + R_JPP); }
+  __device__ __forceinline__ int *jflag() const { return (int *)(p + R_JFLAG); }
+  __device__ __forceinline__ float *kg() const { return (float *)(p + R_KG); }
+  __device__ __forceinline__ float *kp() const { return (float *)(p + R_KP); }
+  __device__ __forceinline__ float *kw() const { return (float *)(p + R_KW); }
+  __device__ __forceinline__ float *kpt() const { return (float *)(p + R_KPT); }
+};
+
+constexpr float T32_MARGIN = (float)(16.0 * 1.1920928955078125e-07);   // 16 ulp of 1
+
+// ------------------------------------------------- histogram bound, pipelined --
+// The global cut is tightened from the problem's score histogram (see
+// hist_bound in l0_common.cuh) whenever this CTA staged something.  Reading
+// the counts takes two dependent trips to L2; tile_kernel's warp 0 waits for
+// both inside the step and the next barrier waits for warp 0.  Here warp 0
+// copies the counts into shared memory with cp.async (L2 only, so the other
+// CTAs' atomics are seen) and uses them a step later, one phase per step:
+//   phase 0: if something was staged, start the copy of the octave counts;
+//   phase 1: find the octave where the running count reaches K', start the
+//            copy of its 16 fine counts;
+//   phase 2: the bin where it reaches K' -> its upper edge bounds the K'-th
+//            best score -> atomicMin on the global cut.
+// Any snapshot undercounts, so a bound from older counts is still valid.
+struct HistPipe {
+  int phase;
+  int oct;
+  unsigned before;
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// warp 0, after each step, no barrier; gprev = the global cut read a step ago
+__device__ __forceinline__ void step_sync32(CtaList<float> &L, u64 *gthr, u64 gprev,
+                                            HistPipe &hp, unsigned char *sb) {
+  if (threadIdx.x >= 32) return;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x;
+  unsigned *hc = (unsigned *)(sb + O_HC), *hf = (unsigned *)(sb + O_HF);
+  u64 g = gprev;
+  if (hp.phase == 2) {
+    cp_async_wait_all();
+    __syncwarp();
+    unsigned f = lane < 16 ? hf[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned t = __shfl_up_sync(FULL, f, o);
+      if (lane >= o) f += t;
+    }
+    const unsigned bl = __ballot_sync(FULL, lane < 16 && hp.before + f >= (unsigned)L.K);
+    // fine counts may lag the octave's: then the octave's top edge
+    const int b = bl ? hp.oct * 16 + __ffs(bl) - 1 : hp.oct * 16 + 15;
+    if (b + 1 < (int)(0x7f800000u >> 19)) {
+      const u64 bound = ord_of(__uint_as_float((unsigned)(b + 1) << 19));
+      if (bound < g) {
+        if (lane == 0) atomicMin(gthr, bound);
+        g = bound;
+      }
+    }
+    hp.phase = 0;
+  } else if (hp.phase == 1) {
+    cp_async_wait_all();
+    __syncwarp();
+    unsigned c[8], s = 0u;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      c[i] = hc[lane * 8 + i];
+      s += c[i];
+    }
+    unsigned inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned t = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc += t;
+    }
+    hp.phase = 0;
+    if (__shfl_sync(FULL, inc, 31) >= (unsigned)L.K) {
+      const int lk = __ffs(__ballot_sync(FULL, inc >= (unsigned)L.K)) - 1;
+      int oct = 0;
+      unsigned before = 0u;
+      if (lane == lk) {
+        unsigned acc = inc - s;
+        bool found = false;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          if (!found && acc + c[i] >= (unsigned)L.K) { oct = lane * 8 + i; before = acc; found = true; }
+          if (!found) acc += c[i];
+        }
+      }
+      hp.oct = __shfl_sync(FULL, oct, lk);
+      hp.before = __shfl_sync(FULL, before, lk);
+      if (lane < 4) cp_async16(tc::smem_u32(hf + 4 * lane), L.hist + hp.oct * 16 + 4 * lane);
+      cp_async_commit();
+      hp.phase = 2;
+    }
+  } else {
+    int dirty = 0;
+    if (lane == 0 && L.hist) dirty = atomicExch(L.dirty, 0);
+    if (__shfl_sync(FULL, dirty, 0)) {
+      const unsigned *src = L.hist + L0_HIST_FINE + lane * 8;
+      cp_async16(tc::smem_u32(hc + lane * 8), src);
+      cp_async16(tc::smem_u32(hc + lane * 8 + 4), src + 4);
+      cp_async_commit();
+      hp.phase = 1;
+    }
+  }
+  if (lane == 0 && g != ~0ull) {
+    const float gs = from_ord<float>(g);
+    if (gs < *(volatile float *)L.gcut) *(volatile float *)L.gcut = gs;
+  }
+}
+
+// per-thread state of one work item
+struct Item32 {
+  ItemCtx<float> c;   // tile position, problem, binomials (shared with tile_kernel's helpers)
+  float G00;          // 1 (the scaled target's own entry)
+  // this thread's record column (row record j0 + t or column record k0 + t - TJ)
+  int col;
+  bool isj, isk;
+  float cdiag, cy;
+  int ccls;
+};
+
+// Records of one step.  DP = 1: prefix i with C_ii = pdg, r_i = pry and
+// class pcls, raw entries C_ij / C_ik from the staged row segment; DP = 0:
+// no prefix.  The arithmetic is tile_kernel's rec_compute for these sizes.
+template <int DP>
+__device__ __forceinline__ void build32(const Item32 &it, int i, float pdg, float pry, int pcls,
+                                        const float *seg, const Rec32 &rb, float cut) {
+  const int t = threadIdx.x;
+  if (!it.isj && !it.isk) return;
+  const ItemCtx<float> &c = it.c;
+  const float ratio = c.ratio;
+  float invd = 1.f, zP = 0.f, pPb = it.G00, craw = 0.f;
+  bool pok = true;
+  if (DP == 1) {
+    pok = pdg > 0.f;
+    invd = rsqrtf(pok ? pdg : 1.f);
+    zP = pry * invd;
+    pPb = it.G00 - zP * zP;
+    // seg: [JSEG] = G[i+1][j0 ..), then [KSEG] = G[i+1][k0 - 1 ..)
+    craw = it.isj ? seg[t + 1] : seg[T32_JSEG + (t - TJ) + 2];
+  }
+  const bool inm = it.col < c.m;
+  const float g = craw * invd;
+  const float piv = it.cdiag - g * g;
+  const float w1 = it.cy - g * zP;
+  const bool elig = (it.cdiag > 0.f) && (piv >= ratio * it.cdiag);
+  const bool dup = DP == 1 && c.cls != nullptr && inm && pcls == it.ccls;
+  if (it.isj) {
+    const bool shape = inm && (DP == 0 || i < it.col);
+    const float invl = rsqrtf(piv > 0.f ? piv : 1.f);
+    const float z2 = w1 * invl;
+    const float pPj = pPb - z2 * z2;
+    const float e = pPj - (cut + T32_MARGIN);
+    const int flag = (!shape || dup) ? 0 : (!pok || !elig) ? 3 : (e > 0.f ? 1 : 2);
+    const bool fast = flag == 1 || flag == 2;
+    const float gn = fast ? -g : 0.f, il = fast ? invl : 0.f, zz = fast ? z2 : 0.f;
+    // +inf never flags a tuple (skipped row); a positive NaN always does (exact
+    // and redo rows: the exact path reads the state, whatever the column)
+    const float ee = flag == 1 ? e : (flag == 0 ? r_inf<float>() : __uint_as_float(0x7fc00000u));
+    ulonglong2 a, b;
+    a.x = f2_pack(gn, gn);
+    a.y = f2_pack(il, il);
+    b.x = f2_pack(zz, zz);
+    b.y = f2_pack(ee, ee);
+    rb.row()[2 * t] = a;
+    rb.row()[2 * t + 1] = b;
+    rb.jpP()[t] = fast ? pPj : 0.f;
+    rb.jflag()[t] = flag;
+  } else {
+    const int kk = t - TJ;
+    const float kpt = ratio * it.cdiag;
+    rb.kg()[kk] = inm ? g : 0.f;
+    rb.kp()[kk] = (!inm || dup) ? -r_inf<float>() : (elig ? kpt - piv : r_inf<float>());
+    rb.kw()[kk] = inm ? -w1 : 0.f;
+    rb.kpt()[kk] = inm ? kpt : 0.f;
+  }
+}
+
+// Fast test of this thread's UJ rows x 4 columns (columns 2 lane + b + 64 q of
+// the tile): the AND of the tuples' sign words (bit 31 clear <=> something
+// flagged).  In the diagonal tile (k0 = j0 + 1) column 2 lane + b of half q = 0
+// is k <= j exactly when 2 lane + b - jl < 0: that sign is OR-ed in.
+template <int UJ, bool DIAG>
+__device__ __forceinline__ unsigned fast32(const u64 (&creg)[UJ][2], const Rec32 &rb, int w,
+                                           int lane) {
+  u64 kg[2], kp[2], kw[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int kk = 2 * lane + 64 * q;
+    kg[q] = *(const u64 *)(rb.kg() + kk);
+    kp[q] = *(const u64 *)(rb.kp() + kk);
+    kw[q] = *(const u64 *)(rb.kw() + kk);
+  }
+  unsigned acc = 0xffffffffu;
+#pragma unroll
+  for (int u = 0; u < UJ; ++u) {
+    const int jl = w * UJ + u;
+    const ulonglong2 a = rb.row()[2 * jl], b = rb.row()[2 * jl + 1];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const u64 h = f2_fma(a.x, kg[q], creg[u][q]);
+      const u64 g2 = f2_mul(h, a.y);
+      const u64 ppn = f2_fma(g2, g2, kp[q]);
+      const u64 wn = f2_fma(g2, b.x, kw[q]);
+      const u64 t = f2_fma(b.y, ppn, f2_mul(wn, wn));
+      const unsigned lo = (unsigned)t, hi = (unsigned)(t >> 32);
+      if (DIAG && q == 0) {
+        const int d0 = 2 * lane - jl;
+        acc &= (lo | (unsigned)d0) & (hi | (unsigned)(d0 + 1));
+      } else {
+        acc &= lo & hi;
+      }
+    }
+  }
+  return acc;
+}
+
+// Exact path of one flagged tuple (tile_kernel's slow_tuple for these
+// layouts): 1 when handled, 0 when the staging area was full (look again
+// after the commit).
+template <int DP>
+__device__ __forceinline__ int slow32(const TileArgs<float> &A, const ItemCtx<float> &c,
+                                      const Rec32 rb, CtaList<float> &L, int i, int jl, int kk,
+                                      float cjk) {
+  const int j = c.j0 + jl, k = c.k0 + kk;
+  const float kpn = rb.kp()[kk];
+  if (kpn == -r_inf<float>()) return 1;   // column past m or a duplicate of the prefix
+  int pidx[1] = {i};
+  if (kpn == r_inf<float>()) {             // column near-singular after the prefix
+    defer_run<float, DP>(A, c, pidx, j, k, 1);
+    return 1;
+  }
+  const float *rf = (const float *)(rb.row() + 2 * jl);   // -g, -g, 1/l, 1/l, z2, z2, e, e
+  float h = cjk;
+  if (DP == 1) h = __fmaf_rn(rf[0], rb.kg()[kk], h);
+  const float g2 = __fmul_rn(h, rf[2]);
+  const float pp = -__fmaf_rn(g2, g2, kpn);
+  const float wn = __fmaf_rn(g2, rf[4], rb.kw()[kk]);
+  if (!(pp >= 0.f)) {                       // pivot of k after (i, j) below the cut
+    if (!same_class(c.cls, j, k)) defer_run<float, DP>(A, c, pidx, j, k, 1);
+    return 1;
+  }
+  const float p = pp + rb.kpt()[kk];
+  const float rel = rb.jpP()[jl] - wn * wn / p;
+  if (rel > cta_cut<float>(L)) return 1;
+  if (A.band) {   // band pass: scored again in FP64
+    defer_run<float, DP>(A, c, pidx, j, k, 1);
+    return 1;
+  }
+  int t[L0_DMAX];
+  if (DP == 1) {
+    t[0] = i;
+    t[1] = j;
+    t[2] = k;
+  } else {
+    t[0] = j;
+    t[1] = k;
+  }
+  const u64 key = lex_rank(c.B, c.m, c.d, t, c.total);
+  if (!cta_list_admits<float>(L, rel, key)) return 1;
+  return cta_list_push<float>(L, rel, key) ? 1 : 0;
+}
+
+// The rare part of a step: some tuple of this thread was flagged.  Every
+// tuple is tested again one by one (the same IEEE operations as the packed
+// test, so the same decisions), C_jk re-read from the Gram; flagged tuples
+// take the exact path, rows in the redo state queue their run once.  `done`
+// has a bit per (u, q, b) already handled in this step (staged, queued or
+// skipped); a pass after an overflow of the staging area skips them.
+template <int DP, int UJ>
+__device__ __noinline__ void recheck32(const TileArgs<float> &A, const ItemCtx<float> &c,
+                                       const Rec32 rb, CtaList<float> &L, int i,
+                                       unsigned *done_p) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned done = *done_p;
+#pragma unroll 1
+  for (int u = 0; u < UJ; ++u) {
+    const int jl = w * UJ + u;
+    const int j = c.j0 + jl;
+    const unsigned rowbits = 0xfu << (4 * u);
+    if ((done & rowbits) == rowbits) continue;
+    const int flag = rb.jflag()[jl];
+    if (flag == 0) {
+      done |= rowbits;
+      continue;
+    }
+    if (flag == 3) {   // prefix or row singular in FP32: the row's run goes to the FP64 redo
+      if (lane == 0) {
+        const int kf = c.k0 > j + 1 ? c.k0 : j + 1;
+        const int kl = c.k0 + TK < c.m ? c.k0 + TK : c.m;
+        int pidx[1] = {i};
+        defer_run<float, DP>(A, c, pidx, j, kf, kl - kf);
+      }
+      done |= rowbits;
+      continue;
+    }
+    const float *rf = (const float *)(rb.row() + 2 * jl);
+    const float jg = rf[0], invl = rf[2], z2 = rf[4], e = rf[6];
+#pragma unroll 1
+    for (int v = 0; v < 4; ++v) {
+      const int q = v >> 1, b = v & 1;
+      const unsigned bit = 1u << (4 * u + v);
+      if (done & bit) continue;
+      const int kk = 2 * lane + b + 64 * q;
+      const int k = c.k0 + kk;
+      if (k >= c.m || k <= j) {   // past m, or below the diagonal of the first k tile
+        done |= bit;
+        continue;
+      }
+      const float cjk = c.G[(long long)(j + 1) * c.ld + k + 1];
+      const float h = __fmaf_rn(jg, rb.kg()[kk], cjk);
+      const float g2 = __fmul_rn(h, invl);
+      const float ppn = __fmaf_rn(g2, g2, rb.kp()[kk]);
+      const float wn = __fmaf_rn(g2, z2, rb.kw()[kk]);
+      const float t = __fmaf_rn(e, ppn, __fmul_rn(wn, wn));
+      if (__float_as_uint(t) >> 31) {   // not flagged
+        done |= bit;
+        continue;
+      }
+      if (slow32<DP>(A, c, rb, L, i, jl, kk, cjk)) done |= bit;
+    }
+  }
+  *done_p = done;
+}
+
+// TMA copy of the two row segments step s of the item needs (thread 0).
+// Copy lengths are clamped to the problem's Gram so no read leaves it; the
+// entries a record reads (columns <= m of row i + 1) always lie inside.
+__device__ __forceinline__ void issue32(const ItemCtx<float> &c, unsigned char *sb, int i,
+                                        unsigned copy_idx) {
+  const int slot = (int)(copy_idx % T32_NS);
+  const long long end = (long long)(c.m + 1) * c.ld;   // floats of this problem's Gram
+  const long long js = (long long)(i + 1) * c.ld + c.j0;
+  const long long ks = (long long)(i + 1) * c.ld + (c.k0 - 1);
+  const long long jn = min((long long)T32_JSEG, end - js);
+  const long long kn = min((long long)T32_KSEG, end - ks);
+  const uint32_t bar = tc::smem_u32(sb + O_BAR + 8 * slot);
+  const uint32_t dst = tc::smem_u32(sb + O_STAGE + slot * T32_SEG * 4);
+  tc::fence_proxy_async_smem();
+  tc::mbar_expect_tx(bar, (uint32_t)((jn + kn) * 4));
+  tc::bulk_load(dst, c.G + js, (uint32_t)(jn * 4), bar);
+  tc::bulk_load(dst + T32_JSEG * 4, c.G + ks, (uint32_t)(kn * 4), bar);
+}
+
+// One work item: the (j, k) tile against prefixes [r0, r1) (DP = 1) or the
+// single prefix-free step (DP = 0).  `cons` counts the ring copies this CTA
+// has consumed (the ring slot and mbarrier parity of every copy follow).
+template <int DP, int UJ>
+__device__ void run32(const TileArgs<float> &A, const ProbDesc &pd, int prob, int bj, int bk,
+                      u64 r0, u64 r1, CtaList<float> &L, unsigned char *sb, u64 *gthr,
+                      unsigned &cons) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  Item32 it;
+  ItemCtx<float> &c = it.c;
+  c.G = A.G + pd.g_off;
+  c.ld = pd.ld;
+  c.prob = prob;
+  c.m = pd.m;
+  c.d = pd.d;
+  c.j0 = bj * TJ;
+  c.k0 = tile_k0(bj, bk);
+  c.diag = bk == 0;   // only the first k tile of a row block reaches k <= j
+  c.total = pd.total;
+  c.B = A.B;
+  c.ratio = (float)A.ratio;
+  c.cls = A.cls;
+  const float *G = c.G;
+  const long long ld = c.ld;
+  it.G00 = G[0];
+  const int nsteps = DP == 1 ? (int)(r1 - r0) : 1;
+  const int i0 = DP == 1 ? (int)r0 : 0;   // colex rank of a one-index prefix is the index
+  if (nsteps > T32_MAXL) {   // the plan never makes such items (uniform exit)
+    set_err(A.err, 9);
+    return;
+  }
+  float *pdg = (float *)(sb + O_PDG), *pry = (float *)(sb + O_PRY);
+  int *pcls = (int *)(sb + O_PCLS);
+  if (DP == 1) {
+    if (tid == 0)
+      for (int s = 0; s < nsteps && s < T32_NS; ++s) issue32(c, sb, i0 + s, cons + s);
+    for (int s = tid; s < nsteps; s += blockDim.x) {
+      const int i = i0 + s;
+      pdg[s] = G[(long long)(i + 1) * (ld + 1)];
+      pry[s] = G[i + 1];
+      pcls[s] = c.cls ? __ldg(c.cls + i) : -1;
+    }
+  }
+  it.isj = tid < TJ;
+  it.isk = !it.isj && tid < TJ + TK;
+  it.col = it.isj ? c.j0 + tid : (it.isk ? c.k0 + tid - TJ : -1);
+  it.cdiag = 0.f;
+  it.cy = 0.f;
+  it.ccls = -2;
+  if (it.col >= 0 && it.col < c.m) {
+    it.cdiag = G[(long long)(it.col + 1) * (ld + 1)];
+    it.cy = G[it.col + 1];
+    if (c.cls) it.ccls = __ldg(c.cls + it.col);
+  }
+  // the tile's Gram entries: rows j0 + w UJ + u, columns k0 + 2 lane + {0, 1} + 64 q
+  u64 creg[UJ][2];
+#pragma unroll
+  for (int u = 0; u < UJ; ++u) {
+    const int j = c.j0 + w * UJ + u;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int k = c.k0 + 2 * lane + 64 * q;
+      u64 v = 0ull;
+      if (j < c.m && k < c.m) {
+        v = *(const u64 *)(G + (long long)(j + 1) * ld + k + 1);
+        if (k + 1 >= c.m) v &= 0xffffffffull;   // the pair's second column is past m
+      }
+      creg[u][q] = v;
+    }
+  }
+  __syncthreads();   // prefix scalars visible
+  const bool rec = it.isj || it.isk;
+  if (DP == 1 && rec)
+    tc::mbar_wait(tc::smem_u32(sb + O_BAR + 8 * (cons % T32_NS)), (cons / T32_NS) & 1u, A.err);
+  build32<DP>(it, i0, DP == 1 ? pdg[0] : 0.f, DP == 1 ? pry[0] : 0.f, DP == 1 ? pcls[0] : -1,
+              (const float *)(sb + O_STAGE) + (cons % T32_NS) * T32_SEG, Rec32{sb},
+              cta_cut<float>(L));
+  __syncthreads();
+  if (DP == 1 && tid == 0 && T32_NS < nsteps) issue32(c, sb, i0 + T32_NS, cons + T32_NS);
+  u64 gnext = ~0ull;   // warp 0: the global bound, read a step before it is used
+  HistPipe hp{0, 0, 0u};
+  for (int s = 0; s < nsteps; ++s) {
+    const Rec32 rb{sb + (s & 1) * T32_REC_BYTES};
+    const u64 gprev = gnext;
+    if (tid < 32) gnext = ld_relaxed(gthr);
+    if (DP == 1 && s + 1 < nsteps) {
+      const unsigned q = cons + (unsigned)s + 1u;
+      if (rec) tc::mbar_wait(tc::smem_u32(sb + O_BAR + 8 * (q % T32_NS)), (q / T32_NS) & 1u, A.err);
+      build32<DP>(it, i0 + s + 1, pdg[s + 1], pry[s + 1], pcls[s + 1],
+                  (const float *)(sb + O_STAGE) + (q % T32_NS) * T32_SEG,
+                  Rec32{sb + ((s + 1) & 1) * T32_REC_BYTES}, cta_cut<float>(L));
+    }
+    unsigned done = 0u;
+    for (int pass = 0;; ++pass) {
+      const unsigned acc = c.diag ? fast32<UJ, true>(creg, rb, w, lane)
+                                  : fast32<UJ, false>(creg, rb, w, lane);
+      if (!(acc >> 31)) recheck32<DP, UJ>(A, c, rb, L, i0 + s, &done);
+      __syncthreads();
+      const bool ovf = *(volatile int *)L.ovf != 0;
+      if (ovf || *(volatile int *)L.n_stage > L.S / 2) cta_list_commit<float>(L, gthr);
+      if (!ovf) break;
+      if (pass > L0_MAX_REDO) {
+        set_err(A.err, 8);
+        break;
+      }
+    }
+    // the stage that held step s + 1's row is free after the barrier above
+    if (DP == 1 && tid == 0 && s + 1 + T32_NS < nsteps)
+      issue32(c, sb, i0 + s + 1 + T32_NS, cons + (unsigned)(s + 1 + T32_NS));
+    step_sync32(L, gthr, gprev, hp, sb);
+  }
+  if (tid < 32) cp_async_wait_all();   // no copy into the histogram buffers outlives the item
+  if (DP == 1) cons += (unsigned)nsteps;
+  cta_list_commit<float>(L, gthr);
+}
+
+template <int DPLO, int DPHI, int UJ, int MINB>
+__global__ void __launch_bounds__(TJ / UJ * 32, MINB)
+tile32_kernel(TileArgs<float> A) {
+  bool ready = false;   // ring mbarriers initialised (first item)
+  unsigned cons = 0u;
+  persistent_items<float>(A, [&](const ProbDesc &pd, int prob, int bj, int bk, u64 r0, u64 r1,
+                                 CtaList<float> &L, unsigned char *recbase, u64 *gthr) {
+    if (!ready) {
+      if (threadIdx.x == 0) {
+        for (int s = 0; s < T32_NS; ++s) tc::mbar_init(tc::smem_u32(recbase + O_BAR + 8 * s), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      }
+      __syncthreads();
+      ready = true;
+    }
+    if (pd.dp == 0) {
+      if (DPLO == 0) run32<0, UJ>(A, pd, prob, bj, bk, r0, r1, L, recbase, gthr, cons);
+    } else if (pd.dp == 1) {
+      if (DPHI >= 1) run32<1, UJ>(A, pd, prob, bj, bk, r0, r1, L, recbase, gthr, cons);
+    }
+  });
+}
+
+}  // namespace
+
+// shape 1: 8 rows per warp, 256 threads, one CTA per SM; shape 2: the same
+// with two CTAs per SM (at most 128 registers); shape 3: 4 rows per warp,
+// 512 threads, one CTA per SM
+static const void *tile32_fn(int variant, int dp_lo, int dp_hi) {
+#define L0_T32(V, UJ, MB)                                                            \
+  if (variant == V) {                                                               \
+    if (dp_lo == 0 && dp_hi == 0) return (const void *)tile32_kernel<0, 0, UJ, MB>; \
+    if (dp_lo == 1 && dp_hi == 1) return (const void *)tile32_kernel<1, 1, UJ, MB>; \
+    if (dp_lo == 0 && dp_hi == 1) return (const void *)tile32_kernel<0, 1, UJ, MB>; \
+  }
+  L0_T32(1, 8, 1)
+  L0_T32(2, 8, 2)
+  L0_T32(3, 4, 1)
+#undef L0_T32
+  return nullptr;
+}
+
+int tile32_threads(int variant) { return variant == 3 ? 512 : 256; }
+
+size_t tile32_smem_bytes(int K, int S) {
+  return align16(cta_list_bytes<float>(K, S)) + 16 + T32_EXTRA_BYTES;
+}
+
+bool tile32_supports(int variant, int dp_lo, int dp_hi) {
+  return tile32_fn(variant, dp_lo, dp_hi) != nullptr;
+}
+
+cudaError_t tile32_occupancy(int variant, int dp_lo, int dp_hi, size_t smem, int *blocks_per_sm) {
+  const void *fn = tile32_fn(variant, dp_lo, dp_hi);
+  if (!fn) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, tile32_threads(variant),
+                                                       smem);
+}
+
+cudaError_t launch_tile32(const TileArgs<float> &a, int variant, int dp_lo, int dp_hi, int grid,
+                          size_t smem, cudaStream_t st) {
+  const void *fn = tile32_fn(variant, dp_lo, dp_hi);
+  if (!fn) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void *args[] = {(void *)&a};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(tile32_threads(variant)), args, smem, st);
+}
+
+}  // namespace l0
