@@ -74,15 +74,30 @@ typedef struct {
   double timeout_seconds;            /* host-side deadline for stream completion (<= 0: none) */
   int32_t fp64_rerun_uncertified;    /* MIXED: when the candidate pool cannot be certified at
                                         max_candidate_pool (FP32 score errors as large as the
-                                        gaps between the best scores), redo the fit in FP64
-                                        (1, default) or return the uncertified result (0) */
+                                        gaps between the best scores), first rerun the FP32
+                                        search as a band pass (every tuple below the k-th
+                                        re-fitted score + 8 delta scored in FP64), then, if
+                                        that is still uncertified, redo the fit in FP64 (1,
+                                        default); or return the uncertified result (0) */
+  int32_t tuple_kernel;              /* shape of the tuple search kernel: -1 (default) picks
+                                        one (the autotuner times them when autotune is on);
+                                        0 the general kernel (any d, FP32 or FP64); 1, 2, 3
+                                        the FP32 kernel for d = 2 and 3 (PER_TASK, exhaustive)
+                                        with 256 threads and one CTA per SM, 256 threads and
+                                        two CTAs per SM, 512 threads and one CTA per SM.  A
+                                        shape that cannot run a fit falls back to 0 */
 } sisso_l0_options;
 
 typedef struct {
   int32_t struct_size;               /* sizeof(sisso_l0_stats) */
   int32_t candidate_pool;            /* K' used by the last fit */
   int32_t pool_enlargements;         /* times K' was doubled by the certificate */
-  int32_t certified;                 /* 1 when every output list passed the certificate */
+  int32_t certified;                 /* 1 when every output list passed the certificate: the
+                                        smallest search score left outside the candidate
+                                        pool exceeds the k-th FP64 re-fitted score by at
+                                        least 4x the largest search-score error measured on
+                                        the pool (an empirical check: the outside tuples
+                                        are not re-fitted) */
   uint64_t tuple_fits;               /* (task, tuple) fits evaluated */
   uint64_t fp64_fallback_tuples;     /* tuples recomputed in FP64 (mixed precision) */
   int64_t n_eligible_min;            /* smallest count of filled output slots over lists */
@@ -99,6 +114,11 @@ typedef struct {
   double ms_prep, ms_gram, ms_tuple, ms_merge, ms_refit, ms_total;
   double ms_tuple_kernel;            /* the tuple kernel alone (last search pass) */
   int64_t proposal_pairs;            /* pairs the pair-restricted search started from */
+  int32_t tuple_kernel;              /* tuple kernel shape the last fit ran (tuple_kernel
+                                        option values 0..3) */
+  int32_t band_pass;                 /* MIXED: 1 when the first FP32 pass could not rank the
+                                        best tuples and a band pass scored every tuple
+                                        below its k-th re-fitted score + 8 delta in FP64 */
 } sisso_l0_stats;
 
 /* Fill *opt with defaults (FP64, PER_TASK, device 0, legacy stream). */
@@ -156,6 +176,22 @@ int sisso_l0_fit_multi(sisso_l0_t h, const double *X, const double *y,
 
 /* Statistics of the last fit on this handle. */
 int sisso_l0_get_stats(sisso_l0_t h, sisso_l0_stats *out);
+
+/* Replace the handle's host-side deadline (options.timeout_seconds; <= 0:
+ * none) for later calls.  A call that hits the deadline returns
+ * SISSO_L0_ETIMEOUT with its device work still queued on the stream; the
+ * handle stays usable (the next call is ordered after that work).  (No
+ * counterpart in the paper: a service-side guard.)  Errors: EINVAL (null
+ * handle or NaN). */
+int sisso_l0_set_timeout(sisso_l0_t h, double timeout_seconds);
+
+/* Test hook: after `after` more device allocations made by the calling
+ * thread inside the library, the next one reports out-of-memory (the call
+ * returns SISSO_L0_ENOMEM) without calling cudaMalloc; after < 0 turns the
+ * hook off.  The failing buffer is left empty, so a later call allocates it
+ * again.  (No counterpart in the paper: it exercises the ENOMEM path without
+ * exhausting a shared GPU.)  Always returns SISSO_L0_OK. */
+int sisso_l0_debug_fail_allocation(int64_t after);
 
 /* Description of the last error on this handle (valid until the next call
  * on the handle); a static string when h is NULL. */

@@ -51,7 +51,7 @@ class Options(ctypes.Structure):
                 ("autotune", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("autotune_cache_path", ctypes.c_char_p),
                 ("timeout_seconds", ctypes.c_double),
-                ("fp64_rerun_uncertified", ctypes.c_int32)]
+                ("fp64_rerun_uncertified", ctypes.c_int32), ("tuple_kernel", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -70,7 +70,8 @@ class Stats(ctypes.Structure):
                 ("ms_prep", ctypes.c_double), ("ms_gram", ctypes.c_double),
                 ("ms_tuple", ctypes.c_double), ("ms_merge", ctypes.c_double),
                 ("ms_refit", ctypes.c_double), ("ms_total", ctypes.c_double),
-                ("ms_tuple_kernel", ctypes.c_double), ("proposal_pairs", ctypes.c_int64)]
+                ("ms_tuple_kernel", ctypes.c_double), ("proposal_pairs", ctypes.c_int64),
+                ("tuple_kernel", ctypes.c_int32), ("band_pass", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "struct_size"}
@@ -97,6 +98,13 @@ SCORER_PARAMS = 67841
 PAIR_FEATURES_LD = 8
 
 
+def debug_fail_allocation(after):
+    """Test hook: the calling thread's device allocation number `after`
+    (counting from 0) inside the library reports out-of-memory; after < 0
+    turns it off."""
+    lib().sisso_l0_debug_fail_allocation(int(after))
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -119,6 +127,8 @@ def lib():
         L.sisso_l0_fit_multi.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_int64), i32, i64,
                                          ctypes.POINTER(Request), i32]
         L.sisso_l0_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+        L.sisso_l0_set_timeout.argtypes = [vp, ctypes.c_double]
+        L.sisso_l0_debug_fail_allocation.argtypes = [i64]
         L.sisso_l0_last_error.argtypes = [vp]
         L.sisso_l0_last_error.restype = ctypes.c_char_p
         L.sisso_l0_destroy.argtypes = [vp]
@@ -197,7 +207,8 @@ class Handle:
     def __init__(self, precision=FP64, task_mode=PER_TASK, device=0, stream=None,
                  candidate_pool=0, max_candidate_pool=2048, timeout_seconds=300.0,
                  fp32_fallback_pivot_ratio=1e-6, rank_deficient_pivot_ratio=1e-12,
-                 autotune=0, use_graph=0, autotune_cache_path=None, fp64_rerun_uncertified=1):
+                 autotune=0, use_graph=0, autotune_cache_path=None, fp64_rerun_uncertified=1,
+                 tuple_kernel=-1):
         L = lib()
         o = Options()
         L.sisso_l0_default_options(ctypes.byref(o))
@@ -213,6 +224,7 @@ class Handle:
         o.autotune = int(autotune)
         o.use_graph = int(use_graph)
         o.fp64_rerun_uncertified = int(fp64_rerun_uncertified)
+        o.tuple_kernel = int(tuple_kernel)
         self._cache_path = (autotune_cache_path.encode() if isinstance(autotune_cache_path, str)
                             else autotune_cache_path)
         o.autotune_cache_path = self._cache_path
@@ -295,6 +307,10 @@ class Handle:
                                       n_sis, reqs, len(requests))
         self._check(rc)
         return outs
+
+    def set_timeout(self, seconds):
+        """Host-side deadline of later calls (<= 0: none)."""
+        self._check(lib().sisso_l0_set_timeout(self._h, float(seconds)))
 
     def stats(self) -> dict:
         s = Stats()

@@ -6,8 +6,10 @@
 //   3. persistent tuple kernel -> per-CTA top-K' lists
 //   4. grid merge -> one top-K' pool per output list
 //   5. FP64 Householder re-fit of the pool from the raw centred columns
-//   6. final ranking; certificate: the pool must provably contain the exact
-//      top k, otherwise K' is doubled and steps 3-6 rerun.
+//   6. final ranking; certificate (an empirical check, see select_kernel):
+//      the outside tuples' search scores must clear the k-th re-fitted score
+//      by four times the largest search-score error measured on the pool,
+//      otherwise K' is doubled and steps 3-6 rerun.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -18,6 +20,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/sisso_l0.h"
@@ -28,6 +31,11 @@ using l0::u64;
 
 namespace {
 
+// Test hook (sisso_l0_debug_fail_allocation): when >= 0, the number of
+// device allocations this thread still makes before one reports
+// cudaErrorMemoryAllocation without calling cudaMalloc.
+thread_local long long g_alloc_fail_countdown = -1;
+
 struct DevBuf {
   void *p = nullptr;
   size_t n = 0;
@@ -36,6 +44,8 @@ struct DevBuf {
     if (p) cudaFree(p);
     p = nullptr;
     n = 0;
+    if (g_alloc_fail_countdown >= 0 && g_alloc_fail_countdown-- == 0)
+      return cudaErrorMemoryAllocation;
     size_t want = std::max<size_t>(bytes, 256);
     cudaError_t e = cudaMalloc(&p, want);
     if (e != cudaSuccess) {
@@ -78,6 +88,7 @@ struct sisso_l0_handle {
   DevBuf abf, bbf, kmeta, gram32;
   DevBuf prop_in, prop_pairs, prop_bits, prop_ctr, sel_hist, sel_bin, scores, diag;
   DevBuf col_hash, col_cls;
+  DevBuf band_thr, band_floor;                        // band pass: cut, previous delta
   DevBuf sis_ex, sis_y;                               // screening: exclusions, targets
   DevBuf gen_ops, gen_c1, gen_c2, gen_valid;          // generated candidates
   DevBuf loop_x, loop_y, loop_xs, loop_res, loop_q, loop_tup, loop_rows;   // dimension loop
@@ -89,8 +100,22 @@ struct sisso_l0_handle {
   float ms_tuple_kernel = 0.f;
   cudaGraphExec_t graph_exec = nullptr;
   std::string graph_key;
-  std::map<std::string, std::pair<int, int>> tune;   // autotuner choices
+  struct Tune { int f, b, v; };                      // items factor, CTAs per SM, kernel shape
+  std::map<std::string, Tune> tune;                   // autotuner choices
   std::string fp64_key;   // inputs whose last mixed-precision fit needed FP64
+  // pinned host staging for the small per-call uploads and status reads (so
+  // they are asynchronous), handed out from the start at every call; ev_pin
+  // follows the last copy that read it
+  unsigned char *pin = nullptr;
+  size_t pin_n = 0, pin_used = 0;
+  cudaEvent_t ev_pin = nullptr;
+  bool pin_pending = false;
+  // last bytes uploaded to a small device table; an identical upload is skipped
+  struct UpCache {
+    const void *dev = nullptr;
+    std::vector<unsigned char> bytes;
+  };
+  UpCache up_probs, up_rowpre, up_rdiv, up_offs, up_kmeta;
 };
 
 namespace {
@@ -136,6 +161,10 @@ bool is_device_ptr(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Wait for the handle's stream with the host-side deadline.  The first 2 ms
+// are polled without sleeping (a fit's tail is a few short kernels, and a
+// sleep would add its whole granularity to every call); after that the
+// host sleeps 20 us between polls.
 int wait_stream(sisso_l0_t h) {
   cudaEvent_t e = h->ev[7];
   L0_CK(cudaEventRecord(e, h->st), "event record");
@@ -145,11 +174,59 @@ int wait_stream(sisso_l0_t h) {
     cudaError_t q = cudaEventQuery(e);
     if (q == cudaSuccess) break;
     if (q != cudaErrorNotReady) return cuda_fail(h, q, "stream");
-    if (tmo > 0) {
-      double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-      if (el > tmo) return fail(h, SISSO_L0_ETIMEOUT, "stream did not finish within timeout_seconds");
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (tmo > 0 && el > tmo)
+      return fail(h, SISSO_L0_ETIMEOUT, "stream did not finish within timeout_seconds");
+    if (el > 2e-3) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    else std::this_thread::yield();
+  }
+  h->pin_pending = false;   // every copy from the staging buffer has completed
+  return SISSO_L0_OK;
+}
+
+// Pinned staging: start handing out the buffer from its beginning (after the
+// copies that last read it, if the previous call returned before its wait).
+int pin_reset(sisso_l0_t h) {
+  if (h->pin_pending && h->ev_pin) L0_CK(cudaEventSynchronize(h->ev_pin), "staging event");
+  h->pin_pending = false;
+  h->pin_used = 0;
+  if (!h->pin) {
+    const size_t n = 256 * 1024;
+    if (cudaHostAlloc((void **)&h->pin, n, cudaHostAllocDefault) != cudaSuccess) {
+      (void)cudaGetLastError();
+      h->pin = nullptr;   // without it, copies go through pageable memory
+      return SISSO_L0_OK;
     }
-    std::this_thread::sleep_for(std::chrono::microseconds(20));
+    h->pin_n = n;
+  }
+  return SISSO_L0_OK;
+}
+
+unsigned char *pin_take(sisso_l0_t h, size_t n) {
+  const size_t a = (h->pin_used + 15) & ~(size_t)15;
+  if (!h->pin || a + n > h->pin_n) return nullptr;
+  h->pin_used = a + n;
+  return h->pin + a;
+}
+
+// Host -> device copy of a small table, skipped when the device buffer
+// already holds exactly these bytes from the previous upload through `c`.
+int upload(sisso_l0_t h, void *dev, const void *src, size_t n, sisso_l0_handle::UpCache *c) {
+  if (n == 0) return SISSO_L0_OK;
+  if (c && c->dev == dev && c->bytes.size() == n && memcmp(c->bytes.data(), src, n) == 0)
+    return SISSO_L0_OK;
+  unsigned char *stg = pin_take(h, n);
+  if (stg) {
+    memcpy(stg, src, n);
+    L0_CK(cudaMemcpyAsync(dev, stg, n, cudaMemcpyHostToDevice, h->st), "upload");
+    L0_CK(cudaEventRecord(h->ev_pin, h->st), "staging event");
+    h->pin_pending = true;
+  } else {
+    L0_CK(cudaMemcpyAsync(dev, src, n, cudaMemcpyHostToDevice, h->st), "upload");
+  }
+  if (c) {
+    c->dev = dev;
+    c->bytes.assign((const unsigned char *)src, (const unsigned char *)src + n);
   }
   return SISSO_L0_OK;
 }
@@ -185,6 +262,12 @@ struct FitPlan {
   int grid = 0;             // tuple-kernel CTAs
   int max_bps = 1;          // largest resident CTAs per SM the kernel allows
   int items_factor = 2;     // work items per tuple-kernel CTA (at least)
+  int variant = 0;          // tuple kernel shape (sisso_l0_options::tuple_kernel values)
+  int kmax_pool = 2048;     // largest candidate pool of the fit (shared-memory sizing)
+  // FP32 band pass (mixed precision): the search reruns with the cut fixed at
+  // the previous pass's k-th re-fitted score + kBandMargin * delta and queues
+  // every tuple below it for the FP64 redo
+  int band = 0;
   long long n_items = 0;
   long long out_t_total = 0, out_r_total = 0;
   bool have_g64 = false;    // FP64 Gram computed (always in FP64 mode)
@@ -195,12 +278,14 @@ struct FitPlan {
   // after_prep runs once the symmetric Gram and its diagonal exist.
   int proposal = 0, prep_only = 0;
   int shard = 0, n_shards = 1;   // the tuple kernel takes items shard, shard + n_shards, ...
+  int exports_pool = 0;          // every pool entry is re-fitted (the caller reads them all)
   long long n_pairs = 0;
   u64 prop_fits = 0;
   std::function<int(sisso_l0_t, FitPlan &)> after_prep;
 };
 
 constexpr int kDeferGroups = 64;
+constexpr double kBandMargin = 8.0;   // band cut = k-th re-fitted score + 8 delta
 constexpr long long kDeferCap = 1LL << 24;
 
 int staging_for(int K) {
@@ -281,9 +366,22 @@ void plan_problems(FitPlan &P) {
   P.n_items = item;
 }
 
+// the d <= 3 FP32 kernel runs PER_TASK exhaustive searches over a Gram whose
+// rows the TMA unit can copy (16-byte aligned leading dimension and stride)
+bool tile32_ok(const FitPlan &P, int v) {
+  return v > 0 && P.mixed && !P.shared && !P.proposal && P.dp_lo >= 0 && P.dp_hi <= 1 &&
+         P.ld % 4 == 0 && P.gstride % 4 == 0 && l0::tile32_supports(v, P.dp_lo, P.dp_hi);
+}
+
 template <typename R>
 int tile_bps(sisso_l0_t h, const FitPlan &P, int Kmax, int *bps) {
   const int S0 = staging_for(Kmax);
+  if (P.variant > 0) {
+    L0_CK(l0::tile32_occupancy(P.variant, std::max(P.dp_lo, 0), std::max(P.dp_hi, 0),
+                               l0::tile32_smem_bytes(Kmax, S0), bps),
+          "occupancy");
+    return SISSO_L0_OK;
+  }
   const size_t smem = l0::tile_smem_bytes<R>(Kmax, S0, std::max(P.dp_hi, 0));
   if (P.shared) L0_CK(l0::shared_occupancy<R>(std::max(P.dp_hi, 0), smem, bps), "occupancy");
   else L0_CK(l0::tile_occupancy<R>(std::max(P.dp_lo, 0), std::max(P.dp_hi, 0), smem, bps), "occupancy");
@@ -296,19 +394,19 @@ int setup_search(sisso_l0_t h, FitPlan &P, int K) {
   cudaStream_t st = h->st;
   const int n_probs = (int)P.pd.size();
   L0_CK(h->probs.ensure(P.pd.size() * sizeof(l0::ProbDesc)), "alloc probs");
-  L0_CK(cudaMemcpyAsync(h->probs.p, P.pd.data(), P.pd.size() * sizeof(l0::ProbDesc),
-                        cudaMemcpyHostToDevice, st), "copy probs");
+  int urc = upload(h, h->probs.p, P.pd.data(), P.pd.size() * sizeof(l0::ProbDesc), &h->up_probs);
+  if (urc) return urc;
   L0_CK(h->rowpre.ensure(std::max<size_t>(1, P.rowpre.size()) * 8), "alloc rowpre");
-  if (!P.rowpre.empty())
-    L0_CK(cudaMemcpyAsync(h->rowpre.p, P.rowpre.data(), P.rowpre.size() * 8,
-                          cudaMemcpyHostToDevice, st), "copy rowpre");
+  urc = upload(h, h->rowpre.p, P.rowpre.data(), P.rowpre.size() * 8, &h->up_rowpre);
+  if (urc) return urc;
   // rmse divisor per problem: n_t (PER_TASK); SHARED scores are already the
   // pooled mean SSE
   std::vector<double> div(P.pd.size());
   for (size_t q = 0; q < P.pd.size(); ++q)
     div[q] = P.shared ? 1.0 : (double)(P.off[P.pd[q].task + 1] - P.off[P.pd[q].task]);
   L0_CK(h->rdiv.ensure(div.size() * 8), "alloc");
-  L0_CK(cudaMemcpyAsync(h->rdiv.p, div.data(), div.size() * 8, cudaMemcpyHostToDevice, st), "copy");
+  urc = upload(h, h->rdiv.p, div.data(), div.size() * 8, &h->up_rdiv);
+  if (urc) return urc;
   L0_CK(h->out_t.ensure((size_t)P.out_t_total * 4), "alloc out");
   L0_CK(h->out_r.ensure((size_t)P.out_r_total * 8), "alloc out");
   L0_CK(h->dfr_n.ensure(24), "alloc");   // queued runs, queued tuples, redone tuples
@@ -423,11 +521,20 @@ l0::TileArgs<R> tile_args(sisso_l0_t h, const FitPlan &P, int K, int S, const R 
   a.mp1 = P.m + 1;
   a.n_total = P.N;
   a.cls = h->col_cls.as<int>();
+  a.band = P.band;
   return a;
 }
 
 template <typename R>
 int launch_tuple_kernel(sisso_l0_t h, const FitPlan &P, const l0::TileArgs<R> &a) {
+  if constexpr (std::is_same<R, float>::value) {
+    if (P.variant > 0) {
+      L0_CK(l0::launch_tile32(a, P.variant, std::max(P.dp_lo, 0), std::max(P.dp_hi, 0), P.grid,
+                              l0::tile32_smem_bytes(a.K, a.S), h->st),
+            "tile32 kernel");
+      return SISSO_L0_OK;
+    }
+  }
   const size_t smem = l0::tile_smem_bytes<R>(a.K, a.S, std::max(P.dp_hi, 0));
   if (P.shared)
     L0_CK(l0::launch_tile_shared<R>(a, std::max(P.dp_hi, 0), P.grid, smem, h->st), "shared tile kernel");
@@ -448,15 +555,30 @@ int search_pass(sisso_l0_t h, FitPlan &P, int K, const R *G) {
   const int n_slots = std::max(P.has_singles ? 64 : 0, P.grid) + (P.mixed ? kDeferGroups : 0);
   L0_CK(cudaMemsetAsync(h->lists_cnt.p, 0, (size_t)n_probs * n_slots * 4, st), "memset");
   L0_CK(cudaEventRecord(h->ev[2], st), "event");
+  if (P.band) {
+    // the band's cut from the previous pass's certificate (read before this
+    // pass overwrites it)
+    L0_CK(h->band_thr.ensure((size_t)n_probs * 8), "alloc band");
+    L0_CK(h->band_floor.ensure((size_t)n_probs * 8), "alloc band");
+    L0_CK(l0::launch_band_cut(h->cert.as<l0::CertOut>(), h->probs.as<l0::ProbDesc>(), n_probs,
+                              h->inv_s.as<double>(), P.m + 1, P.shared, kBandMargin,
+                              h->band_thr.as<u64>(), h->band_floor.as<double>(), st),
+          "band kernel");
+  }
   {
     const double ratio = P.mixed ? h->opt.fp32_fallback_pivot_ratio : h->opt.rank_deficient_pivot_ratio;
-    // a proposal search ranks only its reachable triples: no seed bound from
-    // tuples outside them
+    // a proposal search ranks only its reachable triples, and a band pass
+    // starts from its own cut: no seed bound
     L0_CK(l0::launch_seed<R>(G, h->probs.as<l0::ProbDesc>(), n_probs, K, S,
-                             (P.shared || P.proposal) ? 0 : 1, ratio, B, h->gthr.as<u64>(),
-                             h->hist.as<unsigned>(), std::max(P.m, 2 * K + 64), st),
+                             (P.shared || P.proposal || P.band) ? 0 : 1, ratio, B,
+                             h->gthr.as<u64>(), h->hist.as<unsigned>(),
+                             std::max(P.m, 2 * K + 64), st),
           "seed kernel");
   }
+  if (P.band)
+    L0_CK(cudaMemcpyAsync(h->gthr.p, h->band_thr.p, (size_t)n_probs * 8, cudaMemcpyDeviceToDevice,
+                          st),
+          "band cut");
   if (P.has_singles) {
     const int gx = std::max(1, std::min(64, (P.m + L0_THREADS - 1) / L0_THREADS));
     L0_CK(l0::launch_singles<R>(G, P.pd.data(), h->probs.as<l0::ProbDesc>(), n_probs, K, S, gx,
@@ -573,6 +695,7 @@ int search_pass(sisso_l0_t h, FitPlan &P, int K, const R *G) {
   ra.dmax = P.dmax;
   ra.smem_rows = 0;
   ra.refit = h->refit.as<double>();
+  ra.refit_all = P.exports_pool;   // a shard hands its whole re-fitted pool on
   L0_CK(l0::launch_refit(ra, st), "refit kernel");
   l0::SelectArgs<R> sa{};
   sa.probs = h->probs.as<l0::ProbDesc>();
@@ -592,6 +715,9 @@ int search_pass(sisso_l0_t h, FitPlan &P, int K, const R *G) {
   sa.cert = h->cert.as<l0::CertOut>();
   sa.cert_safety = 4.0;
   sa.gthr = h->gthr.as<u64>();
+  sa.refit_all = ra.refit_all;
+  sa.delta_floor = P.band ? h->band_floor.as<double>() : nullptr;
+  sa.band_thr = P.band ? h->band_thr.as<u64>() : nullptr;
   L0_CK(l0::launch_select<R>(sa, st), "select kernel");
   L0_CK(cudaEventRecord(h->ev[5], st), "event");
   return SISSO_L0_OK;
@@ -599,22 +725,34 @@ int search_pass(sisso_l0_t h, FitPlan &P, int K, const R *G) {
 
 // after a pass: error word, certificate, statistics (host sync)
 int finish_pass(sisso_l0_t h, FitPlan &P, int *certified, double *delta_max, float *ms_tuple,
-                float *ms_merge, float *ms_refit, int *hopeless) {
+                float *ms_merge, float *ms_refit, int *hopeless, int *bandable) {
   cudaStream_t st = h->st;
   const int n_probs = (int)P.pd.size();
-  std::vector<l0::CertOut> cert(n_probs);
-  L0_CK(cudaMemcpyAsync(cert.data(), h->cert.p, n_probs * sizeof(l0::CertOut),
-                        cudaMemcpyDeviceToHost, st), "copy cert");
-  u64 dfr_stats[3] = {0, 0, 0};
+  // status of the pass, read into pinned staging (asynchronous) when there
+  // is room, else into pageable memory
+  const size_t cb = (size_t)n_probs * sizeof(l0::CertOut);
+  unsigned char *pst = pin_take(h, cb + 24 + 16 + 8);
+  std::vector<unsigned char> pageable;
+  if (!pst) {
+    pageable.assign(cb + 24 + 16 + 8, 0);
+    pst = pageable.data();
+  }
+  memset(pst, 0, cb + 24 + 16 + 8);
+  L0_CK(cudaMemcpyAsync(pst, h->cert.p, cb, cudaMemcpyDeviceToHost, st), "copy cert");
   if (P.mixed && P.has_tuples)
-    L0_CK(cudaMemcpyAsync(dfr_stats, h->dfr_n.p, 24, cudaMemcpyDeviceToHost, st), "copy");
-  u64 pfits[2] = {0, 0};
+    L0_CK(cudaMemcpyAsync(pst + cb, h->dfr_n.p, 24, cudaMemcpyDeviceToHost, st), "copy");
   if (P.proposal)
-    L0_CK(cudaMemcpyAsync(pfits, h->prop_ctr.p, 16, cudaMemcpyDeviceToHost, st), "copy");
-  int host_err = 0;
-  L0_CK(cudaMemcpyAsync(&host_err, h->err.p, 4, cudaMemcpyDeviceToHost, st), "copy err");
+    L0_CK(cudaMemcpyAsync(pst + cb + 24, h->prop_ctr.p, 16, cudaMemcpyDeviceToHost, st), "copy");
+  L0_CK(cudaMemcpyAsync(pst + cb + 40, h->err.p, 4, cudaMemcpyDeviceToHost, st), "copy err");
   int rc = wait_stream(h);
   if (rc) return rc;
+  std::vector<l0::CertOut> cert(n_probs);
+  memcpy(cert.data(), pst, cb);
+  u64 dfr_stats[3], pfits[2];
+  memcpy(dfr_stats, pst + cb, 24);
+  memcpy(pfits, pst + cb + 24, 16);
+  int host_err = 0;
+  memcpy(&host_err, pst + cb + 40, 4);
   if (host_err == 5) return fail(h, SISSO_L0_ENONFINITE, "NaN or Inf in X or y");
   if (host_err == 7)
     return fail(h, SISSO_L0_EUNSUPPORTED,
@@ -626,7 +764,9 @@ int finish_pass(sisso_l0_t h, FitPlan &P, int *certified, double *delta_max, flo
   *certified = 1;
   *delta_max = 0;
   *hopeless = 0;
+  *bandable = 1;   // a band cut needs a finite k-th re-fitted score everywhere
   for (auto &c : cert) {
+    if (!std::isfinite(c.kth_refit) || !std::isfinite(c.delta)) *bandable = 0;
     if (!c.certified) {
       *certified = 0;
       // search-score errors of a quarter of the k-th score itself: a larger
@@ -654,16 +794,19 @@ int finish_pass(sisso_l0_t h, FitPlan &P, int *certified, double *delta_max, flo
 // Like the paper's launch tuning (Sec. 2.4: the first batch is timed under a
 // preset list of launch configurations and the best is kept), the first
 // search of a shape times the tuple kernel on the first quarter of its work
-// items under each (work items per CTA, resident CTAs per SM) pair and keeps
-// the fastest; choices persist in autotune_cache_path.
+// items under each (kernel shape, resident CTAs per SM, work items per CTA)
+// triple and keeps the fastest; choices persist in autotune_cache_path.
+// Kernel shapes: the general kernel (8 rows x 4 columns per thread) and, for
+// FP32 searches of d = 2 and 3, the kernel of l0_tile32.cu with 8 rows x 4
+// columns per thread (one or two CTAs per SM) or 4 x 4 (512 threads).
 std::string tune_key(sisso_l0_t h, const FitPlan &P) {
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, h->opt.device);
   int mb = 1;
   while (mb < P.m) mb <<= 1;
   char buf[256];
-  snprintf(buf, sizeof(buf), "%s|prec=%d|shared=%d|dp=%d-%d|m<=%d|T=%d", prop.name, P.mixed,
-           P.shared, P.dp_lo, P.dp_hi, mb, P.T);
+  snprintf(buf, sizeof(buf), "%s|prec=%d|shared=%d|dp=%d-%d|m<=%d|T=%d|shapes=%d", prop.name,
+           P.mixed, P.shared, P.dp_lo, P.dp_hi, mb, P.T, h->opt.tuple_kernel);
   std::string s(buf);
   for (char &c : s)
     if (c == ' ') c = '_';
@@ -674,18 +817,23 @@ void load_tune_cache(sisso_l0_t h) {
   if (!h->opt.autotune_cache_path) return;
   FILE *f = fopen(h->opt.autotune_cache_path, "r");
   if (!f) return;
-  char key[512];
-  int fa = 0, ba = 0;
-  while (fscanf(f, "%511s %d %d", key, &fa, &ba) == 3) h->tune[key] = {fa, ba};
+  // one choice per line: key, items factor, CTAs per SM, kernel shape
+  char line[768], key[512];
+  while (fgets(line, sizeof(line), f)) {
+    int fa = 0, ba = 0, va = 0;
+    if (sscanf(line, "%511s %d %d %d", key, &fa, &ba, &va) == 4 && fa >= 1 && ba >= 1 &&
+        va >= 0 && va <= 3)
+      h->tune[key] = {fa, ba, va};
+  }
   fclose(f);
 }
 
-void store_tune(sisso_l0_t h, const std::string &key, int f, int b) {
-  h->tune[key] = {f, b};
+void store_tune(sisso_l0_t h, const std::string &key, int f, int b, int v) {
+  h->tune[key] = {f, b, v};
   if (!h->opt.autotune_cache_path) return;
   FILE *fp = fopen(h->opt.autotune_cache_path, "a");
   if (!fp) return;
-  fprintf(fp, "%s %d %d\n", key.c_str(), f, b);
+  fprintf(fp, "%s %d %d %d\n", key.c_str(), f, b, v);
   fclose(fp);
 }
 
@@ -693,51 +841,75 @@ template <typename R>
 int autotune(sisso_l0_t h, FitPlan &P, int K, const R *G) {
   const std::string key = tune_key(h, P);
   auto it = h->tune.find(key);
-  if (it != h->tune.end()) {
-    P.items_factor = it->second.first;
-    P.grid = h->n_sm * std::min(it->second.second, P.max_bps);
+  const int Kmax = P.kmax_pool;
+  auto apply = [&](int v, int b) -> int {
+    P.variant = v;
+    int bps = 0;
+    int rc = tile_bps<R>(h, P, Kmax, &bps);
+    if (rc) return rc;
+    P.max_bps = std::max(1, bps);
+    P.grid = h->n_sm * std::min(b, P.max_bps);
     return SISSO_L0_OK;
+  };
+  if (it != h->tune.end()) {
+    const int v = tile32_ok(P, it->second.v) ? it->second.v : 0;
+    P.items_factor = it->second.f;
+    return apply(v, it->second.b);
   }
   cudaStream_t st = h->st;
   const int S = staging_for(K);
   const int n_probs = (int)P.pd.size();
   l0::Binom B{h->binom.as<u64>(), P.m + 1};
   float best = 1e30f;
-  int best_f = P.items_factor, best_b = 1;
+  int best_f = P.items_factor, best_b = 1, best_v = P.variant;
+  std::vector<int> shapes;
+  if (h->opt.tuple_kernel >= 0) {
+    shapes.push_back(tile32_ok(P, h->opt.tuple_kernel) ? h->opt.tuple_kernel : 0);
+  } else {
+    shapes.push_back(0);
+    for (int v = 1; v <= 3; ++v)
+      if (tile32_ok(P, v)) shapes.push_back(v);
+  }
   const int factors[] = {1, 2, 4, 8};
-  for (int b = 1; b <= std::min(P.max_bps, 2); ++b) {
-    for (int f : factors) {
-      P.grid = h->n_sm * b;
-      P.items_factor = f;
-      plan_problems(P);
-      int rc = setup_search<R>(h, P, K);
-      if (rc) return rc;
-      const int n_slots = std::max(P.has_singles ? 64 : 0, P.grid) + (P.mixed ? kDeferGroups : 0);
-      L0_CK(cudaMemsetAsync(h->lists_cnt.p, 0, (size_t)n_probs * n_slots * 4, st), "memset");
-      L0_CK(l0::launch_seed<R>(G, h->probs.as<l0::ProbDesc>(), n_probs, K, S, P.shared ? 0 : 1,
-                               P.mixed ? h->opt.fp32_fallback_pivot_ratio
-                                       : h->opt.rank_deficient_pivot_ratio,
-                               B, h->gthr.as<u64>(), h->hist.as<unsigned>(),
-                             std::max(P.m, 2 * K + 64), st),
-            "seed kernel");
-      L0_CK(cudaMemsetAsync(h->ctr.p, 0, 8, st), "memset");
-      if (P.mixed) L0_CK(cudaMemsetAsync(h->dfr_n.p, 0, 24, st), "memset");
-      l0::TileArgs<R> a = tile_args<R>(h, P, K, S, G, n_slots, std::max(1LL, P.n_items / 4));
-      L0_CK(cudaEventRecord(h->ev[2], st), "event");
-      rc = launch_tuple_kernel<R>(h, P, a);
-      if (rc) return rc;
-      L0_CK(cudaEventRecord(h->ev[3], st), "event");
-      rc = wait_stream(h);
-      if (rc) return rc;
-      float ms = 0;
-      cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]);
-      // the slice is a quarter of the items, whatever their size
-      if (ms < best) { best = ms; best_f = f; best_b = b; }
+  for (int v : shapes) {
+    int rc = apply(v, 1);
+    if (rc) return rc;
+    const int bmax = std::min(P.max_bps, 2);
+    for (int b = 1; b <= bmax; ++b) {
+      for (int f : factors) {
+        P.grid = h->n_sm * b;
+        P.items_factor = f;
+        plan_problems(P);
+        rc = setup_search<R>(h, P, K);
+        if (rc) return rc;
+        const int n_slots = std::max(P.has_singles ? 64 : 0, P.grid) + (P.mixed ? kDeferGroups : 0);
+        L0_CK(cudaMemsetAsync(h->lists_cnt.p, 0, (size_t)n_probs * n_slots * 4, st), "memset");
+        L0_CK(l0::launch_seed<R>(G, h->probs.as<l0::ProbDesc>(), n_probs, K, S, P.shared ? 0 : 1,
+                                 P.mixed ? h->opt.fp32_fallback_pivot_ratio
+                                         : h->opt.rank_deficient_pivot_ratio,
+                                 B, h->gthr.as<u64>(), h->hist.as<unsigned>(),
+                                 std::max(P.m, 2 * K + 64), st),
+              "seed kernel");
+        L0_CK(cudaMemsetAsync(h->ctr.p, 0, 8, st), "memset");
+        if (P.mixed) L0_CK(cudaMemsetAsync(h->dfr_n.p, 0, 24, st), "memset");
+        l0::TileArgs<R> a = tile_args<R>(h, P, K, S, G, n_slots, std::max(1LL, P.n_items / 4));
+        L0_CK(cudaEventRecord(h->ev[2], st), "event");
+        rc = launch_tuple_kernel<R>(h, P, a);
+        if (rc) return rc;
+        L0_CK(cudaEventRecord(h->ev[3], st), "event");
+        rc = wait_stream(h);
+        if (rc) return rc;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]);
+        // the slice is a quarter of the items, whatever their size
+        if (ms < best) { best = ms; best_f = f; best_b = b; best_v = v; }
+      }
     }
   }
   P.items_factor = best_f;
-  P.grid = h->n_sm * best_b;
-  store_tune(h, key, best_f, best_b);
+  int rc = apply(best_v, best_b);
+  if (rc) return rc;
+  store_tune(h, key, best_f, best_b, best_v);
   return SISSO_L0_OK;
 }
 
@@ -747,8 +919,9 @@ int autotune(sisso_l0_t h, FitPlan &P, int K, const R *G) {
 std::string graph_key(sisso_l0_t h, const FitPlan &P, int K) {
   std::string k;
   char buf[128];
-  snprintf(buf, sizeof(buf), "%p|%p|m=%d|N=%lld|T=%d|K=%d|g=%d|f=%d|p=%d|s=%d|", (const void *)P.Xd,
-           (const void *)P.yd, P.m, P.N, P.T, K, P.grid, P.items_factor, P.mixed, P.shared);
+  snprintf(buf, sizeof(buf), "%p|%p|m=%d|N=%lld|T=%d|K=%d|g=%d|f=%d|p=%d|s=%d|v=%d|", (const void *)P.Xd,
+           (const void *)P.yd, P.m, P.N, P.T, K, P.grid, P.items_factor, P.mixed, P.shared,
+           P.variant);
   k += buf;
   for (long long o : P.off) k += std::to_string(o) + ",";
   for (const Req &r : P.req) k += "r" + std::to_string(r.d) + "x" + std::to_string(r.k);
@@ -769,7 +942,7 @@ std::string graph_key(sisso_l0_t h, const FitPlan &P, int K) {
 template <typename R>
 int run_pass(sisso_l0_t h, FitPlan &P, int K, const R *G, bool with_prep, bool *replayed) {
   *replayed = false;
-  if (!h->opt.use_graph || P.proposal || P.n_shards > 1) {
+  if (!h->opt.use_graph || P.proposal || P.n_shards > 1 || P.band) {
     int rc = with_prep ? prep_pass(h, P) : SISSO_L0_OK;
     if (rc) return rc;
     return search_pass<R>(h, P, K, G);
@@ -806,6 +979,7 @@ int run_pass(sisso_l0_t h, FitPlan &P, int K, const R *G, bool with_prep, bool *
 struct Special {
   int proposal = 0, prep_only = 0;
   int shard = 0, n_shards = 1;
+  int exports_pool = 0;   // the caller reads the whole re-fitted pool (a shard)
   std::function<int(sisso_l0_t, FitPlan &)> after_prep;
 };
 
@@ -831,6 +1005,7 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
     P.prep_only = sp->prep_only;
     P.shard = sp->shard;
     P.n_shards = sp->n_shards;
+    P.exports_pool = sp->exports_pool;
     P.after_prep = sp->after_prep;
   }
   int kmax = 0;
@@ -882,7 +1057,12 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
   K = std::min(std::max(K, kmax), 2048);
   if ((u64)K > total_min) K = (int)std::max<u64>(total_min, (u64)kmax);
   Kmax = std::max(Kmax, K);
+  P.kmax_pool = Kmax;
   cudaStream_t st = h->st;
+  {
+    const int prc = pin_reset(h);
+    if (prc) return prc;
+  }
   if (h->own_st) {
     // the caller's earlier work (e.g. producing X) precedes ours
     L0_CK(cudaEventRecord(h->ev_user, h->user_st), "event");
@@ -903,10 +1083,10 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
   P.Xd = Xd;
   P.yd = yd;
   L0_CK(h->offs.ensure((n_tasks + 1) * 8), "alloc offsets");
-  L0_CK(cudaMemcpyAsync(h->offs.p, P.off.data(), (n_tasks + 1) * 8, cudaMemcpyHostToDevice, st),
-        "copy offsets");
+  int rc = upload(h, h->offs.p, P.off.data(), (n_tasks + 1) * 8, &h->up_offs);
+  if (rc) return rc;
   L0_CK(h->err.ensure(16), "alloc err");
-  int rc = ensure_binom(h, m);
+  rc = ensure_binom(h, m);
   if (rc) return rc;
   // buffers of the centring and the Gram
   const int mp1 = m + 1;
@@ -938,8 +1118,8 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
     L0_CK(h->abf.ensure(abytes), "alloc split rows");
     L0_CK(h->bbf.ensure(abytes), "alloc split rows");
     L0_CK(h->kmeta.ensure(meta.size() * 4), "alloc");
-    L0_CK(cudaMemcpyAsync(h->kmeta.p, meta.data(), meta.size() * 4, cudaMemcpyHostToDevice, st),
-          "copy");
+    rc = upload(h, h->kmeta.p, meta.data(), meta.size() * 4, &h->up_kmeta);
+    if (rc) return rc;
     L0_CK(h->gram32.ensure((size_t)n_tasks * P.gstride * 4), "alloc Gram");
   }
   // persistent grid of the tuple kernel (or of the proposal search)
@@ -954,8 +1134,16 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
     P.grid = h->n_sm * bps;
   } else if (P.has_tuples) {
     int bps = 0;
+    // default shape: the d <= 3 FP32 kernel with two CTAs per SM where it applies
+    const int want = h->opt.tuple_kernel < 0 ? 2 : h->opt.tuple_kernel;
+    P.variant = tile32_ok(P, want) ? want : 0;
     rc = P.mixed ? tile_bps<float>(h, P, Kmax, &bps) : tile_bps<double>(h, P, Kmax, &bps);
     if (rc) return rc;
+    if (bps < 1 && P.variant > 0) {
+      P.variant = 0;
+      rc = P.mixed ? tile_bps<float>(h, P, Kmax, &bps) : tile_bps<double>(h, P, Kmax, &bps);
+      if (rc) return rc;
+    }
     if (bps < 1) return fail(h, SISSO_L0_EUNSUPPORTED, "tuple kernel does not fit on an SM");
     P.max_bps = bps;
     P.grid = h->n_sm * bps;
@@ -1021,10 +1209,22 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
                  : run_pass<double>(h, P, K, h->gram.as<double>(), with_prep, &replayed);
     if (rc) break;
     prep_done = true;
-    int hopeless = 0;
-    rc = finish_pass(h, P, &certified, &delta, &ms_tuple, &ms_merge, &ms_refit, &hopeless);
+    int hopeless = 0, bandable = 0;
+    rc = finish_pass(h, P, &certified, &delta, &ms_tuple, &ms_merge, &ms_refit, &hopeless,
+                     &bandable);
     if (rc) break;
-    if (!certified && hopeless && P.mixed && h->opt.fp64_rerun_uncertified) break;
+    // An FP32 pass that cannot rank the best tuples (its score errors reach
+    // the gaps between them, or the pool stays uncertified at the largest
+    // K') is followed by a band pass at the same K': the tuples near the cut
+    // are scored in FP64.  A band pass that still fails ends the mixed fit
+    // (the caller may redo it in FP64).
+    if (!certified && P.mixed && !P.band && h->opt.fp64_rerun_uncertified && !P.proposal &&
+        P.n_shards == 1 && !P.exports_pool && P.has_tuples && bandable &&
+        (hopeless || K >= Kmax)) {
+      P.band = 1;
+      continue;
+    }
+    if (!certified && hopeless && !P.band && P.mixed && h->opt.fp64_rerun_uncertified) break;
     // a shard's pool is certified against the merged result, not its own
     if (certified || K >= Kmax || P.n_shards > 1) break;
     K = std::min(2 * K, Kmax);
@@ -1073,6 +1273,8 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
   S.ms_refit = ms_refit;
   S.ms_total = t_prep + t_gram + ms_tuple + ms_merge + ms_refit;
   S.ms_tuple_kernel = h->ms_tuple_kernel;
+  S.tuple_kernel = P.variant;
+  S.band_pass = P.band;
   return SISSO_L0_OK;
 }
 
@@ -1138,6 +1340,7 @@ int sisso_l0_default_options(sisso_l0_options *opt) {
   opt->autotune_cache_path = nullptr;
   opt->timeout_seconds = 0.0;
   opt->fp64_rerun_uncertified = 1;
+  opt->tuple_kernel = -1;
   return SISSO_L0_OK;
 }
 
@@ -1151,6 +1354,7 @@ int sisso_l0_create(sisso_l0_t *out, const sisso_l0_options *opt) {
     o = *opt;
   }
   if (o.precision < 0 || o.precision > 2 || o.task_mode < 0 || o.task_mode > 1) return SISSO_L0_EINVAL;
+  if (o.tuple_kernel < -1 || o.tuple_kernel > 3) return SISSO_L0_EINVAL;
   if (!(o.rank_deficient_pivot_ratio >= 0) || !(o.fp32_fallback_pivot_ratio >= 0)) return SISSO_L0_EINVAL;
   sisso_l0_handle *h = new (std::nothrow) sisso_l0_handle();
   if (!h) return SISSO_L0_ENOMEM;
@@ -1162,6 +1366,7 @@ int sisso_l0_create(sisso_l0_t *out, const sisso_l0_options *opt) {
   for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaEventCreate(&h->ev[i]);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_user, cudaEventDisableTiming);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreate(&h->ev_k[i]);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_pin, cudaEventDisableTiming);
   if (e == cudaSuccess && o.use_graph && h->st == nullptr) {
     e = cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking);
     h->own_st = (e == cudaSuccess);
@@ -1206,6 +1411,17 @@ int sisso_l0_fit_multi(sisso_l0_t h, const double *X, const double *y,
   }
 }
 
+int sisso_l0_set_timeout(sisso_l0_t h, double timeout_seconds) {
+  if (!h || timeout_seconds != timeout_seconds) return SISSO_L0_EINVAL;
+  h->opt.timeout_seconds = timeout_seconds;
+  return SISSO_L0_OK;
+}
+
+int sisso_l0_debug_fail_allocation(int64_t after) {
+  g_alloc_fail_countdown = after < 0 ? -1 : (long long)after;
+  return SISSO_L0_OK;
+}
+
 int sisso_l0_get_stats(sisso_l0_t h, sisso_l0_stats *out) {
   if (!h || !out) return SISSO_L0_EINVAL;
   *out = h->stats;
@@ -1230,8 +1446,13 @@ void sisso_l0_destroy(sisso_l0_t h) {
                     &h->cert, &h->out_t, &h->out_r, &h->err, &h->dfr_key, &h->dfr_len, &h->dfr_n,
                     &h->dfr_cnt, &h->abf, &h->bbf, &h->kmeta, &h->gram32, &h->prop_in,
                     &h->prop_pairs, &h->prop_bits, &h->prop_ctr, &h->sel_hist, &h->sel_bin,
-                    &h->scores, &h->diag, &h->col_hash, &h->col_cls};
+                    &h->scores, &h->diag, &h->col_hash, &h->col_cls, &h->sis_ex, &h->sis_y,
+                    &h->gen_ops, &h->gen_c1, &h->gen_c2, &h->gen_valid, &h->loop_x, &h->loop_y,
+                    &h->loop_xs, &h->loop_res, &h->loop_q, &h->loop_tup, &h->loop_rows,
+                    &h->band_thr, &h->band_floor};
   for (DevBuf *b : bufs) b->release();
+  if (h->pin) cudaFreeHost(h->pin);
+  if (h->ev_pin) cudaEventDestroy(h->ev_pin);
   for (int i = 0; i < 8; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
@@ -1716,6 +1937,7 @@ int sisso_l0_fit_shard(sisso_l0_t h, const double *X, const double *y, int64_t n
     Special sp;
     sp.shard = shard;
     sp.n_shards = n_shards;
+    sp.exports_pool = 1;
     int rc = fit_requests(h, X, y, off, 1, n_sis, &r, 1, &sp);
     if (rc) return rc;
     const int K = h->stats.candidate_pool;

@@ -36,23 +36,59 @@ __device__ __forceinline__ unsigned ord32f(float x) {
 __device__ __forceinline__ float f32_up(float x) { return x; }
 __device__ __forceinline__ float f32_up(double x) { return __double2float_ru(x); }
 
-// smallest key T with #{keys <= T} >= want (keys[0..n) in shared memory; all
-// threads; binary search over the 32-bit key space, one block count each)
-__device__ unsigned select_key(const unsigned *keys, int n, int want, int *s_cnt) {
-  unsigned lo = 0u, hi = 0xffffffffu;
-  while (lo < hi) {
-    const unsigned mid = lo + ((hi - lo) >> 1);
-    int c = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) c += keys[i] <= mid ? 1 : 0;
-    if (threadIdx.x == 0) *s_cnt = 0;
+// smallest key T with #{keys <= T} >= want, i.e. the want-th smallest key
+// (keys[0..n) in shared memory; all threads; ~0 when n < want).  Radix
+// select from the top byte down: per byte, a 256-bin count of the keys that
+// share the bytes chosen so far, then the bin where the running count
+// reaches the rank still wanted.  Four passes over the keys.
+__device__ unsigned select_key(const unsigned *keys, int n, int want, unsigned *bins,
+                               int *s_sel) {
+  if (n < want || want < 1) return 0xffffffffu;
+  unsigned prefix = 0u, pmask = 0u;
+  int rem = want;
+  const int lane = threadIdx.x & 31;
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) bins[i] = 0u;
     __syncthreads();
-    if (c) atomicAdd(s_cnt, c);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const unsigned k = keys[i];
+      if ((k & pmask) == prefix) atomicAdd(bins + ((k >> shift) & 255u), 1u);
+    }
     __syncthreads();
-    const int tot = *s_cnt;
+    if (threadIdx.x < 32) {
+      unsigned c[8], sum = 0u;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        c[i] = bins[lane * 8 + i];
+        sum += c[i];
+      }
+      unsigned inc = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+      }
+      const unsigned bl = __ballot_sync(0xffffffffu, inc >= (unsigned)rem);
+      const int lk = __ffs(bl) - 1;   // the counts add up to >= rem, so bl != 0
+      if (lane == lk) {
+        unsigned before = inc - sum;
+        int bin = lane * 8 + 7;
+        for (int i = 0; i < 8; ++i) {
+          if (before + c[i] >= (unsigned)rem) { bin = lane * 8 + i; break; }
+          before += c[i];
+        }
+        s_sel[0] = bin;
+        s_sel[1] = (int)before;
+      }
+    }
     __syncthreads();
-    if (tot >= want) hi = mid; else lo = mid + 1u;
+    const int bin = s_sel[0];
+    rem -= s_sel[1];
+    prefix |= (unsigned)bin << shift;
+    pmask |= 255u << shift;
+    __syncthreads();
   }
-  return lo;
+  return prefix;
 }
 
 // The K'-th best score of all d-tuples of the M columns with the best
@@ -64,7 +100,9 @@ seed_kernel(const R *Gbase, const ProbDesc *probs, int K, int S, int seed, doubl
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned *keys = (unsigned *)smem;            // [max(m, tuples)]
   __shared__ int cols[64];
-  __shared__ int s_cnt, s_n;
+  __shared__ int s_n;
+  __shared__ unsigned s_bins[256];
+  __shared__ int s_sel[2];
   const int prob = blockIdx.x;
   const ProbDesc pd = probs[prob];
   if (threadIdx.x == 0) gthr[prob] = ord_inf<R>();
@@ -89,7 +127,7 @@ seed_kernel(const R *Gbase, const ProbDesc *probs, int K, int S, int seed, doubl
     keys[k] = (ckk > R(0)) ? ord32f(f32_up(G00 - ck * ck / ckk)) : 0xffffffffu;
   }
   __syncthreads();
-  const unsigned t1 = select_key(keys, m, M, &s_cnt);
+  const unsigned t1 = select_key(keys, m, M, s_bins, s_sel);
   if (threadIdx.x == 0) s_n = 0;
   __syncthreads();
   for (int k = threadIdx.x; k < m; k += blockDim.x)
@@ -162,7 +200,7 @@ seed_kernel(const R *Gbase, const ProbDesc *probs, int K, int S, int seed, doubl
   __syncthreads();
   // the K'-th smallest score (rounded up to FP32): K' real tuples lie at or
   // below it, so it bounds the search's K'-th best
-  const unsigned t2 = select_key(keys, nt, K, &s_cnt);
+  const unsigned t2 = select_key(keys, nt, K, s_bins, s_sel);
   if (threadIdx.x == 0 && t2 != 0xffffffffu) {
     const unsigned b = (t2 & 0x80000000u) ? (t2 & 0x7fffffffu) : ~t2;
     atomicMin(gthr + prob, ord_of((R)__uint_as_float(b)));

@@ -278,7 +278,7 @@ refit_kernel(RefitArgs a) {
   const int prob = blockIdx.y, cidx = blockIdx.x;
   const ProbDesc pd = a.probs[prob];
   const int cnt = a.pool_cnt[prob];
-  if (cidx >= cnt) return;
+  if (cidx >= refit_count(pd.k, a.K, cnt, a.refit_all)) return;
   const int d = pd.d;
   if (threadIdx.x == 0) {
     int t[L0_DMAX];
@@ -349,7 +349,9 @@ select_kernel(SelectArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int prob = blockIdx.x;
   const ProbDesc pd = a.probs[prob];
-  const int cnt = a.pool_cnt[prob];
+  const int cnt_pool = a.pool_cnt[prob];
+  // only the re-fitted head of the (search-score sorted) pool is ranked
+  const int cnt = refit_count(pd.k, a.K, cnt_pool, a.refit_all);
   int P = 1;
   while (P < a.K) P <<= 1;
   double *ss = (double *)smem;
@@ -404,26 +406,70 @@ select_kernel(SelectArgs<R> a) {
   if (threadIdx.x == 0) {
     CertOut c;
     c.delta = dmax;
-    c.pool_cnt = cnt;
-    c.pool_full = (cnt >= a.K) ? 1 : 0;
+    c.pool_cnt = cnt_pool;
+    c.pool_full = (cnt_pool >= a.K) ? 1 : 0;
     c.n_valid = nvalid;
     // Tuples outside the pool were either cut by the search threshold (their
     // Gram score exceeded it, and it only ever decreased to its final value
     // g) or lost to the pool's K'-th entry when the pool is full.  So every
     // outside tuple has a Gram score >= bound = min(g, pool K'-th).
+    // Pool entries past the re-fitted head have search scores >= that of the
+    // first one left out (the pool is sorted by search score).
     const double g = (double)from_ord<R>(a.gthr[prob]);
     double bound = g;
-    if (c.pool_full) bound = fmin(bound, (double)a.pool_s[(size_t)prob * a.K + cnt - 1]);
+    if (c.pool_full) bound = fmin(bound, (double)a.pool_s[(size_t)prob * a.K + cnt_pool - 1]);
+    if (cnt < cnt_pool) bound = fmin(bound, (double)a.pool_s[(size_t)prob * a.K + cnt]);
     const double inf = __longlong_as_double(0x7ff0000000000000ll);
     c.pool_worst = isinf(bound) ? inf : bound * scale;
     c.kth_refit = (nvalid >= kq) ? ss[kq - 1] : inf;
-    // Its exact score is then at least bound - safety * delta; the pool holds
-    // the exact top k when that clears the k-th re-fitted score, or trivially
+    // The check assumes that no outside tuple's search score is off by more
+    // than safety * delta, delta being the largest error measured on the
+    // pool (the tuples next to the excluded ones in score).  That is an
+    // empirical premise, not a proof: the excluded tuples were never
+    // re-fitted, and an ill-conditioned one (pivot ratio just above the FP64
+    // redo cut) can carry a larger error.  Under it, every outside tuple's
+    // exact score is at least bound - safety * delta, and the pool holds the
+    // exact top k when that clears the k-th re-fitted score; trivially so
     // when nothing was excluded at all.
     if (isinf(bound)) c.certified = 1;
     else c.certified = (c.pool_worst - a.cert_safety * dmax >= c.kth_refit) ? 1 : 0;
+    if (a.delta_floor) {
+      // Band pass: a tuple the FP32 test never flagged scored above the band
+      // cut in FP32, so the previous pass's error bound applies to it; one it
+      // flagged was scored in FP64 and is bounded as above (delta measured
+      // on this pass's pool).  Both must clear the k-th re-fitted score.
+      const double df = a.delta_floor[prob];
+      const double band = (double)from_ord<float>(a.band_thr[prob]) * scale;
+      if (isfinite(band) && !(band - a.cert_safety * df >= c.kth_refit)) c.certified = 0;
+      if (!isfinite(band)) c.certified = 0;
+      c.delta = fmax(dmax, df);   // a further band pass keeps the FP32 error bound
+    }
     a.cert[prob] = c;
   }
+}
+
+// Band pass cut per problem (one thread each): the previous pass re-fitted
+// its pool in FP64 and measured delta, the largest search-score error on it.
+// Tuples whose FP32 score lies below kth + margin * delta (relative units,
+// rounded up to FP32) are the ones the FP32 search cannot rank: the band
+// pass scores all of them in FP64.  No finite k-th (too few eligible tuples
+// in the pool): no cut, +inf.
+__global__ void band_cut_kernel(const CertOut *cert, const ProbDesc *probs, int n_probs,
+                                const double *inv_s, int mp1, int shared, double margin,
+                                u64 *band_thr, double *delta_floor) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_probs) return;
+  const CertOut c = cert[q];
+  double scale = 1.0;   // SSE units per unit of search score
+  if (!shared) {
+    const double is = inv_s[(size_t)probs[q].task * mp1];
+    scale = (is > 0.0) ? 1.0 / (is * is) : 0.0;
+  }
+  const double cut = (scale > 0.0) ? (c.kth_refit + margin * c.delta) / scale
+                                   : __longlong_as_double(0x7ff0000000000000ll);
+  const float cf = isfinite(cut) ? __double2float_ru(cut) : __int_as_float(0x7f800000);
+  band_thr[q] = ord_of(cf);
+  delta_floor[q] = c.delta;
 }
 
 __global__ void unrank_kernel(Binom B, int m, int d, u64 total, const u64 *ranks,
@@ -532,6 +578,14 @@ cudaError_t launch_select(const SelectArgs<R> &a, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(select_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   select_kernel<R><<<a.n_probs, 256, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_band_cut(const CertOut *cert, const ProbDesc *probs, int n_probs,
+                            const double *inv_s, int mp1, int shared, double margin,
+                            u64 *band_thr, double *delta_floor, cudaStream_t st) {
+  band_cut_kernel<<<(n_probs + 127) / 128, 128, 0, st>>>(cert, probs, n_probs, inv_s, mp1,
+                                                         shared, margin, band_thr, delta_floor);
   return cudaGetLastError();
 }
 
