@@ -41,21 +41,31 @@ def fp32_peak_tflops(sm_mhz):
 
 
 # DRAM bytes (read + write) of one tuple-kernel launch on the d=3 workload,
-# from the ncu captures summarised in profiles/tile_kernel_l0_d3_n1000_m1000.md.
-# They describe the kernel built from sources with this hash; once the sources
-# change the figure no longer applies and the bench reports null.
-TRAFFIC_SOURCES = ("l0_common.cuh", "l0_tile.cuh", "l0_tuple.cu", "l0_kernels.cuh")
-TRAFFIC_CAPTURED = {("C2", "mixed"): (2416384 + 2304, "293c3cbe19100b15"),
-                    ("C2", "fp64"): (4533248 + 16896, "293c3cbe19100b15")}
+# from the ncu captures summarised in profiles/tile_kernel_l0_d3_n1000_m1000.md
+# (shape 0, the general kernel) and profiles/tile32_kernel_l0_d3_n1000_m1000.md
+# (shapes 1-3).  They describe the kernel built from sources with this hash;
+# once the sources change the figure no longer applies and the bench reports
+# null.  Keys: (workload, precision, kernel shape).
+TRAFFIC_SOURCES = {0: ("l0_common.cuh", "l0_tile.cuh", "l0_tuple.cu", "l0_kernels.cuh")}
+for _v in (1, 2, 3):
+    TRAFFIC_SOURCES[_v] = ("l0_common.cuh", "l0_tile.cuh", "l0_tile32.cu", "l0_kernels.cuh",
+                           "l0_tc.cuh")
+TRAFFIC_CAPTURED = {}
+TUPLE_KERNEL_NAMES = {
+    0: "tile_kernel (tuple search, any d)",
+    1: "tile32_kernel (d <= 3 FP32 tuple search, 256 threads, one CTA per SM)",
+    2: "tile32_kernel (d <= 3 FP32 tuple search, 256 threads, two CTAs per SM)",
+    3: "tile32_kernel (d <= 3 FP32 tuple search, 512 threads, one CTA per SM)",
+}
 
 
-def tile_traffic(workload, precision):
+def tile_traffic(workload, precision, shape=0):
     import hashlib
-    rec = TRAFFIC_CAPTURED.get((workload, precision))
+    rec = TRAFFIC_CAPTURED.get((workload, precision, int(shape)))
     if rec is None:
         return None
     h = hashlib.sha256()
-    for f in TRAFFIC_SOURCES:
+    for f in TRAFFIC_SOURCES[int(shape)]:
         with open(os.path.join(ROOT, "paper_2502_20072_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return rec[0] if h.hexdigest()[:16] == rec[1] else None
@@ -85,6 +95,16 @@ def flops_per_tuple(d):
     # hoisted per-tuple work of the tuple kernel's fast path:
     # (d-2) FMA for h, MUL g2, FMA pp, FMA w, MUL w^2, FMA t  ->  d+1 FMA + 2 MUL
     return 2 * (d + 1) + 2
+
+
+def flops_per_tuple_hoisted(d):
+    # the per-tuple count of the (d-1)-prefix hoisted augmented-Cholesky form:
+    # forward solve g = L_P^-1 C_Pk ((d-1)(d-2)/2 FMA + (d-1) MUL), pivot
+    # p = C_kk - g.g (d-1 FMA), w = c_k - g.z_P (d-1 FMA), SSE/S_yy = p_P - w^2/p
+    # (1 reciprocal + 2 MUL/FMA); FMA = 2 flop, MUL = 1  ->  15 at d = 3
+    fma = (d - 1) * (d - 2) // 2 + 2 * (d - 1) + 1
+    mul = (d - 1) + 1
+    return 2 * fma + mul + 1
 
 
 def _dist():
@@ -224,6 +244,14 @@ def run_ours(args):
     reqs = [(dd, k) for dd in dims]
     n_fits = sum(math.comb(prob.n_sis, dd) for dd in dims) * prob.n_tasks
     fl_all = sum(flops_per_tuple(dd) * math.comb(prob.n_sis, dd) for dd in dims) * prob.n_tasks
+    fl_hoisted = sum(flops_per_tuple_hoisted(dd) * math.comb(prob.n_sis, dd)
+                     for dd in dims) * prob.n_tasks
+    # N > 1: one search split over the ranks (every N-th work item per rank,
+    # one all-gather of the re-fitted candidate pools, the merge on every
+    # rank): strong scaling.  --replicas runs N independent copies instead.
+    sharded = ws > 1 and not args.replicas and prob.n_tasks == 1 and len(dims) == 1
+    if sharded:
+        from paper_2502_20072_gb300 import shard
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     X = torch.from_numpy(prob.X).cuda()
@@ -238,6 +266,11 @@ def run_ours(args):
                  np.empty((prob.n_tasks, k), dtype=np.float64)) for dd in dims]
 
     def run(handle, Xa, ya, outs):
+        if sharded:
+            t_, r_, _ = shard.fit_sharded(handle, Xa, ya, dims[0], k)
+            outs[0][0].copy_(torch.as_tensor(t_)[None]) if torch.is_tensor(outs[0][0]) else \
+                np.copyto(outs[0][0], np.asarray(t_)[None])
+            return
         if len(dims) == 1:
             handle.fit(Xa, ya, dims[0], k, offsets=prob.offsets, out_tuples=outs[0][0],
                        out_rmse=outs[0][1])
@@ -283,7 +316,7 @@ def run_ours(args):
         t = torch.tensor([ms_step], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms_step = float(t.item())
-    value = ws * n_fits / (ms_step / 1000.0)
+    value = (1 if sharded else ws) * n_fits / (ms_step / 1000.0)
     st = h.stats()
     # e2e: host buffers through the C ABI (copies inside the timed region)
     Xh = torch.from_numpy(prob.X).pin_memory()
@@ -299,7 +332,7 @@ def run_ours(args):
     e2e_val = n_fits / statistics.median(e2e)
     # the plain FP64 GPU path on the same workload, same timing method
     fp64_line = None
-    if precision != l0.FP64 and not args.no_fp64_path:
+    if precision != l0.FP64 and not args.no_fp64_path and not sharded:
         h64 = l0.Handle(precision=l0.FP64, **opts)
         outs64 = outputs(True)
         for _ in range(3):
@@ -323,7 +356,7 @@ def run_ours(args):
     # around its launch on the library's stream; events inside a replayed
     # graph may not be timeable, so measure extra un-graphed fits then
     stage = {s: st["ms_" + s] for s in ("prep", "gram", "tuple", "merge", "refit")}
-    if min(tuple_ms) <= 0.0:
+    if min(tuple_ms) <= 0.0 and not sharded:
         hk = l0.Handle(precision=precision, device=local, stream=stream.cuda_stream,
                        autotune=int(not args.no_autotune), use_graph=0)
         tuple_ms = []
@@ -339,7 +372,9 @@ def run_ours(args):
         hk.close()
         stage = {s: statistics.mean(v) for s, v in acc.items()}
     t_tuple = statistics.mean(tuple_ms) / 1000.0
-    achieved = fl_all / t_tuple / 1e12
+    per_rank = ws if sharded else 1          # a shard's kernel does 1/N of the tuples
+    achieved = fl_hoisted / per_rank / t_tuple / 1e12
+    achieved_kernel_count = fl_all / per_rank / t_tuple / 1e12
     pk = l0.measure_peaks(local)
     if precision == l0.FP64 or st["fp64_rerun"]:
         # an uncertified mixed fit is redone in FP64: its last tuple kernel is the FP64 one
@@ -349,18 +384,21 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": "strong" if sharded else "weak", "vs_baseline": None,
         "dtype": "f64" if precision == l0.FP64 else "f32",
         "data": "synthetic",
         "config": {"workload": _workload_desc(args.workload, prob, d, k),
                    "precision": args.precision,
-                   "parallelism": "replicas" if ws > 1 else "single",
+                   "parallelism": ("sharded over %d GPUs: every %d-th work item per rank, "
+                                   "one all-gather of the re-fitted candidate pools" % (ws, ws)
+                                   if sharded else ("replicas" if ws > 1 else "single")),
                    "l2": "flushed between steps (256 MB write, outside the timed events)",
                    "candidate_pool": st["candidate_pool"], "certified": st["certified"],
                    "fp64_redo_tuples": int(st["fp64_fallback_tuples"]),
                    "graph_replayed": int(st["graph_replayed"]),
                    "fp64_rerun": int(st["fp64_rerun"]),
                    "tuned": [int(st["tuned_items_factor"]), int(st["tuned_ctas_per_sm"])],
+                   "tuple_kernel_shape": int(st["tuple_kernel"]),
                    "stage_ms": {s: round(v, 4) for s, v in stage.items()},
                    "stage_ms_source": ("un-graphed fits on the same inputs"
                                        if st["graph_replayed"] else "the timed fits")},
@@ -370,9 +408,14 @@ def run_ours(args):
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
-                     "traffic": tile_traffic(args.workload, args.precision),
-                     "kernel": "tile_kernel (tuple search)", "peak_source": peak_note,
-                     "flops_per_tuple": {str(dd): flops_per_tuple(dd) for dd in dims}},
+                     "traffic": tile_traffic(args.workload, args.precision, st["tuple_kernel"]),
+                     "kernel": TUPLE_KERNEL_NAMES.get(int(st["tuple_kernel"]), "tuple kernel"),
+                     "peak_source": peak_note,
+                     "flops_per_tuple": {str(dd): flops_per_tuple_hoisted(dd) for dd in dims},
+                     "flops_per_tuple_source": "hoisted (d-1)-prefix augmented Cholesky count",
+                     "achieved_kernel_count": achieved_kernel_count,
+                     "frac_kernel_count": achieved_kernel_count / peak,
+                     "kernel_flops_per_tuple": {str(dd): flops_per_tuple(dd) for dd in dims}},
         "clocks": clk,
         "measured_peaks": {kk: round(v, 1) for kk, v in pk.items()},
     }
@@ -778,6 +821,8 @@ def run_generated(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--replicas", action="store_true",
+                    help="N > 1: N independent copies of the workload instead of one sharded search")
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
