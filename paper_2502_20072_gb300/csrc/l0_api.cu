@@ -571,8 +571,8 @@ int search_pass(sisso_l0_t h, FitPlan &P, int K, const R *G) {
     // starts from its own cut: no seed bound
     L0_CK(l0::launch_seed<R>(G, h->probs.as<l0::ProbDesc>(), n_probs, K, S,
                              (P.shared || P.proposal || P.band) ? 0 : 1, ratio, B,
-                             h->gthr.as<u64>(), h->hist.as<unsigned>(),
-                             std::max(P.m, 2 * K + 64), st),
+                             h->gthr.as<u64>(), h->hist.as<unsigned>(), l0::seed_keys(P.m, K),
+                             st, h->col_cls.as<int>()),
           "seed kernel");
   }
   if (P.band)
@@ -888,7 +888,7 @@ int autotune(sisso_l0_t h, FitPlan &P, int K, const R *G) {
                                  P.mixed ? h->opt.fp32_fallback_pivot_ratio
                                          : h->opt.rank_deficient_pivot_ratio,
                                  B, h->gthr.as<u64>(), h->hist.as<unsigned>(),
-                                 std::max(P.m, 2 * K + 64), st),
+                                 l0::seed_keys(P.m, K), st, h->col_cls.as<int>()),
               "seed kernel");
         L0_CK(cudaMemsetAsync(h->ctr.p, 0, 8, st), "memset");
         if (P.mixed) L0_CK(cudaMemsetAsync(h->dfr_n.p, 0, 24, st), "memset");

@@ -111,12 +111,27 @@ defer_gram_kernel(DeferArgs a) {
     }
     int t[L0_DMAX];
     if (mine && len > 0) {
-      lex_unrank_arith(pd.m, d, key0, pd.total, t);
+      lex_unrank(a.B, pd.m, d, key0, pd.total, t);   // binomial table, no 64-bit divisions
       done_tuples += (unsigned long long)len;
     }
     int redo = 0;
     do {
-      if (mine && len > 0) {
+      if (mine && len > 0 && a.shared_T == 0) {
+        // one task: the run's tuples share every index but the last, so the
+        // prefix is factored once
+        GramEnt ent{a.G64 + (long long)pd.task * a.g64_stride, a.ld64};
+        PrefixFactor f;
+        factor_prefix(ent, t, d - 1, a.ratio, f);
+        if (f.ok) {
+          for (int e = 0; e < len; ++e) {
+            double rel;
+            if (!score_last(ent, t, d - 1, t[d - 1] + e, a.ratio, f, &rel)) continue;
+            const float s = (float)rel;
+            const u64 key = key0 + (u64)e;
+            if (cta_list_admits<float>(L, s, key)) cta_list_push<float>(L, s, key);
+          }
+        }
+      } else if (mine && len > 0) {
         for (int e = 0; e < len; ++e) {
           // SHARED: pooled over the tasks (ineligible if any task is)
           double score = 0.0;

@@ -263,10 +263,16 @@ cudaError_t launch_defer(const DeferArgs &a, int groups, int n_probs, cudaStream
 // initial search threshold per problem: +inf, then the K'-th best score of
 // all d-tuples of the M best single columns (a valid bound: real tuples)
 // seed == 0: only the +inf initialisation; max_keys >= max(n_sis, 2 K' + 64)
+// (d = 3 also scores the completions of the best pairs of those columns while
+// the keys fit: seed_keys() sizes room for them); cls: duplicate classes or null
 template <typename R>
 cudaError_t launch_seed(const R *G, const ProbDesc *probs_dev, int n_probs, int K, int S,
                         int seed, double ratio, const Binom &B, u64 *gthr, unsigned *hist,
-                        int max_keys, cudaStream_t st);
+                        int max_keys, cudaStream_t st, const int *cls);
+inline int seed_keys(int m, int K) {
+  const long long v = (long long)m * 9 + 2LL * K + 2112;
+  return (int)(v < 50000 ? v : 50000);
+}
 template <typename R>
 size_t seed_smem_bytes(int K, int S);
 

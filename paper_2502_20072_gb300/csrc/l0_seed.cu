@@ -91,18 +91,57 @@ __device__ unsigned select_key(const unsigned *keys, int n, int want, unsigned *
   return prefix;
 }
 
+// rel = SSE / S_yy of one tuple t[0..d) (ascending columns) by the augmented
+// Cholesky of (t, target) in R; false when a feature pivot falls below
+// ratio times its diagonal or two columns share a duplicate class
+template <typename R>
+__device__ bool tuple_rel(const R *G, long long ld, const int *t, int d, double ratio,
+                          const int *cls, R *rel_out) {
+  if (cls)
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < i; ++j)
+        if (__ldg(cls + t[i]) == __ldg(cls + t[j])) return false;
+  R Lm[L0_DMAX + 1][L0_DMAX + 1];
+  R rel = R(0);
+  bool ok = true;
+  for (int i = 0; i <= d; ++i) {
+    const int ia = (i < d) ? t[i] + 1 : 0;
+    for (int j = 0; j <= i; ++j) {
+      const int ib = (j < d) ? t[j] + 1 : 0;
+      R c = gram_at<R>(G, ld, ia, ib);
+      const R orig = c;
+      for (int q = 0; q < j; ++q) c -= Lm[i][q] * Lm[j][q];
+      if (j < i) {
+        Lm[i][j] = c / Lm[j][j];
+      } else if (i < d) {
+        ok = ok && orig > R(0) && c >= (R)ratio * orig;
+        Lm[i][i] = sqrt(c > R(0) ? c : R(1));
+      } else {
+        rel = c;
+      }
+    }
+  }
+  *rel_out = rel;
+  return ok;
+}
+
+// best pairs of the seed columns whose completions the d = 3 seed scores
+constexpr int SEED_PAIRS = 8;
+
 // The K'-th best score of all d-tuples of the M columns with the best
 // single-column fits: two order-statistic searches (no sorting).
 template <typename R>
 __global__ void __launch_bounds__(SEED_THREADS)
 seed_kernel(const R *Gbase, const ProbDesc *probs, int K, int S, int seed, double ratio,
-            Binom B, u64 *gthr, unsigned *hist, int max_keys) {
+            Binom B, u64 *gthr, unsigned *hist, int max_keys, const int *cls) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned *keys = (unsigned *)smem;            // [max(m, tuples)]
   __shared__ int cols[64];
   __shared__ int s_n;
   __shared__ unsigned s_bins[256];
   __shared__ int s_sel[2];
+  __shared__ int s_pair[SEED_PAIRS][2];
+  __shared__ int s_npair;
   const int prob = blockIdx.x;
   const ProbDesc pd = probs[prob];
   if (threadIdx.x == 0) gthr[prob] = ord_inf<R>();
@@ -150,11 +189,44 @@ seed_kernel(const R *Gbase, const ProbDesc *probs, int K, int S, int seed, doubl
   }
   __syncthreads();
   const int Mr = s_n;
+  // 2. d = 3: the best SEED_PAIRS pairs of those columns, whose completions
+  // by every other column are the tuples the search's best K' mostly are
+  if (threadIdx.x == 0) s_npair = 0;
+  const int npairs = Mr * (Mr - 1) / 2;
+  const int pb = min(SEED_PAIRS, npairs);
+  if (d == 3 && pb > 0 && npairs <= max_keys) {
+    for (int r = threadIdx.x; r < npairs; r += blockDim.x) {
+      int b = 1;
+      while (b * (b + 1) / 2 <= r) ++b;   // colex: pair (a, b) has rank b (b - 1) / 2 + a
+      const int t[2] = {cols[r - b * (b - 1) / 2], cols[b]};
+      R rel;
+      keys[r] = tuple_rel<R>(G, ld, t, 2, ratio, cls, &rel) ? ord32f(f32_up(rel)) : 0xffffffffu;
+    }
+    __syncthreads();
+    const unsigned tp = select_key(keys, npairs, pb, s_bins, s_sel);
+    for (int r = threadIdx.x; r < npairs; r += blockDim.x) {
+      if (keys[r] <= tp && keys[r] != 0xffffffffu) {
+        const int slot = atomicAdd(&s_npair, 1);
+        if (slot < pb) {
+          int b = 1;
+          while (b * (b + 1) / 2 <= r) ++b;
+          s_pair[slot][0] = cols[r - b * (b - 1) / 2];
+          s_pair[slot][1] = cols[b];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const int nsp = min(s_npair, pb);
+  // 3. every d-tuple of the seed columns (at most the key capacity; a subset
+  // of real tuples bounds the K'-th best just as well), exact augmented
+  // Cholesky; then (d = 3) each chosen pair with every column outside the
+  // seed set -- distinct from those tuples and from each other's
   const u64 total = small_binom(Mr, d);
-  if (total < (u64)K) return;     // too few tuples to bound the K'-th
-  // 2. every d-tuple of those columns (at most the key capacity; a subset of
-  // real tuples bounds the K'-th best just as well), exact augmented Cholesky
   const int nt = (int)(total < (u64)max_keys ? total : (u64)max_keys);
+  const int per_pair = (nsp > 0) ? min(m, (max_keys - nt) / nsp) : 0;
+  const int ntot = nt + nsp * per_pair;
+  if (ntot < K) return;     // too few tuples to bound the K'-th
   for (int r = threadIdx.x; r < nt; r += blockDim.x) {
     int a[L0_DMAX];
     {  // colex unrank over the Mr seed columns
@@ -173,34 +245,29 @@ seed_kernel(const R *Gbase, const ProbDesc *probs, int K, int S, int seed, doubl
     }
     int t[L0_DMAX];
     for (int i = 0; i < d; ++i) t[i] = cols[a[i]];
-    // Cholesky of (t_1 .. t_d, target): pivots of the features checked,
-    // the last pivot is rel = SSE / S_yy
-    R Lm[L0_DMAX + 1][L0_DMAX + 1];
-    R rel = R(0);
-    bool ok = true;
-    for (int i = 0; i <= d; ++i) {
-      const int ia = (i < d) ? t[i] + 1 : 0;
-      for (int j = 0; j <= i; ++j) {
-        const int ib = (j < d) ? t[j] + 1 : 0;
-        R c = gram_at<R>(G, ld, ia, ib);
-        const R orig = c;
-        for (int q = 0; q < j; ++q) c -= Lm[i][q] * Lm[j][q];
-        if (j < i) {
-          Lm[i][j] = c / Lm[j][j];
-        } else if (i < d) {
-          ok = ok && orig > R(0) && c >= (R)ratio * orig;
-          Lm[i][i] = sqrt(c > R(0) ? c : R(1));
-        } else {
-          rel = c;
-        }
-      }
+    R rel;
+    keys[r] = tuple_rel<R>(G, ld, t, d, ratio, cls, &rel) ? ord32f(f32_up(rel)) : 0xffffffffu;
+  }
+  for (int x = threadIdx.x; x < nsp * per_pair; x += blockDim.x) {
+    const int p = x / per_pair, k = x - p * per_pair;
+    bool in_seed = false;
+    for (int i = 0; i < Mr; ++i) in_seed = in_seed || cols[i] == k;
+    unsigned key = 0xffffffffu;
+    if (!in_seed) {
+      const int a = s_pair[p][0], b = s_pair[p][1];
+      int t[3];
+      t[0] = min(a, k);
+      t[2] = max(b, k);
+      t[1] = a + b + k - t[0] - t[2];
+      R rel;
+      if (tuple_rel<R>(G, ld, t, 3, ratio, cls, &rel)) key = ord32f(f32_up(rel));
     }
-    keys[r] = ok ? ord32f(f32_up(rel)) : 0xffffffffu;
+    keys[nt + x] = key;
   }
   __syncthreads();
   // the K'-th smallest score (rounded up to FP32): K' real tuples lie at or
   // below it, so it bounds the search's K'-th best
-  const unsigned t2 = select_key(keys, nt, K, s_bins, s_sel);
+  const unsigned t2 = select_key(keys, ntot, K, s_bins, s_sel);
   if (threadIdx.x == 0 && t2 != 0xffffffffu) {
     const unsigned b = (t2 & 0x80000000u) ? (t2 & 0x7fffffffu) : ~t2;
     atomicMin(gthr + prob, ord_of((R)__uint_as_float(b)));
@@ -218,14 +285,14 @@ size_t seed_smem_bytes(int K, int S) {
 template <typename R>
 cudaError_t launch_seed(const R *G, const ProbDesc *probs_dev, int n_probs, int K, int S,
                         int seed, double ratio, const Binom &B, u64 *gthr, unsigned *hist,
-                        int max_keys, cudaStream_t st) {
+                        int max_keys, cudaStream_t st, const int *cls) {
   if (max_keys > 50000) max_keys = 50000;   // 200 KB of keys
   const size_t smem = (size_t)4 * (size_t)max_keys;
   cudaError_t e =
       cudaFuncSetAttribute(seed_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   seed_kernel<R><<<n_probs, SEED_THREADS, smem, st>>>(G, probs_dev, K, S, seed, ratio, B, gthr,
-                                                                hist, max_keys);
+                                                                hist, max_keys, cls);
   return cudaGetLastError();
 }
 
@@ -233,9 +300,9 @@ template size_t seed_smem_bytes<double>(int, int);
 template size_t seed_smem_bytes<float>(int, int);
 template cudaError_t launch_seed<double>(const double *, const ProbDesc *, int, int, int, int,
                                          double, const Binom &, u64 *, unsigned *, int,
-                                         cudaStream_t);
+                                         cudaStream_t, const int *);
 template cudaError_t launch_seed<float>(const float *, const ProbDesc *, int, int, int, int,
                                         double, const Binom &, u64 *, unsigned *, int,
-                                        cudaStream_t);
+                                        cudaStream_t, const int *);
 
 }  // namespace l0

@@ -18,9 +18,14 @@
 //   -w = g2 z2_j - w1_k,  t = w^2 - e_j p      (flagged when t >= 0),
 //
 // two tuples per fma.rn.f32x2.  What differs from tile_kernel:
-//  * the two row segments of G[i+1] a step needs (64 + 128 entries) are
-//    copied into shared memory by the TMA unit (cp.async.bulk) through a
-//    ring of four stages with mbarrier completion, three steps ahead;
+//  * steps go in groups of T32_G prefixes: the records of a whole group are
+//    built by all threads together (load-balanced, per-record constants in
+//    shared memory), then every thread runs the test of the group's steps
+//    against the same register tile, with one barrier and one list check
+//    per group instead of per step;
+//  * the row segments of G[i+1] a step needs (64 + 128 entries) are copied
+//    into shared memory by the TMA unit (cp.async.bulk) through a ring of
+//    two groups of stages with mbarrier completion, a group ahead;
 //  * records are stored duplicated ((x, x) pairs) so that every operand of
 //    the packed test comes from one 64- or 128-bit shared load, with no
 //    register moves; each lane holds adjacent column pairs (2 lane, 2 lane+1)
@@ -30,9 +35,10 @@
 //    state); no flag loads or masks in the test;
 //  * the diagonal tile masks k <= j with the sign of (2 lane - j), one
 //    integer add per row; every other tile runs the bare test;
-//  * <= 128 registers, so two 256-thread CTAs share an SM (or one 512-thread
-//    CTA with four rows per warp): barrier waits of one CTA hide behind the
-//    other's work.
+//  * the histogram bound that tightens the global cut is read with cp.async
+//    a phase per group, never waited for inside a group;
+//  * shapes of 256 threads (8 rows per warp, one or two CTAs per SM) and
+//    512 threads (4 rows per warp).
 // Flagged tuples take the same exact path as tile_kernel (FP32 relative
 // score, composite admission with the lexicographic rank, FP64 redo of
 // near-singular tuples), so both kernels produce the same candidate lists.
@@ -45,21 +51,24 @@ namespace {
 
 using namespace tile;
 
-constexpr int T32_NS = 4;          // stages of the Gram-row ring
+constexpr int T32_G = 4;           // prefix steps per group (one barrier each)
+constexpr int T32_NS = 2 * T32_G;  // stages of the Gram-row ring: two groups
 constexpr int T32_JSEG = 68;       // floats of G[i+1][j0 .. j0 + 68)
 constexpr int T32_KSEG = 132;      // floats of G[i+1][k0 - 1 .. k0 + 131)
 constexpr int T32_SEG = T32_JSEG + T32_KSEG;
 constexpr int T32_MAXL = 256;      // prefix steps per item (plan_problems caps L)
+constexpr int T32_NREC = TJ + TK;  // records per step
 
 // Shared memory beyond the CTA list, at fixed offsets from one base pointer
 // (one register addresses all of it):
-//   two record buffers, each
+//   2 T32_G record buffers (two groups), each
 //     row   [TJ] x 32 B: {(-g, -g), (1/l, 1/l)}, {(z2, z2), (e, e)}
 //     jpP   [TJ] floats (pP_j, exact path), jflag [TJ] ints (0 skip, 1 fast,
 //           2 exact, 3 redo in FP64)
 //     kg, kp, kw, kpt [TK] floats
 //   the ring [NS][SEG] floats, the item's prefix scalars C_ii, r_i and class
-//   [MAXL] each, the ring's mbarriers [NS]
+//   [MAXL] each, the item's per-record constants (column, C_cc, r_c, class)
+//   [TJ + TK] each, the ring's mbarriers [NS], the histogram copies
 constexpr int R_ROW = 0;
 constexpr int R_JPP = R_ROW + TJ * 32;
 constexpr int R_JFLAG = R_JPP + TJ * 4;
@@ -68,18 +77,22 @@ constexpr int R_KP = R_KG + TK * 4;
 constexpr int R_KW = R_KP + TK * 4;
 constexpr int R_KPT = R_KW + TK * 4;
 constexpr int T32_REC_BYTES = R_KPT + TK * 4;
-constexpr int O_STAGE = 2 * T32_REC_BYTES;
+constexpr int O_STAGE = 2 * T32_G * T32_REC_BYTES;
 constexpr int O_PDG = O_STAGE + T32_NS * T32_SEG * 4;
 constexpr int O_PRY = O_PDG + T32_MAXL * 4;
 constexpr int O_PCLS = O_PRY + T32_MAXL * 4;
-constexpr int O_BAR = O_PCLS + T32_MAXL * 4;
-constexpr int O_HC = O_BAR + 64;                      // histogram octave counts [256]
+constexpr int O_RCOL = O_PCLS + T32_MAXL * 4;
+constexpr int O_RDG = O_RCOL + T32_NREC * 4;
+constexpr int O_RY = O_RDG + T32_NREC * 4;
+constexpr int O_RCLS = O_RY + T32_NREC * 4;
+constexpr int O_BAR = O_RCLS + T32_NREC * 4;
+constexpr int O_HC = O_BAR + T32_NS * 8;              // histogram octave counts [256]
 constexpr int O_HF = O_HC + L0_HIST_COARSE * 4;       // one octave's fine counts [16]
 constexpr size_t T32_EXTRA_BYTES = (size_t)O_HF + 64;
-static_assert(O_HC % 16 == 0 && O_HF % 16 == 0, "cp.async destinations are 16-byte aligned");
 static_assert(O_STAGE % 16 == 0 && (T32_JSEG * 4) % 16 == 0 && (T32_SEG * 4) % 16 == 0,
               "TMA destinations must be 16-byte aligned");
 static_assert(O_BAR % 8 == 0, "mbarriers are 8-byte aligned");
+static_assert(O_HC % 16 == 0 && O_HF % 16 == 0, "cp.async destinations are 16-byte aligned");
 
 // one record buffer
 struct Rec32 {
@@ -94,6 +107,38 @@ struct Rec32 {
 };
 
 constexpr float T32_MARGIN = (float)(16.0 * 1.1920928955078125e-07);   // 16 ulp of 1
+
+// Shared-memory accesses of the hot path by 32-bit shared addresses
+// (ld.shared / st.shared), so they never go through generic addressing.
+__device__ __forceinline__ u64 lds64(uint32_t a) {
+  u64 v;
+  asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ ulonglong2 lds128(uint32_t a) {
+  ulonglong2 v;
+  asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void sts128(uint32_t a, ulonglong2 v) {
+  asm volatile("st.shared.v2.b64 [%0], {%1, %2};" ::"r"(a), "l"(v.x), "l"(v.y) : "memory");
+}
+__device__ __forceinline__ void sts32(uint32_t a, float v) {
+  asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ void sts32i(uint32_t a, int v) {
+  asm volatile("st.shared.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ float lds32(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ int lds32i(uint32_t a) {
+  int v;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
 
 // ------------------------------------------------- histogram bound, pipelined --
 // The global cut is tightened from the problem's score histogram (see
@@ -200,26 +245,27 @@ __device__ __forceinline__ void step_sync32(CtaList<float> &L, u64 *gthr, u64 gp
   }
 }
 
-// per-thread state of one work item
+// state of one work item shared by the record builds
 struct Item32 {
   ItemCtx<float> c;   // tile position, problem, binomials (shared with tile_kernel's helpers)
   float G00;          // 1 (the scaled target's own entry)
-  // this thread's record column (row record j0 + t or column record k0 + t - TJ)
-  int col;
-  bool isj, isk;
-  float cdiag, cy;
-  int ccls;
 };
 
-// Records of one step.  DP = 1: prefix i with C_ii = pdg, r_i = pry and
-// class pcls, raw entries C_ij / C_ik from the staged row segment; DP = 0:
-// no prefix.  The arithmetic is tile_kernel's rec_compute for these sizes.
+// One record (r < TJ: row record of j0 + r; else column record of
+// k0 + r - TJ) of one step.  DP = 1: prefix i with C_ii = pdg, r_i = pry and
+// class pcls, the raw entry C_i,col from the staged row segment; DP = 0: no
+// prefix.  The arithmetic is tile_kernel's rec_compute for these sizes.
 template <int DP>
-__device__ __forceinline__ void build32(const Item32 &it, int i, float pdg, float pry, int pcls,
-                                        const float *seg, const Rec32 &rb, float cut) {
-  const int t = threadIdx.x;
-  if (!it.isj && !it.isk) return;
+__device__ __forceinline__ void build32(const Item32 &it, unsigned char *sb, int r, int i,
+                                        float pdg, float pry, int pcls, const float *seg,
+                                        const Rec32 &rb, float cut) {
   const ItemCtx<float> &c = it.c;
+  const bool isj = r < TJ;
+  const uint32_t s0 = tc::smem_u32(sb);
+  const int col = lds32i(s0 + O_RCOL + 4u * r);
+  const float cdiag = lds32(s0 + O_RDG + 4u * r);
+  const float cy = lds32(s0 + O_RY + 4u * r);
+  const int ccls = lds32i(s0 + O_RCLS + 4u * r);
   const float ratio = c.ratio;
   float invd = 1.f, zP = 0.f, pPb = it.G00, craw = 0.f;
   bool pok = true;
@@ -229,16 +275,16 @@ __device__ __forceinline__ void build32(const Item32 &it, int i, float pdg, floa
     zP = pry * invd;
     pPb = it.G00 - zP * zP;
     // seg: [JSEG] = G[i+1][j0 ..), then [KSEG] = G[i+1][k0 - 1 ..)
-    craw = it.isj ? seg[t + 1] : seg[T32_JSEG + (t - TJ) + 2];
+    craw = isj ? seg[r + 1] : seg[T32_JSEG + (r - TJ) + 2];
   }
-  const bool inm = it.col < c.m;
+  const bool inm = col < c.m;
   const float g = craw * invd;
-  const float piv = it.cdiag - g * g;
-  const float w1 = it.cy - g * zP;
-  const bool elig = (it.cdiag > 0.f) && (piv >= ratio * it.cdiag);
-  const bool dup = DP == 1 && c.cls != nullptr && inm && pcls == it.ccls;
-  if (it.isj) {
-    const bool shape = inm && (DP == 0 || i < it.col);
+  const float piv = cdiag - g * g;
+  const float w1 = cy - g * zP;
+  const bool elig = (cdiag > 0.f) && (piv >= ratio * cdiag);
+  const bool dup = DP == 1 && c.cls != nullptr && inm && pcls == ccls;
+  if (isj) {
+    const bool shape = inm && (DP == 0 || i < col);
     const float invl = rsqrtf(piv > 0.f ? piv : 1.f);
     const float z2 = w1 * invl;
     const float pPj = pPb - z2 * z2;
@@ -254,17 +300,19 @@ __device__ __forceinline__ void build32(const Item32 &it, int i, float pdg, floa
     a.y = f2_pack(il, il);
     b.x = f2_pack(zz, zz);
     b.y = f2_pack(ee, ee);
-    rb.row()[2 * t] = a;
-    rb.row()[2 * t + 1] = b;
-    rb.jpP()[t] = fast ? pPj : 0.f;
-    rb.jflag()[t] = flag;
+    const uint32_t rs = tc::smem_u32(rb.p);
+    sts128(rs + R_ROW + (uint32_t)r * 32u, a);
+    sts128(rs + R_ROW + (uint32_t)r * 32u + 16u, b);
+    sts32(rs + R_JPP + (uint32_t)r * 4u, fast ? pPj : 0.f);
+    sts32i(rs + R_JFLAG + (uint32_t)r * 4u, flag);
   } else {
-    const int kk = t - TJ;
-    const float kpt = ratio * it.cdiag;
-    rb.kg()[kk] = inm ? g : 0.f;
-    rb.kp()[kk] = (!inm || dup) ? -r_inf<float>() : (elig ? kpt - piv : r_inf<float>());
-    rb.kw()[kk] = inm ? -w1 : 0.f;
-    rb.kpt()[kk] = inm ? kpt : 0.f;
+    const uint32_t kk4 = (uint32_t)(r - TJ) * 4u;
+    const float kpt = ratio * cdiag;
+    const uint32_t rs = tc::smem_u32(rb.p);
+    sts32(rs + R_KG + kk4, inm ? g : 0.f);
+    sts32(rs + R_KP + kk4, (!inm || dup) ? -r_inf<float>() : (elig ? kpt - piv : r_inf<float>()));
+    sts32(rs + R_KW + kk4, inm ? -w1 : 0.f);
+    sts32(rs + R_KPT + kk4, inm ? kpt : 0.f);
   }
 }
 
@@ -273,21 +321,22 @@ __device__ __forceinline__ void build32(const Item32 &it, int i, float pdg, floa
 // flagged).  In the diagonal tile (k0 = j0 + 1) column 2 lane + b of half q = 0
 // is k <= j exactly when 2 lane + b - jl < 0: that sign is OR-ed in.
 template <int UJ, bool DIAG>
-__device__ __forceinline__ unsigned fast32(const u64 (&creg)[UJ][2], const Rec32 &rb, int w,
-                                           int lane) {
+__device__ __forceinline__ unsigned fast32(const u64 (&creg)[UJ][2], uint32_t rw, uint32_t rl,
+                                           int d0base) {
+  // rw = record buffer + row records of this warp's first row; rl = record
+  // buffer + this lane's first column pair (kg); the rest are immediates
   u64 kg[2], kp[2], kw[2];
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
-    const int kk = 2 * lane + 64 * q;
-    kg[q] = *(const u64 *)(rb.kg() + kk);
-    kp[q] = *(const u64 *)(rb.kp() + kk);
-    kw[q] = *(const u64 *)(rb.kw() + kk);
+    kg[q] = lds64(rl + 256u * q);
+    kp[q] = lds64(rl + (R_KP - R_KG) + 256u * q);
+    kw[q] = lds64(rl + (R_KW - R_KG) + 256u * q);
   }
   unsigned acc = 0xffffffffu;
 #pragma unroll
   for (int u = 0; u < UJ; ++u) {
-    const int jl = w * UJ + u;
-    const ulonglong2 a = rb.row()[2 * jl], b = rb.row()[2 * jl + 1];
+    const ulonglong2 a = lds128(rw + 32u * u);
+    const ulonglong2 b = lds128(rw + 32u * u + 16u);
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const u64 h = f2_fma(a.x, kg[q], creg[u][q]);
@@ -297,7 +346,7 @@ __device__ __forceinline__ unsigned fast32(const u64 (&creg)[UJ][2], const Rec32
       const u64 t = f2_fma(b.y, ppn, f2_mul(wn, wn));
       const unsigned lo = (unsigned)t, hi = (unsigned)(t >> 32);
       if (DIAG && q == 0) {
-        const int d0 = 2 * lane - jl;
+        const int d0 = d0base - u;   // 2 lane - jl: negative where k <= j
         acc &= (lo | (unsigned)d0) & (hi | (unsigned)(d0 + 1));
       } else {
         acc &= lo & hi;
@@ -434,11 +483,46 @@ __device__ __forceinline__ void issue32(const ItemCtx<float> &c, unsigned char *
   tc::bulk_load(dst + T32_JSEG * 4, c.G + ks, (uint32_t)(kn * 4), bar);
 }
 
+// Records of group g (steps g G .. g G + G - 1 < nsteps) into the group's
+// buffers: all threads, records spread round-robin; each waits for the ring
+// stage of the step it builds.  `cons` = ring copies consumed before this item.
+template <int DP>
+__device__ __forceinline__ void build_group32(const TileArgs<float> &A, const Item32 &it,
+                                              unsigned char *sb, int g, int nsteps, int i0,
+                                              unsigned cons, float cut) {
+  const float *pdg = (const float *)(sb + O_PDG), *pry = (const float *)(sb + O_PRY);
+  const int *pcls = (const int *)(sb + O_PCLS);
+  const int s0 = g * T32_G;
+  const int ns = min(T32_G, nsteps - s0);
+  for (int x = threadIdx.x; x < ns * T32_NREC; x += blockDim.x) {
+    const int q = x / T32_NREC, r = x - q * T32_NREC;
+    const int s = s0 + q;
+    const unsigned copy = cons + (unsigned)s;
+    const float *seg = nullptr;
+    if (DP == 1) {
+      tc::mbar_wait(tc::smem_u32(sb + O_BAR + 8 * (copy % T32_NS)), (copy / T32_NS) & 1u, A.err);
+      seg = (const float *)(sb + O_STAGE) + (copy % T32_NS) * T32_SEG;
+    }
+    const Rec32 rb{sb + ((g & 1) * T32_G + q) * T32_REC_BYTES};
+    build32<DP>(it, sb, r, i0 + s, DP == 1 ? pdg[s] : 0.f, DP == 1 ? pry[s] : 0.f,
+                DP == 1 ? pcls[s] : -1, seg, rb, cut);
+  }
+}
+
+// thread 0: the ring copies of group g's steps
+__device__ __forceinline__ void issue_group32(const ItemCtx<float> &c, unsigned char *sb, int g,
+                                              int nsteps, int i0, unsigned cons) {
+  for (int s = g * T32_G; s < nsteps && s < (g + 1) * T32_G; ++s)
+    issue32(c, sb, i0 + s, cons + (unsigned)s);
+}
+
 // One work item: the (j, k) tile against prefixes [r0, r1) (DP = 1) or the
 // single prefix-free step (DP = 0).  `cons` counts the ring copies this CTA
 // has consumed (the ring slot and mbarrier parity of every copy follow).
+// Group g's records are built while group g - 1 is tested; group g + 2's
+// rows are copied into the stages group g's used, after the barrier.
 template <int DP, int UJ>
-__device__ void run32(const TileArgs<float> &A, const ProbDesc &pd, int prob, int bj, int bk,
+__device__ __forceinline__ void run32(const TileArgs<float> &A, const ProbDesc &pd, int prob, int bj, int bk,
                       u64 r0, u64 r1, CtaList<float> &L, unsigned char *sb, u64 *gthr,
                       unsigned &cons) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -465,11 +549,14 @@ __device__ void run32(const TileArgs<float> &A, const ProbDesc &pd, int prob, in
     set_err(A.err, 9);
     return;
   }
-  float *pdg = (float *)(sb + O_PDG), *pry = (float *)(sb + O_PRY);
-  int *pcls = (int *)(sb + O_PCLS);
+  const int ngroups = (nsteps + T32_G - 1) / T32_G;
   if (DP == 1) {
-    if (tid == 0)
-      for (int s = 0; s < nsteps && s < T32_NS; ++s) issue32(c, sb, i0 + s, cons + s);
+    if (tid == 0) {
+      issue_group32(c, sb, 0, nsteps, i0, cons);
+      issue_group32(c, sb, 1, nsteps, i0, cons);
+    }
+    float *pdg = (float *)(sb + O_PDG), *pry = (float *)(sb + O_PRY);
+    int *pcls = (int *)(sb + O_PCLS);
     for (int s = tid; s < nsteps; s += blockDim.x) {
       const int i = i0 + s;
       pdg[s] = G[(long long)(i + 1) * (ld + 1)];
@@ -477,16 +564,19 @@ __device__ void run32(const TileArgs<float> &A, const ProbDesc &pd, int prob, in
       pcls[s] = c.cls ? __ldg(c.cls + i) : -1;
     }
   }
-  it.isj = tid < TJ;
-  it.isk = !it.isj && tid < TJ + TK;
-  it.col = it.isj ? c.j0 + tid : (it.isk ? c.k0 + tid - TJ : -1);
-  it.cdiag = 0.f;
-  it.cy = 0.f;
-  it.ccls = -2;
-  if (it.col >= 0 && it.col < c.m) {
-    it.cdiag = G[(long long)(it.col + 1) * (ld + 1)];
-    it.cy = G[it.col + 1];
-    if (c.cls) it.ccls = __ldg(c.cls + it.col);
+  for (int r = tid; r < T32_NREC; r += blockDim.x) {
+    const int col = r < TJ ? c.j0 + r : c.k0 + r - TJ;
+    float dg = 0.f, cy = 0.f;
+    int cc = -2;
+    if (col < c.m) {
+      dg = G[(long long)(col + 1) * (ld + 1)];
+      cy = G[col + 1];
+      if (c.cls) cc = __ldg(c.cls + col);
+    }
+    ((int *)(sb + O_RCOL))[r] = col;
+    ((float *)(sb + O_RDG))[r] = dg;
+    ((float *)(sb + O_RY))[r] = cy;
+    ((int *)(sb + O_RCLS))[r] = cc;
   }
   // the tile's Gram entries: rows j0 + w UJ + u, columns k0 + 2 lane + {0, 1} + 64 q
   u64 creg[UJ][2];
@@ -504,33 +594,48 @@ __device__ void run32(const TileArgs<float> &A, const ProbDesc &pd, int prob, in
       creg[u][q] = v;
     }
   }
-  __syncthreads();   // prefix scalars visible
-  const bool rec = it.isj || it.isk;
-  if (DP == 1 && rec)
-    tc::mbar_wait(tc::smem_u32(sb + O_BAR + 8 * (cons % T32_NS)), (cons / T32_NS) & 1u, A.err);
-  build32<DP>(it, i0, DP == 1 ? pdg[0] : 0.f, DP == 1 ? pry[0] : 0.f, DP == 1 ? pcls[0] : -1,
-              (const float *)(sb + O_STAGE) + (cons % T32_NS) * T32_SEG, Rec32{sb},
-              cta_cut<float>(L));
+  __syncthreads();   // prefix scalars and record constants visible
+  build_group32<DP>(A, it, sb, 0, nsteps, i0, cons, cta_cut<float>(L));
   __syncthreads();
-  if (DP == 1 && tid == 0 && T32_NS < nsteps) issue32(c, sb, i0 + T32_NS, cons + T32_NS);
-  u64 gnext = ~0ull;   // warp 0: the global bound, read a step before it is used
+  if (DP == 1 && tid == 0) issue_group32(c, sb, 2, nsteps, i0, cons);
+  u64 gnext = ~0ull;   // warp 0: the global bound, read a group before it is used
   HistPipe hp{0, 0, 0u};
-  for (int s = 0; s < nsteps; ++s) {
-    const Rec32 rb{sb + (s & 1) * T32_REC_BYTES};
+  const uint32_t sbs = tc::smem_u32(sb);
+  const int d0b = 2 * lane - w * UJ;   // diagonal tile: 2 lane - jl = d0b - u
+  for (int g = 0; g < ngroups; ++g) {
     const u64 gprev = gnext;
     if (tid < 32) gnext = ld_relaxed(gthr);
-    if (DP == 1 && s + 1 < nsteps) {
-      const unsigned q = cons + (unsigned)s + 1u;
-      if (rec) tc::mbar_wait(tc::smem_u32(sb + O_BAR + 8 * (q % T32_NS)), (q / T32_NS) & 1u, A.err);
-      build32<DP>(it, i0 + s + 1, pdg[s + 1], pry[s + 1], pcls[s + 1],
-                  (const float *)(sb + O_STAGE) + (q % T32_NS) * T32_SEG,
-                  Rec32{sb + ((s + 1) & 1) * T32_REC_BYTES}, cta_cut<float>(L));
-    }
-    unsigned done = 0u;
+    if (g + 1 < ngroups) build_group32<DP>(A, it, sb, g + 1, nsteps, i0, cons, cta_cut<float>(L));
+    const int ns = min(T32_G, nsteps - g * T32_G);
+    unsigned done[T32_G];
+#pragma unroll
+    for (int q = 0; q < T32_G; ++q) done[q] = 0u;
+    const uint32_t gb = sbs + (uint32_t)((g & 1) * (T32_G * T32_REC_BYTES));
+    const uint32_t rw = gb + R_ROW + (uint32_t)(w * UJ * 32), rl = gb + R_KG + 8u * lane;
     for (int pass = 0;; ++pass) {
-      const unsigned acc = c.diag ? fast32<UJ, true>(creg, rb, w, lane)
-                                  : fast32<UJ, false>(creg, rb, w, lane);
-      if (!(acc >> 31)) recheck32<DP, UJ>(A, c, rb, L, i0 + s, &done);
+      unsigned acc[T32_G];
+      if (ns == T32_G) {   // a full group: the tests straight through, one check
+#pragma unroll
+        for (int q = 0; q < T32_G; ++q)
+          acc[q] = c.diag ? fast32<UJ, true>(creg, rw + q * T32_REC_BYTES, rl + q * T32_REC_BYTES, d0b)
+                          : fast32<UJ, false>(creg, rw + q * T32_REC_BYTES, rl + q * T32_REC_BYTES, d0b);
+      } else {
+#pragma unroll
+        for (int q = 0; q < T32_G; ++q)
+          acc[q] = q >= ns ? 0xffffffffu
+                   : c.diag ? fast32<UJ, true>(creg, rw + q * T32_REC_BYTES, rl + q * T32_REC_BYTES, d0b)
+                            : fast32<UJ, false>(creg, rw + q * T32_REC_BYTES, rl + q * T32_REC_BYTES, d0b);
+      }
+      unsigned all = 0xffffffffu;
+#pragma unroll
+      for (int q = 0; q < T32_G; ++q) all &= acc[q];
+      if (!(all >> 31)) {
+#pragma unroll
+        for (int q = 0; q < T32_G; ++q)
+          if (q < ns && !(acc[q] >> 31))
+            recheck32<DP, UJ>(A, c, Rec32{sb + ((g & 1) * T32_G + q) * T32_REC_BYTES}, L,
+                              i0 + g * T32_G + q, &done[q]);
+      }
       __syncthreads();
       const bool ovf = *(volatile int *)L.ovf != 0;
       if (ovf || *(volatile int *)L.n_stage > L.S / 2) cta_list_commit<float>(L, gthr);
@@ -540,9 +645,8 @@ __device__ void run32(const TileArgs<float> &A, const ProbDesc &pd, int prob, in
         break;
       }
     }
-    // the stage that held step s + 1's row is free after the barrier above
-    if (DP == 1 && tid == 0 && s + 1 + T32_NS < nsteps)
-      issue32(c, sb, i0 + s + 1 + T32_NS, cons + (unsigned)(s + 1 + T32_NS));
+    // the stages that held group g + 1's rows are free after the barrier above
+    if (DP == 1 && tid == 0) issue_group32(c, sb, g + 3, nsteps, i0, cons);
     step_sync32(L, gthr, gprev, hp, sb);
   }
   if (tid < 32) cp_async_wait_all();   // no copy into the histogram buffers outlives the item

@@ -93,7 +93,25 @@ def test_autotuner_choice_is_persisted_and_results_unchanged(tmp_path):
     with l0.Handle(precision=l0.MIXED_BF16X3, autotune=1, autotune_cache_path=cache) as h:
         t1, r1 = h.fit(prob.X, prob.y, 3, 40)
         st1 = h.stats()
-    assert (st1["tuned_items_factor"], st1["tuned_ctas_per_sm"]) == \
-        (st["tuned_items_factor"], st["tuned_ctas_per_sm"])
+    assert (st1["tuned_items_factor"], st1["tuned_ctas_per_sm"], st1["tuple_kernel"]) == \
+        (st["tuned_items_factor"], st["tuned_ctas_per_sm"], st["tuple_kernel"])
     np.testing.assert_array_equal(t0, t1)
     _check_list(prob, 3, 40, t0[0], r0[0])
+    # each line: key, items per CTA factor, CTAs per SM, kernel shape (the shape
+    # the fit ran: the d <= 3 FP32 kernel's shapes are among the candidates)
+    rec = [ln.split() for ln in lines if ln.strip()]
+    assert all(len(f) == 4 for f in rec)
+    assert (int(rec[-1][1]), int(rec[-1][3])) == (st["tuned_items_factor"], st["tuple_kernel"])
+    assert st["tuple_kernel"] in (0, 1, 2, 3)
+
+
+@pytest.mark.parametrize("v", [0, 1, 2, 3])
+def test_forced_kernel_shape_is_the_one_tuned_and_run(tmp_path, v):
+    # with a fixed shape the autotuner only times launch configurations of it
+    prob = make_problem(200, 190, seed=406, n_planted=3, sigma=0.02)
+    with l0.Handle(precision=l0.MIXED_BF16X3, autotune=1, tuple_kernel=v,
+                   autotune_cache_path=str(tmp_path / "t.txt")) as h:
+        t, r = h.fit(prob.X, prob.y, 3, 30)
+        st = h.stats()
+    assert st["tuple_kernel"] == v
+    _check_list(prob, 3, 30, t[0], r[0])

@@ -22,6 +22,7 @@ pytestmark = pytest.mark.gpu
 # 1 / min(1 - r_i^2, 1 - r_j^2, 1 - C_ij^2) (a planted column has r ~ 0.9997).
 FEAT_ATOL = 1e-3
 FEAT_AMP = 1e-5
+EPS_G = 5e-6      # split-BF16 Gram entry error against the FP64 correlation
 # The network: FP32 sums in a different order than the oracle's exact sums
 # can move a BF16-rounded activation by one BF16 ulp (2^-8 relative); summed
 # over a batch such flips stay well under 2 % of a gradient's norm.
@@ -69,6 +70,31 @@ def test_pair_labels_match_oracle():
     # log of an FP32 Schur complement with ~1e-5 absolute error
     np.testing.assert_allclose(got[big], ref[big], atol=0.02)
     assert np.all(got[~big] < np.log(2e-3))
+    # The best completions (relative SSE <= 1e-3, the pairs the scorer must
+    # rank first) in linear space.  rel = 1 - c^T C^-1 c over the standardized
+    # columns moves by at most eps (1 + |beta|_1)^2 to first order when every
+    # Gram entry moves by eps (beta = C^-1 c, the standardized coefficients),
+    # and the minimum over k moves by at most the largest such move: with
+    # eps = EPS_G, doubled for the second order, plus FP32 rounding of O(1)
+    # terms.
+    pairs = ol.all_pairs(30)
+    Z = (p.X - p.X.mean(axis=1, keepdims=True))
+    Z /= np.linalg.norm(Z, axis=1, keepdims=True)
+    yz = p.y - p.y.mean()
+    yz /= np.linalg.norm(yz)
+    for q in np.flatnonzero(~big):
+        i, j = pairs[q]
+        best_k, best = -1, np.inf
+        for kk in range(30):
+            if kk in (i, j):
+                continue
+            A = Z[[i, j, kk]].T
+            beta, *_ = np.linalg.lstsq(A, yz, rcond=None)
+            r = yz - A @ beta
+            if r @ r < best:
+                best, best_k, bb = float(r @ r), kk, beta
+        tol = 2.0 * EPS_G * (1.0 + np.abs(bb).sum()) ** 2 + 1e-6
+        assert abs(np.exp(got[q]) - rel[q]) <= tol, (q, np.exp(got[q]), rel[q], tol)
     # the planted triple's pairs complete it best
     assert np.argmin(got) == np.argmin(ref) or abs(got.min() - ref.min()) < 1.0
 
