@@ -101,10 +101,8 @@ def flops_per_tuple_hoisted(d):
     # the per-tuple count of the (d-1)-prefix hoisted augmented-Cholesky form:
     # forward solve g = L_P^-1 C_Pk ((d-1)(d-2)/2 FMA + (d-1) MUL), pivot
     # p = C_kk - g.g (d-1 FMA), w = c_k - g.z_P (d-1 FMA), SSE/S_yy = p_P - w^2/p
-    # (1 reciprocal + 2 MUL/FMA); FMA = 2 flop, MUL = 1  ->  15 at d = 3
-    fma = (d - 1) * (d - 2) // 2 + 2 * (d - 1) + 1
-    mul = (d - 1) + 1
-    return 2 * fma + mul + 1
+    # (1 reciprocal + 2 multiplications); FMA = 2 flop -> 8, 15, 24 at d = 2, 3, 4
+    return (d - 1) * (d - 2) + 5 * (d - 1) + 3
 
 
 def _dist():

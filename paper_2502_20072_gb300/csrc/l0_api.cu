@@ -89,6 +89,8 @@ struct sisso_l0_handle {
   DevBuf prop_in, prop_pairs, prop_bits, prop_ctr, sel_hist, sel_bin, scores, diag;
   DevBuf col_hash, col_cls;
   DevBuf band_thr, band_floor;                        // band pass: cut, previous delta
+  DevBuf g64_have;                                    // the fit's FP64 Gram exists (mixed)
+  DevBuf dfr_bctr;                                    // FP64 redo: run batches handed out
   DevBuf sis_ex, sis_y;                               // screening: exclusions, targets
   DevBuf gen_ops, gen_c1, gen_c2, gen_valid;          // generated candidates
   DevBuf loop_x, loop_y, loop_xs, loop_res, loop_q, loop_tup, loop_rows;   // dimension loop
@@ -284,7 +286,7 @@ struct FitPlan {
   std::function<int(sisso_l0_t, FitPlan &)> after_prep;
 };
 
-constexpr int kDeferGroups = 64;
+constexpr int kDeferGroups = 148;   // FP64 redo CTAs (and candidate lists) per problem
 constexpr double kBandMargin = 8.0;   // band cut = k-th re-fitted score + 8 delta
 constexpr long long kDeferCap = 1LL << 24;
 
@@ -413,6 +415,7 @@ int setup_search(sisso_l0_t h, FitPlan &P, int K) {
   if (P.mixed && P.has_tuples) {
     L0_CK(h->dfr_key.ensure((size_t)kDeferCap * 8), "alloc deferral buffer");
     L0_CK(h->dfr_len.ensure((size_t)kDeferCap * 4), "alloc deferral buffer");
+    L0_CK(h->dfr_bctr.ensure((size_t)n_probs * 4), "alloc deferral counters");
     if (P.m <= 8192) L0_CK(h->gram.ensure((size_t)P.T * P.gstride * 8), "alloc Gram");
   }
   const int S = staging_for(K);
@@ -470,6 +473,7 @@ int prep_pass(sisso_l0_t h, FitPlan &P) {
           "gram kernel");
   } else {
     const size_t abytes = (size_t)(m + 1) * P.ldk * 2;
+    L0_CK(cudaMemsetAsync(h->g64_have.p, 0, 4, st), "memset");   // new data: no FP64 Gram yet
     L0_CK(cudaMemsetAsync(h->abf.p, 0, abytes, st), "memset");
     L0_CK(cudaMemsetAsync(h->bbf.p, 0, abytes, st), "memset");
     const int *kbeg = h->kmeta.as<int>();
@@ -632,11 +636,14 @@ int search_pass(sisso_l0_t h, FitPlan &P, int K, const R *G) {
       // FP64 Gram and the Gram-mode redo run only when many were queued, the
       // dot-product redo only when a few were (decided on the device)
       const bool can_gram = P.m <= 8192;
-      if (can_gram)
+      if (can_gram) {
         L0_CK(l0::launch_gram64(h->w64.as<double>(), P.N, P.m, P.off.data(), P.T,
                                 h->gram.as<double>(), P.ld, P.gstride, st, h->dfr_n.as<u64>(),
-                                P.dmax),
+                                P.dmax, 0, h->g64_have.as<int>()),
               "gram kernel");
+        L0_CK(l0::launch_mark_gram64(h->dfr_n.as<u64>(), P.m, P.dmax, h->g64_have.as<int>(), st),
+              "gram mark kernel");
+      }
       l0::DeferArgs da{};
       da.G64 = can_gram ? h->gram.as<double>() : nullptr;
       da.ld64 = P.ld;
@@ -663,6 +670,8 @@ int search_pass(sisso_l0_t h, FitPlan &P, int K, const R *G) {
       da.shared_T = P.shared ? P.T : 0;
       da.inv_s = h->inv_s.as<double>();
       da.mp1 = P.m + 1;
+      da.batch_ctr = h->dfr_bctr.as<unsigned>();
+      L0_CK(cudaMemsetAsync(h->dfr_bctr.p, 0, (size_t)n_probs * 4, st), "memset");
       L0_CK(l0::launch_defer(da, kDeferGroups, n_probs, st), "defer kernel");
     }
   }
@@ -931,7 +940,7 @@ std::string graph_key(sisso_l0_t h, const FitPlan &P, int K) {
                           &h->done, &h->pool_s, &h->pool_k, &h->pool_cnt, &h->scratch, &h->refit,
                           &h->rdiv, &h->cert, &h->out_t, &h->out_r, &h->err, &h->dfr_key,
                           &h->dfr_len, &h->dfr_n, &h->abf, &h->bbf, &h->kmeta, &h->gram32,
-                          &h->col_hash, &h->col_cls};
+                          &h->col_hash, &h->col_cls, &h->g64_have, &h->dfr_bctr};
   for (const DevBuf *b : bufs) {
     snprintf(buf, sizeof(buf), "|%p", b->p);
     k += buf;
@@ -1121,6 +1130,7 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
     rc = upload(h, h->kmeta.p, meta.data(), meta.size() * 4, &h->up_kmeta);
     if (rc) return rc;
     L0_CK(h->gram32.ensure((size_t)n_tasks * P.gstride * 4), "alloc Gram");
+    L0_CK(h->g64_have.ensure(4), "alloc");
   }
   // persistent grid of the tuple kernel (or of the proposal search)
   if (P.has_tuples && P.proposal) {
@@ -1134,8 +1144,8 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
     P.grid = h->n_sm * bps;
   } else if (P.has_tuples) {
     int bps = 0;
-    // default shape: the d <= 3 FP32 kernel with two CTAs per SM where it applies
-    const int want = h->opt.tuple_kernel < 0 ? 2 : h->opt.tuple_kernel;
+    // default shape: the d <= 3 FP32 kernel, 512 threads, where it applies
+    const int want = h->opt.tuple_kernel < 0 ? 3 : h->opt.tuple_kernel;
     P.variant = tile32_ok(P, want) ? want : 0;
     rc = P.mixed ? tile_bps<float>(h, P, Kmax, &bps) : tile_bps<double>(h, P, Kmax, &bps);
     if (rc) return rc;
@@ -1449,7 +1459,7 @@ void sisso_l0_destroy(sisso_l0_t h) {
                     &h->scores, &h->diag, &h->col_hash, &h->col_cls, &h->sis_ex, &h->sis_y,
                     &h->gen_ops, &h->gen_c1, &h->gen_c2, &h->gen_valid, &h->loop_x, &h->loop_y,
                     &h->loop_xs, &h->loop_res, &h->loop_q, &h->loop_tup, &h->loop_rows,
-                    &h->band_thr, &h->band_floor};
+                    &h->band_thr, &h->band_floor, &h->g64_have, &h->dfr_bctr};
   for (DevBuf *b : bufs) b->release();
   if (h->pin) cudaFreeHost(h->pin);
   if (h->ev_pin) cudaEventDestroy(h->ev_pin);

@@ -164,6 +164,99 @@ defer_gram_kernel(DeferArgs a) {
   cta_list_flush<float>(L, a.out_s + slot * a.K, a.out_k + slot * a.K, a.out_cnt + slot);
 }
 
+// Gram mode, one task per problem: warps take batches of 32 consecutive
+// queued runs from the problem's counter and score the batch's tuples
+// together -- a warp-wide scan of the run lengths spreads them over the 32
+// lanes -- so single-tuple runs and 128-tuple runs share the work evenly.
+// Each run is unranked once by the lane that read it; a tuple's indices come
+// from that lane by shuffle, its last index advanced by the tuple's offset in
+// the run.  A round ends at a CTA barrier, where the list folds (and, on an
+// overflow of its staging area, the round is redone, the same batches).
+__global__ void __launch_bounds__(L0_THREADS)
+defer_batch_kernel(DeferArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long s_batch[L0_THREADS / 32];
+  __shared__ int s_more;
+  const unsigned FULL = 0xffffffffu;
+  const int prob = blockIdx.y;
+  const ProbDesc pd = a.probs[prob];
+  if (!defer_wants_gram(a.n_runs[1], pd.m, pd.d)) return;
+  unsigned char *p = smem;
+  CtaList<float> L = cta_list_carve<float>(p, a.K, a.S);
+  const int d = pd.d;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  cta_list_reset<float>(L, a.gthr + prob);
+  const long long nr = (long long)a.n_runs[0];
+  const long long nrun = nr < a.cap ? nr : a.cap;
+  const unsigned long long nbatch = (unsigned long long)((nrun + 31) / 32);
+  const GramEnt ent{a.G64 + (long long)pd.task * a.g64_stride, a.ld64};
+  unsigned long long done_tuples = 0;
+  for (;;) {
+    if (lane == 0) s_batch[warp] = atomicAdd(a.batch_ctr + prob, 1u);
+    if (threadIdx.x == 0) s_more = 0;
+    __syncthreads();
+    const unsigned long long b = s_batch[warp];
+    if (lane == 0 && b < nbatch) atomicOr(&s_more, 1);
+    __syncthreads();
+    if (!s_more) break;   // every warp of the CTA is past the last batch (uniform)
+    const long long r = (long long)b * 32 + lane;
+    int len = 0;
+    u64 key0 = 0;
+    if (b < nbatch && r < nrun) {
+      const unsigned pl = a.run_len[r];
+      if ((int)(pl >> 8) == prob) {
+        len = (int)(pl & 0xffu);
+        key0 = a.run_key[r];
+      }
+    }
+    int t[L0_DMAX];
+#pragma unroll
+    for (int q = 0; q < L0_DMAX; ++q) t[q] = 0;
+    if (len > 0) lex_unrank(a.B, pd.m, d, key0, pd.total, t);
+    int inc = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc += v;
+    }
+    const int total = __shfl_sync(FULL, inc, 31);
+    if (lane == 0) done_tuples += (unsigned long long)total;
+    int redo = 0;
+    do {
+      for (int base = 0; base < total; base += 32) {   // uniform over the warp
+        const int x = base + lane;
+        // owner: the lane whose run holds tuple x (the first with inc > x)
+        int own = 0;
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) {
+          const int v = __shfl_sync(FULL, inc, own + s - 1);
+          if (v <= x) own += s;
+        }
+        own = own > 31 ? 31 : own;
+        const int oinc = __shfl_sync(FULL, inc, own), olen = __shfl_sync(FULL, len, own);
+        const u64 okey = __shfl_sync(FULL, key0, own);
+        int tt[L0_DMAX];
+#pragma unroll
+        for (int q = 0; q < L0_DMAX; ++q) tt[q] = __shfl_sync(FULL, t[q], own);
+        if (x >= total) continue;
+        const int e = x - (oinc - olen);
+        PrefixFactor f;
+        factor_prefix(ent, tt, d - 1, a.ratio, f);
+        double rel;
+        if (!f.ok || !score_last(ent, tt, d - 1, tt[d - 1] + e, a.ratio, f, &rel)) continue;
+        const float s = (float)rel;
+        const u64 key = okey + (u64)e;
+        if (cta_list_admits<float>(L, s, key)) cta_list_push<float>(L, s, key);
+      }
+      __syncthreads();
+      if (++redo > L0_MAX_REDO) break;
+    } while (cta_list_fold<float>(L, a.gthr + prob));
+  }
+  if (done_tuples) atomicAdd(a.n_tuples, done_tuples);
+  const size_t slot = (size_t)prob * a.n_slots + a.slot0 + blockIdx.x;
+  cta_list_flush<float>(L, a.out_s + slot * a.K, a.out_k + slot * a.K, a.out_cnt + slot);
+}
+
 // Dot mode (few queued tuples): one CTA per run at a time.  The CTA computes
 // the FP64 correlations the run needs -- rows (target, prefix) against
 // (target, prefix, every k of the run), and each k with itself -- as dot
@@ -312,8 +405,15 @@ cudaError_t launch_defer(const DeferArgs &a, int groups, int n_probs, cudaStream
   e = cudaFuncSetAttribute(defer_dot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
   if (e != cudaSuccess) return e;
-  if (a.G64) {
+  if (a.G64 && a.shared_T > 0) {
     defer_gram_kernel<<<dim3(groups, n_probs), L0_THREADS, smem, st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  } else if (a.G64) {
+    e = cudaFuncSetAttribute(defer_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    defer_batch_kernel<<<dim3(groups, n_probs), L0_THREADS, smem, st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

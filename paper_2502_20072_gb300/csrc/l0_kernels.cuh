@@ -125,7 +125,10 @@ cudaError_t launch_gram64(const double *W64, long long n_total, int m,
                           const long long *offsets_host, int T, double *G,
                           long long ld, long long g_stride, cudaStream_t st,
                           const u64 *gate = nullptr, int gate_d = 0,
-                          int upper_only = 0);
+                          int upper_only = 0, const int *skip = nullptr);
+// after a gated FP64 Gram: *have = 1 when the gate let it run (a later pass of
+// the same fit can skip it through launch_gram64's skip flag)
+cudaError_t launch_mark_gram64(const u64 *gate, int m, int gate_d, int *have, cudaStream_t st);
 
 template <typename R>
 cudaError_t launch_tile(const TileArgs<R> &a, int dp_lo, int dp_hi, int grid,
@@ -256,6 +259,7 @@ struct DeferArgs {
   int shared_T;
   const double *inv_s;
   int mp1;
+  unsigned *batch_ctr;         // [n_probs] run batches handed out (zeroed before the launch)
 };
 // both launched; exactly one does work (see defer_wants_gram)
 cudaError_t launch_defer(const DeferArgs &a, int groups, int n_probs, cudaStream_t st);

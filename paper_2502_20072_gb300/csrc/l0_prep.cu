@@ -140,7 +140,8 @@ cudaError_t launch_centre(const double *X, const double *y, long long n_total,
 __global__ void __launch_bounds__(256)
 gram64_kernel(const double *__restrict__ W, long long n_total, int mp1,
               long long lo, long long hi, double *__restrict__ G, long long ld,
-              int nb, const u64 *gate, int gate_d, int upper_only) {
+              int nb, const u64 *gate, int gate_d, int upper_only, const int *skip) {
+  if (skip && *skip) return;   // computed by an earlier pass of this fit
   if (gate && !defer_wants_gram(gate[1], mp1 - 1, gate_d)) return;
   // decode the upper-triangular tile index (bi <= bj)
   int idx = blockIdx.x;
@@ -201,7 +202,7 @@ gram64_kernel(const double *__restrict__ W, long long n_total, int mp1,
 cudaError_t launch_gram64(const double *W64, long long n_total, int m,
                           const long long *offsets_host, int T, double *G,
                           long long ld, long long g_stride, cudaStream_t st,
-                          const u64 *gate, int gate_d, int upper_only) {
+                          const u64 *gate, int gate_d, int upper_only, const int *skip) {
   const int mp1 = m + 1;
   const int nb = (mp1 + 63) / 64;
   const int ntiles = nb * (nb + 1) / 2;
@@ -209,11 +210,20 @@ cudaError_t launch_gram64(const double *W64, long long n_total, int m,
     gram64_kernel<<<ntiles, 256, 0, st>>>(W64, n_total, mp1, offsets_host[t],
                                           offsets_host[t + 1],
                                           G + (long long)t * g_stride, ld, nb, gate, gate_d,
-                                          upper_only);
+                                          upper_only, skip);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+__global__ void mark_gram64_kernel(const u64 *gate, int m, int gate_d, int *have) {
+  if (defer_wants_gram(gate[1], m, gate_d)) *have = 1;
+}
+
+cudaError_t launch_mark_gram64(const u64 *gate, int m, int gate_d, int *have, cudaStream_t st) {
+  mark_gram64_kernel<<<1, 1, 0, st>>>(gate, m, gate_d, have);
+  return cudaGetLastError();
 }
 
 }  // namespace l0

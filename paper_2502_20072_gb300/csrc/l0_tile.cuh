@@ -614,7 +614,10 @@ __device__ __forceinline__ void persistent_items(const TileArgs<R> &A, RunItem r
     __syncthreads();
     if (prob < 0) break;   // past the last item (uniform)
     const ProbDesc pd = A.probs[prob];
-    const long long local = item - pd.item_begin;
+    // items are laid out by row block, the later blocks holding the most
+    // prefix steps: hand them out last block first, so the persistent CTAs
+    // end on the small items and finish together
+    const long long local = pd.item_end - 1 - item;
     const long long *rp = (rp_smem ? s_rowpre : A.row_prefix) + pd.prefix_off;
     int lo = 0, hi = pd.n_jt - 1;
     while (lo < hi) {
@@ -627,8 +630,12 @@ __device__ __forceinline__ void persistent_items(const TileArgs<R> &A, RunItem r
     const u64 np = binom_arith(jend - 1, pd.dp);
     const long long nch = (long long)((np + (u64)pd.L - 1) / (u64)pd.L);
     const int bk = (int)(rem / nch);
-    const u64 r0 = (u64)(rem % nch) * (u64)pd.L;
-    const u64 r1 = (r0 + (u64)pd.L < np) ? r0 + (u64)pd.L : np;
+    // the tile's nch chunks split its prefixes evenly (sizes differ by at
+    // most one, none above L), so items of one tile cost the same
+    const u64 ch = (u64)(rem % nch);
+    const u64 q = np / (u64)nch, rr = np % (u64)nch;   // the first rr chunks hold q + 1
+    const u64 r0 = ch * q + (ch < rr ? ch : rr);
+    const u64 r1 = r0 + q + (ch < rr ? 1ull : 0ull);
     if (bk >= tile_k_count(bj, pd.m) || r1 <= r0 || r1 - r0 > (u64)pd.L) {   // inconsistent plan
       set_err(A.err, 9);
       break;

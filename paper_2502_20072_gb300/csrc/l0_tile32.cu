@@ -66,8 +66,8 @@ constexpr int T32_NREC = TJ + TK;  // records per step
 //     jpP   [TJ] floats (pP_j, exact path), jflag [TJ] ints (0 skip, 1 fast,
 //           2 exact, 3 redo in FP64)
 //     kg, kp, kw, kpt [TK] floats
-//   the ring [NS][SEG] floats, the item's prefix scalars C_ii, r_i and class
-//   [MAXL] each, the item's per-record constants (column, C_cc, r_c, class)
+//   the ring [NS][SEG] floats, the item's prefix scalars (1/l_i, z_i, pP_i,
+//   class) [MAXL] each, the item's per-record constants (column, C_cc, r_c, class)
 //   [TJ + TK] each, the ring's mbarriers [NS], the histogram copies
 constexpr int R_ROW = 0;
 constexpr int R_JPP = R_ROW + TJ * 32;
@@ -81,7 +81,8 @@ constexpr int O_STAGE = 2 * T32_G * T32_REC_BYTES;
 constexpr int O_PDG = O_STAGE + T32_NS * T32_SEG * 4;
 constexpr int O_PRY = O_PDG + T32_MAXL * 4;
 constexpr int O_PCLS = O_PRY + T32_MAXL * 4;
-constexpr int O_RCOL = O_PCLS + T32_MAXL * 4;
+constexpr int O_PPB = O_PCLS + T32_MAXL * 4;
+constexpr int O_RCOL = O_PPB + T32_MAXL * 4;
 constexpr int O_RDG = O_RCOL + T32_NREC * 4;
 constexpr int O_RY = O_RDG + T32_NREC * 4;
 constexpr int O_RCLS = O_RY + T32_NREC * 4;
@@ -252,13 +253,15 @@ struct Item32 {
 };
 
 // One record (r < TJ: row record of j0 + r; else column record of
-// k0 + r - TJ) of one step.  DP = 1: prefix i with C_ii = pdg, r_i = pry and
-// class pcls, the raw entry C_i,col from the staged row segment; DP = 0: no
-// prefix.  The arithmetic is tile_kernel's rec_compute for these sizes.
+// k0 + r - TJ) of one step.  DP = 1: prefix i with 1/l_i = |pinv| (negative
+// when C_ii is not positive), z_i = pz, pP_i = ppb and class pcls (computed
+// once per step for all the step's records), the raw entry C_i,col from the
+// staged row segment; DP = 0: no prefix.  The arithmetic is tile_kernel's
+// rec_compute for these sizes.
 template <int DP>
 __device__ __forceinline__ void build32(const Item32 &it, unsigned char *sb, int r, int i,
-                                        float pdg, float pry, int pcls, const float *seg,
-                                        const Rec32 &rb, float cut) {
+                                        float pinv, float pz, float ppb, int pcls,
+                                        const float *seg, const Rec32 &rb, float cut) {
   const ItemCtx<float> &c = it.c;
   const bool isj = r < TJ;
   const uint32_t s0 = tc::smem_u32(sb);
@@ -270,10 +273,10 @@ __device__ __forceinline__ void build32(const Item32 &it, unsigned char *sb, int
   float invd = 1.f, zP = 0.f, pPb = it.G00, craw = 0.f;
   bool pok = true;
   if (DP == 1) {
-    pok = pdg > 0.f;
-    invd = rsqrtf(pok ? pdg : 1.f);
-    zP = pry * invd;
-    pPb = it.G00 - zP * zP;
+    pok = pinv > 0.f;
+    invd = fabsf(pinv);
+    zP = pz;
+    pPb = ppb;
     // seg: [JSEG] = G[i+1][j0 ..), then [KSEG] = G[i+1][k0 - 1 ..)
     craw = isj ? seg[r + 1] : seg[T32_JSEG + (r - TJ) + 2];
   }
@@ -464,9 +467,10 @@ __device__ __noinline__ void recheck32(const TileArgs<float> &A, const ItemCtx<f
   *done_p = done;
 }
 
-// TMA copy of the two row segments step s of the item needs (thread 0).
-// Copy lengths are clamped to the problem's Gram so no read leaves it; the
-// entries a record reads (columns <= m of row i + 1) always lie inside.
+// TMA copy of the two row segments step s of the item needs (one thread,
+// after a fence.proxy.async that orders the block's earlier reads of the
+// stage).  Copy lengths are clamped to the problem's Gram so no read leaves
+// it; the entries a record reads (columns <= m of row i + 1) lie inside.
 __device__ __forceinline__ void issue32(const ItemCtx<float> &c, unsigned char *sb, int i,
                                         unsigned copy_idx) {
   const int slot = (int)(copy_idx % T32_NS);
@@ -477,7 +481,6 @@ __device__ __forceinline__ void issue32(const ItemCtx<float> &c, unsigned char *
   const long long kn = min((long long)T32_KSEG, end - ks);
   const uint32_t bar = tc::smem_u32(sb + O_BAR + 8 * slot);
   const uint32_t dst = tc::smem_u32(sb + O_STAGE + slot * T32_SEG * 4);
-  tc::fence_proxy_async_smem();
   tc::mbar_expect_tx(bar, (uint32_t)((jn + kn) * 4));
   tc::bulk_load(dst, c.G + js, (uint32_t)(jn * 4), bar);
   tc::bulk_load(dst + T32_JSEG * 4, c.G + ks, (uint32_t)(kn * 4), bar);
@@ -491,6 +494,7 @@ __device__ __forceinline__ void build_group32(const TileArgs<float> &A, const It
                                               unsigned char *sb, int g, int nsteps, int i0,
                                               unsigned cons, float cut) {
   const float *pdg = (const float *)(sb + O_PDG), *pry = (const float *)(sb + O_PRY);
+  const float *ppb = (const float *)(sb + O_PPB);
   const int *pcls = (const int *)(sb + O_PCLS);
   const int s0 = g * T32_G;
   const int ns = min(T32_G, nsteps - s0);
@@ -505,13 +509,15 @@ __device__ __forceinline__ void build_group32(const TileArgs<float> &A, const It
     }
     const Rec32 rb{sb + ((g & 1) * T32_G + q) * T32_REC_BYTES};
     build32<DP>(it, sb, r, i0 + s, DP == 1 ? pdg[s] : 0.f, DP == 1 ? pry[s] : 0.f,
-                DP == 1 ? pcls[s] : -1, seg, rb, cut);
+                DP == 1 ? ppb[s] : 0.f, DP == 1 ? pcls[s] : -1, seg, rb, cut);
   }
 }
 
-// thread 0: the ring copies of group g's steps
+// one thread: the ring copies of group g's steps
 __device__ __forceinline__ void issue_group32(const ItemCtx<float> &c, unsigned char *sb, int g,
                                               int nsteps, int i0, unsigned cons) {
+  if (g * T32_G >= nsteps) return;
+  tc::fence_proxy_async_smem();
   for (int s = g * T32_G; s < nsteps && s < (g + 1) * T32_G; ++s)
     issue32(c, sb, i0 + s, cons + (unsigned)s);
 }
@@ -550,17 +556,26 @@ __device__ __forceinline__ void run32(const TileArgs<float> &A, const ProbDesc &
     return;
   }
   const int ngroups = (nsteps + T32_G - 1) / T32_G;
+  const bool issuer = tid == (int)blockDim.x - 32;   // lane 0 of the last warp: the ring copies
   if (DP == 1) {
-    if (tid == 0) {
+    if (issuer) {
       issue_group32(c, sb, 0, nsteps, i0, cons);
       issue_group32(c, sb, 1, nsteps, i0, cons);
     }
     float *pdg = (float *)(sb + O_PDG), *pry = (float *)(sb + O_PRY);
+    float *ppb = (float *)(sb + O_PPB);
     int *pcls = (int *)(sb + O_PCLS);
     for (int s = tid; s < nsteps; s += blockDim.x) {
+      // the prefix's own factor, shared by the step's records: 1/l_i (its
+      // sign marks C_ii <= 0), z_i = r_i / l_i, pP_i = 1 - z_i^2
       const int i = i0 + s;
-      pdg[s] = G[(long long)(i + 1) * (ld + 1)];
-      pry[s] = G[i + 1];
+      const float cii = G[(long long)(i + 1) * (ld + 1)];
+      const bool pok = cii > 0.f;
+      const float invd = rsqrtf(pok ? cii : 1.f);
+      const float zP = G[i + 1] * invd;
+      pdg[s] = pok ? invd : -invd;
+      pry[s] = zP;
+      ppb[s] = it.G00 - zP * zP;
       pcls[s] = c.cls ? __ldg(c.cls + i) : -1;
     }
   }
@@ -597,7 +612,7 @@ __device__ __forceinline__ void run32(const TileArgs<float> &A, const ProbDesc &
   __syncthreads();   // prefix scalars and record constants visible
   build_group32<DP>(A, it, sb, 0, nsteps, i0, cons, cta_cut<float>(L));
   __syncthreads();
-  if (DP == 1 && tid == 0) issue_group32(c, sb, 2, nsteps, i0, cons);
+  if (DP == 1 && issuer) issue_group32(c, sb, 2, nsteps, i0, cons);
   u64 gnext = ~0ull;   // warp 0: the global bound, read a group before it is used
   HistPipe hp{0, 0, 0u};
   const uint32_t sbs = tc::smem_u32(sb);
@@ -646,7 +661,7 @@ __device__ __forceinline__ void run32(const TileArgs<float> &A, const ProbDesc &
       }
     }
     // the stages that held group g + 1's rows are free after the barrier above
-    if (DP == 1 && tid == 0) issue_group32(c, sb, g + 3, nsteps, i0, cons);
+    if (DP == 1 && issuer) issue_group32(c, sb, g + 3, nsteps, i0, cons);
     step_sync32(L, gthr, gprev, hp, sb);
   }
   if (tid < 32) cp_async_wait_all();   // no copy into the histogram buffers outlives the item
