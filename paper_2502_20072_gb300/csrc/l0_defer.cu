@@ -314,7 +314,7 @@ defer_dot_kernel(DeferArgs a) {
     const u64 key0 = a.run_key[r];
     if (threadIdx.x == 0) {
       int t[L0_DMAX];
-      lex_unrank_arith(pd.m, d, key0, pd.total, t);
+      lex_unrank(a.B, pd.m, d, key0, pd.total, t);
       for (int i = 0; i < d; ++i) s_t[i] = t[i];
       s_idx[0] = 0;
       for (int i = 0; i < dp; ++i) s_idx[i + 1] = t[i] + 1;

@@ -248,19 +248,45 @@ seed_kernel(const R *Gbase, const ProbDesc *probs, int K, int S, int seed, doubl
     R rel;
     keys[r] = tuple_rel<R>(G, ld, t, d, ratio, cls, &rel) ? ord32f(f32_up(rel)) : 0xffffffffu;
   }
+  // each chosen pair's factor with the target, once: l11, l21, l22 of the
+  // Cholesky of C[a,b][a,b], z of the target, pP = 1 - |z|^2
+  __shared__ R s_pf[SEED_PAIRS][6];
+  __shared__ int s_pok[SEED_PAIRS];
+  if (threadIdx.x < nsp) {
+    const int a = s_pair[threadIdx.x][0], b = s_pair[threadIdx.x][1];
+    const R caa = gram_at<R>(G, ld, a + 1, a + 1), cbb = gram_at<R>(G, ld, b + 1, b + 1);
+    const R cab = gram_at<R>(G, ld, a + 1, b + 1);
+    const R l11 = sqrt(caa > R(0) ? caa : R(1));
+    const R l21 = cab / l11;
+    const R p2 = cbb - l21 * l21;
+    const R l22 = sqrt(p2 > R(0) ? p2 : R(1));
+    const R z1 = G[a + 1] / l11;
+    const R z2 = (G[b + 1] - l21 * z1) / l22;
+    s_pf[threadIdx.x][0] = l11;
+    s_pf[threadIdx.x][1] = l21;
+    s_pf[threadIdx.x][2] = l22;
+    s_pf[threadIdx.x][3] = z1;
+    s_pf[threadIdx.x][4] = z2;
+    s_pf[threadIdx.x][5] = G00 - z1 * z1 - z2 * z2;
+    s_pok[threadIdx.x] = caa > R(0) && p2 >= (R)ratio * cbb;
+  }
+  __syncthreads();
   for (int x = threadIdx.x; x < nsp * per_pair; x += blockDim.x) {
     const int p = x / per_pair, k = x - p * per_pair;
     bool in_seed = false;
     for (int i = 0; i < Mr; ++i) in_seed = in_seed || cols[i] == k;
     unsigned key = 0xffffffffu;
-    if (!in_seed) {
-      const int a = s_pair[p][0], b = s_pair[p][1];
-      int t[3];
-      t[0] = min(a, k);
-      t[2] = max(b, k);
-      t[1] = a + b + k - t[0] - t[2];
-      R rel;
-      if (tuple_rel<R>(G, ld, t, 3, ratio, cls, &rel)) key = ord32f(f32_up(rel));
+    const int a = s_pair[p][0], b = s_pair[p][1];
+    const bool dup = cls && (__ldg(cls + k) == __ldg(cls + a) || __ldg(cls + k) == __ldg(cls + b));
+    if (!in_seed && !dup && s_pok[p]) {
+      // the completion k after the pair: pivot and target coordinate, then
+      // rel = pP - w^2 / pivot
+      const R ckk = gram_at<R>(G, ld, k + 1, k + 1);
+      const R g1 = gram_at<R>(G, ld, a + 1, k + 1) / s_pf[p][0];
+      const R g2 = (gram_at<R>(G, ld, b + 1, k + 1) - s_pf[p][1] * g1) / s_pf[p][2];
+      const R piv = ckk - g1 * g1 - g2 * g2;
+      const R w = G[k + 1] - g1 * s_pf[p][3] - g2 * s_pf[p][4];
+      if (ckk > R(0) && piv >= (R)ratio * ckk) key = ord32f(f32_up(s_pf[p][5] - w * w / piv));
     }
     keys[nt + x] = key;
   }

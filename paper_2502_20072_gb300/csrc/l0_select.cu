@@ -282,7 +282,7 @@ refit_kernel(RefitArgs a) {
   const int d = pd.d;
   if (threadIdx.x == 0) {
     int t[L0_DMAX];
-    lex_unrank_arith(pd.m, d, a.pool_k[(size_t)prob * a.K + cidx], pd.total, t);
+    lex_unrank(a.B, pd.m, d, a.pool_k[(size_t)prob * a.K + cidx], pd.total, t);
     for (int q = 0; q < d; ++q) s_t[q] = t[q];
   }
   __syncthreads();
@@ -356,6 +356,9 @@ select_kernel(SelectArgs<R> a) {
   while (P < a.K) P <<= 1;
   double *ss = (double *)smem;
   u64 *sk = (u64 *)(ss + P);
+  double *us = (double *)(sk + P);   // the head as read (rank-by-counting input)
+  u64 *uk = (u64 *)(us + P);
+  const bool by_rank = cnt <= 1024;
   __shared__ double red[32];
   double scale = 1.0;
   if (!a.shared) {
@@ -363,11 +366,13 @@ select_kernel(SelectArgs<R> a) {
     scale = (is > 0.0) ? 1.0 / (is * is) : 0.0;
   }
   double dmax = 0.0;
+  double *ws = by_rank ? us : ss;
+  u64 *wk = by_rank ? uk : sk;
   for (int i = threadIdx.x; i < P; i += blockDim.x) {
     if (i < cnt) {
       const double rf = a.refit[(size_t)prob * a.K + i];
-      ss[i] = rf;
-      sk[i] = a.pool_k[(size_t)prob * a.K + i];
+      ws[i] = rf;
+      wk[i] = a.pool_k[(size_t)prob * a.K + i];
       if (isfinite(rf)) {
         const double gs = (double)a.pool_s[(size_t)prob * a.K + i] * scale;
         dmax = fmax(dmax, fabs(gs - rf));
@@ -378,7 +383,21 @@ select_kernel(SelectArgs<R> a) {
     }
   }
   __syncthreads();
-  cta_bitonic_sort<double>(ss, sk, P);
+  if (by_rank) {
+    // keys are unique, so each entry's rank -- the count of entries before
+    // it in (score, key) order -- is its place: one pass, one barrier
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      const double s_i = us[i];
+      const u64 k_i = uk[i];
+      int r = 0;
+      for (int j = 0; j < cnt; ++j) r += cand_less<double>(us[j], uk[j], s_i, k_i) ? 1 : 0;
+      ss[r] = s_i;
+      sk[r] = k_i;
+    }
+    __syncthreads();
+  } else {
+    cta_bitonic_sort<double>(ss, sk, P);
+  }
   dmax = block_max(dmax, red);
   int nv_local = 0;
   for (int i = threadIdx.x; i < cnt; i += blockDim.x) nv_local += isfinite(ss[i]) ? 1 : 0;
@@ -395,7 +414,7 @@ select_kernel(SelectArgs<R> a) {
     double *orr = a.out_rmse + pd.out_r_off + i;
     if (i < nvalid) {
       int t[L0_DMAX];
-      lex_unrank_arith(pd.m, d, sk[i], pd.total, t);
+      lex_unrank(a.B, pd.m, d, sk[i], pd.total, t);
       for (int q = 0; q < d; ++q) ot[q] = t[q];
       *orr = sqrt(fmax(ss[i], 0.0) / div);
     } else {
@@ -574,7 +593,7 @@ template <typename R>
 cudaError_t launch_select(const SelectArgs<R> &a, cudaStream_t st) {
   int P = 1;
   while (P < a.K) P <<= 1;
-  size_t smem = (size_t)P * 16;
+  size_t smem = (size_t)P * 32;
   cudaError_t e = cudaFuncSetAttribute(select_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   select_kernel<R><<<a.n_probs, 256, smem, st>>>(a);

@@ -80,6 +80,7 @@ struct ItemCtx {
   Binom B;
   R ratio;
   const int *cls;   // duplicate classes (or null)
+  unsigned smem_dq; // tile32_kernel: shared address of its scratch (FP64-redo queue)
 };
 
 __device__ __forceinline__ bool same_class(const int *cls, int a, int b) {

@@ -89,11 +89,20 @@ constexpr int O_RCLS = O_RY + T32_NREC * 4;
 constexpr int O_BAR = O_RCLS + T32_NREC * 4;
 constexpr int O_HC = O_BAR + T32_NS * 8;              // histogram octave counts [256]
 constexpr int O_HF = O_HC + L0_HIST_COARSE * 4;       // one octave's fine counts [16]
-constexpr size_t T32_EXTRA_BYTES = (size_t)O_HF + 64;
+constexpr int T32_DQ = 512;                           // FP64-redo runs queued per group
+constexpr int O_DQK = O_HF + 64;                      // queued runs: first lex rank [DQ]
+constexpr int O_DQL = O_DQK + T32_DQ * 8;             // (problem << 8) | length [DQ]
+constexpr int O_DQN = O_DQL + T32_DQ * 4;             // runs, tuples, global base
+constexpr int T32_FQ = 2048;                          // flagged tuples queued per group
+constexpr int O_FQ = O_DQN + 16;                      // flagged tuples [FQ] (see fq_pack)
+constexpr int O_FQS = O_FQ + T32_FQ * 8;              // their state: 1 once handled [FQ]
+constexpr int O_FQN = O_FQS + T32_FQ;                 // queued count, overflow flag
+constexpr size_t T32_EXTRA_BYTES = (size_t)O_FQN + 16;
 static_assert(O_STAGE % 16 == 0 && (T32_JSEG * 4) % 16 == 0 && (T32_SEG * 4) % 16 == 0,
               "TMA destinations must be 16-byte aligned");
 static_assert(O_BAR % 8 == 0, "mbarriers are 8-byte aligned");
 static_assert(O_HC % 16 == 0 && O_HF % 16 == 0, "cp.async destinations are 16-byte aligned");
+static_assert(O_DQK % 8 == 0 && O_FQ % 8 == 0 && O_FQN % 4 == 0, "queue alignment");
 
 // one record buffer
 struct Rec32 {
@@ -359,6 +368,66 @@ __device__ __forceinline__ unsigned fast32(const u64 (&creg)[UJ][2], uint32_t rw
   return acc;
 }
 
+// FP64-redo runs of a group are queued in shared memory (a shared atomic
+// each) and handed to the global queue by flush32 after the group's barrier,
+// with one global atomic per counter per CTA instead of two per run.  A full
+// shared queue falls back to the global queue directly.
+template <int DP>
+__device__ __forceinline__ void defer32(const TileArgs<float> &A, const ItemCtx<float> &c, int i,
+                                        int j, int kfirst, int count) {
+  if (count <= 0) return;
+  unsigned char *sb = (unsigned char *)__cvta_shared_to_generic(c.smem_dq);
+  int *dqn = (int *)(sb + O_DQN);
+  const int slot = atomicAdd(dqn, 1);
+  if (slot < T32_DQ) {
+    int t[L0_DMAX];
+    if (DP == 1) {
+      t[0] = i;
+      t[1] = j;
+      t[2] = kfirst;
+    } else {
+      t[0] = j;
+      t[1] = kfirst;
+    }
+    ((u64 *)(sb + O_DQK))[slot] = lex_rank(c.B, c.m, c.d, t, c.total);
+    ((unsigned *)(sb + O_DQL))[slot] = ((unsigned)c.prob << 8) | (unsigned)count;
+    atomicAdd(dqn + 1, count);
+  } else {
+    int pidx[1] = {i};
+    defer_run<float, DP>(A, c, pidx, j, kfirst, count);
+  }
+}
+
+// After a group's barrier, when runs were queued (uniform: read after the
+// barrier): reserve their slots in the global queue with one atomic, copy,
+// and empty the shared queue.  Two barriers: the slots are known to all
+// before the copy, and the copy ends before the queue is written again.
+__device__ __forceinline__ void flush32(const TileArgs<float> &A, unsigned char *sb, int n_q) {
+  int *dqn = (int *)(sb + O_DQN);
+  const int n = n_q < T32_DQ ? n_q : T32_DQ;
+  if (threadIdx.x == 0) {
+    const u64 base = atomicAdd(A.dfr_n, (u64)n);
+    atomicAdd(A.dfr_n + 1, (u64)dqn[1]);
+    ((u64 *)(dqn + 2))[0] = base;
+  }
+  __syncthreads();
+  const u64 base = ((const u64 *)(dqn + 2))[0];
+  if (threadIdx.x == 0) {
+    dqn[0] = 0;
+    dqn[1] = 0;
+  }
+  for (int x = threadIdx.x; x < n; x += blockDim.x) {
+    const u64 slot = base + (u64)x;
+    if ((long long)slot < A.dfr_cap) {
+      A.dfr_key[slot] = ((const u64 *)(sb + O_DQK))[x];
+      A.dfr_len[slot] = ((const unsigned *)(sb + O_DQL))[x];
+    } else {
+      set_err(A.err, 7);   // deferral buffer overflow
+    }
+  }
+  __syncthreads();
+}
+
 // Exact path of one flagged tuple (tile_kernel's slow_tuple for these
 // layouts): 1 when handled, 0 when the staging area was full (look again
 // after the commit).
@@ -369,9 +438,8 @@ __device__ __forceinline__ int slow32(const TileArgs<float> &A, const ItemCtx<fl
   const int j = c.j0 + jl, k = c.k0 + kk;
   const float kpn = rb.kp()[kk];
   if (kpn == -r_inf<float>()) return 1;   // column past m or a duplicate of the prefix
-  int pidx[1] = {i};
   if (kpn == r_inf<float>()) {             // column near-singular after the prefix
-    defer_run<float, DP>(A, c, pidx, j, k, 1);
+    defer32<DP>(A, c, i, j, k, 1);
     return 1;
   }
   const float *rf = (const float *)(rb.row() + 2 * jl);   // -g, -g, 1/l, 1/l, z2, z2, e, e
@@ -381,14 +449,14 @@ __device__ __forceinline__ int slow32(const TileArgs<float> &A, const ItemCtx<fl
   const float pp = -__fmaf_rn(g2, g2, kpn);
   const float wn = __fmaf_rn(g2, rf[4], rb.kw()[kk]);
   if (!(pp >= 0.f)) {                       // pivot of k after (i, j) below the cut
-    if (!same_class(c.cls, j, k)) defer_run<float, DP>(A, c, pidx, j, k, 1);
+    if (!same_class(c.cls, j, k)) defer32<DP>(A, c, i, j, k, 1);
     return 1;
   }
   const float p = pp + rb.kpt()[kk];
   const float rel = rb.jpP()[jl] - wn * wn / p;
   if (rel > cta_cut<float>(L)) return 1;
   if (A.band) {   // band pass: scored again in FP64
-    defer_run<float, DP>(A, c, pidx, j, k, 1);
+    defer32<DP>(A, c, i, j, k, 1);
     return 1;
   }
   int t[L0_DMAX];
@@ -417,6 +485,17 @@ __device__ __noinline__ void recheck32(const TileArgs<float> &A, const ItemCtx<f
                                        unsigned *done_p) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned done = *done_p;
+  // this thread's C_jk, all loads issued before any is used
+  float cj[UJ * 4];
+#pragma unroll
+  for (int u = 0; u < UJ; ++u) {
+    const int j = c.j0 + w * UJ + u;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int k = c.k0 + 2 * lane + (v & 1) + 64 * (v >> 1);
+      cj[4 * u + v] = (j < c.m && k < c.m && k > j) ? c.G[(long long)(j + 1) * c.ld + k + 1] : 0.f;
+    }
+  }
 #pragma unroll 1
   for (int u = 0; u < UJ; ++u) {
     const int jl = w * UJ + u;
@@ -432,8 +511,7 @@ __device__ __noinline__ void recheck32(const TileArgs<float> &A, const ItemCtx<f
       if (lane == 0) {
         const int kf = c.k0 > j + 1 ? c.k0 : j + 1;
         const int kl = c.k0 + TK < c.m ? c.k0 + TK : c.m;
-        int pidx[1] = {i};
-        defer_run<float, DP>(A, c, pidx, j, kf, kl - kf);
+        defer32<DP>(A, c, i, j, kf, kl - kf);
       }
       done |= rowbits;
       continue;
@@ -451,7 +529,7 @@ __device__ __noinline__ void recheck32(const TileArgs<float> &A, const ItemCtx<f
         done |= bit;
         continue;
       }
-      const float cjk = c.G[(long long)(j + 1) * c.ld + k + 1];
+      const float cjk = cj[4 * u + v];
       const float h = __fmaf_rn(jg, rb.kg()[kk], cjk);
       const float g2 = __fmul_rn(h, invl);
       const float ppn = __fmaf_rn(g2, g2, rb.kp()[kk]);
@@ -465,6 +543,103 @@ __device__ __noinline__ void recheck32(const TileArgs<float> &A, const ItemCtx<f
     }
   }
   *done_p = done;
+}
+
+// ------------------------------------------------------------ flagged tuples --
+// A thread whose fast test flagged something appends its flagged tuples
+// (step of the group, row, column, C_jk) to a queue in shared memory, inline
+// in the hot loop; after the group's barrier the whole CTA takes the exact
+// path of the queued tuples, one per thread.  So a tile whose tuples flag on
+// every step (one holding two columns of the best descriptor) costs one
+// queue append per flag, and no warp of the CTA waits on another's exact
+// path.  A full queue sends the group to the per-thread exact path instead.
+__device__ __forceinline__ u64 fq_pack(int q, int jl, int kk, float cjk) {
+  return ((u64)__float_as_uint(cjk) << 32) | ((u64)q << 16) | ((u64)jl << 8) | (u64)kk;
+}
+
+// the thread's flagged tuples of step q of the group (the same IEEE
+// operations as the packed test, so the same decisions); false if the queue
+// was full
+template <int UJ, bool DIAG>
+__device__ __forceinline__ bool enqueue32(const u64 (&creg)[UJ][2], uint32_t rbs, int w, int lane,
+                                          int q, unsigned char *sb) {
+  bool ok = true;
+  int *fqn = (int *)(sb + O_FQN);
+#pragma unroll
+  for (int u = 0; u < UJ; ++u) {
+    const int jl = w * UJ + u;
+    const uint32_t ra = rbs + R_ROW + (uint32_t)jl * 32u;
+    const float jg = lds32(ra), invl = lds32(ra + 8u), z2 = lds32(ra + 16u), e = lds32(ra + 24u);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int qq = v >> 1, b = v & 1;
+      const int kk = 2 * lane + b + 64 * qq;
+      if (DIAG && qq == 0 && kk < jl) continue;   // k <= j in the diagonal tile
+      const u64 cw = creg[u][qq];
+      const float cjk = __uint_as_float(b ? (unsigned)(cw >> 32) : (unsigned)cw);
+      const float h = __fmaf_rn(jg, lds32(rbs + R_KG + 4u * kk), cjk);
+      const float g2 = __fmul_rn(h, invl);
+      const float ppn = __fmaf_rn(g2, g2, lds32(rbs + R_KP + 4u * kk));
+      const float wn = __fmaf_rn(g2, z2, lds32(rbs + R_KW + 4u * kk));
+      const float t = __fmaf_rn(e, ppn, __fmul_rn(wn, wn));
+      if (__float_as_uint(t) >> 31) continue;   // not flagged
+      const int slot = atomicAdd(fqn, 1);
+      if (slot < T32_FQ) ((u64 *)(sb + O_FQ))[slot] = fq_pack(q, jl, kk, cjk);
+      else ok = false;
+    }
+  }
+  return ok;
+}
+
+// exact path of one queued tuple: 1 handled, 0 staging area full (again
+// after the commit)
+template <int DP>
+__device__ __forceinline__ int exact32(const TileArgs<float> &A, const ItemCtx<float> &c,
+                                       unsigned char *sb, CtaList<float> &L, int g, int i0,
+                                       u64 ent) {
+  const int q = (int)((ent >> 16) & 0xffu), jl = (int)((ent >> 8) & 0xffu), kk = (int)(ent & 0xffu);
+  const float cjk = __uint_as_float((unsigned)(ent >> 32));
+  const Rec32 rb{sb + ((g & 1) * T32_G + q) * T32_REC_BYTES};
+  const int i = i0 + g * T32_G + q;
+  const int j = c.j0 + jl, k = c.k0 + kk;
+  if (k >= c.m || k <= j) return 1;
+  const int flag = rb.jflag()[jl];
+  if (flag == 0) return 1;
+  if (flag == 3) {   // prefix or row singular in FP32: the row's run, once (its first column)
+    const int kf = c.k0 > j + 1 ? c.k0 : j + 1;
+    if (k == kf) {
+      const int kl = c.k0 + TK < c.m ? c.k0 + TK : c.m;
+      defer32<DP>(A, c, i, j, kf, kl - kf);
+    }
+    return 1;
+  }
+  return slow32<DP>(A, c, rb, L, i, jl, kk, cjk);
+}
+
+// the whole CTA, after the group's barrier, nq > 0 queued (all threads read
+// nq before this call): empty the counters, then rounds of exact paths until
+// none is left waiting for room in the staging area
+template <int DP>
+__device__ __noinline__ void drain32(const TileArgs<float> &A, const ItemCtx<float> &c,
+                                     unsigned char *sb, CtaList<float> &L, u64 *gthr, int g,
+                                     int i0, int nq) {
+  unsigned char *st = sb + O_FQS;
+  const u64 *fq = (const u64 *)(sb + O_FQ);
+  for (int x = threadIdx.x; x < nq; x += blockDim.x) st[x] = 0;
+  __syncthreads();   // every thread has read nq; the counters can be emptied
+  if (threadIdx.x == 0) ((int *)(sb + O_FQN))[0] = 0;
+  for (int round = 0;; ++round) {
+    for (int x = threadIdx.x; x < nq; x += blockDim.x)
+      if (!st[x] && exact32<DP>(A, c, sb, L, g, i0, fq[x])) st[x] = 1;
+    __syncthreads();
+    const bool ovf = *(volatile int *)L.ovf != 0;
+    if (ovf || *(volatile int *)L.n_stage > L.S / 2) cta_list_commit<float>(L, gthr);
+    if (!ovf) break;
+    if (round > L0_MAX_REDO) {
+      set_err(A.err, 8);
+      break;
+    }
+  }
 }
 
 // TMA copy of the two row segments step s of the item needs (one thread,
@@ -546,9 +721,16 @@ __device__ __forceinline__ void run32(const TileArgs<float> &A, const ProbDesc &
   c.B = A.B;
   c.ratio = (float)A.ratio;
   c.cls = A.cls;
+  c.smem_dq = tc::smem_u32(sb);
   const float *G = c.G;
   const long long ld = c.ld;
   it.G00 = G[0];
+  if (tid == 0) {   // the queues start empty (the previous item emptied them)
+    ((int *)(sb + O_DQN))[0] = 0;
+    ((int *)(sb + O_DQN))[1] = 0;
+    ((int *)(sb + O_FQN))[0] = 0;
+    ((int *)(sb + O_FQN))[1] = 0;
+  }
   const int nsteps = DP == 1 ? (int)(r1 - r0) : 1;
   const int i0 = DP == 1 ? (int)r0 : 0;   // colex rank of a one-index prefix is the index
   if (nsteps > T32_MAXL) {   // the plan never makes such items (uniform exit)
@@ -627,38 +809,66 @@ __device__ __forceinline__ void run32(const TileArgs<float> &A, const ProbDesc &
     for (int q = 0; q < T32_G; ++q) done[q] = 0u;
     const uint32_t gb = sbs + (uint32_t)((g & 1) * (T32_G * T32_REC_BYTES));
     const uint32_t rw = gb + R_ROW + (uint32_t)(w * UJ * 32), rl = gb + R_KG + 8u * lane;
-    for (int pass = 0;; ++pass) {
-      unsigned acc[T32_G];
-      if (ns == T32_G) {   // a full group: the tests straight through, one check
+    unsigned acc[T32_G];
+    if (ns == T32_G) {   // a full group: the tests straight through, one check
 #pragma unroll
-        for (int q = 0; q < T32_G; ++q)
-          acc[q] = c.diag ? fast32<UJ, true>(creg, rw + q * T32_REC_BYTES, rl + q * T32_REC_BYTES, d0b)
+      for (int q = 0; q < T32_G; ++q)
+        acc[q] = c.diag ? fast32<UJ, true>(creg, rw + q * T32_REC_BYTES, rl + q * T32_REC_BYTES, d0b)
+                        : fast32<UJ, false>(creg, rw + q * T32_REC_BYTES, rl + q * T32_REC_BYTES, d0b);
+    } else {
+#pragma unroll
+      for (int q = 0; q < T32_G; ++q)
+        acc[q] = q >= ns ? 0xffffffffu
+                 : c.diag ? fast32<UJ, true>(creg, rw + q * T32_REC_BYTES, rl + q * T32_REC_BYTES, d0b)
                           : fast32<UJ, false>(creg, rw + q * T32_REC_BYTES, rl + q * T32_REC_BYTES, d0b);
-      } else {
+    }
+    unsigned all = 0xffffffffu;
 #pragma unroll
-        for (int q = 0; q < T32_G; ++q)
-          acc[q] = q >= ns ? 0xffffffffu
-                   : c.diag ? fast32<UJ, true>(creg, rw + q * T32_REC_BYTES, rl + q * T32_REC_BYTES, d0b)
-                            : fast32<UJ, false>(creg, rw + q * T32_REC_BYTES, rl + q * T32_REC_BYTES, d0b);
-      }
-      unsigned all = 0xffffffffu;
+    for (int q = 0; q < T32_G; ++q) all &= acc[q];
+    if (!(all >> 31)) {   // something of this thread flagged: queue it
+      bool qok = true;
 #pragma unroll
-      for (int q = 0; q < T32_G; ++q) all &= acc[q];
-      if (!(all >> 31)) {
-#pragma unroll
-        for (int q = 0; q < T32_G; ++q)
-          if (q < ns && !(acc[q] >> 31))
-            recheck32<DP, UJ>(A, c, Rec32{sb + ((g & 1) * T32_G + q) * T32_REC_BYTES}, L,
-                              i0 + g * T32_G + q, &done[q]);
-      }
+      for (int q = 0; q < T32_G; ++q)
+        if (q < ns && !(acc[q] >> 31)) {
+          const uint32_t rbs = gb + (uint32_t)(q * T32_REC_BYTES);
+          qok = (c.diag ? enqueue32<UJ, true>(creg, rbs, w, lane, q, sb)
+                        : enqueue32<UJ, false>(creg, rbs, w, lane, q, sb)) && qok;
+        }
+      if (!qok) ((volatile int *)(sb + O_FQN))[1] = 1;
+    }
+    __syncthreads();
+    const int nq = *(volatile int *)(sb + O_FQN), qovf = ((volatile int *)(sb + O_FQN))[1];
+    if (qovf) {
+      // the queue overflowed: the group's flagged tuples take the exact path
+      // thread by thread (the queued entries are dropped)
       __syncthreads();
-      const bool ovf = *(volatile int *)L.ovf != 0;
-      if (ovf || *(volatile int *)L.n_stage > L.S / 2) cta_list_commit<float>(L, gthr);
-      if (!ovf) break;
-      if (pass > L0_MAX_REDO) {
-        set_err(A.err, 8);
-        break;
+      if (tid == 0) {
+        ((int *)(sb + O_FQN))[0] = 0;
+        ((int *)(sb + O_FQN))[1] = 0;
       }
+      for (int pass = 0;; ++pass) {
+        if (!(all >> 31)) {
+#pragma unroll
+          for (int q = 0; q < T32_G; ++q)
+            if (q < ns && !(acc[q] >> 31))
+              recheck32<DP, UJ>(A, c, Rec32{sb + ((g & 1) * T32_G + q) * T32_REC_BYTES}, L,
+                                i0 + g * T32_G + q, &done[q]);
+        }
+        __syncthreads();
+        const bool ovf = *(volatile int *)L.ovf != 0;
+        if (ovf || *(volatile int *)L.n_stage > L.S / 2) cta_list_commit<float>(L, gthr);
+        if (!ovf) break;
+        if (pass > L0_MAX_REDO) {
+          set_err(A.err, 8);
+          break;
+        }
+      }
+    } else if (nq > 0) {
+      drain32<DP>(A, c, sb, L, gthr, g, i0, nq);
+    }
+    {
+      const int nq = *(volatile int *)(sb + O_DQN);   // read after the barrier: uniform
+      if (nq > 0) flush32(A, sb, nq);
     }
     // the stages that held group g + 1's rows are free after the barrier above
     if (DP == 1 && issuer) issue_group32(c, sb, g + 3, nsteps, i0, cons);
