@@ -86,6 +86,7 @@ struct sisso_l0_handle {
   DevBuf scratch, refit, rdiv, cert, out_t, out_r, err;
   DevBuf dfr_key, dfr_len, dfr_n, dfr_cnt;
   DevBuf abf, bbf, kmeta, gram32;
+  DevBuf gpart, gctr;                                 // split-K partial Gram tiles, tile counters
   DevBuf prop_in, prop_pairs, prop_bits, prop_ctr, sel_hist, sel_bin, scores, diag;
   DevBuf col_hash, col_cls;
   DevBuf band_thr, band_floor;                        // band pass: cut, previous delta
@@ -257,6 +258,7 @@ struct FitPlan {
   bool has_singles = false, has_tuples = false;
   const double *Xd = nullptr, *yd = nullptr;   // device copies of the inputs
   long long N = 0, nmax = 0, ld = 0, gstride = 0, ldk = 0;
+  int gsplit = 1;           // K splits of the tensor-core Gram
   std::vector<long long> off;
   std::vector<Req> req;
   std::vector<l0::ProbDesc> pd;
@@ -472,10 +474,9 @@ int prep_pass(sisso_l0_t h, FitPlan &P) {
                             h->gram.as<double>(), P.ld, P.gstride, st),
           "gram kernel");
   } else {
-    const size_t abytes = (size_t)(m + 1) * P.ldk * 2;
+    // (the split rows need no clearing: the centring kernel writes every
+    // entry of rows 0..m, padding included; TMA fills rows past m with zeros)
     L0_CK(cudaMemsetAsync(h->g64_have.p, 0, 4, st), "memset");   // new data: no FP64 Gram yet
-    L0_CK(cudaMemsetAsync(h->abf.p, 0, abytes, st), "memset");
-    L0_CK(cudaMemsetAsync(h->bbf.p, 0, abytes, st), "memset");
     const int *kbeg = h->kmeta.as<int>();
     L0_CK(l0::launch_centre_split(P.Xd, P.yd, N, m, h->offs.as<long long>(), n_tasks,
                                   h->mu.as<double>(), h->inv_s.as<double>(), h->w64.as<double>(),
@@ -483,8 +484,11 @@ int prep_pass(sisso_l0_t h, FitPlan &P) {
                                   h->err.as<int>(), st),
           "centre kernel");
     L0_CK(cudaEventRecord(h->ev[1], st), "event");
+    if (P.gsplit > 1)
+      L0_CK(cudaMemsetAsync(h->gctr.p, 0, (size_t)l0::gram_tc_tiles(m) * n_tasks * 4, st), "memset");
     L0_CK(l0::launch_gram_tc(h->abf.p, h->bbf.p, P.ldk, m, n_tasks, kbeg, kbeg + 2 * n_tasks,
-                             h->gram32.as<float>(), P.ld, P.gstride, h->err.as<int>(), st),
+                             h->gram32.as<float>(), P.ld, P.gstride, h->err.as<int>(), st,
+                             P.gsplit, h->gpart.as<float>(), h->gctr.as<unsigned>()),
           "tensor-core gram kernel");
   }
   L0_CK(cudaEventRecord(h->ev[6], st), "event");
@@ -676,7 +680,9 @@ int search_pass(sisso_l0_t h, FitPlan &P, int K, const R *G) {
     }
   }
   L0_CK(cudaEventRecord(h->ev[3], st), "event");
-  const int groups = std::max(1, std::min(n_slots, 32));
+  // up to 1024 slot lists: one CTA per problem searches them all at once and
+  // writes the pool; more: groups and a second level
+  const int groups = n_slots <= 1024 ? 1 : std::min(n_slots, 32);
   L0_CK(l0::launch_merge<R>(h->lists_s.as<R>(), h->lists_k.as<u64>(), h->lists_cnt.as<int>(),
                             n_slots, n_probs, K, S, groups, h->gthr.as<u64>(), h->part_s.as<R>(),
                             h->part_k.as<u64>(), h->part_cnt.as<int>(), h->done.as<unsigned>(),
@@ -879,7 +885,7 @@ int autotune(sisso_l0_t h, FitPlan &P, int K, const R *G) {
     for (int v = 1; v <= 3; ++v)
       if (tile32_ok(P, v)) shapes.push_back(v);
   }
-  const int factors[] = {1, 2, 4, 8};
+  const int factors[] = {1, 2, 4, 8, 16};
   for (int v : shapes) {
     int rc = apply(v, 1);
     if (rc) return rc;
@@ -940,7 +946,8 @@ std::string graph_key(sisso_l0_t h, const FitPlan &P, int K) {
                           &h->done, &h->pool_s, &h->pool_k, &h->pool_cnt, &h->scratch, &h->refit,
                           &h->rdiv, &h->cert, &h->out_t, &h->out_r, &h->err, &h->dfr_key,
                           &h->dfr_len, &h->dfr_n, &h->abf, &h->bbf, &h->kmeta, &h->gram32,
-                          &h->col_hash, &h->col_cls, &h->g64_have, &h->dfr_bctr};
+                          &h->col_hash, &h->col_cls, &h->g64_have, &h->dfr_bctr, &h->gpart,
+                          &h->gctr};
   for (const DevBuf *b : bufs) {
     snprintf(buf, sizeof(buf), "|%p", b->p);
     k += buf;
@@ -1131,6 +1138,18 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
     if (rc) return rc;
     L0_CK(h->gram32.ensure((size_t)n_tasks * P.gstride * 4), "alloc Gram");
     L0_CK(h->g64_have.ensure(4), "alloc");
+    // K splits of the tensor-core Gram: about one CTA per SM in all (one
+    // fits an SM), no more than the fewest K blocks of a task, at most 8
+    {
+      int nk_min = 1 << 30;
+      for (int t = 0; t < n_tasks; ++t) nk_min = std::min(nk_min, meta[2 * n_tasks + t]);
+      const int tiles = l0::gram_tc_tiles(m) * n_tasks;
+      P.gsplit = std::max(1, std::min(std::min(8, nk_min), h->n_sm / std::max(1, tiles)));
+      if (P.gsplit > 1) {
+        L0_CK(h->gpart.ensure(l0::gram_tc_part_floats(m, n_tasks, P.gsplit) * 4), "alloc Gram split");
+        L0_CK(h->gctr.ensure((size_t)tiles * 4), "alloc Gram split");
+      }
+    }
   }
   // persistent grid of the tuple kernel (or of the proposal search)
   if (P.has_tuples && P.proposal) {
@@ -1158,7 +1177,10 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
     P.max_bps = bps;
     P.grid = h->n_sm * bps;
   }
-  P.items_factor = 2;
+  // untuned: the FP32 d <= 3 kernel balances best with small items (8 per
+  // CTA measured fastest on the d = 3, 1000-column search), the general one
+  // with 2
+  P.items_factor = P.variant > 0 ? 8 : 2;
   plan_problems(P);
   rc = P.mixed ? setup_search<float>(h, P, K) : setup_search<double>(h, P, K);
   if (rc) return rc;
@@ -1459,7 +1481,8 @@ void sisso_l0_destroy(sisso_l0_t h) {
                     &h->scores, &h->diag, &h->col_hash, &h->col_cls, &h->sis_ex, &h->sis_y,
                     &h->gen_ops, &h->gen_c1, &h->gen_c2, &h->gen_valid, &h->loop_x, &h->loop_y,
                     &h->loop_xs, &h->loop_res, &h->loop_q, &h->loop_tup, &h->loop_rows,
-                    &h->band_thr, &h->band_floor, &h->g64_have, &h->dfr_bctr};
+                    &h->band_thr, &h->band_floor, &h->g64_have, &h->dfr_bctr, &h->gpart,
+                    &h->gctr};
   for (DevBuf *b : bufs) b->release();
   if (h->pin) cudaFreeHost(h->pin);
   if (h->ev_pin) cudaEventDestroy(h->ev_pin);

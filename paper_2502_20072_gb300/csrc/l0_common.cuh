@@ -76,11 +76,35 @@ __device__ __forceinline__ u64 lex_rank(const Binom &B, int m, int d,
   return total - 1ull - q;
 }
 
-// largest x in [lo, hi] with C(x, p) <= q  (C(lo, p) <= q required)
+// largest x in [lo, hi] with C(x, p) <= q  (C(lo, p) <= q required).
+// C(x, p) ~ (x - (p - 1) / 2)^p / p! gives x to within a step or two; the
+// table then confirms it (two independent loads, C(x, p) and C(x + 1, p)),
+// so a level of an unrank waits for one or two trips to memory instead of
+// the log2(hi - lo) of a bisection.
 __device__ __forceinline__ int binom_floor(const Binom &B, int p, u64 q, int lo,
                                            int hi) {
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
+  if (lo >= hi) return lo;
+  if (p == 1) return q < (u64)hi ? (int)q : hi;   // C(x, 1) = x (q >= lo by the premise)
+  // in FP32 (FP64 is a narrow pipe here): q to 2^-24, x to well within a step
+  float f = 1.f;
+  for (int i = 2; i <= p; ++i) f *= (float)i;
+  const float xe = exp2f(__log2f((float)q * f) / (float)p) + 0.5f * (float)(p - 1);
+  int x = !(xe >= (float)lo) ? lo : (xe > (float)hi ? hi : (int)xe);
+  for (int guard = 0; guard < 64; ++guard) {
+    const u64 c0 = binom(B, p, x);
+    const u64 c1 = x < hi ? binom(B, p, x + 1) : 0ull;
+    if (c0 > q) {            // too far: step down (C(lo, p) <= q ends it)
+      --x;
+      continue;
+    }
+    if (x < hi && c1 <= q) { // not far enough
+      ++x;
+      continue;
+    }
+    return x;
+  }
+  while (lo < hi) {          // the estimate was far off: bisection
+    const int mid = (lo + hi + 1) >> 1;
     if (binom(B, p, mid) <= q) lo = mid; else hi = mid - 1;
   }
   return lo;

@@ -233,9 +233,17 @@ cudaError_t launch_centre_split(const double *X, const double *y, long long n_to
                                 const int *kbeg_dev, const int *npad_dev, int *err,
                                 cudaStream_t st);
 size_t gram_tc_smem_bytes();
+// upper-triangular 128 x 128 tiles of an (m + 1)-square Gram
+int gram_tc_tiles(int m);
+// scratch floats for nsplit-way K splits of T tasks' tiles (0 when nsplit = 1)
+size_t gram_tc_part_floats(int m, int T, int nsplit);
+// nsplit >= 1 ways of splitting every task's K blocks (at most the fewest K
+// blocks of a task); nsplit > 1 needs part (gram_tc_part_floats) and
+// tile_ctr (gram_tc_tiles(m) * T counters, zero; left zero)
 cudaError_t launch_gram_tc(const void *A, const void *B, long long ldk, int m, int T,
                            const int *kbeg_dev, const int *nkb_dev, float *G, long long ld,
-                           long long g_stride, int *err, cudaStream_t st);
+                           long long g_stride, int *err, cudaStream_t st, int nsplit = 1,
+                           float *part = nullptr, unsigned *tile_ctr = nullptr);
 
 // FP64 redo of the runs the FP32 tuple kernel queued
 struct DeferArgs {

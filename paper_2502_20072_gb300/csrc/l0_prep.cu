@@ -77,17 +77,30 @@ column_hash_kernel(const double *__restrict__ X, long long n_total, int m, u64 *
   if (c >= m) return;
   const double *src = X + (long long)c * n_total;
   u64 h = 0;
-  for (long long i = lane; i < n_total; i += 32) {
-    const u64 b = ((u64)__double_as_longlong(src[i]) + 0x8000ull) & ~0xFFFFull;
-    h ^= mix64(b ^ ((u64)i * 0x9E3779B97F4A7C15ull));
+  for (long long i0 = lane; i0 < n_total; i0 += 256) {   // eight loads in flight
+    long long raw[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const long long i = i0 + 32 * u;
+      raw[u] = i < n_total ? __double_as_longlong(__ldg(src + i)) : 0ll;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const long long i = i0 + 32 * u;
+      if (i < n_total) {
+        const u64 b = ((u64)raw[u] + 0x8000ull) & ~0xFFFFull;
+        h ^= mix64(b ^ ((u64)i * 0x9E3779B97F4A7C15ull));
+      }
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) h ^= __shfl_xor_sync(0xffffffffu, h, o);
   if (lane == 0) hash[c] = h;
 }
 
-// one warp per column j: lanes scan the hashes of the columns before it, 32
-// at a time; each hash match is verified by the whole warp (coalesced rows)
+// one warp per column j: lanes scan the hashes of the columns before it, 256
+// at a time (eight loads in flight per lane); each hash match is verified by
+// the whole warp (coalesced rows)
 __global__ void __launch_bounds__(256)
 column_class_kernel(const double *__restrict__ X, long long n_total, int m, const u64 *hash,
                     int *cls) {
@@ -97,19 +110,27 @@ column_class_kernel(const double *__restrict__ X, long long n_total, int m, cons
   const u64 hj = hash[j];
   const double *xj = X + (long long)j * n_total;
   int c = j;
-  for (int i0 = 0; i0 < j && c == j; i0 += 32) {
-    const int i = i0 + lane;
-    unsigned hit = __ballot_sync(0xffffffffu, i < j && __ldg(hash + i) == hj);
-    while (hit && c == j) {
-      const int q = i0 + __ffs(hit) - 1;
-      hit &= hit - 1;
-      const double *xi = X + (long long)q * n_total;
-      bool same = true;
-      for (long long r = lane; r < n_total; r += 32) {
-        const double a = xi[r], b = xj[r];
-        same = same && fabs(a - b) <= 1e-12 * fmax(fabs(a), fabs(b));
+  for (int i00 = 0; i00 < j && c == j; i00 += 256) {
+    unsigned eq = 0u;   // bit u: the hash of column i00 + 32 u + lane matches
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = i00 + 32 * u + lane;
+      if (i < j && __ldg(hash + i) == hj) eq |= 1u << u;
+    }
+    for (int u = 0; u < 8 && c == j; ++u) {
+      const int i0 = i00 + 32 * u;
+      unsigned hit = __ballot_sync(0xffffffffu, (eq >> u) & 1u);
+      while (hit && c == j) {
+        const int q = i0 + __ffs(hit) - 1;
+        hit &= hit - 1;
+        const double *xi = X + (long long)q * n_total;
+        bool same = true;
+        for (long long r = lane; r < n_total; r += 32) {
+          const double a = xi[r], b = xj[r];
+          same = same && fabs(a - b) <= 1e-12 * fmax(fabs(a), fabs(b));
+        }
+        if (__all_sync(0xffffffffu, same)) c = q;
       }
-      if (__all_sync(0xffffffffu, same)) c = q;
     }
   }
   if (lane == 0) cls[j] = c;

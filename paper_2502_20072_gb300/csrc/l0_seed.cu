@@ -14,13 +14,6 @@ namespace l0 {
 
 namespace {
 
-__device__ __forceinline__ u64 small_binom(int n, int k) {
-  if (k < 0 || n < k) return 0;
-  u64 r = 1;
-  for (int i = 1; i <= k; ++i) r = r * (u64)(n - k + i) / (u64)i;
-  return r;
-}
-
 template <typename R>
 __device__ __forceinline__ R gram_at(const R *G, long long ld, int a, int b) {
   return a <= b ? G[(long long)a * ld + b] : G[(long long)b * ld + a];
@@ -91,24 +84,26 @@ __device__ unsigned select_key(const unsigned *keys, int n, int want, unsigned *
   return prefix;
 }
 
-// rel = SSE / S_yy of one tuple t[0..d) (ascending columns) by the augmented
-// Cholesky of (t, target) in R; false when a feature pivot falls below
-// ratio times its diagonal or two columns share a duplicate class
+// rel = SSE / S_yy of one tuple of seed columns by the augmented Cholesky of
+// (tuple, target) in R, from the seed block Bs (nb x nb, index 0 the target,
+// s + 1 seed column s); a[0..d) are ascending seed positions, cols[] their
+// columns.  False when a feature pivot falls below ratio times its diagonal
+// or two columns share a duplicate class.
 template <typename R>
-__device__ bool tuple_rel(const R *G, long long ld, const int *t, int d, double ratio,
+__device__ bool tuple_rel(const R *Bs, int nb, const int *a, const int *cols, int d, double ratio,
                           const int *cls, R *rel_out) {
   if (cls)
     for (int i = 0; i < d; ++i)
       for (int j = 0; j < i; ++j)
-        if (__ldg(cls + t[i]) == __ldg(cls + t[j])) return false;
+        if (__ldg(cls + cols[a[i]]) == __ldg(cls + cols[a[j]])) return false;
   R Lm[L0_DMAX + 1][L0_DMAX + 1];
   R rel = R(0);
   bool ok = true;
   for (int i = 0; i <= d; ++i) {
-    const int ia = (i < d) ? t[i] + 1 : 0;
+    const int ia = (i < d) ? a[i] + 1 : 0;
     for (int j = 0; j <= i; ++j) {
-      const int ib = (j < d) ? t[j] + 1 : 0;
-      R c = gram_at<R>(G, ld, ia, ib);
+      const int ib = (j < d) ? a[j] + 1 : 0;
+      R c = Bs[ia * nb + ib];
       const R orig = c;
       for (int q = 0; q < j; ++q) c -= Lm[i][q] * Lm[j][q];
       if (j < i) {
@@ -125,6 +120,10 @@ __device__ bool tuple_rel(const R *G, long long ld, const int *t, int d, double 
   return ok;
 }
 
+// largest number of seed columns (the block of their Gram is staged in
+// shared memory behind the keys)
+constexpr int SEED_MAXM = 64;
+
 // best pairs of the seed columns whose completions the d = 3 seed scores
 constexpr int SEED_PAIRS = 8;
 
@@ -136,12 +135,13 @@ seed_kernel(const R *Gbase, const ProbDesc *probs, int K, int S, int seed, doubl
             Binom B, u64 *gthr, unsigned *hist, int max_keys, const int *cls) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned *keys = (unsigned *)smem;            // [max(m, tuples)]
-  __shared__ int cols[64];
+  __shared__ int cols[SEED_MAXM], cols2[SEED_MAXM];
   __shared__ int s_n;
   __shared__ unsigned s_bins[256];
   __shared__ int s_sel[2];
   __shared__ int s_pair[SEED_PAIRS][2];
   __shared__ int s_npair;
+  __shared__ u64 s_C[SEED_MAXM + 1][L0_DMAX + 1];   // C(n, i), n <= SEED_MAXM
   const int prob = blockIdx.x;
   const ProbDesc pd = probs[prob];
   if (threadIdx.x == 0) gthr[prob] = ord_inf<R>();
@@ -150,10 +150,20 @@ seed_kernel(const R *Gbase, const ProbDesc *probs, int K, int S, int seed, doubl
       hist[(size_t)prob * L0_HIST_WORDS + i] = 0u;
   if (!seed || pd.d < 2) return;
   // smallest M with C(M, d) >= 2 K', at most min(m, 64, K')
-  const int Mcap = min(min(pd.m, 64), K);
+  const int Mcap = min(min(pd.m, SEED_MAXM), K);
   int M = Mcap;
-  for (int q = pd.d; q <= Mcap; ++q)
-    if (small_binom(q, pd.d) >= 2ull * (u64)K) { M = q; break; }
+  {
+    // C(q, d) >= 2K  <=>  q (q - 1) .. (q - d + 1) >= 2K d!  (no divisions;
+    // 64^8 < 2^63)
+    u64 fact = 1ull;
+    for (int i = 2; i <= pd.d; ++i) fact *= (u64)i;
+    const u64 want = 2ull * (u64)K * fact;
+    for (int q = pd.d; q <= Mcap; ++q) {
+      u64 f = 1ull;
+      for (int i = 0; i < pd.d; ++i) f *= (u64)(q - i);
+      if (f >= want) { M = q; break; }
+    }
+  }
   const R *G = Gbase + pd.g_off;
   const long long ld = pd.ld;
   const int d = pd.d;
@@ -178,29 +188,46 @@ seed_kernel(const R *Gbase, const ProbDesc *probs, int K, int S, int seed, doubl
       if (slot < M) cols[slot] = k;
     }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    const int Mr = min(s_n, M);
-    s_n = Mr;
-    for (int i = 1; i < Mr; ++i) {     // ascending column order
-      int v = cols[i], q = i - 1;
-      while (q >= 0 && cols[q] > v) { cols[q + 1] = cols[q]; --q; }
-      cols[q + 1] = v;
-    }
+  // ascending column order: each column's rank is the number of smaller ones
+  const int Mr = min(s_n, M);
+  if (threadIdx.x < Mr) {
+    const int v = cols[threadIdx.x];
+    int rk = 0;
+    for (int i = 0; i < Mr; ++i) rk += cols[i] < v;
+    cols2[rk] = v;
   }
   __syncthreads();
-  const int Mr = s_n;
+  if (threadIdx.x < Mr) cols[threadIdx.x] = cols2[threadIdx.x];
+  if (threadIdx.x == 0) s_npair = 0;   // visible after the barrier below
+  if (threadIdx.x <= SEED_MAXM) {      // row n of Pascal's triangle, exact divisions
+    const int n = threadIdx.x;
+    u64 c = 1ull;
+    s_C[n][0] = 1ull;
+    for (int i = 1; i <= L0_DMAX; ++i) {
+      c = (i <= n) ? c * (u64)(n - i + 1) / (u64)i : 0ull;
+      s_C[n][i] = c;
+    }
+  }
+  // the seed columns' augmented block, target first (one trip to L2 for all
+  // the tuples of seed columns below)
+  const int nb = Mr + 1;
+  R *Bs = (R *)(keys + ((max_keys + 3) & ~3));   // 16-byte aligned
+  for (int x = threadIdx.x; x < nb * nb; x += blockDim.x) {
+    const int ia = x / nb, ib = x - (x / nb) * nb;
+    Bs[x] = gram_at<R>(G, ld, ia ? cols2[ia - 1] + 1 : 0, ib ? cols2[ib - 1] + 1 : 0);
+  }
+  __syncthreads();
   // 2. d = 3: the best SEED_PAIRS pairs of those columns, whose completions
   // by every other column are the tuples the search's best K' mostly are
-  if (threadIdx.x == 0) s_npair = 0;
   const int npairs = Mr * (Mr - 1) / 2;
   const int pb = min(SEED_PAIRS, npairs);
   if (d == 3 && pb > 0 && npairs <= max_keys) {
     for (int r = threadIdx.x; r < npairs; r += blockDim.x) {
       int b = 1;
       while (b * (b + 1) / 2 <= r) ++b;   // colex: pair (a, b) has rank b (b - 1) / 2 + a
-      const int t[2] = {cols[r - b * (b - 1) / 2], cols[b]};
+      const int t[2] = {r - b * (b - 1) / 2, b};
       R rel;
-      keys[r] = tuple_rel<R>(G, ld, t, 2, ratio, cls, &rel) ? ord32f(f32_up(rel)) : 0xffffffffu;
+      keys[r] = tuple_rel<R>(Bs, nb, t, cols, 2, ratio, cls, &rel) ? ord32f(f32_up(rel)) : 0xffffffffu;
     }
     __syncthreads();
     const unsigned tp = select_key(keys, npairs, pb, s_bins, s_sel);
@@ -210,19 +237,19 @@ seed_kernel(const R *Gbase, const ProbDesc *probs, int K, int S, int seed, doubl
         if (slot < pb) {
           int b = 1;
           while (b * (b + 1) / 2 <= r) ++b;
-          s_pair[slot][0] = cols[r - b * (b - 1) / 2];
-          s_pair[slot][1] = cols[b];
+          s_pair[slot][0] = r - b * (b - 1) / 2;   // seed positions
+          s_pair[slot][1] = b;
         }
       }
     }
     __syncthreads();
   }
-  const int nsp = min(s_npair, pb);
+  const int nsp = d == 3 ? min(s_npair, pb) : 0;
   // 3. every d-tuple of the seed columns (at most the key capacity; a subset
   // of real tuples bounds the K'-th best just as well), exact augmented
   // Cholesky; then (d = 3) each chosen pair with every column outside the
   // seed set -- distinct from those tuples and from each other's
-  const u64 total = small_binom(Mr, d);
+  const u64 total = s_C[Mr][d];
   const int nt = (int)(total < (u64)max_keys ? total : (u64)max_keys);
   const int per_pair = (nsp > 0) ? min(m, (max_keys - nt) / nsp) : 0;
   const int ntot = nt + nsp * per_pair;
@@ -236,59 +263,84 @@ seed_kernel(const R *Gbase, const ProbDesc *probs, int K, int S, int seed, doubl
         int lo = i - 1, h = hi;
         while (lo < h) {
           const int mid = (lo + h + 1) >> 1;
-          if (small_binom(mid, i) <= q) lo = mid; else h = mid - 1;
+          if (s_C[mid][i] <= q) lo = mid; else h = mid - 1;
         }
-        q -= small_binom(lo, i);
+        q -= s_C[lo][i];
         a[i - 1] = lo;
         hi = lo - 1;
       }
     }
-    int t[L0_DMAX];
-    for (int i = 0; i < d; ++i) t[i] = cols[a[i]];
     R rel;
-    keys[r] = tuple_rel<R>(G, ld, t, d, ratio, cls, &rel) ? ord32f(f32_up(rel)) : 0xffffffffu;
+    keys[r] = tuple_rel<R>(Bs, nb, a, cols, d, ratio, cls, &rel) ? ord32f(f32_up(rel)) : 0xffffffffu;
   }
-  // each chosen pair's factor with the target, once: l11, l21, l22 of the
+  // each chosen pair's factor with the target, once: 1/l11, l21, 1/l22 of the
   // Cholesky of C[a,b][a,b], z of the target, pP = 1 - |z|^2
   __shared__ R s_pf[SEED_PAIRS][6];
   __shared__ int s_pok[SEED_PAIRS];
   if (threadIdx.x < nsp) {
-    const int a = s_pair[threadIdx.x][0], b = s_pair[threadIdx.x][1];
-    const R caa = gram_at<R>(G, ld, a + 1, a + 1), cbb = gram_at<R>(G, ld, b + 1, b + 1);
-    const R cab = gram_at<R>(G, ld, a + 1, b + 1);
+    const int a = s_pair[threadIdx.x][0] + 1, b = s_pair[threadIdx.x][1] + 1;   // block indices
+    const R caa = Bs[a * nb + a], cbb = Bs[b * nb + b], cab = Bs[a * nb + b];
     const R l11 = sqrt(caa > R(0) ? caa : R(1));
     const R l21 = cab / l11;
     const R p2 = cbb - l21 * l21;
     const R l22 = sqrt(p2 > R(0) ? p2 : R(1));
-    const R z1 = G[a + 1] / l11;
-    const R z2 = (G[b + 1] - l21 * z1) / l22;
-    s_pf[threadIdx.x][0] = l11;
+    const R z1 = Bs[a] / l11;
+    const R z2 = (Bs[b] - l21 * z1) / l22;
+    s_pf[threadIdx.x][0] = R(1) / l11;
     s_pf[threadIdx.x][1] = l21;
-    s_pf[threadIdx.x][2] = l22;
+    s_pf[threadIdx.x][2] = R(1) / l22;
     s_pf[threadIdx.x][3] = z1;
     s_pf[threadIdx.x][4] = z2;
     s_pf[threadIdx.x][5] = G00 - z1 * z1 - z2 * z2;
     s_pok[threadIdx.x] = caa > R(0) && p2 >= (R)ratio * cbb;
   }
   __syncthreads();
-  for (int x = threadIdx.x; x < nsp * per_pair; x += blockDim.x) {
-    const int p = x / per_pair, k = x - p * per_pair;
-    bool in_seed = false;
-    for (int i = 0; i < Mr; ++i) in_seed = in_seed || cols[i] == k;
-    unsigned key = 0xffffffffu;
-    const int a = s_pair[p][0], b = s_pair[p][1];
-    const bool dup = cls && (__ldg(cls + k) == __ldg(cls + a) || __ldg(cls + k) == __ldg(cls + b));
-    if (!in_seed && !dup && s_pok[p]) {
-      // the completion k after the pair: pivot and target coordinate, then
-      // rel = pP - w^2 / pivot
-      const R ckk = gram_at<R>(G, ld, k + 1, k + 1);
-      const R g1 = gram_at<R>(G, ld, a + 1, k + 1) / s_pf[p][0];
-      const R g2 = (gram_at<R>(G, ld, b + 1, k + 1) - s_pf[p][1] * g1) / s_pf[p][2];
-      const R piv = ckk - g1 * g1 - g2 * g2;
-      const R w = G[k + 1] - g1 * s_pf[p][3] - g2 * s_pf[p][4];
-      if (ckk > R(0) && piv >= (R)ratio * ckk) key = ord32f(f32_up(s_pf[p][5] - w * w / piv));
+  // completions: a thread per column k, its Gram entries with both columns
+  // of every chosen pair loaded before any is used
+  int pa[SEED_PAIRS], pb2[SEED_PAIRS];
+#pragma unroll
+  for (int p = 0; p < SEED_PAIRS; ++p) {
+    pa[p] = p < nsp ? cols[s_pair[p][0]] : 0;
+    pb2[p] = p < nsp ? cols[s_pair[p][1]] : 0;
+  }
+  constexpr int PC = sizeof(R) == 8 ? 4 : SEED_PAIRS;   // pairs whose loads go together
+  for (int k = threadIdx.x; k < per_pair; k += blockDim.x) {
+    const R ckk = G[(long long)(k + 1) * (ld + 1)], ck = G[k + 1];
+    const int ck_cls = cls ? __ldg(cls + k) : 0;
+#pragma unroll
+    for (int p0 = 0; p0 < SEED_PAIRS; p0 += PC) {
+      if (p0 >= nsp) break;
+      R cak[PC], cbk[PC];
+#pragma unroll
+      for (int u = 0; u < PC; ++u) {
+        const int p = p0 + u;
+        cak[u] = p < nsp ? gram_at<R>(G, ld, pa[p] + 1, k + 1) : R(0);
+        cbk[u] = p < nsp ? gram_at<R>(G, ld, pb2[p] + 1, k + 1) : R(0);
+      }
+#pragma unroll
+      for (int u = 0; u < PC; ++u) {
+        const int p = p0 + u;
+        if (p >= nsp) break;
+        unsigned key = 0xffffffffu;
+        const bool dup = cls && (ck_cls == __ldg(cls + pa[p]) || ck_cls == __ldg(cls + pb2[p]));
+        if (!dup && s_pok[p]) {
+          // the completion k after the pair: pivot and target coordinate,
+          // then rel = pP - w^2 / pivot
+          const R g1 = cak[u] * s_pf[p][0];
+          const R g2 = (cbk[u] - s_pf[p][1] * g1) * s_pf[p][2];
+          const R piv = ckk - g1 * g1 - g2 * g2;
+          const R w = ck - g1 * s_pf[p][3] - g2 * s_pf[p][4];
+          if (ckk > R(0) && piv >= (R)ratio * ckk) key = ord32f(f32_up(s_pf[p][5] - w * w / piv));
+        }
+        keys[nt + p * per_pair + k] = key;
+      }
     }
-    keys[nt + x] = key;
+  }
+  __syncthreads();
+  // a completion by a seed column repeats a tuple scored above: dropped
+  for (int x = threadIdx.x; x < nsp * Mr; x += blockDim.x) {
+    const int p = x / Mr, c = cols[x - p * Mr];
+    if (c < per_pair) keys[nt + p * per_pair + c] = 0xffffffffu;
   }
   __syncthreads();
   // the K'-th smallest score (rounded up to FP32): K' real tuples lie at or
@@ -312,8 +364,9 @@ template <typename R>
 cudaError_t launch_seed(const R *G, const ProbDesc *probs_dev, int n_probs, int K, int S,
                         int seed, double ratio, const Binom &B, u64 *gthr, unsigned *hist,
                         int max_keys, cudaStream_t st, const int *cls) {
-  if (max_keys > 50000) max_keys = 50000;   // 200 KB of keys
-  const size_t smem = (size_t)4 * (size_t)max_keys;
+  if (max_keys > 47000) max_keys = 47000;   // 188 KB of keys, then the seed block
+  const size_t smem = (size_t)4 * (size_t)((max_keys + 3) & ~3) +
+                      sizeof(R) * (size_t)(SEED_MAXM + 1) * (size_t)(SEED_MAXM + 1);
   cudaError_t e =
       cudaFuncSetAttribute(seed_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -27,38 +27,101 @@ __device__ void stream_entries(CtaList<R> &L, const R *s, const u64 *k, int n) {
   }
 }
 
+// exclusive prefix sum of one int per thread over the CTA (blockDim a
+// multiple of 32, at most 1024); *total gets the sum.  ws: [32] shared.
+__device__ int block_excl_scan(int v, int *ws, int *total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) ws[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    int x = lane < nw ? ws[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += t;
+    }
+    if (lane < nw) ws[lane] = x;   // inclusive warp totals
+  }
+  __syncthreads();
+  const int before = (w > 0 ? ws[w - 1] : 0) + inc - v;
+  *total = ws[nw - 1];
+  __syncthreads();   // ws is free again
+  return before;
+}
+
 // Gather the prefix (score <= cut) of n_lists sorted lists into shared
 // memory (up to cap entries), sort once, keep the first K.  Returns the
 // number kept, or -1 when more than cap entries qualified (nothing written).
+// With at most blockDim lists, thread l finds list l's prefix (all searches
+// in flight together), a scan places the prefixes, and each thread copies
+// entries found by a search of the placements; otherwise one warp per list.
+// off: [blockDim + 1] ints of shared scratch.
 template <typename R>
 __device__ int gather_sort_lists(const R *ls_base, const u64 *lk_base, const int *cnt,
                                  size_t stride, int n_lists, R cut, int K, int cap, R *ss,
-                                 u64 *sk, R *out_s, u64 *out_k, int *s_tot) {
-  if (threadIdx.x == 0) *s_tot = 0;
-  __syncthreads();
-  // one warp per list: binary search of the prefix, then copy
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int l = warp; l < n_lists; l += nw) {
-    const R *ls = ls_base + (size_t)l * stride;
-    const u64 *lk = lk_base + (size_t)l * stride;
-    int lo = 0, hi = cnt[l];
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (ls[mid] <= cut) lo = mid + 1; else hi = mid;
-    }
-    int base = 0;
-    if (lane == 0 && lo > 0) base = atomicAdd(s_tot, lo);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    for (int i = lane; i < lo; i += 32) {
-      if (base + i < cap) {
-        ss[base + i] = ls[i];
-        sk[base + i] = lk[i];
+                                 u64 *sk, R *out_s, u64 *out_k, int *s_tot, int *off) {
+  __shared__ int ws[32];
+  int total = 0;
+  if (n_lists <= (int)blockDim.x) {
+    const int l = threadIdx.x;
+    int lo = 0;
+    if (l < n_lists) {
+      const R *ls = ls_base + (size_t)l * stride;
+      int hi = cnt[l];
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (ls[mid] <= cut) lo = mid + 1; else hi = mid;
       }
     }
+    const int before = block_excl_scan(lo, ws, &total);
+    off[threadIdx.x] = before;
+    if (threadIdx.x == blockDim.x - 1) off[blockDim.x] = total;
+    __syncthreads();
+    if (total > cap) return -1;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+      // the list holding placement e: last l with off[l] <= e
+      int a = 0, b = n_lists - 1;
+      while (a < b) {
+        const int mid = (a + b + 1) >> 1;
+        if (off[mid] <= e) a = mid; else b = mid - 1;
+      }
+      const int i = e - off[a];
+      ss[e] = ls_base[(size_t)a * stride + i];
+      sk[e] = lk_base[(size_t)a * stride + i];
+    }
+  } else {
+    if (threadIdx.x == 0) *s_tot = 0;
+    __syncthreads();
+    // one warp per list: binary search of the prefix, then copy
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int l = warp; l < n_lists; l += nw) {
+      const R *ls = ls_base + (size_t)l * stride;
+      const u64 *lk = lk_base + (size_t)l * stride;
+      int lo = 0, hi = cnt[l];
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (ls[mid] <= cut) lo = mid + 1; else hi = mid;
+      }
+      int base = 0;
+      if (lane == 0 && lo > 0) base = atomicAdd(s_tot, lo);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      for (int i = lane; i < lo; i += 32) {
+        if (base + i < cap) {
+          ss[base + i] = ls[i];
+          sk[base + i] = lk[i];
+        }
+      }
+    }
+    __syncthreads();
+    total = *s_tot;
+    if (total > cap) return -1;
   }
-  __syncthreads();
-  const int total = *s_tot;
-  if (total > cap) return -1;
   int P = 1;
   while (P < total) P <<= 1;
   for (int i = total + threadIdx.x; i < P; i += blockDim.x) {
@@ -103,19 +166,22 @@ __device__ int stream_lists(const R *ls_base, const u64 *lk_base, const int *cnt
   return n;
 }
 
-// grid (groups, n_probs), 1024 threads.  The slot lists are sorted and only
+// grid (groups, n_probs), 1024 threads.  With one group the CTA of a problem
+// gathers every slot list's qualifying prefix, sorts once and writes the
+// pool.  Otherwise: the slot lists are sorted and only
 // their prefixes at or below the search threshold g can reach the pool.
 // Level 1: CTA x sorts the qualifying entries of its share of slots and keeps
 // its best K' (a partial list); a full partial's K'-th score is a tighter
 // bound g2 (atomicMin).  Level 2: the last CTA of the problem (counter, no
 // waiting) gathers the partial prefixes <= g2, sorts them once and keeps K'.
 template <typename R>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(1024, 1)
 merge_kernel(const R *in_s, const u64 *in_k, const int *in_cnt, int n_slots,
              int K, int S, const u64 *gthr, R *part_s, u64 *part_k, int *part_cnt, int cap,
              unsigned *counters, R *pool_s, u64 *pool_k, int *pool_cnt) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_last, s_tot;
+  __shared__ int s_off[1025];
   const int prob = blockIdx.y, g = blockIdx.x, G = gridDim.x;
   unsigned *done = counters + 4 * prob;
   u64 *g2 = (u64 *)(counters + 4 * prob + 2);
@@ -128,8 +194,19 @@ merge_kernel(const R *in_s, const u64 *in_k, const int *in_cnt, int n_slots,
   R *ps = part_s + pslot * K;
   u64 *pk = part_k + pslot * K;
   const size_t s0 = (size_t)prob * n_slots + a;
+  if (G == 1) {   // one CTA per problem: straight into the pool
+    R *os = pool_s + (size_t)prob * K;
+    u64 *ok = pool_k + (size_t)prob * K;
+    int n1 = gather_sort_lists<R>(in_s + s0 * K, in_k + s0 * K, in_cnt + s0, (size_t)K, b - a,
+                                  gcut, K, cap, ss, sk, os, ok, &s_tot, s_off);
+    if (n1 < 0)
+      n1 = stream_lists<R>(in_s + s0 * K, in_k + s0 * K, in_cnt + s0, (size_t)K, b - a, gcut,
+                           smem, K, S, os, ok);
+    if (threadIdx.x == 0) pool_cnt[prob] = n1;
+    return;
+  }
   int n = gather_sort_lists<R>(in_s + s0 * K, in_k + s0 * K, in_cnt + s0, (size_t)K, b - a,
-                               gcut, K, cap, ss, sk, ps, pk, &s_tot);
+                               gcut, K, cap, ss, sk, ps, pk, &s_tot, s_off);
   if (n < 0)
     n = stream_lists<R>(in_s + s0 * K, in_k + s0 * K, in_cnt + s0, (size_t)K, b - a, gcut, smem,
                         K, S, ps, pk);
@@ -149,7 +226,7 @@ merge_kernel(const R *in_s, const u64 *in_k, const int *in_cnt, int n_slots,
   R *os = pool_s + (size_t)prob * K;
   u64 *ok = pool_k + (size_t)prob * K;
   int n2 = gather_sort_lists<R>(part_s + p0 * K, part_k + p0 * K, part_cnt + p0, (size_t)K, G,
-                                cut2, K, cap, ss, sk, os, ok, &s_tot);
+                                cut2, K, cap, ss, sk, os, ok, &s_tot, s_off);
   if (n2 < 0)
     n2 = stream_lists<R>(part_s + p0 * K, part_k + p0 * K, part_cnt + p0, (size_t)K, G, cut2,
                          smem, K, S, os, ok);
@@ -371,7 +448,10 @@ select_kernel(SelectArgs<R> a) {
   for (int i = threadIdx.x; i < P; i += blockDim.x) {
     if (i < cnt) {
       const double rf = a.refit[(size_t)prob * a.K + i];
-      ws[i] = rf;
+      // ranking by counting compares order-preserving integer images of the
+      // scores (on this part a double comparison runs on the narrow FP64 pipe)
+      if (by_rank) ((u64 *)ws)[i] = ord_of(rf);
+      else ws[i] = rf;
       wk[i] = a.pool_k[(size_t)prob * a.K + i];
       if (isfinite(rf)) {
         const double gs = (double)a.pool_s[(size_t)prob * a.K + i] * scale;
@@ -386,12 +466,16 @@ select_kernel(SelectArgs<R> a) {
   if (by_rank) {
     // keys are unique, so each entry's rank -- the count of entries before
     // it in (score, key) order -- is its place: one pass, one barrier
+    const u64 *uo = (const u64 *)us;
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-      const double s_i = us[i];
+      const u64 o_i = uo[i];
       const u64 k_i = uk[i];
       int r = 0;
-      for (int j = 0; j < cnt; ++j) r += cand_less<double>(us[j], uk[j], s_i, k_i) ? 1 : 0;
-      ss[r] = s_i;
+      for (int j = 0; j < cnt; ++j) {
+        const u64 o_j = uo[j];
+        r += (o_j < o_i || (o_j == o_i && uk[j] < k_i)) ? 1 : 0;
+      }
+      ss[r] = from_ord<double>(o_i);
       sk[r] = k_i;
     }
     __syncthreads();

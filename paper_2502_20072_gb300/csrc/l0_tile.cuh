@@ -592,10 +592,15 @@ __device__ __forceinline__ void persistent_items(const TileArgs<R> &A, RunItem r
   const bool rp_smem = A.rowpre_len <= 1024;
   if (rp_smem)
     for (int i = tid; i < A.rowpre_len; i += blockDim.x) s_rowpre[i] = A.row_prefix[i];
+  // thread 0 takes the next item's number while the CTA runs the current
+  // one, so no item waits for the atomic's round trip
+  long long nxt = 0;
+  if (tid == 0) nxt = (long long)atomicAdd(A.item_counter, 1ull);
   for (;;) {
-    if (tid == 0) s_item = (long long)atomicAdd(A.item_counter, 1ull);
+    if (tid == 0) s_item = nxt;
     __syncthreads();
     const long long item = s_item * A.item_stride + A.item_offset;
+    if (tid == 0 && item < A.item_limit) nxt = (long long)atomicAdd(A.item_counter, 1ull);
     int prob = -1;
     if (item < A.item_limit)
       for (int q = 0; q < A.n_probs; ++q)

@@ -85,7 +85,7 @@ def test_autotuner_choice_is_persisted_and_results_unchanged(tmp_path):
     with l0.Handle(precision=l0.MIXED_BF16X3, autotune=1, autotune_cache_path=cache) as h:
         t0, r0 = h.fit(prob.X, prob.y, 3, 40)
         st = h.stats()
-    assert st["tuned_items_factor"] in (1, 2, 4, 8)
+    assert st["tuned_items_factor"] in (1, 2, 4, 8, 16)
     assert st["tuned_ctas_per_sm"] in (1, 2)
     lines = open(cache).read().split("\n")
     assert any(line.strip() for line in lines)
