@@ -112,6 +112,10 @@ struct sisso_l0_handle {
   unsigned char *pin = nullptr;
   size_t pin_n = 0, pin_used = 0;
   cudaEvent_t ev_pin = nullptr;
+  // side stream: the duplicate-class kernels run beside the centring and
+  // the Gram (they read only X), forked and joined by events
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool pin_pending = false;
   // last bytes uploaded to a small device table; an identical upload is skipped
   struct UpCache {
@@ -463,8 +467,11 @@ int prep_pass(sisso_l0_t h, FitPlan &P) {
   const long long N = P.N;
   L0_CK(cudaMemsetAsync(h->err.p, 0, 16, st), "memset");
   L0_CK(cudaEventRecord(h->ev[0], st), "event");
-  L0_CK(l0::launch_column_classes(P.Xd, N, m, h->col_hash.as<u64>(), h->col_cls.as<int>(), st),
+  L0_CK(cudaEventRecord(h->ev_fork, st), "event");
+  L0_CK(cudaStreamWaitEvent(h->st2, h->ev_fork, 0), "event");
+  L0_CK(l0::launch_column_classes(P.Xd, N, m, h->col_hash.as<u64>(), h->col_cls.as<int>(), h->st2),
         "class kernel");
+  L0_CK(cudaEventRecord(h->ev_join, h->st2), "event");
   if (!P.mixed) {
     L0_CK(l0::launch_centre(P.Xd, P.yd, N, m, h->offs.as<long long>(), n_tasks, h->mu.as<double>(),
                             h->inv_s.as<double>(), h->w64.as<double>(), h->err.as<int>(), st),
@@ -492,6 +499,7 @@ int prep_pass(sisso_l0_t h, FitPlan &P) {
           "tensor-core gram kernel");
   }
   L0_CK(cudaEventRecord(h->ev[6], st), "event");
+  L0_CK(cudaStreamWaitEvent(st, h->ev_join, 0), "event");   // the classes, before any reader
   return SISSO_L0_OK;
 }
 
@@ -1399,6 +1407,9 @@ int sisso_l0_create(sisso_l0_t *out, const sisso_l0_options *opt) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_user, cudaEventDisableTiming);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreate(&h->ev_k[i]);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_pin, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking);
   if (e == cudaSuccess && o.use_graph && h->st == nullptr) {
     e = cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking);
     h->own_st = (e == cudaSuccess);
@@ -1493,6 +1504,9 @@ void sisso_l0_destroy(sisso_l0_t h) {
   for (int i = 0; i < 2; ++i)
     if (h->ev_k[i]) cudaEventDestroy(h->ev_k[i]);
   if (h->own_st) cudaStreamDestroy(h->st);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->st2) cudaStreamDestroy(h->st2);
   delete h;
 }
 

@@ -285,61 +285,108 @@ __device__ double norm_scaled(const double *a, long long lo, long long n,
   return m1 * sqrt(v[0]);
 }
 
-__device__ double householder_cta(double *A, long long n, int d,
-                                  double (*red)[L0_DMAX + 1], double *rho) {
-  const int tid = threadIdx.x;
-  double v[L0_DMAX + 1], cn[L0_DMAX];
-  // norms of the original centred columns
-  for (int j = 0; j < d; ++j) v[j] = 0.0;
-  for (long long i = tid; i < n; i += REFIT_THREADS)
-    for (int j = 0; j < d; ++j) {
-      const double x = A[(long long)j * n + i];
-      v[j] = fma(x, x, v[j]);
+// Sum over the CTA of nv per-thread partials, by warp 0 alone: an FP64
+// instruction costs the SM the same whatever its active lanes (measured:
+// one warp instruction per ~20 cycles), so the cross-thread sums and the
+// scalar work that follows run once per CTA, not in every warp.  The sums
+// are returned in v[] of warp 0's threads (lane 0 is the one that uses
+// them).  part: [REFIT_NV][REFIT_THREADS] shared.
+constexpr int REFIT_NV = 2 * L0_DMAX;
+static_assert(REFIT_THREADS == 128, "four partials per lane of warp 0");
+__device__ void sum_warp0(double *v, int nv, double *part) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int i = 0; i < nv; ++i) part[i * REFIT_THREADS + tid] = v[i];
+  __syncthreads();
+  if (tid < 32)
+    for (int i = 0; i < nv; ++i) {
+      const double *q = part + i * REFIT_THREADS;
+      double x = (q[lane] + q[lane + 32]) + (q[lane + 64] + q[lane + 96]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      v[i] = x;
     }
-  block_reduce(v, d, false, red);
-  for (int j = 0; j < d; ++j) {
-    cn[j] = sqrt(v[j]);
-    if (!isfinite(v[j])) cn[j] = norm_scaled(A + (long long)j * n, 0, n, red);
-  }
+}
+
+// sc: shared scalars, [2 * L0_DMAX + 8]: [0] rescale sigma, [1..d) rescale
+// the norm of original column c, [5] skip the update, [8..8+nc) the update
+// coefficients of the later columns.  Thread 0 returns SSE and *rho.
+__device__ double householder_cta(double *A, long long n, int d, double (*red)[L0_DMAX + 1],
+                                  double *part, double *sc, double *rho) {
+  const int tid = threadIdx.x;
+  double v[REFIT_NV], cn[L0_DMAX];
   double r = DBL_MAX;
   for (int j = 0; j < d; ++j) {
     double *aj = A + (long long)j * n;
-    const int nc = d - j;   // columns j+1 .. d (the target is column d)
-    // one pass: ||aj[j..n)||^2 and aj[j+1..n) . ac[j+1..n) for the later columns
-    for (int c = 0; c <= nc; ++c) v[c] = 0.0;
+    const int nc = d - j;                 // columns j+1 .. d (the target is column d)
+    const int nn = (j == 0) ? d - 1 : 0;  // first pass: norms of the original columns 1..d-1
+    // one pass: ||aj[j..n)||^2, aj[j+1..n) . ac[j+1..n) for the later columns
+    // (and, in the first pass, ||ac||^2 of the original feature columns)
+    for (int c = 0; c <= nc + nn; ++c) v[c] = 0.0;
     for (long long i = j + tid; i < n; i += REFIT_THREADS) {
       const double ai = aj[i];
       v[nc] = fma(ai, ai, v[nc]);
       if (i > j)
         for (int c = 0; c < nc; ++c) v[c] = fma(ai, A[(long long)(j + 1 + c) * n + i], v[c]);
+      for (int c = 0; c < nn; ++c) {
+        const double x = A[(long long)(1 + c) * n + i];
+        v[nc + 1 + c] = fma(x, x, v[nc + 1 + c]);
+      }
     }
-    block_reduce(v, nc + 1, false, red);
-    double sigma = sqrt(v[nc]);
-    if (!isfinite(v[nc])) sigma = norm_scaled(aj, j, n, red);
-    if (sigma == 0.0) {
-      r = 0.0;
-      continue;
-    }
-    const double x0 = aj[j];
-    const double alpha = (x0 >= 0.0) ? -sigma : sigma;
-    const double v0 = x0 - alpha;
-    const double beta = 1.0 / (sigma * (sigma + fabs(x0)));
-    for (int c = 0; c < nc; ++c) {
-      double *ac = A + (long long)(j + 1 + c) * n;
-      const double sdot = (v[c] + v0 * ac[j]) * beta;
-      for (long long i = j + 1 + tid; i < n; i += REFIT_THREADS) ac[i] -= sdot * aj[i];
-      v[c] = sdot;
+    sum_warp0(v, nc + 1 + nn, part);
+    if (tid == 0) {
+      sc[0] = isfinite(v[nc]) ? 0.0 : 1.0;
+      for (int c = 0; c < nn; ++c) sc[1 + c] = isfinite(v[nc + 1 + c]) ? 0.0 : 1.0;
     }
     __syncthreads();
-    if (tid == (int)(j % REFIT_THREADS))
-      for (int c = 0; c < nc; ++c) A[(long long)(j + 1 + c) * n + j] -= v[c] * v0;
+    // sums of squares that overflowed: rescaled by their column maxima (rare;
+    // the whole CTA)
+    double sigma = 0.0;
+    if (sc[0] != 0.0) {
+      sigma = norm_scaled(aj, j, n, red);
+    } else if (tid == 0) {
+      sigma = sqrt(v[nc]);
+    }
+    for (int c = 0; c < nn; ++c) {
+      if (sc[1 + c] != 0.0) {
+        const double t = norm_scaled(A + (long long)(1 + c) * n, 0, n, red);
+        if (tid == 0) cn[1 + c] = t;
+      } else if (tid == 0) {
+        cn[1 + c] = sqrt(v[nc + 1 + c]);
+      }
+    }
+    if (tid == 0) {
+      if (j == 0) cn[0] = sigma;   // nothing has touched column 0 yet
+      if (sigma == 0.0) {
+        r = 0.0;
+        sc[5] = 1.0;
+      } else {
+        const double x0 = aj[j];
+        const double alpha = (x0 >= 0.0) ? -sigma : sigma;
+        const double v0 = x0 - alpha;
+        const double beta = 1.0 / (sigma * (sigma + fabs(x0)));
+        for (int c = 0; c < nc; ++c) {
+          double *ac = A + (long long)(j + 1 + c) * n;
+          const double sdot = (v[c] + v0 * ac[j]) * beta;
+          sc[8 + c] = sdot;
+          ac[j] -= sdot * v0;   // row j of the reflected column (rows > j below)
+        }
+        r = fmin(r, (cn[j] > 0.0) ? fabs(alpha) / cn[j] : 0.0);
+        sc[5] = 0.0;
+      }
+    }
     __syncthreads();
-    r = fmin(r, (cn[j] > 0.0) ? fabs(alpha) / cn[j] : 0.0);
+    if (sc[5] == 0.0)
+      for (int c = 0; c < nc; ++c) {
+        double *ac = A + (long long)(j + 1 + c) * n;
+        const double sdot = sc[8 + c];
+        for (long long i = j + 1 + tid; i < n; i += REFIT_THREADS) ac[i] -= sdot * aj[i];
+      }
+    __syncthreads();
   }
   const double *b = A + (long long)d * n;
   v[0] = 0.0;
-  for (long long i = d + tid; i < n; i += REFIT_THREADS) v[0] += b[i] * b[i];
-  block_reduce(v, 1, false, red);
+  for (long long i = d + tid; i < n; i += REFIT_THREADS) v[0] = fma(b[i], b[i], v[0]);
+  sum_warp0(v, 1, part);
   *rho = r;
   return v[0];
 }
@@ -351,6 +398,8 @@ __global__ void __launch_bounds__(REFIT_THREADS)
 refit_kernel(RefitArgs a) {
   extern __shared__ __align__(16) double sA[];
   __shared__ double red[REFIT_THREADS / 32][L0_DMAX + 1];
+  __shared__ double s_part[REFIT_NV * REFIT_THREADS];
+  __shared__ double s_sc[2 * L0_DMAX + 8];
   __shared__ int s_t[L0_DMAX];
   const int prob = blockIdx.y, cidx = blockIdx.x;
   const ProbDesc pd = a.probs[prob];
@@ -393,7 +442,7 @@ refit_kernel(RefitArgs a) {
     }
     __syncthreads();
     double rho;
-    total += householder_cta(A, n, d, red, &rho);
+    total += householder_cta(A, n, d, red, s_part, s_sc, &rho);
     if (!(rho >= a.rho_min)) elig = false;
     __syncthreads();
   }
