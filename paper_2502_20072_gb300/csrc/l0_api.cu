@@ -350,23 +350,33 @@ void plan_problems(FitPlan &P) {
       if (items >= (long long)P.items_factor * std::max(1, P.grid)) break;
     }
   }
+  // per row block, l0::ROWINFO words: cumulative items before it, then the
+  // chunking of a tile's prefixes (chunks, chunk size, chunks one larger) so
+  // the kernels decode an item without 64-bit divisions
   long long item = 0;
   P.rowpre.clear();
   for (l0::ProbDesc &d : P.pd) {
     d.n_jt = n_jt;
     d.n_kt = n_kt;
     d.L = Lsel;
-    d.prefix_off = (int)P.rowpre.size();
+    d.prefix_off = (int)(P.rowpre.size() / l0::ROWINFO);
     d.item_begin = item;
     long long acc = 0;
-    if (d.d >= 2) {
-      for (int bj = 0; bj < n_jt; ++bj) {
-        P.rowpre.push_back(acc);
-        acc += l0::tile_row_items(bj, P.m, d.dp, Lsel, n_kt, np_of(bj, d.dp));
+    for (int bj = 0; bj <= n_jt; ++bj) {
+      long long nch = 0, q = 0, rr = 0;
+      if (d.d >= 2 && bj < n_jt) {
+        const u64 np = np_of(bj, d.dp);
+        nch = (long long)((np + (u64)Lsel - 1) / (u64)Lsel);
+        if (nch > 0) {
+          q = (long long)(np / (u64)nch);
+          rr = (long long)(np % (u64)nch);
+        }
       }
       P.rowpre.push_back(acc);
-    } else {
-      for (int bj = 0; bj <= n_jt; ++bj) P.rowpre.push_back(0);
+      P.rowpre.push_back(nch);
+      P.rowpre.push_back(q);
+      P.rowpre.push_back(rr);
+      if (d.d >= 2 && bj < n_jt) acc += l0::tile_row_items(bj, P.m, d.dp, Lsel, n_kt, np_of(bj, d.dp));
     }
     item += acc;
     d.item_end = item;

@@ -35,7 +35,9 @@ struct TileArgs {
   const R *G;
   const ProbDesc *probs;
   int n_probs;
-  const long long *row_prefix;     // per problem: n_jt + 1 cumulative item counts
+  const long long *row_prefix;     // per problem and row block bj <= n_jt, ROWINFO words:
+                                   // items before bj, then bj's tiles' prefix chunks:
+                                   // count, size q, number of size q + 1
   int rowpre_len;                  // total entries of row_prefix
   Binom B;
   double ratio;                    // pivot ratio: ineligible (FP64) / redo in FP64 (FP32)
@@ -74,6 +76,8 @@ __host__ __device__ inline int tile_k_count(int bj, int m) {
   return first < m ? (m - first + TILE_TK - 1) / TILE_TK : 0;
 }
 __host__ __device__ inline int tile_k0(int bj, int bk) { return bj * TILE_TJ + 1 + bk * TILE_TK; }
+
+constexpr int ROWINFO = 4;   // words per row block in TileArgs::row_prefix
 
 // work items of one j-tile row: (#k tiles) x (#prefix chunks)
 __host__ __device__ inline long long tile_row_items(int bj, int m, int dp, int L,

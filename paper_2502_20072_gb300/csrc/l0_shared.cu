@@ -159,7 +159,6 @@ __device__ void run_item_shared(const TileArgs<R> &A, const ProbDesc &pd, int pr
     cta_step_sync<R>(L, gthr, gprev);
     if (DP > 0) colex_next<DP>(pidx);
   }
-  cta_list_commit<R>(L, gthr);
 }
 
 template <typename R, int DP>

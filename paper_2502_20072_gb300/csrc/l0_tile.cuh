@@ -578,6 +578,13 @@ __device__ __forceinline__ void run_steps(const TileArgs<R> &A, const ItemCtx<R>
 // Persistent work loop shared by the tuple kernels: fetch a work item with
 // one atomic, decode it into (problem, j tile, k tile, prefix range), hand it
 // to run(), and write the CTA's list to its slot whenever the problem changes.
+// Per item the loop costs one barrier pair and no trip to global memory: the
+// next item's number is fetched during the current one, the decode reads the
+// row-block table (cached in shared memory) with 32-bit arithmetic, the
+// item bodies keep the global cut fresh themselves (a relaxed read a step or
+// group ahead), and staged candidates are committed to the CTA list only when
+// the staging area fills, by the item bodies, and before the list is
+// written out.
 template <typename R, typename RunItem>
 __device__ __forceinline__ void persistent_items(const TileArgs<R> &A, RunItem run) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -607,6 +614,8 @@ __device__ __forceinline__ void persistent_items(const TileArgs<R> &A, RunItem r
         if (item >= A.probs[q].item_begin && item < A.probs[q].item_end) { prob = q; break; }
     if (prob != cur) {
       if (cur >= 0) {
+        cta_list_commit<R>(L, A.gthr + cur);   // what is still staged joins the list
+        __syncthreads();
         const size_t slot = (size_t)cur * A.n_slots + blockIdx.x;
         cta_list_flush<R>(L, A.out_s + slot * A.K, A.out_k + slot * A.K, A.out_cnt + slot);
       }
@@ -614,8 +623,6 @@ __device__ __forceinline__ void persistent_items(const TileArgs<R> &A, RunItem r
       cur = prob;
       if (prob >= 0) cta_list_reset<R>(L, A.gthr + prob);
       L.hist = (prob >= 0 && A.hist) ? A.hist + (size_t)prob * L0_HIST_WORDS : nullptr;
-    } else if (prob >= 0) {
-      cta_list_pull_global<R>(L, A.gthr + prob);
     }
     __syncthreads();
     if (prob < 0) break;   // past the last item (uniform)
@@ -624,25 +631,26 @@ __device__ __forceinline__ void persistent_items(const TileArgs<R> &A, RunItem r
     // prefix steps: hand them out last block first, so the persistent CTAs
     // end on the small items and finish together
     const long long local = pd.item_end - 1 - item;
-    const long long *rp = (rp_smem ? s_rowpre : A.row_prefix) + pd.prefix_off;
+    const long long *rp =
+        (rp_smem ? s_rowpre : A.row_prefix) + (size_t)pd.prefix_off * ROWINFO;
     int lo = 0, hi = pd.n_jt - 1;
     while (lo < hi) {
       int mid = (lo + hi + 1) >> 1;
-      if (rp[mid] <= local) lo = mid; else hi = mid - 1;
+      if (rp[(size_t)mid * ROWINFO] <= local) lo = mid; else hi = mid - 1;
     }
     const int bj = lo;
-    const long long rem = local - rp[bj];
-    const int jend = min((bj + 1) * TJ, pd.m);
-    const u64 np = binom_arith(jend - 1, pd.dp);
-    const long long nch = (long long)((np + (u64)pd.L - 1) / (u64)pd.L);
-    const int bk = (int)(rem / nch);
-    // the tile's nch chunks split its prefixes evenly (sizes differ by at
-    // most one, none above L), so items of one tile cost the same
-    const u64 ch = (u64)(rem % nch);
-    const u64 q = np / (u64)nch, rr = np % (u64)nch;   // the first rr chunks hold q + 1
+    const long long *ri = rp + (size_t)bj * ROWINFO;
+    // the row block's items: k tile major, then the tile's nch prefix
+    // chunks, which split its prefixes evenly (the first rr hold q + 1, the
+    // rest q; none above L), so items of one tile cost the same
+    const int rem = (int)(local - ri[0]);   // < k tiles x chunks of one row block
+    const int nch = (int)ri[1];
+    const int bk = nch > 0 ? rem / nch : 0;
+    const u64 ch = (u64)(rem - bk * nch);
+    const u64 q = (u64)ri[2], rr = (u64)ri[3];
     const u64 r0 = ch * q + (ch < rr ? ch : rr);
     const u64 r1 = r0 + q + (ch < rr ? 1ull : 0ull);
-    if (bk >= tile_k_count(bj, pd.m) || r1 <= r0 || r1 - r0 > (u64)pd.L) {   // inconsistent plan
+    if (nch <= 0 || bk >= tile_k_count(bj, pd.m) || r1 <= r0 || r1 - r0 > (u64)pd.L) {   // inconsistent plan
       set_err(A.err, 9);
       break;
     }

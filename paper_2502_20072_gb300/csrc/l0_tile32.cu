@@ -876,7 +876,6 @@ __device__ __forceinline__ void run32(const TileArgs<float> &A, const ProbDesc &
   }
   if (tid < 32) cp_async_wait_all();   // no copy into the histogram buffers outlives the item
   if (DP == 1) cons += (unsigned)nsteps;
-  cta_list_commit<float>(L, gthr);
 }
 
 template <int DPLO, int DPHI, int UJ, int MINB>

@@ -90,7 +90,6 @@ __device__ void run_item(const TileArgs<R> &A, const ProbDesc &pd, int prob, int
     run_steps<R, DP, true>(A, c, pidx, r0, r1, cdiag, cy, G00, rbs, creg, L, gthr);
   else
     run_steps<R, DP, false>(A, c, pidx, r0, r1, cdiag, cy, G00, rbs, creg, L, gthr);
-  cta_list_commit<R>(L, gthr);
 }
 
 template <typename R, int DPLO, int DPHI>
