@@ -826,9 +826,10 @@ int finish_pass(sisso_l0_t h, FitPlan &P, int *certified, double *delta_max, flo
 // ---------------------------------------------------------------- tuning --
 // Like the paper's launch tuning (Sec. 2.4: the first batch is timed under a
 // preset list of launch configurations and the best is kept), the first
-// search of a shape times the tuple kernel on the first quarter of its work
-// items under each (kernel shape, resident CTAs per SM, work items per CTA)
-// triple and keeps the fastest; choices persist in autotune_cache_path.
+// search of a shape times the tuple kernel (the whole search up to 1e9
+// tuples, else its first quarter of work items; best of two runs) under each
+// (kernel shape, resident CTAs per SM, work items per CTA) triple and keeps
+// the fastest; choices persist in autotune_cache_path.
 // Kernel shapes: the general kernel (8 rows x 4 columns per thread) and, for
 // FP32 searches of d = 2 and 3, the kernel of l0_tile32.cu with 8 rows x 4
 // columns per thread (one or two CTAs per SM) or 4 x 4 (512 threads).
@@ -904,6 +905,8 @@ int autotune(sisso_l0_t h, FitPlan &P, int K, const R *G) {
       if (tile32_ok(P, v)) shapes.push_back(v);
   }
   const int factors[] = {1, 2, 4, 8, 16};
+  double tuples_all = 0.0;
+  for (const l0::ProbDesc &d : P.pd) tuples_all += (double)d.total;
   for (int v : shapes) {
     int rc = apply(v, 1);
     if (rc) return rc;
@@ -916,26 +919,33 @@ int autotune(sisso_l0_t h, FitPlan &P, int K, const R *G) {
         rc = setup_search<R>(h, P, K);
         if (rc) return rc;
         const int n_slots = std::max(P.has_singles ? 64 : 0, P.grid) + (P.mixed ? kDeferGroups : 0);
-        L0_CK(cudaMemsetAsync(h->lists_cnt.p, 0, (size_t)n_probs * n_slots * 4, st), "memset");
-        L0_CK(l0::launch_seed<R>(G, h->probs.as<l0::ProbDesc>(), n_probs, K, S, P.shared ? 0 : 1,
-                                 P.mixed ? h->opt.fp32_fallback_pivot_ratio
-                                         : h->opt.rank_deficient_pivot_ratio,
-                                 B, h->gthr.as<u64>(), h->hist.as<unsigned>(),
-                                 l0::seed_keys(P.m, K), st, h->col_cls.as<int>()),
-              "seed kernel");
-        L0_CK(cudaMemsetAsync(h->ctr.p, 0, 8, st), "memset");
-        if (P.mixed) L0_CK(cudaMemsetAsync(h->dfr_n.p, 0, 24, st), "memset");
-        l0::TileArgs<R> a = tile_args<R>(h, P, K, S, G, n_slots, std::max(1LL, P.n_items / 4));
-        L0_CK(cudaEventRecord(h->ev[2], st), "event");
-        rc = launch_tuple_kernel<R>(h, P, a);
-        if (rc) return rc;
-        L0_CK(cudaEventRecord(h->ev[3], st), "event");
-        rc = wait_stream(h);
-        if (rc) return rc;
-        float ms = 0;
-        cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]);
-        // the slice is a quarter of the items, whatever their size
-        if (ms < best) { best = ms; best_f = f; best_b = b; best_v = v; }
+        // each configuration runs twice and keeps its faster time; a search of
+        // up to 1e9 tuples runs whole (a slice favours the shapes that suit
+        // its own row blocks), a larger one its first quarter of items
+        float ms_cfg = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+          L0_CK(cudaMemsetAsync(h->lists_cnt.p, 0, (size_t)n_probs * n_slots * 4, st), "memset");
+          L0_CK(l0::launch_seed<R>(G, h->probs.as<l0::ProbDesc>(), n_probs, K, S, P.shared ? 0 : 1,
+                                   P.mixed ? h->opt.fp32_fallback_pivot_ratio
+                                           : h->opt.rank_deficient_pivot_ratio,
+                                   B, h->gthr.as<u64>(), h->hist.as<unsigned>(),
+                                   l0::seed_keys(P.m, K), st, h->col_cls.as<int>()),
+                "seed kernel");
+          L0_CK(cudaMemsetAsync(h->ctr.p, 0, 8, st), "memset");
+          if (P.mixed) L0_CK(cudaMemsetAsync(h->dfr_n.p, 0, 24, st), "memset");
+          const long long limit = tuples_all <= 1e9 ? P.n_items : std::max(1LL, P.n_items / 4);
+          l0::TileArgs<R> a = tile_args<R>(h, P, K, S, G, n_slots, limit);
+          L0_CK(cudaEventRecord(h->ev[2], st), "event");
+          rc = launch_tuple_kernel<R>(h, P, a);
+          if (rc) return rc;
+          L0_CK(cudaEventRecord(h->ev[3], st), "event");
+          rc = wait_stream(h);
+          if (rc) return rc;
+          float ms = 0;
+          cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]);
+          ms_cfg = std::min(ms_cfg, ms);
+        }
+        if (ms_cfg < best) { best = ms_cfg; best_f = f; best_b = b; best_v = v; }
       }
     }
   }

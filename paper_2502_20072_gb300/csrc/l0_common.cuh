@@ -565,6 +565,23 @@ __device__ __forceinline__ u64 ld_relaxed(const u64 *p) {
   return v;
 }
 
+// ------------------------------------------------------ packed FP32 pairs --
+// two IEEE FP32 operations per instruction (fma.rn.f32x2: each half an fmaf)
+__device__ __forceinline__ unsigned long long f2_pack(float a, float b) {
+  return (unsigned long long)__float_as_uint(a) | ((unsigned long long)__float_as_uint(b) << 32);
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
 // --------------------------------------------------------- misc helpers --
 __device__ __forceinline__ void set_err(int *err, int code) {
   if (err) atomicCAS(err, 0, code);

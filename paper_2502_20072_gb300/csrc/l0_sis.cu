@@ -602,16 +602,20 @@ sis_prescreen_bulk_kernel(const double *__restrict__ X, long long n, long long n
 
 // Several targets in one pass over X (the residual screening of the
 // dimension loop): the FP32 centred values of all R targets sit in shared
-// memory ([R][n], n <= PM_NMAX), each lane accumulates S3 for every target,
-// and the epilogue takes, per feature, the largest lower and upper bounds
-// over the targets -- an interval around max_t |r_t|.  Same staging, error
-// model and cursors as sis_prescreen_bulk_kernel; 12 warps so that the
-// targets fit beside the rings.
+// memory as target pairs ([R/2][n] float2, n <= PM_NMAX; an odd R padded
+// with a zero target), each lane accumulates S3 for every target two at a
+// time with fma.rn.f32x2 (each half the same fmaf as one at a time: the
+// sums, and so the bounds, are unchanged, for half the instructions), and
+// the epilogue takes, per feature, the largest lower and upper bounds over
+// the targets -- an interval around max_t |r_t|.  Same staging, error model
+// and cursors as sis_prescreen_bulk_kernel; 12 warps so that the targets fit
+// beside the rings.
 constexpr int PM_WARPS = 12;
 constexpr int PM_NMAX = 2 * PB_SEG;
+constexpr int PM_PAIRS = (SIS_MAX_TARGETS + 1) / 2;
 constexpr size_t PM_RING_BYTES = (size_t)PM_WARPS * PB_STAGES * PB_STAGE_BYTES;
 constexpr size_t pm_smem(int R, long long n) {
-  return PM_RING_BYTES + (size_t)PM_WARPS * PB_STAGES * 8 + (size_t)R * n * 4;
+  return PM_RING_BYTES + (size_t)PM_WARPS * PB_STAGES * 8 + (size_t)((R + 1) / 2) * n * 8;
 }
 
 __global__ void __launch_bounds__(PM_WARPS * 32, 1)
@@ -625,6 +629,7 @@ sis_prescreen_multi_kernel(const double *__restrict__ X, long long n, long long 
   unsigned char *ring = smem + (size_t)w * PB_STAGES * PB_STAGE_BYTES;
   const uint32_t bar0 = tc::smem_u32(smem + PM_RING_BYTES) + w * PB_STAGES * 8;
   float *ys = (float *)(smem + PM_RING_BYTES + (size_t)PM_WARPS * PB_STAGES * 8);
+  const int RP = (R + 1) / 2;   // target pairs
   const uint32_t ring0 = tc::smem_u32(ring);
   const int nseg = (int)((n + PB_SEG - 1) / PB_SEG);    // 1 or 2
   if (lane == 0) {
@@ -638,14 +643,23 @@ sis_prescreen_multi_kernel(const double *__restrict__ X, long long n, long long 
     if (lane == 0 && j.valid) pb_issue(j, X, ring0 + q * PB_STAGE_BYTES, bar0 + 8 * q);
     pc.advance(nseg);
   }
-  for (long long i = threadIdx.x; i < (long long)R * n; i += blockDim.x) ys[i] = yc[i];
+  // ys[(p n + i) 2 + h] = target 2p + h at sample i (0 past R)
+  for (long long x = threadIdx.x; x < (long long)RP * n * 2; x += blockDim.x) {
+    const long long pi = x >> 1;
+    const int u = (int)(pi / n) * 2 + (int)(x & 1);
+    const long long i = pi - (pi / n) * n;
+    ys[x] = u < R ? yc[(long long)u * n + i] : 0.f;
+  }
   __syncthreads();
   float F1 = 0.f, F2 = 0.f, F3[SIS_MAX_TARGETS];      // lane t: feature t of the group
   double cm = 0.0;
   bool badm = false;
-  float a1 = 0.f, a2 = 0.f, a3[SIS_MAX_TARGETS];
+  float a1 = 0.f, a2 = 0.f;
+  unsigned long long a3p[PM_PAIRS];   // S3 of targets 2p, 2p + 1
 #pragma unroll
-  for (int t = 0; t < SIS_MAX_TARGETS; ++t) a3[t] = F3[t] = 0.f;
+  for (int t = 0; t < SIS_MAX_TARGETS; ++t) F3[t] = 0.f;
+#pragma unroll
+  for (int q = 0; q < PM_PAIRS; ++q) a3p[q] = 0ull;
   double c = 0.0;
   float fc = 0.f;
   unsigned mx = 0;
@@ -672,7 +686,7 @@ sis_prescreen_multi_kernel(const double *__restrict__ X, long long n, long long 
       if (lane == 0) ((double *)sv)[j.len - 1] = __ldg(X + j.e0 + j.len - 1);
       __syncwarp();
     }
-    const float *yb = ys + (long long)j.s * PB_SEG;
+    const unsigned long long *yb2 = (const unsigned long long *)ys + (long long)j.s * PB_SEG;
 #pragma unroll 4
     for (int k = 0; k < PB_K; ++k) {
       const int i = lane + 32 * k;
@@ -680,13 +694,21 @@ sis_prescreen_multi_kernel(const double *__restrict__ X, long long n, long long 
         const float d = sis_trunc32(sv[i], mx) - fc;
         a1 += d;
         a2 = fmaf(d, d, a2);
+        const unsigned long long d2 = f2_pack(d, d);
 #pragma unroll
-        for (int u = 0; u < SIS_MAX_TARGETS; ++u)
-          if (u < R) a3[u] = fmaf(d, yb[(long long)u * n + i], a3[u]);
+        for (int q = 0; q < PM_PAIRS; ++q)
+          if (q < RP) a3p[q] = f2_fma(d2, yb2[(long long)q * n + i], a3p[q]);
       }
     }
     const bool last = j.s == nseg - 1;
     if (last) {                                     // <= 32 terms per lane
+#pragma unroll
+      float a3[SIS_MAX_TARGETS];
+#pragma unroll
+      for (int q = 0; q < PM_PAIRS; ++q) {
+        a3[2 * q] = __uint_as_float((unsigned)a3p[q]);
+        if (2 * q + 1 < SIS_MAX_TARGETS) a3[2 * q + 1] = __uint_as_float((unsigned)(a3p[q] >> 32));
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         a1 += __shfl_xor_sync(0xffffffffu, a1, o);
@@ -706,7 +728,7 @@ sis_prescreen_multi_kernel(const double *__restrict__ X, long long n, long long 
       }
       a1 = a2 = 0.f;
 #pragma unroll
-      for (int u = 0; u < SIS_MAX_TARGETS; ++u) a3[u] = 0.f;
+      for (int q = 0; q < PM_PAIRS; ++q) a3p[q] = 0ull;
     }
     __syncwarp();
     {

@@ -343,21 +343,6 @@ __device__ __noinline__ int slow_tuple(const TileArgs<R> &A, const ItemCtx<R> &c
 __device__ __forceinline__ unsigned sign_word(float t) { return __float_as_uint(t); }
 __device__ __forceinline__ unsigned sign_word(double t) { return (unsigned)__double2hiint(t); }
 
-// packed FP32 pairs
-__device__ __forceinline__ unsigned long long f2_pack(float a, float b) {
-  return (unsigned long long)__float_as_uint(a) | ((unsigned long long)__float_as_uint(b) << 32);
-}
-__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
-                                                     unsigned long long c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
-  unsigned long long d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
 
 // Fast test of one row u against this thread's UK columns; returns the AND
 // of the tuples' sign words (sign bit clear <=> some tuple flagged).
@@ -595,23 +580,30 @@ __device__ __forceinline__ void persistent_items(const TileArgs<R> &A, RunItem r
   __shared__ long long s_item;
   __shared__ long long s_rowpre[1024];
   int cur = -1;
+  // the problem descriptors, when few, live in shared memory for the loop
+  constexpr int PD_SMEM = 16;
+  __shared__ ProbDesc s_pd[PD_SMEM];
   const int tid = threadIdx.x;
   const bool rp_smem = A.rowpre_len <= 1024;
   if (rp_smem)
     for (int i = tid; i < A.rowpre_len; i += blockDim.x) s_rowpre[i] = A.row_prefix[i];
+  const bool pd_smem = A.n_probs <= PD_SMEM;
+  if (pd_smem)
+    for (int q = tid; q < A.n_probs; q += blockDim.x) s_pd[q] = A.probs[q];
+  const ProbDesc *probs = pd_smem ? s_pd : A.probs;
   // thread 0 takes the next item's number while the CTA runs the current
-  // one, so no item waits for the atomic's round trip
+  // one, so no item waits for the atomic's round trip, and publishes it in
+  // s_item before the barrier that ends each item
+  if (tid == 0) s_item = (long long)atomicAdd(A.item_counter, 1ull);
   long long nxt = 0;
-  if (tid == 0) nxt = (long long)atomicAdd(A.item_counter, 1ull);
+  __syncthreads();
   for (;;) {
-    if (tid == 0) s_item = nxt;
-    __syncthreads();
     const long long item = s_item * A.item_stride + A.item_offset;
     if (tid == 0 && item < A.item_limit) nxt = (long long)atomicAdd(A.item_counter, 1ull);
     int prob = -1;
     if (item < A.item_limit)
       for (int q = 0; q < A.n_probs; ++q)
-        if (item >= A.probs[q].item_begin && item < A.probs[q].item_end) { prob = q; break; }
+        if (item >= probs[q].item_begin && item < probs[q].item_end) { prob = q; break; }
     if (prob != cur) {
       if (cur >= 0) {
         cta_list_commit<R>(L, A.gthr + cur);   // what is still staged joins the list
@@ -623,10 +615,10 @@ __device__ __forceinline__ void persistent_items(const TileArgs<R> &A, RunItem r
       cur = prob;
       if (prob >= 0) cta_list_reset<R>(L, A.gthr + prob);
       L.hist = (prob >= 0 && A.hist) ? A.hist + (size_t)prob * L0_HIST_WORDS : nullptr;
+      __syncthreads();
     }
-    __syncthreads();
     if (prob < 0) break;   // past the last item (uniform)
-    const ProbDesc pd = A.probs[prob];
+    const ProbDesc pd = probs[prob];
     // items are laid out by row block, the later blocks holding the most
     // prefix steps: hand them out last block first, so the persistent CTAs
     // end on the small items and finish together
@@ -656,6 +648,7 @@ __device__ __forceinline__ void persistent_items(const TileArgs<R> &A, RunItem r
     }
     u64 *gthr = A.gthr + prob;
     run(pd, prob, bj, bk, r0, r1, L, recbase, gthr);
+    if (tid == 0) s_item = nxt;   // every thread read this item's number before run()
     __syncthreads();
   }
 }

@@ -724,57 +724,22 @@ __device__ __forceinline__ void run32(const TileArgs<float> &A, const ProbDesc &
   c.smem_dq = tc::smem_u32(sb);
   const float *G = c.G;
   const long long ld = c.ld;
-  it.G00 = G[0];
-  if (tid == 0) {   // the queues start empty (the previous item emptied them)
-    ((int *)(sb + O_DQN))[0] = 0;
-    ((int *)(sb + O_DQN))[1] = 0;
-    ((int *)(sb + O_FQN))[0] = 0;
-    ((int *)(sb + O_FQN))[1] = 0;
-  }
   const int nsteps = DP == 1 ? (int)(r1 - r0) : 1;
   const int i0 = DP == 1 ? (int)r0 : 0;   // colex rank of a one-index prefix is the index
-  if (nsteps > T32_MAXL) {   // the plan never makes such items (uniform exit)
+  if (nsteps > T32_MAXL || nsteps > (int)blockDim.x) {   // the plan never makes such items
     set_err(A.err, 9);
     return;
   }
   const int ngroups = (nsteps + T32_G - 1) / T32_G;
   const bool issuer = tid == (int)blockDim.x - 32;   // lane 0 of the last warp: the ring copies
-  if (DP == 1) {
-    if (issuer) {
-      issue_group32(c, sb, 0, nsteps, i0, cons);
-      issue_group32(c, sb, 1, nsteps, i0, cons);
-    }
-    float *pdg = (float *)(sb + O_PDG), *pry = (float *)(sb + O_PRY);
-    float *ppb = (float *)(sb + O_PPB);
-    int *pcls = (int *)(sb + O_PCLS);
-    for (int s = tid; s < nsteps; s += blockDim.x) {
-      // the prefix's own factor, shared by the step's records: 1/l_i (its
-      // sign marks C_ii <= 0), z_i = r_i / l_i, pP_i = 1 - z_i^2
-      const int i = i0 + s;
-      const float cii = G[(long long)(i + 1) * (ld + 1)];
-      const bool pok = cii > 0.f;
-      const float invd = rsqrtf(pok ? cii : 1.f);
-      const float zP = G[i + 1] * invd;
-      pdg[s] = pok ? invd : -invd;
-      pry[s] = zP;
-      ppb[s] = it.G00 - zP * zP;
-      pcls[s] = c.cls ? __ldg(c.cls + i) : -1;
-    }
+  if (DP == 1 && issuer) {
+    issue_group32(c, sb, 0, nsteps, i0, cons);
+    issue_group32(c, sb, 1, nsteps, i0, cons);
   }
-  for (int r = tid; r < T32_NREC; r += blockDim.x) {
-    const int col = r < TJ ? c.j0 + r : c.k0 + r - TJ;
-    float dg = 0.f, cy = 0.f;
-    int cc = -2;
-    if (col < c.m) {
-      dg = G[(long long)(col + 1) * (ld + 1)];
-      cy = G[col + 1];
-      if (c.cls) cc = __ldg(c.cls + col);
-    }
-    ((int *)(sb + O_RCOL))[r] = col;
-    ((float *)(sb + O_RDG))[r] = dg;
-    ((float *)(sb + O_RY))[r] = cy;
-    ((int *)(sb + O_RCLS))[r] = cc;
-  }
+  // Set-up of the item: every load is issued before the first shared store
+  // (a store through a generic pointer may not be moved above a later global
+  // load), so the item waits for one round trip to L2, not three.  Thread s
+  // takes prefix step s (nsteps <= blockDim) and record s (T32_NREC <= blockDim).
   // the tile's Gram entries: rows j0 + w UJ + u, columns k0 + 2 lane + {0, 1} + 64 q
   u64 creg[UJ][2];
 #pragma unroll
@@ -785,11 +750,51 @@ __device__ __forceinline__ void run32(const TileArgs<float> &A, const ProbDesc &
       const int k = c.k0 + 2 * lane + 64 * q;
       u64 v = 0ull;
       if (j < c.m && k < c.m) {
-        v = *(const u64 *)(G + (long long)(j + 1) * ld + k + 1);
+        v = __ldg((const unsigned long long *)(G + (long long)(j + 1) * ld + k + 1));
         if (k + 1 >= c.m) v &= 0xffffffffull;   // the pair's second column is past m
       }
       creg[u][q] = v;
     }
+  }
+  it.G00 = __ldg(G);
+  float p_cii = 1.f, p_ry = 0.f;
+  int p_cls = -1;
+  if (DP == 1 && tid < nsteps) {
+    const int i = i0 + tid;
+    p_cii = __ldg(G + (long long)(i + 1) * (ld + 1));
+    p_ry = __ldg(G + i + 1);
+    if (c.cls) p_cls = __ldg(c.cls + i);
+  }
+  const int rcol = tid < TJ ? c.j0 + tid : c.k0 + tid - TJ;
+  float r_dg = 0.f, r_cy = 0.f;
+  int r_cc = -2;
+  if (tid < T32_NREC && rcol < c.m) {
+    r_dg = __ldg(G + (long long)(rcol + 1) * (ld + 1));
+    r_cy = __ldg(G + rcol + 1);
+    if (c.cls) r_cc = __ldg(c.cls + rcol);
+  }
+  if (tid == 0) {   // the queues start empty (the previous item emptied them)
+    ((int *)(sb + O_DQN))[0] = 0;
+    ((int *)(sb + O_DQN))[1] = 0;
+    ((int *)(sb + O_FQN))[0] = 0;
+    ((int *)(sb + O_FQN))[1] = 0;
+  }
+  if (DP == 1 && tid < nsteps) {
+    // the prefix's own factor, shared by the step's records: 1/l_i (its
+    // sign marks C_ii <= 0), z_i = r_i / l_i, pP_i = 1 - z_i^2
+    const bool pok = p_cii > 0.f;
+    const float invd = rsqrtf(pok ? p_cii : 1.f);
+    const float zP = p_ry * invd;
+    ((float *)(sb + O_PDG))[tid] = pok ? invd : -invd;
+    ((float *)(sb + O_PRY))[tid] = zP;
+    ((float *)(sb + O_PPB))[tid] = it.G00 - zP * zP;
+    ((int *)(sb + O_PCLS))[tid] = p_cls;
+  }
+  if (tid < T32_NREC) {
+    ((int *)(sb + O_RCOL))[tid] = rcol;
+    ((float *)(sb + O_RDG))[tid] = r_dg;
+    ((float *)(sb + O_RY))[tid] = r_cy;
+    ((int *)(sb + O_RCLS))[tid] = r_cc;
   }
   __syncthreads();   // prefix scalars and record constants visible
   build_group32<DP>(A, it, sb, 0, nsteps, i0, cons, cta_cut<float>(L));
