@@ -50,7 +50,7 @@ TRAFFIC_SOURCES = {0: ("l0_common.cuh", "l0_tile.cuh", "l0_tuple.cu", "l0_kernel
 for _v in (1, 2, 3):
     TRAFFIC_SOURCES[_v] = ("l0_common.cuh", "l0_tile.cuh", "l0_tile32.cu", "l0_kernels.cuh",
                            "l0_tc.cuh")
-TRAFFIC_CAPTURED = {}
+TRAFFIC_CAPTURED = {("C2", "mixed", 3): (3053312 + 32256, "4d7b9f9a94e0e47e")}
 TUPLE_KERNEL_NAMES = {
     0: "tile_kernel (tuple search, any d)",
     1: "tile32_kernel (d <= 3 FP32 tuple search, 256 threads, one CTA per SM)",
@@ -89,6 +89,29 @@ def sis_traffic(fp64, n_feat, n):
         with open(os.path.join(ROOT, "paper_2502_20072_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return rec[0] * n_feat if h.hexdigest()[:16] == rec[1] else None
+
+
+def same_up_to_ties(t_ref, r_ref, t_got, r_got, rel_gap=1e-9):
+    """The same tuples at every rank, where positions whose reference RMSEs lie
+    within rel_gap of each other form a tie group whose tuple sets must match
+    (the order inside a group is rounding).  Per task; both as tensors."""
+    t_ref, r_ref = t_ref.cpu().numpy(), r_ref.cpu().numpy()
+    t_got, r_got = t_got.cpu().numpy(), r_got.cpu().numpy()
+    for task in range(t_ref.shape[0]):
+        rr = r_ref[task]
+        i = 0
+        while i < len(rr):
+            j = i + 1
+            while j < len(rr) and (rr[j] == rr[j - 1] or
+                                   abs(rr[j] - rr[j - 1]) <= rel_gap * max(abs(rr[j]), 1e-300)):
+                j += 1
+            a = sorted(map(tuple, t_ref[task][i:j].tolist()))
+            b = sorted(map(tuple, t_got[task][i:j].tolist()))
+            # a tie group that reaches rank k may continue past it: not compared
+            if a != b and not (j == len(rr) and j - i > 1):
+                return False
+            i = j
+    return True
 
 
 def flops_per_tuple(d):
@@ -348,7 +371,9 @@ def run_ours(args):
         same = all(bool(torch.equal(a[0], b[0])) for a, b in zip(outs64, outs_dev))
         fp64_line = {"value": v64, "ms_per_step": statistics.mean(ms64),
                      "speedup_of_this_path": value / v64 / ws,
-                     "same_top_k_tuples": same}
+                     "same_top_k_tuples": same,
+                     "same_top_k_up_to_ties": same or all(
+                         same_up_to_ties(a[0], a[1], b[0], b[1]) for a, b in zip(outs64, outs_dev))}
         h64.close()
     # roofline of the dominant kernel (the tuple kernel), timed by CUDA events
     # around its launch on the library's stream; events inside a replayed

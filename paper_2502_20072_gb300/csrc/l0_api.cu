@@ -104,6 +104,8 @@ struct sisso_l0_handle {
   cudaGraphExec_t graph_exec = nullptr;
   std::string graph_key;
   struct Tune { int f, b, v; };                      // items factor, CTAs per SM, kernel shape
+  std::map<std::string, int> bps_cache;              // resident tuple-kernel CTAs per SM
+  std::string dev_name;                              // device name (tuning keys)
   std::map<std::string, Tune> tune;                   // autotuner choices
   std::string fp64_key;   // inputs whose last mixed-precision fit needed FP64
   // pinned host staging for the small per-call uploads and status reads (so
@@ -393,16 +395,27 @@ bool tile32_ok(const FitPlan &P, int v) {
 
 template <typename R>
 int tile_bps(sisso_l0_t h, const FitPlan &P, int Kmax, int *bps) {
+  // the driver's occupancy answer is fixed per kernel and shared memory:
+  // asked once per handle, not on every fit
+  char key[96];
+  snprintf(key, sizeof(key), "%d|%d|%d|%d|%d|%d|%zu", P.variant, P.dp_lo, P.dp_hi, P.shared,
+           Kmax, (int)sizeof(R), sizeof(l0::ProbDesc));
+  auto it = h->bps_cache.find(key);
+  if (it != h->bps_cache.end()) {
+    *bps = it->second;
+    return SISSO_L0_OK;
+  }
   const int S0 = staging_for(Kmax);
   if (P.variant > 0) {
     L0_CK(l0::tile32_occupancy(P.variant, std::max(P.dp_lo, 0), std::max(P.dp_hi, 0),
                                l0::tile32_smem_bytes(Kmax, S0), bps),
           "occupancy");
-    return SISSO_L0_OK;
+  } else {
+    const size_t smem = l0::tile_smem_bytes<R>(Kmax, S0, std::max(P.dp_hi, 0));
+    if (P.shared) L0_CK(l0::shared_occupancy<R>(std::max(P.dp_hi, 0), smem, bps), "occupancy");
+    else L0_CK(l0::tile_occupancy<R>(std::max(P.dp_lo, 0), std::max(P.dp_hi, 0), smem, bps), "occupancy");
   }
-  const size_t smem = l0::tile_smem_bytes<R>(Kmax, S0, std::max(P.dp_hi, 0));
-  if (P.shared) L0_CK(l0::shared_occupancy<R>(std::max(P.dp_hi, 0), smem, bps), "occupancy");
-  else L0_CK(l0::tile_occupancy<R>(std::max(P.dp_lo, 0), std::max(P.dp_hi, 0), smem, bps), "occupancy");
+  h->bps_cache[key] = *bps;
   return SISSO_L0_OK;
 }
 
@@ -834,12 +847,15 @@ int finish_pass(sisso_l0_t h, FitPlan &P, int *certified, double *delta_max, flo
 // FP32 searches of d = 2 and 3, the kernel of l0_tile32.cu with 8 rows x 4
 // columns per thread (one or two CTAs per SM) or 4 x 4 (512 threads).
 std::string tune_key(sisso_l0_t h, const FitPlan &P) {
-  cudaDeviceProp prop;
-  cudaGetDeviceProperties(&prop, h->opt.device);
+  if (h->dev_name.empty()) {   // one property query per handle, not per fit
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, h->opt.device) == cudaSuccess) h->dev_name = prop.name;
+    else h->dev_name = "unknown";
+  }
   int mb = 1;
   while (mb < P.m) mb <<= 1;
   char buf[256];
-  snprintf(buf, sizeof(buf), "%s|prec=%d|shared=%d|dp=%d-%d|m<=%d|T=%d|shapes=%d", prop.name,
+  snprintf(buf, sizeof(buf), "%s|prec=%d|shared=%d|dp=%d-%d|m<=%d|T=%d|shapes=%d", h->dev_name.c_str(),
            P.mixed, P.shared, P.dp_lo, P.dp_hi, mb, P.T, h->opt.tuple_kernel);
   std::string s(buf);
   for (char &c : s)
