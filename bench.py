@@ -766,37 +766,52 @@ def run_generated(args):
     n_cand = int(ops.shape[0])
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    h = l0.Handle(precision=l0.FP64, device=local, stream=stream.cuda_stream)
-    idx = torch.empty(m, dtype=torch.int32, device="cuda")
-    r = torch.empty(m, dtype=torch.float64, device="cuda")
+    mixed = args.precision != "fp64"
     lib = l0.lib()
     import ctypes
 
-    def step():
-        rc = lib.sisso_l0_sis_generated(
-            h._h, ctypes.c_void_p(C.data_ptr()), nc, n, ctypes.c_void_p(ops.data_ptr()),
-            ctypes.c_void_p(c1.data_ptr()), ctypes.c_void_p(c2.data_ptr()), n_cand,
-            ctypes.c_void_p(y.data_ptr()), m, 1e-5, 1e8, ctypes.c_void_p(idx.data_ptr()),
-            ctypes.c_void_p(r.data_ptr()), None)
-        h._check(rc)
+    def timed(handle, idx, r):
+        def step():
+            rc = lib.sisso_l0_sis_generated(
+                handle._h, ctypes.c_void_p(C.data_ptr()), nc, n, ctypes.c_void_p(ops.data_ptr()),
+                ctypes.c_void_p(c1.data_ptr()), ctypes.c_void_p(c2.data_ptr()), n_cand,
+                ctypes.c_void_p(y.data_ptr()), m, 1e-5, 1e8, ctypes.c_void_p(idx.data_ptr()),
+                ctypes.c_void_p(r.data_ptr()), None)
+            handle._check(rc)
 
-    for _ in range(max(3, args.warmup)):
-        step()
+        for _ in range(max(3, args.warmup)):
+            step()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for _ in range(args.steps):
+            step()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / args.steps
+
+    # the headline path: FP32 pre-screen + FP64 re-score (mixed handle), or
+    # the FP64 evaluation of every candidate (--precision fp64)
+    h = l0.Handle(precision=l0.MIXED_BF16X3 if mixed else l0.FP64, device=local,
+                  stream=stream.cuda_stream)
+    idx = torch.empty(m, dtype=torch.int32, device="cuda")
+    r = torch.empty(m, dtype=torch.float64, device="cuda")
     clocks = Clocks(local)
     clocks.start()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    torch.cuda.synchronize()
-    ev[0].record(stream)
-    for _ in range(args.steps):
-        step()
-    ev[1].record(stream)
-    torch.cuda.synchronize()
+    ms = timed(h, idx, r)
     clk = clocks.stop()
-    ms = ev[0].elapsed_time(ev[1]) / args.steps
     st = h.stats()
     ms_k = st["ms_tuple_kernel"]
-    # FP64 operations per sample of the arithmetic operators: the value, the
-    # shift, S1, and the FMAs of S2 and S3
+    fp64_line = None
+    if mixed:
+        h64 = l0.Handle(precision=l0.FP64, device=local, stream=stream.cuda_stream)
+        idx64 = torch.empty(m, dtype=torch.int32, device="cuda")
+        r64 = torch.empty(m, dtype=torch.float64, device="cuda")
+        ms64 = timed(h64, idx64, r64)
+        h64.close()
+        same = bool(torch.equal(idx, idx64)) and bool(torch.allclose(r, r64, rtol=1e-12, atol=0))
+        fp64_line = {"ms_per_step": ms64, "value": n_cand / (ms64 * 1e-3),
+                     "speedup_of_this_path": ms64 / ms, "same_selection": same}
     flop = n_cand * n * 7
     tf = flop / (ms_k * 1e-3) / 1e12 if ms_k > 0 else None
     peaks = {}
@@ -804,7 +819,7 @@ def run_generated(args):
         peaks = l0.measure_peaks(local)
     except Exception:
         pass
-    pk = peaks.get("fp64_tflops")
+    pk = peaks.get("fp32_tflops" if mixed else "fp64_tflops")
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
         sys.path.insert(0, ROOT)
@@ -823,7 +838,8 @@ def run_generated(args):
                       "+ top-m)",
             "value": n_cand / (ms * 1e-3), "unit": "candidates/s", "n_gpus": ws,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 pre-screen + f64" if mixed else "f64",
             "data": "synthetic (seeded uniform children on the device)",
             "config": {"workload": "GEN: n_child=%d n_samples=%d candidates=%d m=%d"
                                    % (nc, n, n_cand, m),
@@ -832,10 +848,14 @@ def run_generated(args):
             "gpu_launches": int(st["kernel_launches"]) * args.steps,
             "roofline": {"bound": "alu", "achieved": tf, "peak": pk, "unit": "TFLOP/s",
                          "frac": tf / pk if (tf and pk) else None, "traffic": None,
-                         "kernel": "gen_score_kernel (FP64)", "kernel_ms": ms_k,
-                         "peak_source": "measured FP64 FMA rate (sisso_l0_measure_peaks)",
+                         "kernel": "gen_prescreen_kernel (FP32)" if mixed else
+                                   "gen_score_kernel (FP64)", "kernel_ms": ms_k,
+                         "peak_source": "measured %s FMA rate (sisso_l0_measure_peaks)"
+                                        % ("FP32" if mixed else "FP64"),
                          "flop_per_sample": 7},
             "cpu_baseline": cpu, "clocks": clk}
+    if fp64_line:
+        line["fp64_path"] = fp64_line
     h.close()
     if rank == 0:
         print(json.dumps(line))

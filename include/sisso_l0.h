@@ -414,7 +414,13 @@ enum {
  * operators applied to child features, their values evaluated and checked
  * on the GPU; the last rung evaluated inside SIS, Sec. 2.3, Sec. 3).
  * Candidate t is ops[t](C[c1[t]], C[c2[t]]) -- codes 0-4 binary, 5-13
- * unary on c1[t] (c2[t] ignored) -- evaluated in FP64.  A candidate is valid
+ * unary on c1[t] (c2[t] ignored) -- evaluated in FP64.  On a handle of
+ * precision MIXED_BF16X3 and with out_valid NULL, every candidate is first
+ * evaluated in FP32 with a rigorous interval around its |r| (per-sample
+ * bounds on the FP32 values from the operators' rounding and CUDA's
+ * documented accuracy of logf / expf / cbrtf) and only the candidates whose
+ * interval reaches the m-th largest lower bound of a certainly valid one are
+ * evaluated in FP64: the result is the FP64 evaluation's.  A candidate is valid
  * when every value is finite, max |value| lies in [l_bound, u_bound], the
  * values are not all equal and not equal sample by sample to a child; the m
  * valid candidates of largest |r| with y (Eq. 1) are returned, ties to the

@@ -94,6 +94,7 @@ struct sisso_l0_handle {
   DevBuf dfr_bctr;                                    // FP64 redo: run batches handed out
   DevBuf sis_ex, sis_y;                               // screening: exclusions, targets
   DevBuf gen_ops, gen_c1, gen_c2, gen_valid;          // generated candidates
+  DevBuf gen_cf, gen_csafe;                           // their FP32 children (pre-screen)
   DevBuf loop_x, loop_y, loop_xs, loop_res, loop_q, loop_tup, loop_rows;   // dimension loop
   int binom_m = -1;
   int done_init_for = 0;
@@ -1526,7 +1527,8 @@ void sisso_l0_destroy(sisso_l0_t h) {
                     &h->dfr_cnt, &h->abf, &h->bbf, &h->kmeta, &h->gram32, &h->prop_in,
                     &h->prop_pairs, &h->prop_bits, &h->prop_ctr, &h->sel_hist, &h->sel_bin,
                     &h->scores, &h->diag, &h->col_hash, &h->col_cls, &h->sis_ex, &h->sis_y,
-                    &h->gen_ops, &h->gen_c1, &h->gen_c2, &h->gen_valid, &h->loop_x, &h->loop_y,
+                    &h->gen_ops, &h->gen_c1, &h->gen_c2, &h->gen_valid, &h->gen_cf, &h->gen_csafe,
+                    &h->loop_x, &h->loop_y,
                     &h->loop_xs, &h->loop_res, &h->loop_q, &h->loop_tup, &h->loop_rows,
                     &h->band_thr, &h->band_floor, &h->g64_have, &h->dfr_bctr, &h->gpart,
                     &h->gctr};
@@ -2255,13 +2257,22 @@ extern "C" int sisso_l0_sis_generated(sisso_l0_t h, const double *C, int64_t n_c
         g.valid = (unsigned char *)h->gen_valid.p;
       }
     }
+    // a mixed-precision handle screens in FP32 first when no per-candidate
+    // validity is asked for (validity needs every candidate in FP64)
+    const int pre = (h->opt.precision != SISSO_L0_FP64 && !out_valid) ? 1 : 0;
+    if (pre) {
+      L0_CK(h->gen_cf.ensure((size_t)n_child * (size_t)n_total * 4), "alloc FP32 children");
+      L0_CK(h->gen_csafe.ensure((size_t)n_child), "alloc");
+      g.cf = h->gen_cf.as<float>();
+      g.csafe = (unsigned char *)h->gen_csafe.p;
+    }
     L0_CK(h->scores.ensure(l0::sis_scratch_bytes(n_cand, m, n_total, 1)), "alloc screening scratch");
     L0_CK(h->out_t.ensure((size_t)m * 4), "alloc");
     L0_CK(h->out_r.ensure((size_t)m * 8), "alloc");
     L0_CK(h->err.ensure(16), "alloc");
     L0_CK(cudaMemsetAsync(h->err.p, 0, 16, st), "memset");
     L0_CK(cudaEventRecord(h->ev[0], st), "event");
-    L0_CK(l0::launch_sis(Cd, yd, 1, n_total, n_cand, m, nullptr, 0, 0, h->scores.p,
+    L0_CK(l0::launch_sis(Cd, yd, 1, n_total, n_cand, m, nullptr, 0, pre, h->scores.p,
                          h->out_t.as<int>(), h->out_r.as<double>(), h->err.as<int>(), st,
                          h->ev_k[0], h->ev_k[1], &g),
           "generated screening kernels");
@@ -2279,8 +2290,8 @@ extern "C" int sisso_l0_sis_generated(sisso_l0_t h, const double *C, int64_t n_c
     S = sisso_l0_stats{};
     S.struct_size = (int32_t)sizeof(sisso_l0_stats);
     S.certified = 1;
-    S.fp64_fallback_tuples = (uint64_t)n_cand;
-    S.kernel_launches = 13;
+    S.fp64_fallback_tuples = pre ? 0 : (uint64_t)n_cand;
+    S.kernel_launches = pre ? 19 : 13;
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]) != cudaSuccess) {
       cudaGetLastError();

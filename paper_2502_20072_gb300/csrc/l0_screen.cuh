@@ -20,6 +20,10 @@ struct SisGen {
   const int *ops, *c1, *c2;
   double lb, ub;
   unsigned char *valid;
+  // FP32 pre-screen (with prescreen set and valid null): an FP32 copy of the
+  // children [n_child][n] and a flag per child (scratch the caller owns)
+  float *cf = nullptr;
+  unsigned char *csafe = nullptr;
 };
 size_t sis_scratch_bytes(long long n_feat, int m, long long n, int R);
 cudaError_t launch_sis(const double *X, const double *y, int R, long long n, long long n_feat,

@@ -702,7 +702,6 @@ sis_prescreen_multi_kernel(const double *__restrict__ X, long long n, long long 
     }
     const bool last = j.s == nseg - 1;
     if (last) {                                     // <= 32 terms per lane
-#pragma unroll
       float a3[SIS_MAX_TARGETS];
 #pragma unroll
       for (int q = 0; q < PM_PAIRS; ++q) {
@@ -798,6 +797,58 @@ __device__ __forceinline__ double gen_apply(int op, double a, double b) {
   }
 }
 
+// FP64 r of candidate t by one warp (lane 0 returns it; NaN when the
+// candidate breaks a value rule); *ok (all lanes) tells whether it is valid.
+// A malformed candidate is reported (err 14) and never read.
+__device__ double gen_r64_warp(const double *__restrict__ C, long long n, long long n_child,
+                               const int *__restrict__ ops, const int *__restrict__ c1,
+                               const int *__restrict__ c2, long long t,
+                               const double *__restrict__ yd, double syy, double sy0, double lb,
+                               double ub, int lane, bool *ok_out, int *err) {
+  const int op = ops[t];
+  const bool binary = op <= 4;
+  if (op < 0 || op > 13 || c1[t] < 0 || c1[t] >= n_child ||
+      (binary && (c2[t] < 0 || c2[t] >= n_child))) {
+    if (lane == 0) set_err(err, 14);
+    *ok_out = false;
+    return __longlong_as_double(0x7ff8000000000000ll);
+  }
+  const double *xa = C + (long long)c1[t] * n;
+  const double *xb = C + (long long)(binary ? c2[t] : c1[t]) * n;
+  const double v0 = gen_apply(op, __ldg(xa), __ldg(xb));
+  double S1 = 0.0, S2 = 0.0, S3 = 0.0, mx = 0.0;
+  bool finite = true, same = true, eqa = true, eqb = binary;
+  for (long long i = lane; i < n; i += 32) {
+    const double a = __ldg(xa + i), b = __ldg(xb + i);
+    const double v = gen_apply(op, a, b);
+    finite &= ((unsigned)__double2hiint(v) & 0x7ff00000u) != 0x7ff00000u;
+    mx = fmax(mx, fabs(v));
+    same &= v == v0;
+    eqa &= v == a;
+    eqb &= v == b;
+    const double d = v - v0;
+    S1 += d;
+    S2 = fma(d, d, S2);
+    S3 = fma(d, __ldg(yd + i), S3);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    S1 += __shfl_xor_sync(0xffffffffu, S1, o);
+    S2 += __shfl_xor_sync(0xffffffffu, S2, o);
+    S3 += __shfl_xor_sync(0xffffffffu, S3, o);
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  const bool ok = __all_sync(0xffffffffu, finite) && !__all_sync(0xffffffffu, same) &&
+                  !__all_sync(0xffffffffu, eqa) && !(binary && __all_sync(0xffffffffu, eqb)) &&
+                  mx <= ub && mx >= lb;
+  *ok_out = ok;
+  const double sxx = S2 - S1 * S1 / (double)n;
+  const double sxy = S3 - S1 * sy0 / (double)n;
+  double r = (sxx > 0.0 && syy > 0.0) ? sxy / sqrt(sxx * syy) : 0.0;
+  if (!ok) r = __longlong_as_double(0x7ff8000000000000ll);
+  return r;
+}
+
 __global__ void __launch_bounds__(256)
 gen_score_kernel(const double *__restrict__ C, long long n, long long n_child,
                  const int *__restrict__ ops, const int *__restrict__ c1,
@@ -809,53 +860,252 @@ gen_score_kernel(const double *__restrict__ C, long long n, long long n_child,
   const double syy = tgt[1], sy0 = tgt[2];
   for (long long t = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < n_cand;
        t += warps) {
-    const int op = ops[t];
-    const bool binary = op <= 4;
-    // a malformed candidate is reported and never read
-    if (op < 0 || op > 13 || c1[t] < 0 || c1[t] >= n_child ||
-        (binary && (c2[t] < 0 || c2[t] >= n_child))) {
-      if (lane == 0) {
-        set_err(err, 14);
-        r_out[t] = __longlong_as_double(0x7ff8000000000000ll);
-        if (valid_out) valid_out[t] = 0;
-      }
-      continue;
-    }
-    const double *xa = C + (long long)c1[t] * n;
-    const double *xb = C + (long long)(binary ? c2[t] : c1[t]) * n;
-    const double v0 = gen_apply(op, __ldg(xa), __ldg(xb));
-    double S1 = 0.0, S2 = 0.0, S3 = 0.0, mx = 0.0;
-    bool finite = true, same = true, eqa = true, eqb = binary;
-    for (long long i = lane; i < n; i += 32) {
-      const double a = __ldg(xa + i), b = __ldg(xb + i);
-      const double v = gen_apply(op, a, b);
-      finite &= ((unsigned)__double2hiint(v) & 0x7ff00000u) != 0x7ff00000u;
-      mx = fmax(mx, fabs(v));
-      same &= v == v0;
-      eqa &= v == a;
-      eqb &= v == b;
-      const double d = v - v0;
-      S1 += d;
-      S2 = fma(d, d, S2);
-      S3 = fma(d, __ldg(yd + i), S3);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      S1 += __shfl_xor_sync(0xffffffffu, S1, o);
-      S2 += __shfl_xor_sync(0xffffffffu, S2, o);
-      S3 += __shfl_xor_sync(0xffffffffu, S3, o);
-      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    }
-    const bool ok = __all_sync(0xffffffffu, finite) && !__all_sync(0xffffffffu, same) &&
-                    !__all_sync(0xffffffffu, eqa) && !(binary && __all_sync(0xffffffffu, eqb)) &&
-                    mx <= ub && mx >= lb;
+    bool ok = false;
+    const double r = gen_r64_warp(C, n, n_child, ops, c1, c2, t, yd, syy, sy0, lb, ub, lane, &ok,
+                                  err);
     if (lane == 0) {
-      const double sxx = S2 - S1 * S1 / (double)n;
-      const double sxy = S3 - S1 * sy0 / (double)n;
-      double r = (sxx > 0.0 && syy > 0.0) ? sxy / sqrt(sxx * syy) : 0.0;
-      if (!ok) r = __longlong_as_double(0x7ff8000000000000ll);
       r_out[t] = r;
       if (valid_out) valid_out[t] = ok ? 1 : 0;
+    }
+  }
+}
+
+// FP64 r of the listed candidates (the pre-screen's survivors), one warp each
+__global__ void __launch_bounds__(256)
+gen_rescore_kernel(const double *__restrict__ C, long long n, long long n_child,
+                   const int *__restrict__ ops, const int *__restrict__ c1,
+                   const int *__restrict__ c2, const unsigned *list,
+                   const unsigned long long *count, const double *__restrict__ yd,
+                   const double *__restrict__ tgt, double lb, double ub,
+                   double *__restrict__ r_out, int *err) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  const long long nc = (long long)*count;
+  const double syy = tgt[1], sy0 = tgt[2];
+  for (long long q = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < nc;
+       q += warps) {
+    const long long t = list[q];
+    bool ok = false;
+    const double r = gen_r64_warp(C, n, n_child, ops, c1, c2, t, yd, syy, sy0, lb, ub, lane, &ok,
+                                  err);
+    if (lane == 0) r_out[t] = r;
+  }
+}
+
+// ------------------------------------- generated features: FP32 pre-screen --
+// The FP64 evaluation above keeps GB300's FP64 pipe busy (~10 FP64
+// instructions per sample).  The pre-screen evaluates every candidate in FP32
+// from an FP32 copy of the children, carries for each sample a bound beta on
+// |value32 - value| (the operator's rounding, CUDA's documented accuracy of
+// logf / expf / cbrtf -- 1, 2 and 1 ulp; sqrtf and division are IEEE --, and
+// the inputs' own rounding), and turns the FP32 Pearson sums into an interval
+// [lo, hi] around the exact |r| with the error model of sis_bounds, E being
+// the norm of the per-sample bounds of the shifted values.  The value rules
+// are decided only when the bounds settle them: "certainly invalid" (a
+// non-finite FP32 value, or max |value| outside [lb, ub] by more than its
+// bound) gives hi = NaN; "certainly valid" (finite, inside the bounds with
+// room, some sample distinct from the first and from each child by more than
+// the bounds) keeps lo; anything unsettled gets lo = 0 and, when the bounds
+// do not hold (children or values outside [1e-30, 1e30]), hi = +inf.  The
+// m-th largest lo is then a score at least m valid candidates reach, and
+// only candidates whose hi reaches it are evaluated in FP64.
+
+__device__ __forceinline__ float gen_apply32(int op, float a, float b) {
+  switch (op) {
+    case 0: return a + b;
+    case 1: return a - b;
+    case 2: return a * b;
+    case 3: return a / b;
+    case 4: return fabsf(a - b);
+    case 5: return logf(a);
+    case 6: return expf(a);
+    case 7: return expf(-a);
+    case 8: return fabsf(a);
+    case 9: return sqrtf(a);
+    case 10: return cbrtf(a);
+    case 11: return a * a;
+    case 12: return a * a * a;
+    default: return 1.f / a;
+  }
+}
+
+// bound on |v - op(a_exact, b_exact)| for v = gen_apply32(op, a, b), where a
+// and b are the round-to-nearest FP32 images of the exact children (relative
+// error <= u each) and v is finite
+__device__ __forceinline__ float gen_beta32(int op, float a, float b, float v) {
+  constexpr float u = 5.9604644775390625e-8f;   // 2^-24
+  const float av = fabsf(v);
+  float rel, abs0 = 0.f;
+  switch (op) {
+    case 0: case 1: case 4: abs0 = u * (fabsf(a) + fabsf(b) + av); rel = 0.f; break;
+    case 2: case 3: case 11: rel = 4.f * u; break;
+    case 5: abs0 = 1.01f * u; rel = 2.01f * u; break;   // input: log(1 + d) ~ d; logf 1 ulp
+    case 6: case 7: rel = 1.01f * u * fabsf(a) + 4.01f * u; break;   // exp(a + e) = exp(a)(1 + e); expf 2 ulp
+    case 8: rel = 1.01f * u; break;
+    case 9: rel = 1.6f * u; break;    // sqrt(a(1 + d)) = sqrt(a)(1 + d/2); sqrtf correctly rounded
+    case 10: rel = 2.5f * u; break;   // input d/3; cbrtf 1 ulp
+    case 12: rel = 6.f * u; break;
+    default: rel = 3.f * u; break;    // 1/a: input + one rounding
+  }
+  return (abs0 + rel * av) * 1.001f + 1e-37f;
+}
+
+// children in FP32 (round to nearest) and, per child, whether every value is
+// 0 or within [1e-30, 1e30] (the FP32 error model's range); one warp each
+__global__ void __launch_bounds__(256)
+gen_child32_kernel(const double *__restrict__ C, long long n, long long n_child,
+                   float *__restrict__ Cf, unsigned char *__restrict__ safe) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long c = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < n_child;
+       c += warps) {
+    bool ok = true;
+    for (long long i = lane; i < n; i += 32) {
+      const double x = __ldg(C + c * n + i);
+      const double ax = fabs(x);
+      ok &= (x == 0.0) || (ax >= 1e-30 && ax <= 1e30);
+      Cf[c * n + i] = __double2float_rn(x);
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (lane == 0) safe[c] = ok ? 1 : 0;
+  }
+}
+
+// [lo, hi] around |r| from FP32 sums of shifted values whose error vector has
+// norm <= E (see sis_bounds; the partial sums hold ceil(n / 32) terms a lane)
+__device__ __forceinline__ void gen_bounds(double S1, double S2, double S3, double E,
+                                           const double *tgt, long long n, double &lo,
+                                           double &hi) {
+  const double syy_s = tgt[3], syc2 = tgt[4], sy0 = tgt[5];
+  const double nn = (double)n;
+  const double terms = (double)((n + 31) / 32) + 16.0;
+  const double g = fmax(80.0, 1.1 * terms) * SIS_U + nn * 2.220446049250313e-16;
+  const double sxx = S2 - S1 * S1 / nn;
+  const double sxy = S3 - S1 * sy0 / nn;
+  const double sxx_lo = sxx - 3.0 * g * S2;
+  lo = 0.0;
+  hi = INFINITY;
+  if (isfinite(S1) && isfinite(S2) && isfinite(S3) && isfinite(E) && syy_s > 0.0 &&
+      sxx_lo > 0.0 && 9.0 * E * E < sxx_lo && 30.0 * g * S2 < sxx_lo) {
+    const double a = fabs(sxy / sqrt(sxx * syy_s));
+    const double nx = sqrt(sxx_lo);
+    const double eps =
+        1.01 * (1.05 * E / (nx - E) + SIS_U + 2.0 * g * sqrt(S2 * syc2 / (sxx_lo * syy_s)) +
+                a * 1.65 * g * S2 / sxx_lo) +
+        1e-10;
+    lo = fmax(a - eps, 0.0);
+    hi = a + eps;
+  }
+}
+
+// One warp per group of 32 candidates: the warp evaluates them one after
+// the other (lanes over samples) and leaves candidate t's sums and flags in
+// lane t; the FP64 epilogue (interval, rules) then runs once for all 32 -- an
+// FP64 instruction costs the SM the same whatever its active lanes.
+__global__ void __launch_bounds__(256)
+gen_prescreen_kernel(const float *__restrict__ Cf, const unsigned char *__restrict__ safe,
+                     long long n, long long n_child, const int *__restrict__ ops,
+                     const int *__restrict__ c1, const int *__restrict__ c2, long long n_cand,
+                     const float *__restrict__ yc, const double *__restrict__ tgt, double lb,
+                     double ub, double *__restrict__ lo_out, double *__restrict__ hi_out) {
+  constexpr float u = 5.9604644775390625e-8f;
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long g0 = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
+       g0 < n_cand; g0 += warps * 32) {
+    const int G = (int)min(32ll, n_cand - g0);
+    // lane t: candidate g0 + t
+    float S1 = 0.f, S2 = 0.f, S3 = 0.f, E2 = 0.f, MXH = 0.f, MXL = 0.f;
+    unsigned F = 0u;   // bits: 1 malformed, 2 finite, 4 vsafe, 8 dif0, 16 difa, 32 difb,
+                       // 64 binary, 128 children safe
+    for (int t = 0; t < G; ++t) {
+      const long long c = g0 + t;
+      const int op = ops[c];
+      const bool binary = op <= 4;
+      if (op < 0 || op > 13 || c1[c] < 0 || c1[c] >= n_child ||
+          (binary && (c2[c] < 0 || c2[c] >= n_child))) {
+        if (lane == t) F = 1u;   // malformed: the FP64 re-score reports it
+        continue;
+      }
+      const long long ca = c1[c], cb = binary ? c2[c] : ca;
+      const float *xa = Cf + ca * n, *xb = Cf + cb * n;
+      const float a0 = __ldg(xa), b0 = __ldg(xb);
+      const float v0 = gen_apply32(op, a0, b0);
+      const float be0 = isfinite(v0) ? gen_beta32(op, a0, b0, v0) : 0.f;
+      float s1 = 0.f, s2 = 0.f, s3 = 0.f, e2 = 0.f, mxhi = 0.f, mxlo = 0.f;
+      bool finite = true, vsafe = true, dif0 = false, difa = false, difb = false;
+      for (long long i = lane; i < n; i += 32) {
+        const float a = __ldg(xa + i), b = __ldg(xb + i);
+        const float v = gen_apply32(op, a, b);
+        const float av = fabsf(v);
+        const bool fin = isfinite(v);
+        finite &= fin;
+        vsafe &= (v == 0.f) || (av >= 1e-30f && av <= 1e30f);
+        const float be = fin ? gen_beta32(op, a, b, v) : 0.f;
+        mxhi = fmaxf(mxhi, av + be);
+        mxlo = fmaxf(mxlo, av - be);
+        // distinct beyond the bounds (1e-6 covers the FP32 rounding of these tests)
+        dif0 |= fabsf(v - v0) > 1.001f * (be + be0) + 1e-6f * (av + fabsf(v0));
+        difa |= fabsf(v - a) > 1.001f * (be + u * fabsf(a)) + 1e-6f * (av + fabsf(a));
+        difb |= binary && fabsf(v - b) > 1.001f * (be + u * fabsf(b)) + 1e-6f * (av + fabsf(b));
+        const float d = v - v0;
+        s1 += d;
+        s2 = fmaf(d, d, s2);
+        s3 = fmaf(d, __ldg(yc + i), s3);
+        const float ed = be + be0 + u * fabsf(d);
+        e2 = fmaf(ed, ed, e2);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+        e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+        mxhi = fmaxf(mxhi, __shfl_xor_sync(0xffffffffu, mxhi, o));
+        mxlo = fmaxf(mxlo, __shfl_xor_sync(0xffffffffu, mxlo, o));
+      }
+      const unsigned f = (__all_sync(0xffffffffu, finite) ? 2u : 0u) |
+                         (__all_sync(0xffffffffu, vsafe) ? 4u : 0u) |
+                         (__any_sync(0xffffffffu, dif0) ? 8u : 0u) |
+                         (__any_sync(0xffffffffu, difa) ? 16u : 0u) |
+                         (__any_sync(0xffffffffu, difb) ? 32u : 0u) | (binary ? 64u : 0u) |
+                         ((safe[ca] && safe[cb]) ? 128u : 0u);
+      if (lane == t) {
+        S1 = s1;
+        S2 = s2;
+        S3 = s3;
+        E2 = e2;
+        MXH = mxhi;
+        MXL = mxlo;
+        F = f;
+      }
+    }
+    if (lane < G) {
+      double lo = 0.0, hi = INFINITY;
+      if (!(F & 1u)) {
+        const bool children_safe = F & 128u, finite = F & 2u, vsafe = F & 4u;
+        const bool bounded = children_safe && vsafe && finite;
+        // certainly invalid: decided by FP32 values whatever their error (the
+        // 1e-6 margins cover the FP32 rounding of |v| +- beta)
+        const bool invalid =
+            children_safe && ub <= 1e30 &&
+            (!finite || (double)MXL > ub * (1.0 + 1e-6) ||
+             (finite && vsafe && (double)MXH < lb * (1.0 - 1e-6)));
+        const bool valid = bounded && (double)MXH <= ub * (1.0 - 1e-6) &&
+                           (double)MXL >= lb * (1.0 + 1e-6) && (F & 8u) && (F & 16u) &&
+                           (!(F & 64u) || (F & 32u));
+        if (invalid) {
+          lo = hi = __longlong_as_double(0x7ff8000000000000ll);
+        } else if (bounded) {
+          // the FP32 sum of squared bounds, inflated for its own rounding
+          const double E = sqrt((double)E2 * (1.0 + 64.0 * (double)u * (double)((n + 31) / 32 + 8))) *
+                               1.0001 + 1e-30;
+          gen_bounds((double)S1, (double)S2, (double)S3, E, tgt, n, lo, hi);
+          if (!valid) lo = 0.0;
+        }
+      }
+      lo_out[g0 + lane] = lo;
+      hi_out[g0 + lane] = hi;
     }
   }
 }
@@ -1333,7 +1583,21 @@ cudaError_t launch_sis(const double *X, const double *y, int R, long long n, lon
   };
   const unsigned gx = (unsigned)std::min<long long>((n_ex + 255) / 256, 1024);
   sis_target_kernel<<<R, 1024, 0, st>>>(y, n, tgt, yd, err);
-  if (gen) {                           // generated candidates, FP64 (R = 1)
+  if (gen && prescreen && gen->cf && gen->csafe && !gen->valid) {
+    // generated candidates, FP32 pre-screen, FP64 re-score of the survivors
+    sis_target32_kernel<<<1, 1024, 0, st>>>(y, n, tgt, yc);
+    const unsigned gc = (unsigned)std::min<long long>((gen->n_child + 7) / 8, 152 * 32);
+    gen_child32_kernel<<<gc, 256, 0, st>>>(X, n, gen->n_child, gen->cf, gen->csafe);
+    if (scan0 && (e = cudaEventRecord(scan0, st)) != cudaSuccess) return e;
+    gen_prescreen_kernel<<<gw, 256, 0, st>>>(gen->cf, gen->csafe, n, gen->n_child, gen->ops,
+                                             gen->c1, gen->c2, n_feat, yc, tgt, gen->lb, gen->ub,
+                                             r, hi);
+    if (scan1 && (e = cudaEventRecord(scan1, st)) != cudaSuccess) return e;
+    if ((e = cut_of(r, pcuts, pcnt)) != cudaSuccess) return e;
+    sis_candidates_kernel<<<g, 256, 0, st>>>(hi, n_feat, pcuts, pcuts + 1, r, list, pcnt + 1);
+    gen_rescore_kernel<<<gw, 256, 0, st>>>(X, n, gen->n_child, gen->ops, gen->c1, gen->c2, list,
+                                           pcnt + 1, yd, tgt, gen->lb, gen->ub, r, err);
+  } else if (gen) {                    // generated candidates, FP64 (R = 1)
     if (scan0 && (e = cudaEventRecord(scan0, st)) != cudaSuccess) return e;
     gen_score_kernel<<<gw, 256, 0, st>>>(X, n, gen->n_child, gen->ops, gen->c1, gen->c2, n_feat,
                                          yd, tgt, gen->lb, gen->ub, r, gen->valid, err);
