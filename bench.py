@@ -50,7 +50,7 @@ TRAFFIC_SOURCES = {0: ("l0_common.cuh", "l0_tile.cuh", "l0_tuple.cu", "l0_kernel
 for _v in (1, 2, 3):
     TRAFFIC_SOURCES[_v] = ("l0_common.cuh", "l0_tile.cuh", "l0_tile32.cu", "l0_kernels.cuh",
                            "l0_tc.cuh")
-TRAFFIC_CAPTURED = {("C2", "mixed", 3): (3053312 + 32256, "4d7b9f9a94e0e47e")}
+TRAFFIC_CAPTURED = {("C2", "mixed", 3): (3051264 + 31744, "61a98c245ab10f0d")}
 TUPLE_KERNEL_NAMES = {
     0: "tile_kernel (tuple search, any d)",
     1: "tile32_kernel (d <= 3 FP32 tuple search, 256 threads, one CTA per SM)",

@@ -1222,10 +1222,10 @@ int fit_requests(sisso_l0_t h, const double *X, const double *y, const int64_t *
     P.max_bps = bps;
     P.grid = h->n_sm * bps;
   }
-  // untuned: the FP32 d <= 3 kernel balances best with small items (8 per
-  // CTA measured fastest on the d = 3, 1000-column search), the general one
-  // with 2
-  P.items_factor = P.variant > 0 ? 8 : 2;
+  // untuned: 4 items per CTA for the FP32 d <= 3 kernel (fastest on the
+  // d = 3, 1000-column search once the tiles holding the strongest columns
+  // go out first), 2 for the general one
+  P.items_factor = P.variant > 0 ? 4 : 2;
   plan_problems(P);
   rc = P.mixed ? setup_search<float>(h, P, K) : setup_search<double>(h, P, K);
   if (rc) return rc;

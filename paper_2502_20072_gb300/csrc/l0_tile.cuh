@@ -569,9 +569,11 @@ __device__ __forceinline__ void run_steps(const TileArgs<R> &A, const ItemCtx<R>
 // item bodies keep the global cut fresh themselves (a relaxed read a step or
 // group ahead), and staged candidates are committed to the CTA list only when
 // the staging area fills, by the item bodies, and before the list is
-// written out.
+// written out.  `forward`: items go out in row-block order, first row block
+// first (see the decode below).
 template <typename R, typename RunItem>
-__device__ __forceinline__ void persistent_items(const TileArgs<R> &A, RunItem run) {
+__device__ __forceinline__ void persistent_items(const TileArgs<R> &A, RunItem run,
+                                                 bool forward = false) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char *p = smem;
   CtaList<R> L = cta_list_carve<R>(p, A.K, A.S);
@@ -619,10 +621,15 @@ __device__ __forceinline__ void persistent_items(const TileArgs<R> &A, RunItem r
     }
     if (prob < 0) break;   // past the last item (uniform)
     const ProbDesc pd = probs[prob];
-    // items are laid out by row block, the later blocks holding the most
-    // prefix steps: hand them out last block first, so the persistent CTAs
-    // end on the small items and finish together
-    const long long local = pd.item_end - 1 - item;
+    // Items are laid out by row block, the later blocks holding the most
+    // prefix steps.  By default they go out last block first, so the
+    // persistent CTAs end on the small items and finish together.  With
+    // equal chunks (the FP32 d <= 3 kernel) the cost of an item is set by
+    // how often its tuples flag instead: a tile holding the strongest
+    // columns flags on every group.  Columns come ranked by SIS score, so
+    // the first row blocks hold the strongest; `forward` hands those out
+    // first, and the tail of the launch is made of ordinary items.
+    const long long local = forward ? item - pd.item_begin : pd.item_end - 1 - item;
     const long long *rp =
         (rp_smem ? s_rowpre : A.row_prefix) + (size_t)pd.prefix_off * ROWINFO;
     int lo = 0, hi = pd.n_jt - 1;

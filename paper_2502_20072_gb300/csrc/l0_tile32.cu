@@ -903,7 +903,7 @@ tile32_kernel(TileArgs<float> A) {
     } else if (pd.dp == 1) {
       if (DPHI >= 1) run32<1, UJ>(A, pd, prob, bj, bk, r0, r1, L, recbase, gthr, cons);
     }
-  });
+  }, /*forward=*/true);
 }
 
 }  // namespace
