@@ -72,11 +72,11 @@ def tile_traffic(workload, precision, shape=0):
 
 
 # DRAM bytes of one pre-screen launch per feature of n_samples=1000, from the
-# ncu capture in profiles/sis_prescreen_n1000.md (500000 features: 4000165632
-# read + 10473216 written), scaled by the features of a launch (the kernel
+# ncu capture in profiles/sis_prescreen_n1000.md (500000 features: 4000389632
+# read + 10852352 written), scaled by the features of a launch (the kernel
 # reads each row once).  Tied to the sources it was taken from, as above.
 SIS_TRAFFIC_SOURCES = ("l0_sis.cu", "l0_tc.cuh", "l0_screen.cuh")
-SIS_TRAFFIC_CAPTURED = {1000: ((4000165632 + 10473216) / 500000, "0b9e2aa642e2a37e")}
+SIS_TRAFFIC_CAPTURED = {1000: ((4000389632 + 10852352) / 500000, "46094b2b70d46d7e")}
 
 
 def sis_traffic(fp64, n_feat, n):
