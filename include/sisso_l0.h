@@ -104,7 +104,9 @@ typedef struct {
   double max_pool_rel_error;         /* max |SSE_gram - SSE_refit| over the pools, SSE units */
   int64_t kernel_launches;           /* library kernels launched by the last fit */
   int32_t graph_replayed;            /* 1 when the last search pass replayed a CUDA graph */
-  int32_t tuned_items_factor;        /* autotuner choice: work items per CTA (x2) */
+  int32_t tuned_items_factor;        /* autotuner choice: work items per CTA (at least);
+                                        0 when the autotuner did not run (the untuned
+                                        default is 4 for the FP32 d <= 3 kernel, else 2) */
   int32_t tuned_ctas_per_sm;         /* autotuner choice: resident CTAs per SM */
   int32_t fp64_rerun;                /* 1: the last fit was redone in FP64 after an
                                         uncertified mixed pass (see options); 2: it ran in
